@@ -1,0 +1,862 @@
+/*
+ * ut3d_oracle.c — plain, slow FP64 CPU oracle of the 3DGUT hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * it is loaded by the tests, by __graft_entry__.smoke() and by the CPU
+ * baseline leg of bench.py, and by nothing else.  It shares no code, header,
+ * constant table or helper with the CUDA library.
+ *
+ * What it computes (each function cites the passage it restates):
+ *   - 3D Gaussian particles: response rho(x) = exp(-1/2 (x-mu)^T Sigma^-1 (x-mu)),
+ *     Sigma = R S S^T R^T (Sec. 3, eq. gaussian_kernel, eq. gaussian_covariance).
+ *   - The Unscented Transform projection of every particle (Sec. 4.1,
+ *     eq. sigma_points, eq. weights_1/2, eq. 2d_conic_1/2; Algorithms 1 and 2
+ *     of the supplementary), through a pinhole, a polynomial (Kannala-Brandt)
+ *     fisheye or a test-only orthographic camera, with an optional rolling
+ *     shutter ("a different extrinsic matrix" per sigma point, Sec. 1).
+ *   - Duplicate keys (tile | depth) and their global stable sort per tile
+ *     (Sec. 4.3, Table 2 phases Duplicate and Sort).
+ *   - Front-to-back volumetric compositing (eq. QuadratureVolumeRendering) with
+ *     each particle evaluated in 3D at its maximum response along the pixel ray
+ *     (Sec. 4.2, eq. GaussianMaxResponse), brute force over ALL particles in
+ *     global depth order with no tiling.
+ *   - The reverse-mode gradient of the composited colour and opacity with
+ *     respect to every particle parameter (supplementary Sec. B, extended to
+ *     S, R, opacity and SH as the paper says "follow analogously").
+ *
+ * Readings where the paper is silent (listed with reasons in the design notes):
+ *   pinhole / fisheye formulas, rolling-shutter time rule (fixed point on the
+ *   projected row), depth = Euclidean distance, extent = min(cap, sqrt(2 ln(sigma/alpha_min)))
+ *   standard deviations, pixel-centre-in-rect membership, alpha = min(alpha_max, sigma rho),
+ *   skip below alpha_min, stop before blending when T(1-alpha) < t_min, SH colour
+ *   max(sum beta Y + 0.5, 0) at the pixel's ray direction.
+ *
+ * Everything is computed in double precision from FP32 inputs promoted to FP64.
+ * The only decisions taken in FP32 are the ones the key format fixes: the
+ * depth that enters the sort key is the FP64 depth rounded to FP32.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+  int32_t model;           /* 0 pinhole, 1 fisheye (polynomial), 2 orthographic (test-only affine) */
+  int32_t width, height;
+  int32_t rolling_shutter; /* 0 global shutter (start pose), 1 rows exposed top to bottom */
+  double fx, fy, cx, cy;
+  double k[4];
+  double q_start[4], t_start[3]; /* world->camera rotation (w,x,y,z) and translation at row 0 */
+  double q_end[4], t_end[3];     /* same at row H-1 */
+  double near_plane;
+} orc_camera;
+
+typedef struct {
+  const float *means, *log_scales, *quats, *opacity_logits, *sh;
+  int32_t n, sh_degree;
+} orc_scene;
+
+typedef struct {
+  int32_t tile_w, tile_h;
+  double t_min, alpha_min, alpha_max;
+  int32_t rs_iters;
+  double ut_alpha, ut_beta, ut_kappa;
+  double extent_sigma;
+} orc_options;
+
+/* near-tie tolerances used only to flag pixels whose FP32 result may legitimately differ */
+typedef struct {
+  double eps_px;   /* rect edge distance in pixels */
+  double eps_rel;  /* relative distance of alpha / transmittance / culling to a threshold */
+  int32_t depth_ulps; /* depth keys closer than this many FP32 ulps may swap */
+  double cond_min; /* fisheye: pixels where d theta_d / d theta is below this are ill-conditioned */
+} orc_tol;
+
+/* pixel flag bits */
+enum {
+  ORC_F_RECT_EDGE = 1, ORC_F_ALPHA_MIN = 2, ORC_F_TSTOP = 4, ORC_F_DEPTH_TIE = 8,
+  ORC_F_CULL_TIE = 16, ORC_F_PIXEL_EDGE = 32, ORC_F_ILL_COND = 64, ORC_F_ALPHA_MAX = 128,
+  ORC_F_INVALID_PIXEL = 256
+};
+
+/* ------------------------------------------------------------------ rotations */
+
+/* Rotation matrix of a unit quaternion (w,x,y,z), row-major. */
+static void orc_quat_to_rot(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void orc_normalize4(const double *q, double out[4]) {
+  double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int i = 0; i < 4; ++i) out[i] = q[i] / n;
+}
+
+/* Spherical linear interpolation between unit quaternions along the shorter arc. */
+static void orc_slerp(const double a[4], const double b_in[4], double t, double out[4]) {
+  double b[4];
+  double dot = a[0] * b_in[0] + a[1] * b_in[1] + a[2] * b_in[2] + a[3] * b_in[3];
+  double sgn = dot < 0 ? -1.0 : 1.0;
+  for (int i = 0; i < 4; ++i) b[i] = sgn * b_in[i];
+  dot = fabs(dot);
+  if (dot > 1.0) dot = 1.0;
+  double th = acos(dot);
+  double wa, wb;
+  if (th < 1e-12) { wa = 1.0 - t; wb = t; }
+  else { wa = sin((1.0 - t) * th) / sin(th); wb = sin(t * th) / sin(th); }
+  double q[4];
+  for (int i = 0; i < 4; ++i) q[i] = wa * a[i] + wb * b[i];
+  orc_normalize4(q, out);
+}
+
+/* World->camera pose at shutter time t in [0,1]: rotation slerped, translation lerped. */
+static void orc_pose_at(const orc_camera *c, double t, double R[9], double T[3]) {
+  double qa[4], qb[4], q[4];
+  orc_normalize4(c->q_start, qa);
+  if (!c->rolling_shutter) {
+    orc_quat_to_rot(qa, R);
+    for (int i = 0; i < 3; ++i) T[i] = c->t_start[i];
+    return;
+  }
+  orc_normalize4(c->q_end, qb);
+  orc_slerp(qa, qb, t, q);
+  orc_quat_to_rot(q, R);
+  for (int i = 0; i < 3; ++i) T[i] = (1.0 - t) * c->t_start[i] + t * c->t_end[i];
+}
+
+/* ------------------------------------------------------------------ fisheye polynomial */
+
+static double orc_theta_d(const double k[4], double th) {
+  double t2 = th * th;
+  return th * (1.0 + t2 * (k[0] + t2 * (k[1] + t2 * (k[2] + t2 * k[3]))));
+}
+
+static double orc_theta_d_prime(const double k[4], double th) {
+  double t2 = th * th;
+  return 1.0 + t2 * (3 * k[0] + t2 * (5 * k[1] + t2 * (7 * k[2] + t2 * 9 * k[3])));
+}
+
+/* Largest angle the polynomial fisheye can image: pi/2, or the first zero of
+ * d theta_d / d theta on (0, pi/2] when the distortion polynomial turns over. */
+double orc_theta_max(const double k[4]) {
+  const int steps = 1 << 14;
+  double lo = 0.0, prev = orc_theta_d_prime(k, 0.0);
+  for (int i = 1; i <= steps; ++i) {
+    double th = 0.5 * ORC_PI * (double)i / steps;
+    double v = orc_theta_d_prime(k, th);
+    if (v <= 0.0 && prev > 0.0) {
+      double a = lo, b = th;
+      for (int it = 0; it < 200; ++it) {
+        double m = 0.5 * (a + b);
+        if (orc_theta_d_prime(k, m) > 0.0) a = m; else b = m;
+      }
+      return a;
+    }
+    lo = th; prev = v;
+  }
+  return 0.5 * ORC_PI;
+}
+
+/* theta in [0, theta_max] with theta_d(theta) = rd (theta_d is increasing there) */
+static double orc_theta_inverse(const double k[4], double theta_max, double rd) {
+  double a = 0.0, b = theta_max;
+  double th = rd < theta_max ? rd : theta_max;
+  for (int it = 0; it < 200; ++it) {
+    double f = orc_theta_d(k, th) - rd;
+    if (f > 0) b = th; else a = th;
+    double fp = orc_theta_d_prime(k, th);
+    double nt = fp > 0 ? th - f / fp : 0.5 * (a + b);
+    if (!(nt > a && nt < b)) nt = 0.5 * (a + b);
+    if (fabs(nt - th) < 1e-16 * (1.0 + th)) { th = nt; break; }
+    th = nt;
+    if (b - a < 1e-17) break;
+  }
+  return th;
+}
+
+/* ------------------------------------------------------------------ camera model g(x) */
+
+/* Projects a camera-space point; returns 1 if it is imaged.  *margin receives the
+ * signed relative distance to the validity boundary (positive = valid). */
+static int orc_project_cam(const orc_camera *c, double theta_max, const double xc[3], double uv[2],
+                           double *margin) {
+  double X = xc[0], Y = xc[1], Z = xc[2];
+  if (c->model == 0) {
+    *margin = (Z - c->near_plane) / c->near_plane;
+    if (!(Z > c->near_plane)) return 0;
+    uv[0] = c->fx * X / Z + c->cx;
+    uv[1] = c->fy * Y / Z + c->cy;
+    return 1;
+  } else if (c->model == 1) {
+    double rho = sqrt(X * X + Y * Y);
+    double r3 = sqrt(X * X + Y * Y + Z * Z);
+    double th = atan2(rho, Z);
+    double m1 = (r3 - c->near_plane) / c->near_plane;
+    double m2 = (theta_max - th) / theta_max;
+    *margin = m1 < m2 ? m1 : m2;
+    if (!(r3 > c->near_plane) || !(th <= theta_max)) return 0;
+    if (rho > 0.0) {
+      double s = orc_theta_d(c->k, th) / rho;
+      uv[0] = c->fx * s * X + c->cx;
+      uv[1] = c->fy * s * Y + c->cy;
+    } else {
+      uv[0] = c->cx;
+      uv[1] = c->cy;
+    }
+    return 1;
+  } else {
+    *margin = INFINITY;
+    uv[0] = c->fx * X + c->cx;
+    uv[1] = c->fy * Y + c->cy;
+    return 1;
+  }
+}
+
+/* g(x) for a world point, with the rolling-shutter time found as a fixed point on
+ * the projected row: t <- clamp((v - 1/2)/(H-1), 0, 1), rs_iters updates from t = 1/2,
+ * then the final projection at the last t.  Every projection must be valid. */
+int orc_project_world(const orc_camera *c, double theta_max, int rs_iters, const double x[3],
+                      double uv[2], double *t_out, double *margin_out) {
+  double R[9], T[3], xc[3], m, margin = INFINITY;
+  int valid = 1;
+  double t = 0.0;
+  if (c->rolling_shutter) {
+    t = 0.5;
+    for (int it = 0; it < rs_iters; ++it) {
+      orc_pose_at(c, t, R, T);
+      for (int r = 0; r < 3; ++r) xc[r] = R[3 * r] * x[0] + R[3 * r + 1] * x[1] + R[3 * r + 2] * x[2] + T[r];
+      valid &= orc_project_cam(c, theta_max, xc, uv, &m);
+      if (m < margin) margin = m;
+      if (!valid) break;
+      t = (uv[1] - 0.5) / (double)(c->height - 1);
+      if (t < 0.0) t = 0.0;
+      if (t > 1.0) t = 1.0;
+    }
+  }
+  if (valid) {
+    orc_pose_at(c, t, R, T);
+    for (int r = 0; r < 3; ++r) xc[r] = R[3 * r] * x[0] + R[3 * r + 1] * x[1] + R[3 * r + 2] * x[2] + T[r];
+    valid &= orc_project_cam(c, theta_max, xc, uv, &m);
+    if (m < margin) margin = m;
+  }
+  if (t_out) *t_out = t;
+  if (margin_out) *margin_out = margin;
+  return valid;
+}
+
+/* Camera ray of the pixel-plane point (px, py) (pixel centres at integer + 1/2), in world
+ * space; rolling shutter uses the row time (py - 1/2)/(H-1).  Returns 1 if the point is
+ * inside the imaged region.  *dprime receives d theta_d / d theta at the ray (fisheye) or 1. */
+int orc_pixel_ray(const orc_camera *c, double theta_max, double px, double py, double o[3], double d[3],
+                  double *edge_margin, double *dprime) {
+  double t = 0.0;
+  if (c->rolling_shutter) {
+    t = (py - 0.5) / (double)(c->height - 1);
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+  }
+  double R[9], T[3];
+  orc_pose_at(c, t, R, T);
+  double oc[3] = {0, 0, 0}, dc[3];
+  double mx = (px - c->cx) / c->fx, my = (py - c->cy) / c->fy;
+  *edge_margin = INFINITY;
+  *dprime = 1.0;
+  if (c->model == 0) {
+    dc[0] = mx; dc[1] = my; dc[2] = 1.0;
+  } else if (c->model == 1) {
+    double rd = sqrt(mx * mx + my * my);
+    double rmax = orc_theta_d(c->k, theta_max);
+    *edge_margin = (rmax - rd) / rmax;
+    if (!(rd <= rmax)) return 0;
+    double th = orc_theta_inverse(c->k, theta_max, rd);
+    *dprime = orc_theta_d_prime(c->k, th);
+    if (rd > 0) {
+      double s = sin(th) / rd;
+      dc[0] = s * mx; dc[1] = s * my; dc[2] = cos(th);
+    } else {
+      dc[0] = 0; dc[1] = 0; dc[2] = 1;
+    }
+  } else {
+    oc[0] = mx; oc[1] = my;
+    dc[0] = 0; dc[1] = 0; dc[2] = 1;
+  }
+  /* camera -> world: x = R^T (x_c - T) */
+  for (int j = 0; j < 3; ++j) {
+    o[j] = R[j] * (oc[0] - T[0]) + R[3 + j] * (oc[1] - T[1]) + R[6 + j] * (oc[2] - T[2]);
+    d[j] = R[j] * dc[0] + R[3 + j] * dc[1] + R[6 + j] * dc[2];
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------ spherical harmonics */
+
+/* Real spherical harmonics with the Condon-Shortley phase, orthonormal on the sphere,
+ * for the unit direction d, degrees 0..deg, index l*l + l + m (m = -l..l).
+ * Built from associated Legendre functions P_l^m (three-term recurrence) divided by
+ * (1 - z^2)^{m/2}, times Re / Im of (x + i y)^m.  (Radiance phi_beta(d), Sec. 3.) */
+void orc_sh_basis(int deg, const double dir[3], double *Y) {
+  double x = dir[0], y = dir[1], z = dir[2];
+  double cm = 1.0, sm = 0.0; /* Re, Im of (x + i y)^m */
+  double pmm = 1.0;          /* (-1)^m (2m-1)!! */
+  for (int m = 0; m <= deg; ++m) {
+    if (m > 0) {
+      double ncm = cm * x - sm * y, nsm = cm * y + sm * x;
+      cm = ncm; sm = nsm;
+      pmm *= -(2.0 * m - 1.0);
+    }
+    double p_lm2 = 0.0, p_lm1 = 0.0;
+    for (int l = m; l <= deg; ++l) {
+      double p;
+      if (l == m) p = pmm;
+      else if (l == m + 1) p = z * (2.0 * m + 1.0) * pmm;
+      else p = ((2.0 * l - 1.0) * z * p_lm1 - (l + m - 1.0) * p_lm2) / (double)(l - m);
+      p_lm2 = p_lm1; p_lm1 = p;
+      double ratio = 1.0; /* (l-m)!/(l+m)! */
+      for (int f = l - m + 1; f <= l + m; ++f) ratio /= (double)f;
+      double K = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * ratio);
+      if (m == 0) Y[l * l + l] = K * p;
+      else {
+        Y[l * l + l + m] = sqrt(2.0) * K * cm * p;
+        Y[l * l + l - m] = sqrt(2.0) * K * sm * p;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ particles */
+
+typedef struct {
+  double mu[3], s[3], qn[4], qnorm, R[9], M[9], sigma;
+  int ok; /* finite parameters and a normalisable quaternion */
+} orc_particle;
+
+static void orc_load_particle(const orc_scene *sc, int i, orc_particle *p) {
+  double q[4];
+  p->ok = 1;
+  for (int j = 0; j < 3; ++j) {
+    p->mu[j] = sc->means[3 * i + j];
+    p->s[j] = exp((double)sc->log_scales[3 * i + j]);
+    if (!isfinite(p->mu[j]) || !isfinite(p->s[j]) || !(p->s[j] > 0)) p->ok = 0;
+  }
+  for (int j = 0; j < 4; ++j) q[j] = sc->quats[4 * i + j];
+  p->qnorm = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(p->qnorm > 0) || !isfinite(p->qnorm)) { p->ok = 0; p->qnorm = 1; q[0] = 1; q[1] = q[2] = q[3] = 0; }
+  for (int j = 0; j < 4; ++j) p->qn[j] = q[j] / p->qnorm;
+  double lg = sc->opacity_logits[i];
+  p->sigma = 1.0 / (1.0 + exp(-lg));
+  if (!isfinite(lg)) p->ok = 0;
+  orc_quat_to_rot(p->qn, p->R);
+  /* M = S^-1 R^T : row k is column k of R divided by s_k */
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) p->M[3 * k + j] = p->R[3 * j + k] / p->s[k];
+}
+
+/* Unscented-Transform estimate of the 2D mean and covariance of a particle
+ * (Algorithm 2; eq. sigma_points, weights_1, weights_2, 2d_conic_1, 2d_conic_2).
+ * Sigma points use the square root R S of Sigma = R S S^T R^T: column k is s_k R[:,k]. */
+int orc_ut_estimate(const orc_camera *c, double theta_max, int rs_iters, double a, double b, double kappa,
+                    const double mu[3], const double R[9], const double s[3], double vmu[2], double cov[3],
+                    double *t_mean, double *margin) {
+  double lam = a * a * (3.0 + kappa) - 3.0;
+  double gam = sqrt(3.0 + lam);
+  double wm0 = lam / (3.0 + lam), wi = 1.0 / (2.0 * (3.0 + lam));
+  double wc0 = wm0 + (1.0 - a * a + b);
+  double X[7][3], V[7][2];
+  for (int j = 0; j < 3; ++j) X[0][j] = mu[j];
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) {
+      double col = gam * s[k] * R[3 * j + k];
+      X[1 + k][j] = mu[j] + col;
+      X[4 + k][j] = mu[j] - col;
+    }
+  int valid = 1;
+  double mg = INFINITY;
+  for (int i = 0; i < 7; ++i) {
+    double m, t;
+    int v = orc_project_world(c, theta_max, rs_iters, X[i], V[i], &t, &m);
+    if (i == 0 && t_mean) *t_mean = t;
+    if (m < mg) mg = m;
+    valid &= v;
+  }
+  if (margin) *margin = mg;
+  if (!valid) return 0;
+  vmu[0] = wm0 * V[0][0]; vmu[1] = wm0 * V[0][1];
+  for (int i = 1; i < 7; ++i) { vmu[0] += wi * V[i][0]; vmu[1] += wi * V[i][1]; }
+  cov[0] = cov[1] = cov[2] = 0.0;
+  for (int i = 0; i < 7; ++i) {
+    double w = i == 0 ? wc0 : wi;
+    double dx = V[i][0] - vmu[0], dy = V[i][1] - vmu[1];
+    cov[0] += w * dx * dx; cov[1] += w * dx * dy; cov[2] += w * dy * dy;
+  }
+  return 1;
+}
+
+/* Per-particle projection (Algorithm 1): UT estimate, opacity-tightened extent,
+ * pixel rectangle, depth, tile count.
+ * Outputs (arrays of n): mean2d[2], cov2d[3], depth (FP64), depth32 (the FP64 depth rounded
+ * to FP32, which enters the sort key), rect[4] = (x0,y0,x1,y1) inclusive pixel indices
+ * (culled: 0,0,-1,-1), ntiles, edges[4] = unrounded (x0,x1,y0,y1) edge values before
+ * clipping (NaN when unavailable), tie[n] = 1 when a culling decision is within eps_rel
+ * of its threshold. */
+void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
+                 double *mean2d, double *cov2d, double *depth, float *depth32, int32_t *rect,
+                 int32_t *ntiles, double *edges, int32_t *tie) {
+  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  int W = c->width, H = c->height;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int i = 0; i < sc->n; ++i) {
+    orc_particle p;
+    orc_load_particle(sc, i, &p);
+    int32_t *r = rect + 4 * i;
+    r[0] = 0; r[1] = 0; r[2] = -1; r[3] = -1;
+    ntiles[i] = 0;
+    depth[i] = 0.0; depth32[i] = 0.0f;
+    mean2d[2 * i] = mean2d[2 * i + 1] = NAN;
+    cov2d[3 * i] = cov2d[3 * i + 1] = cov2d[3 * i + 2] = NAN;
+    for (int j = 0; j < 4; ++j) edges[4 * i + j] = NAN;
+    tie[i] = 0;
+    if (!p.ok) continue;
+    double sig_margin = (p.sigma - op->alpha_min) / op->alpha_min;
+    if (fabs(sig_margin) < tol->eps_rel) tie[i] = 1;
+    double vmu[2], cov[3], tmu = 0.0, vm;
+    int valid = orc_ut_estimate(c, theta_max, op->rs_iters, op->ut_alpha, op->ut_beta, op->ut_kappa, p.mu,
+                                p.R, p.s, vmu, cov, &tmu, &vm);
+    if (fabs(vm) < tol->eps_rel) tie[i] = 1;
+    if (!valid) {
+      if (tie[i]) {
+        /* a near-valid particle: estimate its footprint anyway so that pixels under it get flagged */
+        orc_camera c2 = *c;
+        c2.near_plane = 1e-9;
+        double th2 = 0.5 * ORC_PI;
+        if (orc_ut_estimate(&c2, th2 > theta_max ? th2 : theta_max, op->rs_iters, op->ut_alpha, op->ut_beta,
+                            op->ut_kappa, p.mu, p.R, p.s, vmu, cov, NULL, NULL)) {
+          double k = op->extent_sigma;
+          double hx = k * sqrt(cov[0]), hy = k * sqrt(cov[2]);
+          edges[4 * i + 0] = vmu[0] - hx - 0.5; edges[4 * i + 1] = vmu[0] + hx - 0.5;
+          edges[4 * i + 2] = vmu[1] - hy - 0.5; edges[4 * i + 3] = vmu[1] + hy - 0.5;
+        }
+      }
+      continue;
+    }
+    mean2d[2 * i] = vmu[0]; mean2d[2 * i + 1] = vmu[1];
+    cov2d[3 * i] = cov[0]; cov2d[3 * i + 1] = cov[1]; cov2d[3 * i + 2] = cov[2];
+    /* depth: distance from the camera centre to the mean at the mean's shutter time */
+    double Rm[9], Tm[3], xc[3];
+    orc_pose_at(c, tmu, Rm, Tm);
+    for (int rr = 0; rr < 3; ++rr)
+      xc[rr] = Rm[3 * rr] * p.mu[0] + Rm[3 * rr + 1] * p.mu[1] + Rm[3 * rr + 2] * p.mu[2] + Tm[rr];
+    double dep = sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
+    depth[i] = dep;
+    depth32[i] = (float)dep;
+    if (!(p.sigma >= op->alpha_min)) continue;
+    /* opacity-tightened extent: where sigma * exp(-k^2/2) falls to alpha_min, capped */
+    double k = sqrt(2.0 * log(p.sigma / op->alpha_min));
+    if (k > op->extent_sigma) k = op->extent_sigma;
+    double hx = k * sqrt(cov[0]), hy = k * sqrt(cov[2]);
+    double e0 = vmu[0] - hx - 0.5, e1 = vmu[0] + hx - 0.5, e2 = vmu[1] - hy - 0.5, e3 = vmu[1] + hy - 0.5;
+    edges[4 * i + 0] = e0; edges[4 * i + 1] = e1; edges[4 * i + 2] = e2; edges[4 * i + 3] = e3;
+    if (!isfinite(e0) || !isfinite(e1) || !isfinite(e2) || !isfinite(e3)) continue;
+    double x0 = ceil(e0), x1 = floor(e1), y0 = ceil(e2), y1 = floor(e3);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > W - 1) x1 = W - 1;
+    if (y1 > H - 1) y1 = H - 1;
+    if (x0 > x1 || y0 > y1) continue;
+    r[0] = (int32_t)x0; r[1] = (int32_t)y0; r[2] = (int32_t)x1; r[3] = (int32_t)y1;
+    int tx0 = r[0] / op->tile_w, tx1 = r[2] / op->tile_w, ty0 = r[1] / op->tile_h, ty1 = r[3] / op->tile_h;
+    ntiles[i] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+  }
+}
+
+/* ------------------------------------------------------------------ duplicate + sort */
+
+typedef struct { uint64_t key; uint64_t seq; uint32_t val; } orc_kv;
+
+static int orc_kv_cmp(const void *a, const void *b) {
+  const orc_kv *x = (const orc_kv *)a, *y = (const orc_kv *)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->seq != y->seq) return x->seq < y->seq ? -1 : 1;
+  return 0;
+}
+
+static uint32_t orc_f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* Number of duplicated keys for the given rects. */
+int64_t orc_count_keys(int n, const int32_t *rect, int tile_w, int tile_h) {
+  int64_t K = 0;
+  for (int i = 0; i < n; ++i) {
+    const int32_t *r = rect + 4 * i;
+    if (r[0] > r[2] || r[1] > r[3]) continue;
+    K += (int64_t)(r[2] / tile_w - r[0] / tile_w + 1) * (r[3] / tile_h - r[1] / tile_h + 1);
+  }
+  return K;
+}
+
+/* Duplicate (Table 2, "Duplicate"): one key (tile << 32 | bits(depth32)) per tile a particle's
+ * rect overlaps, particles in index order, tiles row-major; then a stable sort ("Sort"), and
+ * per-tile ranges [start, end) into the sorted list (empty tiles: [0, 0)).
+ * keys/vals must hold orc_count_keys() entries; ranges holds 2 * tiles_x * tiles_y. */
+void orc_bin(int n, const float *depth32, const int32_t *rect, int W, int H, int tile_w, int tile_h,
+             uint64_t *keys, uint32_t *vals, uint32_t *ranges) {
+  int tx = (W + tile_w - 1) / tile_w, ty = (H + tile_h - 1) / tile_h;
+  int64_t K = orc_count_keys(n, rect, tile_w, tile_h);
+  orc_kv *kv = (orc_kv *)malloc(sizeof(orc_kv) * (size_t)(K > 0 ? K : 1));
+  int64_t e = 0;
+  for (int i = 0; i < n; ++i) {
+    const int32_t *r = rect + 4 * i;
+    if (r[0] > r[2] || r[1] > r[3]) continue;
+    for (int y = r[1] / tile_h; y <= r[3] / tile_h; ++y)
+      for (int x = r[0] / tile_w; x <= r[2] / tile_w; ++x) {
+        uint64_t tile = (uint64_t)y * tx + x;
+        kv[e].key = (tile << 32) | orc_f32_bits(depth32[i]);
+        kv[e].seq = (uint64_t)e;
+        kv[e].val = (uint32_t)i;
+        ++e;
+      }
+  }
+  qsort(kv, (size_t)K, sizeof(orc_kv), orc_kv_cmp);
+  for (int t = 0; t < tx * ty; ++t) { ranges[2 * t] = 0; ranges[2 * t + 1] = 0; }
+  for (int64_t j = 0; j < K; ++j) {
+    keys[j] = kv[j].key;
+    vals[j] = kv[j].val;
+    uint32_t t = (uint32_t)(kv[j].key >> 32);
+    if (j == 0 || (uint32_t)(kv[j - 1].key >> 32) != t) ranges[2 * t] = (uint32_t)j;
+    if (j == K - 1 || (uint32_t)(kv[j + 1].key >> 32) != t) ranges[2 * t + 1] = (uint32_t)(j + 1);
+  }
+  free(kv);
+}
+
+/* ------------------------------------------------------------------ compositing */
+
+typedef struct {
+  int n, deg, nsh;
+  orc_particle *P;
+  const int32_t *rect;
+  const float *depth32;
+  const double *edges;
+  const int32_t *tie;
+  int32_t *order; /* valid particles sorted by (bits(depth32), index) */
+  int norder;
+  int32_t *tie_list;
+  int ntie;
+} orc_ctx;
+
+static const float *orc_depth_sort_key;
+static int orc_order_cmp(const void *a, const void *b) {
+  int i = *(const int32_t *)a, j = *(const int32_t *)b;
+  uint32_t ki = orc_f32_bits(orc_depth_sort_key[i]), kj = orc_f32_bits(orc_depth_sort_key[j]);
+  if (ki != kj) return ki < kj ? -1 : 1;
+  return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+static void orc_ctx_init(orc_ctx *x, const orc_scene *sc, const int32_t *rect, const float *depth32,
+                         const double *edges, const int32_t *tie) {
+  x->n = sc->n;
+  x->deg = sc->sh_degree;
+  x->nsh = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+  x->P = (orc_particle *)malloc(sizeof(orc_particle) * (size_t)(sc->n > 0 ? sc->n : 1));
+  x->order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sc->n > 0 ? sc->n : 1));
+  x->tie_list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sc->n > 0 ? sc->n : 1));
+  x->rect = rect; x->depth32 = depth32; x->edges = edges; x->tie = tie;
+  x->norder = 0; x->ntie = 0;
+  for (int i = 0; i < sc->n; ++i) {
+    orc_load_particle(sc, i, &x->P[i]);
+    const int32_t *r = rect + 4 * i;
+    if (x->P[i].ok && r[0] <= r[2] && r[1] <= r[3]) x->order[x->norder++] = i;
+    if (tie && tie[i]) x->tie_list[x->ntie++] = i;
+  }
+  orc_depth_sort_key = depth32;
+  qsort(x->order, (size_t)x->norder, sizeof(int32_t), orc_order_cmp);
+}
+
+static void orc_ctx_free(orc_ctx *x) { free(x->P); free(x->order); free(x->tie_list); }
+
+/* Maximum response of particle p along the ray o + tau d (eq. GaussianMaxResponse):
+ * o_g = S^-1 R^T (o - mu), d_g = S^-1 R^T d, tau_max = -o_g.d_g / d_g.d_g, and the squared
+ * canonical distance omega^2 = |o_g + tau_max d_g|^2 = |o_g x d_g|^2 / |d_g|^2. */
+static double orc_omega2(const orc_particle *p, const double o[3], const double d[3], double og[3], double dg[3],
+                         double *tau) {
+  double om[3] = {o[0] - p->mu[0], o[1] - p->mu[1], o[2] - p->mu[2]};
+  for (int k = 0; k < 3; ++k) {
+    og[k] = p->M[3 * k] * om[0] + p->M[3 * k + 1] * om[1] + p->M[3 * k + 2] * om[2];
+    dg[k] = p->M[3 * k] * d[0] + p->M[3 * k + 1] * d[1] + p->M[3 * k + 2] * d[2];
+  }
+  double dd = dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
+  double od = og[0] * dg[0] + og[1] * dg[1] + og[2] * dg[2];
+  double cx = og[1] * dg[2] - og[2] * dg[1], cy = og[2] * dg[0] - og[0] * dg[2], cz = og[0] * dg[1] - og[1] * dg[0];
+  *tau = -od / dd;
+  return (cx * cx + cy * cy + cz * cz) / dd;
+}
+
+typedef struct {
+  int i;
+  double alpha, a, T, rho, tau, og[3], dg[3], raw[3], col[3];
+} orc_contrib;
+
+/* Composites one pixel ray over the particles in `order` (eq. QuadratureVolumeRendering with
+ * alpha_i = sigma_i rho_i at tau_max).  Returns the number of blended particles; fills rgb, T.
+ * When `rec` is given, records every blended particle (up to cap). */
+static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_options *op, const orc_tol *tol,
+                             int px, int py, const double o[3], const double d[3], const double *Y, double rgb[3],
+                             double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect) {
+  double T = 1.0;
+  int nb = 0;
+  uint32_t last_bits = 0;
+  int have_last = 0;
+  rgb[0] = rgb[1] = rgb[2] = 0.0;
+  for (int j = 0; j < x->norder; ++j) {
+    int i = x->order[j];
+    const orc_particle *p = &x->P[i];
+    const int32_t *r = x->rect + 4 * i;
+    int inside = px >= r[0] && px <= r[2] && py >= r[1] && py <= r[3];
+    double og[3], dg[3], tau;
+    if (!inside && !no_rect) {
+      /* only a rect edge within eps of this pixel could flip membership */
+      if (x->edges && flags) {
+        const double *e = x->edges + 4 * i;
+        double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
+        int nx = px >= e[0] - tol->eps_px && px <= e[1] + tol->eps_px;
+        int ny = py >= e[2] - tol->eps_px && py <= e[3] + tol->eps_px;
+        if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && px >= 0 && py >= 0) {
+          double w2 = orc_omega2(p, o, d, og, dg, &tau);
+          if (p->sigma * exp(-0.5 * w2) >= op->alpha_min * (1.0 - tol->eps_rel)) *flags |= ORC_F_RECT_EDGE;
+        }
+      }
+      continue;
+    }
+    double w2 = orc_omega2(p, o, d, og, dg, &tau);
+    double rho = exp(-0.5 * w2);
+    double a = p->sigma * rho;
+    if (flags && x->edges && !no_rect) {
+      const double *e = x->edges + 4 * i;
+      double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
+      if ((ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel))
+        *flags |= ORC_F_RECT_EDGE;
+    }
+    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) *flags |= ORC_F_ALPHA_MIN;
+    if (a < op->alpha_min) continue;
+    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
+    double alpha = a < op->alpha_max ? a : op->alpha_max;
+    double Tn = T * (1.0 - alpha);
+    if (flags && fabs(Tn - op->t_min) < tol->eps_rel * op->t_min) *flags |= ORC_F_TSTOP;
+    if (Tn < op->t_min) break;
+    uint32_t bits = orc_f32_bits(x->depth32[i]);
+    if (flags && have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) *flags |= ORC_F_DEPTH_TIE;
+    last_bits = bits; have_last = 1;
+    const float *beta = sc->sh + (size_t)i * x->nsh * 3;
+    double raw[3], col[3];
+    for (int ch = 0; ch < 3; ++ch) {
+      double s = 0.5;
+      for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Y[kk];
+      raw[ch] = s;
+      col[ch] = s > 0.0 ? s : 0.0;
+      rgb[ch] += col[ch] * alpha * T;
+    }
+    if (rec && nb < cap) {
+      orc_contrib *c = &rec[nb];
+      c->i = i; c->alpha = alpha; c->a = a; c->T = T; c->rho = rho; c->tau = tau;
+      for (int k = 0; k < 3; ++k) { c->og[k] = og[k]; c->dg[k] = dg[k]; c->raw[k] = raw[k]; c->col[k] = col[k]; }
+    }
+    ++nb;
+    T = Tn;
+  }
+  *Tout = T;
+  return nb;
+}
+
+static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int px, int py, const orc_tol *tol,
+                            double o[3], double d[3], double *Y, int *valid, int32_t *flags) {
+  double em, dp;
+  *valid = orc_pixel_ray(c, theta_max, px + 0.5, py + 0.5, o, d, &em, &dp);
+  if (flags && c->model == 1 && fabs(em) < tol->eps_rel) *flags |= ORC_F_PIXEL_EDGE;
+  if (!*valid) { if (flags) *flags |= ORC_F_INVALID_PIXEL; return; }
+  if (flags && dp < tol->cond_min) *flags |= ORC_F_ILL_COND;
+  double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  double dh[3] = {d[0] / nd, d[1] / nd, d[2] / nd};
+  orc_sh_basis(deg, dh, Y);
+}
+
+/* Renders the listed pixels by brute force over all particles in global depth order.
+ * rect / depth32 / valid come from orc_project or are given directly (synthetic).
+ * edges / tie may be NULL (then no near-tie flags of those kinds).  no_rect != 0 evaluates
+ * every particle at every pixel (culling disabled).
+ * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags. */
+void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
+                const int32_t *rect, const float *depth32, const double *edges, const int32_t *tie, int npix,
+                const int32_t *pix_x, const int32_t *pix_y, int no_rect, double *rgb, double *alpha,
+                double *tfinal, int32_t *nblend, int32_t *flags) {
+  orc_ctx x;
+  orc_ctx_init(&x, sc, rect, depth32, edges, tie);
+  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int q = 0; q < npix; ++q) {
+    int px = pix_x[q], py = pix_y[q];
+    double o[3], d[3], Y[16];
+    int valid;
+    int32_t fl = 0;
+    orc_pixel_setup(c, theta_max, x.deg, px, py, tol, o, d, Y, &valid, &fl);
+    if (!valid) {
+      rgb[3 * q] = rgb[3 * q + 1] = rgb[3 * q + 2] = 0.0;
+      alpha[q] = 0.0; tfinal[q] = 1.0; nblend[q] = 0; flags[q] = fl;
+      continue;
+    }
+    for (int t = 0; t < x.ntie; ++t) {
+      const double *e = edges ? edges + 4 * x.tie_list[t] : NULL;
+      /* a near-tie particle without a footprint estimate flags every pixel */
+      if (!e || isnan(e[0]) || (px >= e[0] - 1 && px <= e[1] + 1 && py >= e[2] - 1 && py <= e[3] + 1))
+        fl |= ORC_F_CULL_TIE;
+    }
+    double T;
+    nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect);
+    alpha[q] = 1.0 - T;
+    tfinal[q] = T;
+    flags[q] = fl;
+  }
+  orc_ctx_free(&x);
+}
+
+/* Composites an explicitly given ordered particle list for one pixel (used to check that
+ * per-tile lists reproduce the brute-force order). */
+void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options *op, const int32_t *rect,
+                     const float *depth32, int px, int py, int nlist, const uint32_t *list, double rgb[3],
+                     double *tfinal) {
+  orc_ctx x;
+  orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
+  for (int j = 0; j < nlist; ++j) x.order[j] = (int32_t)list[j];
+  x.norder = nlist;
+  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  orc_tol tol = {0, 0, 0, 0};
+  double o[3], d[3], Y[16];
+  int valid;
+  orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
+  if (!valid) { rgb[0] = rgb[1] = rgb[2] = 0; *tfinal = 1.0; }
+  else orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, tfinal, NULL, NULL, 0, 0);
+  orc_ctx_free(&x);
+}
+
+/* ------------------------------------------------------------------ gradients */
+
+/* d rotation / d unit quaternion, contracted with G = dL/dR (row-major). */
+static void orc_rot_grad(const double q[4], const double G[9], double gq[4]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  gq[0] = 2 * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+  gq[1] = 2 * (y * G[1] + z * G[2] + y * G[3] - 2 * x * G[4] - w * G[5] + z * G[6] + w * G[7] - 2 * x * G[8]);
+  gq[2] = 2 * (-2 * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] + z * G[7] - 2 * y * G[8]);
+  gq[3] = 2 * (-2 * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2 * z * G[4] + y * G[5] + x * G[6] + y * G[7]);
+}
+
+/* Reverse-mode gradient of L with respect to every particle parameter, given dL/drgb and
+ * dL/dalpha at the listed pixels (supplementary Sec. B: d alpha / d omega^2 = -1/2 sigma
+ * exp(-omega^2/2); d omega^2 / d o_g = 2 (o_g + tau d_g); d o_g / d mu = -S^-1 R^T; the S, R
+ * terms follow from d omega^2 / d d_g = 2 tau (o_g + tau d_g) and M = S^-1 R^T).  The 2D
+ * projection contributes no gradient: it only selects particles (Sec. 4.1).
+ * Outputs are overwritten: d_means[n][3], d_log_scales[n][3], d_quats[n][4],
+ * d_logits[n], d_sh[n][nsh][3]. */
+void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *op, const int32_t *rect,
+                  const float *depth32, int npix, const int32_t *pix_x, const int32_t *pix_y, const double *g_rgb,
+                  const double *g_alpha, double *d_means, double *d_log_scales, double *d_quats,
+                  double *d_logits, double *d_sh) {
+  orc_ctx x;
+  orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
+  int n = sc->n, nsh = x.nsh;
+  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  /* accumulators: dM (9), dmu (3), dsigma (1) */
+  double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 13, sizeof(double));
+  memset(d_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
+  orc_tol tol = {0, 0, 0, 0};
+#pragma omp parallel
+  {
+    orc_contrib *rec = (orc_contrib *)malloc(sizeof(orc_contrib) * (size_t)(x.norder > 0 ? x.norder : 1));
+#pragma omp for schedule(dynamic, 4)
+    for (int q = 0; q < npix; ++q) {
+      int px = pix_x[q], py = pix_y[q];
+      double o[3], d[3], Y[16];
+      int valid;
+      orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
+      if (!valid) continue;
+      double rgb[3], Tf;
+      int nb = orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0);
+      const double *g = g_rgb + 3 * q;
+      double gA = g_alpha[q];
+      double S[3] = {0, 0, 0}; /* sum over later blended particles of c alpha T */
+      for (int b = nb - 1; b >= 0; --b) {
+        orc_contrib *k = &rec[b];
+        const orc_particle *p = &x.P[k->i];
+        double om1 = 1.0 - k->alpha;
+        double dalpha = gA * Tf / om1;
+        for (int ch = 0; ch < 3; ++ch) dalpha += g[ch] * (k->col[ch] * k->T - S[ch] / om1);
+        for (int ch = 0; ch < 3; ++ch) S[ch] += k->col[ch] * k->alpha * k->T;
+        /* colour: d c / d beta = Y where the clamp is inactive */
+        for (int ch = 0; ch < 3; ++ch) {
+          if (!(k->raw[ch] > 0.0)) continue;
+          double gc = g[ch] * k->alpha * k->T;
+          for (int kk = 0; kk < nsh; ++kk) {
+#pragma omp atomic
+            d_sh[((size_t)k->i * nsh + kk) * 3 + ch] += gc * Y[kk];
+          }
+        }
+        double da = k->a > op->alpha_max ? 0.0 : dalpha;
+        double dsig = da * k->rho;
+        double dw2 = da * (-0.5 * k->a);
+        double pv[3], xw[3];
+        for (int j = 0; j < 3; ++j) {
+          pv[j] = 2.0 * dw2 * (k->og[j] + k->tau * k->dg[j]); /* dL/d o_g */
+          xw[j] = o[j] - p->mu[j] + k->tau * d[j];             /* o - mu + tau d */
+        }
+        double *A = acc + 13 * (size_t)k->i;
+        for (int r = 0; r < 3; ++r)
+          for (int j = 0; j < 3; ++j) {
+#pragma omp atomic
+            A[3 * r + j] += pv[r] * xw[j];
+          }
+        for (int j = 0; j < 3; ++j) {
+          double dm = -(p->M[j] * pv[0] + p->M[3 + j] * pv[1] + p->M[6 + j] * pv[2]);
+#pragma omp atomic
+          A[9 + j] += dm;
+        }
+#pragma omp atomic
+        A[12] += dsig;
+      }
+    }
+    free(rec);
+  }
+  for (int i = 0; i < n; ++i) {
+    const orc_particle *p = &x.P[i];
+    const double *A = acc + 13 * (size_t)i;
+    for (int j = 0; j < 3; ++j) d_means[3 * i + j] = A[9 + j];
+    /* M_kj = R_jk / s_k, s_k = exp(l_k): dL/dl_k = -sum_j dM_kj M_kj; dL/dR_jk = dM_kj / s_k */
+    double G[9];
+    for (int k = 0; k < 3; ++k) {
+      double acc_l = 0;
+      for (int j = 0; j < 3; ++j) {
+        acc_l += A[3 * k + j] * p->M[3 * k + j];
+        G[3 * j + k] = A[3 * k + j] / p->s[k];
+      }
+      d_log_scales[3 * i + k] = -acc_l;
+    }
+    double gq[4];
+    orc_rot_grad(p->qn, G, gq);
+    double dot = gq[0] * p->qn[0] + gq[1] * p->qn[1] + gq[2] * p->qn[2] + gq[3] * p->qn[3];
+    for (int j = 0; j < 4; ++j) d_quats[4 * i + j] = (gq[j] - p->qn[j] * dot) / p->qnorm;
+    d_logits[i] = A[12] * p->sigma * (1.0 - p->sigma);
+  }
+  free(acc);
+  orc_ctx_free(&x);
+}
+
+/* ------------------------------------------------------------------ misc */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

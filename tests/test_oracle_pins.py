@@ -1,0 +1,546 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these tests retypes the oracle's formulas: each compares it with a closed
+form, an invariant, a library routine, brute force, or a hand-derived expansion,
+chosen so that a dropped term, a wrong sign / index or a transposed operand in the
+oracle fails at least one of them.  CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2412_12507_gb300 import synth
+
+
+def rot(q):
+    q = np.asarray(q, float)
+    q = q / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def axis_angle_rot(axis, ang):
+    """Rodrigues' formula (an independent route to a rotation matrix)."""
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+def one_scene(mu, log_s, q, logit, sh, deg=0):
+    return dict(means=np.array([mu], np.float32), log_scales=np.array([log_s], np.float32),
+                quats=np.array([q], np.float32), opacity_logits=np.array([logit], np.float32),
+                sh=np.array(sh, np.float32).reshape(1, (deg + 1) ** 2, 3), sh_degree=deg)
+
+
+# ------------------------------------------------------------------ rotations
+
+def test_quaternion_rotation_matches_rodrigues(orc):
+    """R(q) of the oracle (through an orthographic UT of a needle Gaussian) equals the
+    axis-angle rotation built by Rodrigues' formula."""
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        axis = rng.standard_normal(3)
+        ang = rng.uniform(0, math.pi)
+        a = axis / np.linalg.norm(axis)
+        q = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * a])
+        R = axis_angle_rot(axis, ang)
+        assert np.allclose(rot(q), R, atol=1e-12)
+        # the oracle sees R through the 2D covariance of an orthographic camera: A R S^2 R^T A^T
+        s = np.array([0.3, 0.1, 0.05])
+        cam = synth.camera("ortho", 64, 64, fx=10.0, fy=10.0)
+        ok, vmu, cov = orc.ut_estimate(cam, [0.1, 0.2, 3.0], R, s)
+        Sig = (R * s**2) @ R.T
+        assert ok
+        assert np.allclose(cov, [100 * Sig[0, 0], 100 * Sig[0, 1], 100 * Sig[1, 1]], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ Unscented Transform
+
+@pytest.mark.parametrize("ut", [(1.0, 2.0, 0.0), (0.5, 2.0, 0.0), (1.0, 0.0, 1.0), (1.3, 2.0, -0.5)])
+def test_ut_exact_for_affine_camera(orc, ut):
+    """For an affine g the UT mean and covariance are A mu + b and A Sigma A^T exactly, for
+    any (alpha, beta, kappa) with 3 + lambda > 0 (moment matching, Sec. 4.1)."""
+    rng = np.random.default_rng(11)
+    Rc = axis_angle_rot([0.3, -1.0, 0.2], 0.7)
+    qc = synth._rot_to_quat(Rc)
+    tc = np.array([0.2, -0.1, 1.5])
+    cam = synth.camera("ortho", 100, 80, fx=37.0, fy=29.0, cx=41.0, cy=33.0, q=qc, t=tc)
+    for _ in range(10):
+        mu = rng.uniform(-1, 1, 3)
+        R = rot(rng.standard_normal(4))
+        s = np.exp(rng.normal(-1.5, 0.5, 3))
+        ok, vmu, cov = orc.ut_estimate(cam, mu, R, s, ut=ut)
+        assert ok
+        A = np.array([[37.0, 0, 0], [0, 29.0, 0]]) @ Rc
+        b = np.array([37.0 * tc[0] + 41.0, 29.0 * tc[1] + 33.0])
+        Sig = R @ np.diag(s**2) @ R.T
+        C2 = A @ Sig @ A.T
+        assert np.allclose(vmu, A @ mu + b, rtol=0, atol=1e-10)
+        assert np.allclose(cov, [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-10, atol=1e-10)
+
+
+def test_ut_pinhole_constant_depth_is_exact(orc):
+    """A flat Gaussian parallel to the image plane of a pinhole camera sees an affine map on
+    its support, so the UT recovers the projected moments exactly."""
+    cam = synth.camera("pinhole", 640, 480, fx=500.0, fy=450.0, cx=320.0, cy=240.0)
+    ang = 0.6
+    R = axis_angle_rot([0, 0, 1], ang)
+    s = np.array([0.05, 0.02, 1e-12])
+    mu = np.array([0.3, -0.2, 2.5])
+    ok, vmu, cov = orc.ut_estimate(cam, mu, R, s)
+    assert ok
+    assert np.allclose(vmu, [500 * 0.3 / 2.5 + 320, 450 * -0.2 / 2.5 + 240], atol=1e-9)
+    J = np.diag([500 / 2.5, 450 / 2.5])
+    C2 = J @ (R[:2, :2] @ np.diag(s[:2] ** 2) @ R[:2, :2].T) @ J
+    assert np.allclose(cov, [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-9)
+
+
+def test_ut_depth_expansion_pins_weights(orc):
+    """Needle Gaussian along the optical axis, offset in x, pinhole camera: with
+    eps = (s_z / Z0)^2 and a = f X / Z0, a hand expansion of eq. weights_1/2 and
+    eq. 2d_conic_1/2 at (alpha, beta, kappa) = (1, 2, 0) gives
+        mean / a = 1 + eps + 3 eps^2 + O(eps^3)
+        var  / a^2 = eps + 10 eps^2 + O(eps^3)
+    The true moments of f X / Z are 1 + eps + 3 eps^2 and eps + 8 eps^2; the extra 2 eps^2 is
+    the (1 - alpha^2 + beta) covariance weight of the centre point, so dropping that term,
+    or a wrong sqrt(3 + lambda) spread, fails here."""
+    cam = synth.camera("pinhole", 64, 64, fx=100.0, fy=100.0, cx=0.0, cy=0.0)
+    X, Z0 = 0.7, 3.0
+    a = 100.0 * X / Z0
+    E, C1, C2 = [], [], []
+    for sz in (0.015, 0.03, 0.045, 0.06):
+        eps = (sz / Z0) ** 2
+        ok, vmu, cov = orc.ut_estimate(cam, [X, 0.0, Z0], np.eye(3), [1e-14, 1e-14, sz])
+        assert ok
+        E.append(eps)
+        C1.append((vmu[0] / a - 1 - eps) / eps**2)
+        C2.append((cov[0] / a**2 - eps) / eps**2)
+    # the second-order coefficients, extrapolated to eps -> 0 by a linear fit in eps
+    c1 = np.polyfit(E, C1, 1)[1]
+    c2 = np.polyfit(E, C2, 1)[1]
+    assert abs(c1 - 3.0) < 2e-3, c1
+    assert abs(c2 - 10.0) < 2e-3, c2
+
+
+@pytest.mark.parametrize("model", ["pinhole", "fisheye"])
+def test_ut_close_to_monte_carlo(orc, model):
+    """Sanity check of the UT against Monte Carlo moments (the supplementary's reference):
+    for small Gaussians the UT mean / covariance agree with MC up to sampling error and
+    higher-order terms."""
+    rng = np.random.default_rng(3)
+    if model == "pinhole":
+        cam = synth.camera("pinhole", 640, 480, fx=400.0, fy=400.0)
+    else:
+        cam = synth.camera("fisheye", 640, 480, k=[0.03, -0.01, 0.004, -0.001])
+    for _ in range(4):
+        mu = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(2.5, 4)])
+        R = rot(rng.standard_normal(4))
+        s = np.exp(rng.normal(-3.5, 0.3, 3))
+        ok, vmu, cov = orc.ut_estimate(cam, mu, R, s)
+        assert ok
+        x = mu + (rng.standard_normal((200_000, 3)) * s) @ R.T
+        uv = np.array([orc.project_point(cam, xi)[1] for xi in x[:20000]])
+        m = uv.mean(0)
+        C = np.cov(uv.T)
+        se = np.sqrt(np.diag(C) / len(uv))
+        assert np.all(np.abs(m - vmu) < 6 * se + 1e-3 * np.sqrt(np.diag(C)))
+        assert np.allclose(cov, [C[0, 0], C[0, 1], C[1, 1]], rtol=0.08, atol=0.05 * np.sqrt(C[0, 0] * C[1, 1]))
+
+
+# ------------------------------------------------------------------ cameras
+
+def test_fisheye_equidistant_closed_form(orc):
+    """k = 0: the polynomial fisheye is equidistant, radius = f * angle from the axis."""
+    cam = synth.camera("fisheye", 800, 600, fx=300.0, fy=300.0)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        x = rng.standard_normal(3)
+        x[2] = abs(x[2]) + 0.1
+        ok, uv, _ = orc.project_point(cam, x)
+        assert ok
+        ang = math.acos(x[2] / np.linalg.norm(x))
+        r = math.hypot(uv[0] - 400, uv[1] - 300)
+        assert abs(r - 300 * ang) < 1e-9
+        # direction in the image plane is the direction of (X, Y)
+        assert abs(math.atan2(uv[1] - 300, uv[0] - 400) - math.atan2(x[1], x[0])) < 1e-9
+
+
+def test_theta_max_is_first_root_of_derivative(orc):
+    assert abs(orc.theta_max([0, 0, 0, 0]) - math.pi / 2) < 1e-15
+    # strongly negative distortion: d theta_d / d theta turns over before pi/2
+    k = [-0.05, -0.04, 0.03, -0.05]
+    tm = orc.theta_max(k)
+    # roots of 1 + 3 k1 u + 5 k2 u^2 + 7 k3 u^3 + 9 k4 u^4 in u = theta^2 (numpy.roots)
+    r = np.roots([9 * k[3], 7 * k[2], 5 * k[1], 3 * k[0], 1.0])
+    u = min(v.real for v in r if abs(v.imag) < 1e-12 and v.real > 0)
+    assert tm < math.pi / 2
+    assert abs(tm - math.sqrt(u)) < 1e-12
+
+
+@pytest.mark.parametrize("model,rs", [("pinhole", 0), ("fisheye", 0), ("pinhole", 1), ("fisheye", 1)])
+def test_pixel_ray_passes_through_projected_point(orc, model, rs):
+    """Inverse consistency of g: the pixel ray at g(x) passes through x, including under a
+    rolling shutter once the row-time fixed point has converged."""
+    rng = np.random.default_rng(7)
+    qe, te = synth.rs_end_pose(0.05, 2.0)
+    k = [0.02, -0.01, 0.003, -0.0005] if model == "fisheye" else [0, 0, 0, 0]
+    cam = synth.camera(model, 640, 480, fx=300.0 if model == "pinhole" else None, k=k, q_end=qe, t_end=te,
+                       rolling_shutter=rs)
+    for _ in range(20):
+        x = np.array([rng.uniform(-1, 1), rng.uniform(-0.7, 0.7), rng.uniform(2, 4)])
+        ok, uv, t = orc.project_point(cam, x, rs_iters=80)
+        assert ok
+        ok2, o, d = orc.pixel_ray(cam, uv[0], uv[1])
+        assert ok2
+        dn = d / np.linalg.norm(d)
+        v = x - o
+        dist = np.linalg.norm(v - (v @ dn) * dn)
+        assert dist < 1e-9, dist
+        assert v @ dn > 0
+
+
+def test_rolling_shutter_with_static_pose_equals_global(orc):
+    cam = synth.camera("fisheye", 640, 480, k=[0.01, 0, 0, 0])
+    cam_rs = dict(cam, rolling_shutter=1)
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        x = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(2, 4)])
+        a = orc.project_point(cam, x)
+        b = orc.project_point(cam_rs, x)
+        assert a[0] and b[0]
+        assert np.array_equal(a[1], b[1])
+
+
+def test_rolling_shutter_fixed_point_converges_to_row_time(orc):
+    """With many updates the sigma-point time equals the time of the row it lands on."""
+    qe, te = synth.rs_end_pose(0.05, 2.0)
+    cam = synth.camera("fisheye", 1920, 1080, q_end=qe, t_end=te, rolling_shutter=1)
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        x = np.array([rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(2, 4)])
+        ok, uv, t = orc.project_point(cam, x, rs_iters=60)
+        assert ok
+        assert abs(t - np.clip((uv[1] - 0.5) / 1079, 0, 1)) < 1e-12
+
+
+# ------------------------------------------------------------------ spherical harmonics
+
+def test_sh_orthonormal(orc):
+    """Orthonormality of the degree-3 real basis by Gauss-Legendre x uniform quadrature."""
+    z, wz = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    G = np.zeros((16, 16))
+    for zi, wi in zip(z, wz):
+        r = math.sqrt(1 - zi * zi)
+        for p in phi:
+            Y = orc.sh_basis(3, [r * math.cos(p), r * math.sin(p), zi])
+            G += wi * (2 * np.pi / nphi) * np.outer(Y, Y)
+    assert np.allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_matches_scipy(orc):
+    """Real basis with the Condon-Shortley phase: Y_l0 = Re Y_l^0, Y_lm = sqrt2 Re Y_l^m and
+    Y_l,-m = sqrt2 Im Y_l^m (m > 0), against scipy's complex spherical harmonics."""
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        Y = orc.sh_basis(3, d)
+        for l in range(4):
+            for m in range(0, l + 1):
+                if hasattr(sp, "sph_harm_y"):
+                    c = sp.sph_harm_y(l, m, theta, phi)
+                else:
+                    c = sp.sph_harm(m, l, phi, theta)
+                if m == 0:
+                    assert abs(Y[l * l + l] - c.real) < 1e-12
+                else:
+                    assert abs(Y[l * l + l + m] - math.sqrt(2) * c.real) < 1e-12
+                    assert abs(Y[l * l + l - m] - math.sqrt(2) * c.imag) < 1e-12
+
+
+# ------------------------------------------------------------------ particle response
+
+def _single_alpha(orc, mu, log_s, q, logit, cam, px, py, opts=None):
+    sc = one_scene(mu, log_s, q, logit, [[0.5 * 2 * math.sqrt(math.pi)] * 3])
+    proj = dict(rect=np.array([[0, 0, cam["width"] - 1, cam["height"] - 1]], np.int32),
+                depth32=np.array([1.0], np.float32))
+    out = orc.render(sc, cam, opts or synth.options(alpha_min=1e-300, t_min=0.0), proj=proj,
+                     pixels=([px], [py]), no_rect=True)
+    return out["alpha"][0]
+
+
+def test_max_response_along_ray_matches_dense_scan(orc):
+    """alpha / sigma equals max over tau of rho(o + tau d) (eq. GaussianMaxResponse), checked
+    by a dense 1-D scan of eq. gaussian_kernel with Sigma^-1 built explicitly."""
+    rng = np.random.default_rng(21)
+    cam = synth.camera("pinhole", 32, 32, fx=30.0, fy=30.0)
+    for _ in range(8):
+        mu = np.array([rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), rng.uniform(2, 3)]).astype(np.float32)
+        ls = rng.normal(-2.0, 0.3, 3).astype(np.float32)
+        q = rng.standard_normal(4).astype(np.float32)
+        logit = np.float32(0.3)
+        px, py = int(rng.integers(8, 24)), int(rng.integers(8, 24))
+        a = _single_alpha(orc, mu, ls, q, logit, cam, px, py)
+        sigma = 1 / (1 + math.exp(-float(logit)))
+        R = rot(q.astype(float))
+        Sinv = R @ np.diag(np.exp(-2 * ls.astype(float))) @ R.T
+        d = np.array([(px + 0.5 - 16) / 30, (py + 0.5 - 16) / 30, 1.0])
+        taus = np.linspace(0, 6, 200001)
+        X = taus[:, None] * d[None, :] - mu.astype(float)[None, :]
+        m2 = np.einsum("ni,ij,nj->n", X, Sinv, X)
+        j = int(np.argmin(m2))
+        # refine with the exact 1-D minimiser of the quadratic around the scan's best point
+        tau_w = (mu.astype(float) @ Sinv @ d) / (d @ Sinv @ d)  # world-space form of eq. GaussianMaxResponse
+        assert abs(tau_w - taus[j]) < 1e-4
+        Xs = tau_w * d - mu.astype(float)
+        rho = math.exp(-0.5 * Xs @ Sinv @ Xs)
+        assert abs(a - sigma * rho) < 1e-12 * max(1.0, sigma * rho) + 1e-15
+        assert sigma * math.exp(-0.5 * m2[j]) <= sigma * rho + 1e-15
+
+
+def test_isotropic_response_closed_form(orc):
+    """Isotropic Gaussian: omega = distance from mu to the ray / s."""
+    cam = synth.camera("pinhole", 32, 32, fx=30.0, fy=30.0)
+    mu = np.array([0.1, -0.05, 2.0], np.float32)
+    s = 0.125
+    ls = np.full(3, math.log(s), np.float32)
+    for (px, py) in [(16, 16), (18, 15), (20, 11)]:
+        a = _single_alpha(orc, mu, ls, [1, 0, 0, 0], 0.0, cam, px, py)
+        d = np.array([(px + 0.5 - 16) / 30, (py + 0.5 - 16) / 30, 1.0])
+        d /= np.linalg.norm(d)
+        m = mu.astype(float)
+        dist = np.linalg.norm(m - (m @ d) * d)
+        s_true = math.exp(float(ls[0]))
+        assert abs(a - 0.5 * math.exp(-0.5 * (dist / s_true) ** 2)) < 1e-12
+
+
+# ------------------------------------------------------------------ compositing
+
+def test_opaque_particle_gives_clamped_alpha(orc):
+    cam = synth.camera("pinhole", 8, 8, fx=8.0, fy=8.0)
+    c = np.array([0.2, 0.5, 0.9])
+    beta = (c - 0.5) * 2 * math.sqrt(math.pi)
+    sc = one_scene([0.0, 0.0, 2.0], [1.0, 1.0, 1.0], [1, 0, 0, 0], 12.0, [beta])
+    proj = dict(rect=np.array([[0, 0, 7, 7]], np.int32), depth32=np.array([2.0], np.float32))
+    out = orc.render(sc, cam, synth.options(), proj=proj, pixels=([3, 4], [3, 4]))
+    for q in range(2):
+        assert np.allclose(out["rgb"][q], 0.99 * np.float32(beta).astype(float) / (2 * math.sqrt(math.pi)) + 0.99 * 0.5,
+                           atol=1e-12)
+        assert abs(out["alpha"][q] - 0.99) < 1e-15
+
+
+def test_two_particles_quadrature_closed_form(orc):
+    """c = c1 a1 + c2 a2 (1 - a1) (eq. QuadratureVolumeRendering) for two particles in depth order,
+    with a1, a2 the single-particle alphas."""
+    cam = synth.camera("pinhole", 16, 16, fx=16.0, fy=16.0)
+    p1 = ([0.05, 0.0, 2.0], [-1.5, -1.8, -1.2], [0.9, 0.1, 0.2, -0.3], 0.4, [0.9, 0.1, 0.3])
+    p2 = ([-0.05, 0.02, 2.6], [-1.3, -1.4, -1.6], [0.2, 0.8, -0.1, 0.4], -0.2, [0.2, 0.7, 0.5])
+    cols = []
+    alphas = []
+    px, py = 8, 8
+    for mu, ls, q, lg, col in (p1, p2):
+        beta = (np.array(col) - 0.5) * 2 * math.sqrt(math.pi)
+        sc = one_scene(mu, ls, q, lg, [beta])
+        o = orc.render(sc, cam, synth.options(), pixels=([px], [py]), no_rect=True)
+        alphas.append(o["alpha"][0])
+        cols.append(np.float32(beta).astype(float) / (2 * math.sqrt(math.pi)) + 0.5)
+    sc2 = {k: (np.concatenate([one_scene(*p1[:4], [(np.array(p1[4]) - .5) * 2 * math.sqrt(math.pi)])[k],
+                               one_scene(*p2[:4], [(np.array(p2[4]) - .5) * 2 * math.sqrt(math.pi)])[k]])
+               if k != "sh_degree" else 0) for k in ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                                      "sh_degree")}
+    o = orc.render(sc2, cam, synth.options(), pixels=([px], [py]), no_rect=True)
+    a1, a2 = alphas
+    assert 1 / 255 < a1 < 0.99 and 1 / 255 < a2 < 0.99
+    exp = cols[0] * a1 + cols[1] * a2 * (1 - a1)
+    assert np.allclose(o["rgb"][0], exp, atol=1e-12)
+    assert abs(o["alpha"][0] - (1 - (1 - a1) * (1 - a2))) < 1e-12
+
+
+def test_transmittance_monotone_and_alpha_bounded(orc):
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    proj = orc.project(sc, cam, op)
+    out = orc.render(sc, cam, op, proj=proj)
+    assert np.all(out["alpha"] >= 0) and np.all(out["alpha"] <= 1)
+    assert np.all(out["tfinal"] >= 0) and np.all(out["tfinal"] <= 1)
+    assert np.all(out["tfinal"][out["nblend"] > 0] >= op["t_min"])
+    # along one pixel's ordered list, the transmittance of every prefix is non-increasing
+    keys, vals, ranges = orc.bin_keys(proj["depth32"], proj["rect"], 64, 64)
+    t = 2 * 4 + 1
+    lst = vals[ranges[t, 0]:ranges[t, 1]]
+    px, py = 16 + 5, 32 + 7
+    prev = 1.0
+    for j in range(0, len(lst) + 1, max(1, len(lst) // 20)):
+        _, tf = orc.render_list(sc, cam, op, proj["rect"], proj["depth32"], px, py, lst[:j])
+        assert tf <= prev + 1e-15 and 0 <= tf <= 1
+        prev = tf
+
+
+# ------------------------------------------------------------------ tiling == brute force
+
+def test_tile_lists_reproduce_brute_force(orc):
+    """Compositing each pixel over its tile's sorted list gives bit-identical results to the
+    brute-force render over all particles in global order (pixel predicate = centre in rect)."""
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    proj = orc.project(sc, cam, op)
+    ref = orc.render(sc, cam, op, proj=proj)
+    for tw, th in ((16, 16), (8, 8), (32, 8), (13, 7)):
+        keys, vals, ranges = orc.bin_keys(proj["depth32"], proj["rect"], 64, 64, tw, th)
+        txn = (64 + tw - 1) // tw
+        for (px, py) in [(0, 0), (17, 33), (40, 12), (63, 63), (31, 31), (5, 60)]:
+            t = (py // th) * txn + px // tw
+            lst = vals[ranges[t, 0]:ranges[t, 1]]
+            rgb, tf = orc.render_list(sc, cam, op, proj["rect"], proj["depth32"], px, py, lst)
+            q = py * 64 + px
+            assert np.array_equal(rgb, ref["rgb"][q]) and tf == ref["tfinal"][q]
+
+
+def test_rect_culling_lossless_for_orthographic_camera(orc):
+    """Orthographic camera: the UT is exact and the 2D Mahalanobis distance of a pixel equals the
+    canonical distance omega along its ray, so with the extent cap lifted the opacity-tightened
+    rectangle drops only particles with alpha < alpha_min: culled == unculled brute force."""
+    sc = synth.scene_cube(300, 12, log_s=(-2.5, 0.4), deg=1, lo=(-1, -1, 1), hi=(1, 1, 3))
+    cam = synth.camera("ortho", 48, 40, fx=20.0, fy=20.0, cx=24.0, cy=20.0)
+    op = synth.options(extent_sigma=10.0, t_min=0.0)
+    proj = orc.project(sc, cam, op)
+    a = orc.render(sc, cam, op, proj=proj)
+    b = orc.render(sc, cam, op, proj=proj, no_rect=True)
+    assert np.max(np.abs(a["rgb"] - b["rgb"])) < 1e-12
+    assert np.max(np.abs(a["alpha"] - b["alpha"])) < 1e-12
+    # and with the default 3-sigma cap the loss is visible but small
+    op3 = synth.options(t_min=0.0)
+    c = orc.render(sc, cam, op3, proj=orc.project(sc, cam, op3))
+    assert np.max(np.abs(c["rgb"] - b["rgb"])) < 0.05
+
+
+# ------------------------------------------------------------------ integer stage
+
+def _brute_bin(depth32, rect, W, H, tw, th):
+    txn = (W + tw - 1) // tw
+    items = []
+    for i in range(len(rect)):
+        x0, y0, x1, y1 = (int(v) for v in rect[i])
+        if x0 > x1 or y0 > y1:
+            continue
+        for ty in range(y0 // th, y1 // th + 1):
+            for tx in range(x0 // tw, x1 // tw + 1):
+                key = ((ty * txn + tx) << 32) | int(np.float32(depth32[i]).view(np.uint32))
+                items.append((key, len(items), i))
+    items.sort()
+    T = txn * ((H + th - 1) // th)
+    ranges = np.zeros((T, 2), np.uint32)
+    for j, (k, _, _) in enumerate(items):
+        t = k >> 32
+        if j == 0 or (items[j - 1][0] >> 32) != t:
+            ranges[t, 0] = j
+        ranges[t, 1] = j + 1
+    return (np.array([k for k, _, _ in items], np.uint64), np.array([i for _, _, i in items], np.uint32), ranges)
+
+
+@pytest.mark.parametrize("W,H,tw,th", [(64, 48, 16, 16), (70, 33, 16, 16), (37, 29, 8, 4), (100, 10, 32, 8)])
+def test_bin_matches_brute_force(orc, W, H, tw, th):
+    rect, depth = synth.random_rects(3, 200, W, H, max_w=30, max_h=20)
+    k1, v1, r1 = orc.bin_keys(depth, rect, W, H, tw, th)
+    k2, v2, r2 = _brute_bin(depth, rect, W, H, tw, th)
+    assert np.array_equal(k1, k2) and np.array_equal(v1, v2) and np.array_equal(r1, r2)
+
+
+def test_bin_edge_cases(orc):
+    # empty input, all culled
+    k, v, r = orc.bin_keys(np.zeros(0, np.float32), np.zeros((0, 4), np.int32), 32, 32)
+    assert len(k) == 0 and not r.any()
+    rect = np.array([[0, 0, -1, -1]] * 5, np.int32)
+    k, v, r = orc.bin_keys(np.ones(5, np.float32), rect, 32, 32)
+    assert len(k) == 0 and not r.any()
+
+
+# ------------------------------------------------------------------ gradients
+
+def _fd_scene(n=12, deg=1, seed=31):
+    sc = synth.scene_cube(n, seed, log_s=(-2.2, 0.3), deg=deg, lo=(-0.4, -0.4, 2.0), hi=(0.4, 0.4, 3.0))
+    # exact FP32 perturbations: every base value is a multiple of 2^-12 well inside float32 range
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        sc[k] = (np.round(sc[k].astype(np.float64) * 4096) / 4096).astype(np.float32)
+    return sc
+
+
+def _loss(orc, sc, cam, op, proj, pix, g_rgb, g_a):
+    o = orc.render(sc, cam, op, proj=proj, pixels=pix)
+    return float(np.sum(o["rgb"] * g_rgb) + np.sum(o["alpha"] * g_a))
+
+
+def test_gradients_match_central_differences(orc):
+    """FP64 analytic gradients vs Richardson-extrapolated central differences (steps 2^-9, 2^-10,
+    exact in FP32) with the culling decisions held fixed (they carry no gradient, Sec. 4.1)."""
+    sc = _fd_scene()
+    cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
+    op = synth.options(t_min=1e-4)
+    proj = orc.project(sc, cam, op)
+    yy, xx = np.mgrid[0:20, 0:24]
+    px, py = xx.reshape(-1), yy.reshape(-1)
+    fl = orc.render(sc, cam, op, proj=proj, tol=dict(eps_rel=0.1, eps_px=0.0), pixels=(px, py))["flags"]
+    keep = (fl & (orc.F_ALPHA_MIN | orc.F_TSTOP | orc.F_ALPHA_MAX)) == 0
+    rng = np.random.default_rng(0)
+    g_rgb = rng.standard_normal((len(px), 3)) * keep[:, None]
+    g_a = rng.standard_normal(len(px)) * keep
+    pix = (px, py)
+    gr = orc.backward(sc, cam, op, proj, pix, g_rgb, g_a)
+    checked = 0
+    for name, arr in (("means", "means"), ("log_scales", "log_scales"), ("quats", "quats"),
+                      ("opacity_logits", "opacity_logits"), ("sh", "sh")):
+        base = sc[arr]
+        flat = base.reshape(-1)
+        ga = gr[name].reshape(-1)
+        for j in range(flat.size):
+            def f(h):
+                s2 = dict(sc)
+                b2 = base.copy().reshape(-1)
+                b2[j] = np.float32(float(flat[j]) + h)
+                assert float(b2[j]) == float(flat[j]) + h
+                s2[arr] = b2.reshape(base.shape)
+                return _loss(orc, s2, cam, op, proj, pix, g_rgb, g_a)
+            h = 2.0**-9
+            d1 = (f(h) - f(-h)) / (2 * h)
+            d2 = (f(h / 2) - f(-h / 2)) / h
+            fd = (4 * d2 - d1) / 3
+            assert abs(fd - ga[j]) <= 1e-6 * max(1.0, abs(ga[j])) + 1e-7, (name, j, fd, ga[j])
+            checked += 1
+    assert checked > 200
+
+
+def test_dalpha_dmu_matches_printed_chain(orc):
+    """d alpha / d mu = (-1/2 sigma e^{-omega^2/2}) (2 o_g + 2 tau d_g)^T (-S^-1 R^T), the chain the
+    supplementary prints (Sec. B), for one particle and one pixel with loss = alpha."""
+    cam = synth.camera("pinhole", 16, 16, fx=16.0, fy=16.0)
+    mu = np.array([0.03, -0.02, 2.0], np.float32)
+    ls = np.array([-1.6, -1.9, -1.3], np.float32)
+    q = np.array([0.8, 0.2, -0.3, 0.4], np.float32)
+    logit = np.float32(0.7)
+    sc = one_scene(mu, ls, q, logit, [[0.1, 0.2, 0.3]])
+    proj = dict(rect=np.array([[0, 0, 15, 15]], np.int32), depth32=np.array([2.0], np.float32))
+    px, py = 9, 7
+    gr = orc.backward(sc, cam, synth.options(t_min=0.0), proj, ([px], [py]), np.zeros((1, 3)), np.ones(1))
+    R = rot(q.astype(float))
+    S_inv = np.diag(np.exp(-ls.astype(float)))
+    M = S_inv @ R.T
+    o = np.zeros(3)
+    d = np.array([(px + 0.5 - 8) / 16, (py + 0.5 - 8) / 16, 1.0])
+    og = M @ (o - mu.astype(float))
+    dg = M @ d
+    dgn = dg / np.linalg.norm(dg)
+    tau_g = -og @ dgn
+    w2 = np.sum((og + tau_g * dgn) ** 2)
+    sigma = 1 / (1 + math.exp(-float(logit)))
+    dalpha_dw2 = -0.5 * sigma * math.exp(-0.5 * w2)
+    dw2_dog = 2 * og + 2 * tau_g * dgn
+    dog_dmu = -M
+    expect = dalpha_dw2 * dw2_dog @ dog_dmu
+    assert np.allclose(gr["means"][0], expect, rtol=1e-12, atol=1e-14)
