@@ -1,0 +1,358 @@
+"""Benchmark of the 3DGUT hot path on GB300 (one JSON line on stdout).
+
+Workload (default): 1,000,000 Gaussians (box in front of the camera, log-scales N(-3, 0.5),
+SH degree 3), a 1920x1080 polynomial fisheye with a rolling shutter (0.05 units / 2 degrees
+over the frame), 16x16 tiles.  A step is one pass of the whole path: UT projection,
+binning + radix sort + ranges, compositing forward, and (fwd+bwd phase) the backward for a
+fixed seeded upstream gradient dL/drgb, dL/dalpha resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+value = forward Mpix/s over all ranks (each rank renders its own replica of the workload:
+weak scaling, no collective on the data path).  Extra keys: fwd_ms, fwd_bwd_ms_per_view,
+per-call times, roofline of the dominant kernel, the oracle's CPU baseline, clocks, e2e.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rs_fisheye_1m_1080p")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle's CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2412_12507_gb300 import synth
+    if name == "rs_fisheye_1m_1080p":
+        return synth.rs_fisheye(seed=2, n=1_000_000, width=1920, height=1080, deg=3)
+    if name == "fisheye_shell_100k_720p":
+        return synth.fisheye_shell(seed=1, n=100_000, width=1280, height=720)
+    if name == "pinhole_1k_64":
+        return synth.small_pinhole()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nme, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nme)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm: the oracle on host cores
+
+def oracle_frame_time(case, budget_s, seed=0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload: the projection of
+    all particles, then brute-force compositing of a seeded pixel sample sized to the budget.
+    Returns (seconds per full frame extrapolated from the sample, description, threads)."""
+    import oracle
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    W, H = cam["width"], cam["height"]
+    t0 = time.perf_counter()
+    proj = oracle.project(sc, cam, op)
+    t_proj = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    npx = 64
+    t_pix = None
+    while True:
+        q = rng.choice(W * H, size=npx, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(sc, cam, op, proj=proj, pixels=(q % W, q // W))
+        dt = time.perf_counter() - t0
+        t_pix = dt / npx
+        spent = t_proj + dt
+        if dt > 0.25 * budget_s or npx >= W * H or spent > budget_s:
+            break
+        npx = int(min(W * H, max(2 * npx, npx * 0.5 * budget_s / max(dt, 1e-3))))
+    frame = t_proj + t_pix * W * H
+    desc = (f"projection of all {len(sc['means'])} particles ({t_proj:.2f} s) + brute-force compositing of "
+            f"{npx} seeded pixels ({dt:.2f} s), extrapolated to {W}x{H}")
+    return frame, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    case = workload(args.workload)
+    W, H = case["camera"]["width"], case["camera"]["height"]
+    frames = []
+    desc, thr = "", 1
+    per = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup + args.steps):
+        f, desc, thr = oracle_frame_time(case, per)
+        frames.append(f)
+    frames = frames[args.warmup:]
+    ms = 1e3 * statistics.median(frames)
+    v = W * H / (ms / 1e3) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case["name"]},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": thr, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = "Mpix/s fwd & fwd+bwd ms/view, 1M Gaussians fisheye 1080p; serve p50/p99 ms"
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_12507_gb300 import abi, build, render
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    L = abi.lib()
+
+    case = workload(args.workload)
+    sc_np, cam, op = case["scene"], case["camera"], case["options"]
+    W, H = cam["width"], cam["height"]
+    P = W * H
+    scene = render.Scene.from_arrays(sc_np, dev)
+    r = render.Renderer(cam, op, capacity=1 << 20)
+    r.forward(scene)                       # sizes the key capacity (one sync, outside timing)
+    torch.cuda.synchronize()
+    K = r.binning.count()
+    r.capacity = int(K * 1.05) + 1024
+    r.binning = None
+    r.forward(scene)
+    rng = np.random.default_rng(77)
+    d_rgb = torch.as_tensor(rng.standard_normal((3, H, W)).astype(np.float32) / P).to(dev)
+    d_alpha = torch.as_tensor(rng.standard_normal((H, W)).astype(np.float32) / P).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        r.forward(scene, sync_check=False)
+
+    def fwd_bwd():
+        r.forward(scene, sync_check=False)
+        r.backward(scene, d_rgb, d_alpha)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps
+
+    # launches per step (host-side counter of the library)
+    c0 = L.ut_kernel_launch_count()
+    fwd()
+    launches_fwd = L.ut_kernel_launch_count() - c0
+    c0 = L.ut_kernel_launch_count()
+    fwd_bwd()
+    launches_fb = L.ut_kernel_launch_count() - c0
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    fwd_ms = timed(fwd, args.steps, max(3, args.warmup))
+    fb_ms = timed(fwd_bwd, args.steps, max(3, args.warmup))
+    clk = clocks.stop()
+    if K > r.binning.capacity or r.binning.count() != K:
+        raise SystemExit("key count changed during the timed region")
+
+    # per-call durations (events on the launching stream around each ABI call, eager steps)
+    calls = {"ut_project": [], "bin_and_sort": [], "composite_forward": [], "composite_backward": []}
+    for _ in range(max(3, args.steps // 2)):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        render.project(scene, cam, op, r.proj)
+        ev[1].record(stream)
+        render.bin_and_sort(r.proj, cam, op, r.capacity, ws=r.ws, out=r.binning)
+        ev[2].record(stream)
+        render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame)
+        ev[3].record(stream)
+        r.backward(scene, d_rgb, d_alpha)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        for j, k in enumerate(calls):
+            calls[k].append(ev[j].elapsed_time(ev[j + 1]))
+    call_ms = {k: statistics.median(v) for k, v in calls.items()}
+
+    # algorithmic work: evaluations / blends counted by the forward kernel itself
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, stats=stats)
+    torch.cuda.synchronize()
+    n_eval, n_blend = (int(v) for v in stats.cpu())
+    n = scene.n
+    hbm, sm_max, src = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    # per-evaluation / per-blend FP32 operation counts of the compositing arithmetic (see the design notes)
+    F_EVAL, F_BLEND_FWD, F_BLEND_BWD, F_PIX = 40, 110, 230, 120
+    work = {
+        "ut_project": ("hbm", 80.0 * n / 1e9, "GB"),
+        "bin_and_sort": ("hbm", (44.0 * K + 8.0 * n) / 1e9, "GB"),
+        "composite_forward": ("alu", (F_EVAL * n_eval + F_BLEND_FWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
+        "composite_backward": ("alu", (F_EVAL * n_eval + F_BLEND_BWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
+    }
+    kernels = {}
+    for k, (bound, amount, unit) in work.items():
+        sec = call_ms[k] / 1e3
+        ach = amount / sec
+        peak = hbm if bound == "hbm" else fp32_peak
+        kernels[k] = {"ms": call_ms[k], "bound": bound, "achieved": ach, "peak": peak,
+                      "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / peak}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": None,
+                "peak_source": (f"{src} HBM copy" if d["bound"] == "hbm" else
+                                f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz")}
+
+    # end to end through the public API with host buffers: pinned inputs copied in, image copied out
+    host = {k: torch.as_tensor(sc_np[k]).pin_memory() for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    out_host = torch.empty((4, H, W), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = out_host.numel() * out_host.element_size()
+
+    def e2e_step():
+        scene.means.copy_(host["means"].view_as(scene.means), non_blocking=True)
+        scene.log_scales.copy_(host["log_scales"].view_as(scene.log_scales), non_blocking=True)
+        scene.quats.copy_(host["quats"].view_as(scene.quats), non_blocking=True)
+        scene.opacity_logits.copy_(host["opacity_logits"].view_as(scene.opacity_logits), non_blocking=True)
+        scene.sh.copy_(host["sh"].view_as(scene.sh), non_blocking=True)
+        f = r.forward(scene, sync_check=False)
+        out_host[:3].copy_(f.rgb, non_blocking=True)
+        out_host[3].copy_(f.alpha, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, max(3, args.steps // 2), 2)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        f_s, desc, thr = oracle_frame_time(case, args.cpu_seconds)
+        cpu = {"value": P / f_s / 1e6, "unit": "Mpix/s", "cores": thr, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * P / (fwd_ms / 1e3) / 1e6, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": fwd_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": case["name"], "particles": n, "width": W, "height": H,
+                       "camera": "fisheye+rolling_shutter", "sh_degree": int(sc_np["sh_degree"]),
+                       "tile": f"{op['tile_w']}x{op['tile_h']}", "keys": K, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (236 MB scene + 2 x keys), no flush"},
+            "fwd_ms": fwd_ms, "fwd_bwd_ms_per_view": fb_ms, "fwd_bwd_mpix_s": world * P / (fb_ms / 1e3) / 1e6,
+            "kernels": kernels, "evaluations": n_eval, "blended": n_blend,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "e2e": {"value": world * P / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
+            "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ut3d.h — C ABI of the GB300-native 3DGUT hot path (one GPU, sm_103a).
+ *
+ * 3DGUT renders a set of 3D Gaussian particles by (1) estimating every particle's
+ * 2D footprint with the Unscented Transform through an arbitrary camera model
+ * (Sec. 4.1, Algorithms 1-2 of the supplementary), (2) duplicating and sorting
+ * (tile | depth) keys (Sec. 4.3; the Duplicate and Sort phases of Table 2), and
+ * (3) compositing each pixel front to back, evaluating every particle in 3D at the
+ * point of maximum response along the pixel ray (Sec. 4.2, eq. GaussianMaxResponse,
+ * eq. QuadratureVolumeRendering).  A hand-written backward (supplementary Sec. B)
+ * differentiates (3) with respect to all particle parameters.
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer to array data is a DEVICE pointer unless stated otherwise; the
+ *     caller owns all memory.  Structs (ut_scene, ut_camera, ...) are host structs
+ *     passed by host pointer and only read during the call.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream) and
+ *     return a ut_status.  Host-side validation failures return without launching
+ *     anything.  UT_ERR_CUDA reports a launch error seen by cudaGetLastError().
+ *     Nothing aborts and no C++ exception crosses the ABI.
+ *   - Nothing allocates device memory: scratch memory is passed in by the caller,
+ *     sized with the *_workspace_size() queries.
+ *   - Arrays are structure-of-arrays, FP32, row-major, with no padding:
+ *       means[n][3], log_scales[n][3] (s = exp), quats[n][4] (w,x,y,z; need not be
+ *       normalised), opacity_logits[n] (sigma = sigmoid), sh[n][(deg+1)^2][3]
+ *       (real spherical harmonics with the Condon-Shortley phase, index l*l+l+m,
+ *       colour = max(sum beta Y(d) + 1/2, 0) at the unit pixel-ray direction d).
+ *   - Cameras map world to camera as x_c = R x + t, +z forward, +y down; pixel
+ *     centres are at integer + 1/2.  Images are H rows of W pixels.
+ */
+#ifndef UT3D_H
+#define UT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ut_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  UT_OK = 0,
+  UT_ERR_INVALID_ARG = 1, /* a size, enum, pointer or camera field failed validation */
+  UT_ERR_CAPACITY = 2,    /* a caller buffer is too small (see bin_and_sort) */
+  UT_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+  UT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  UT_ERR_UNSUPPORTED = 5  /* a valid request this build does not implement */
+} ut_status;
+
+typedef enum { UT_CAM_PINHOLE = 0, UT_CAM_FISHEYE = 1 } ut_cam_model;
+
+/* Camera (the extrinsic W and intrinsic D of Algorithm 1).
+ *   pinhole: valid iff z > near_plane; (u,v) = (fx x/z + cx, fy y/z + cy).
+ *   fisheye (polynomial, Kannala-Brandt): theta = atan2(sqrt(x^2+y^2), z),
+ *     theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8),
+ *     (u,v) = (fx theta_d x/r + cx, fy theta_d y/r + cy), r = sqrt(x^2+y^2);
+ *     valid iff |x_c| > near_plane and theta <= theta_max, where theta_max is pi/2 or
+ *     the first zero of d theta_d / d theta on (0, pi/2].
+ *   rolling_shutter = 1: row v is exposed at time t = v / (H-1); the pose at t has the
+ *     translation lerped and the rotation slerped between (q_start, t_start) and
+ *     (q_end, t_end).  A projected point takes its time from a fixed point on its
+ *     own projected row (see ut_project).  rolling_shutter = 0 uses the start pose.
+ *   Limits: 1 <= width, height <= 32767 (rectangles are int16); rolling shutter needs
+ *   height >= 2; fx, fy > 0; near_plane > 0; quaternions non-zero; all finite. */
+typedef struct {
+  int32_t model;
+  int32_t width, height;
+  int32_t rolling_shutter;
+  float fx, fy, cx, cy;
+  float k[4];
+  float q_start[4], t_start[3];
+  float q_end[4], t_end[3];
+  float near_plane;
+} ut_camera;
+
+/* Unscented-Transform hyperparameters (eq. weights_1/2): lambda = alpha^2 (3 + kappa) - 3;
+ * the paper uses (alpha, beta, kappa) = (1, 2, 0).  Requires 3 + lambda > 0. */
+typedef struct {
+  float alpha, beta, kappa;
+} ut_params;
+
+/* The particles (Sec. 3): device pointers, n >= 0, 0 <= sh_degree <= 3. */
+typedef struct {
+  const float *means;
+  const float *log_scales;
+  const float *quats;
+  const float *opacity_logits;
+  const float *sh;
+  int32_t n, sh_degree;
+} ut_scene;
+
+/* Renderer knobs.  Defaults (ut_default_options): 16x16 tiles, t_min = 1e-4,
+ * alpha_min = 1/255, alpha_max = 0.99, rs_iters = 3, newton_iters = 12, extent_sigma = 3.
+ *   alpha = min(alpha_max, sigma rho); a particle with sigma rho < alpha_min is skipped;
+ *   compositing stops BEFORE blending a particle that would take T below t_min.
+ *   extent: half-widths k sqrt(Sigma'_xx), k sqrt(Sigma'_yy) with
+ *   k = min(extent_sigma, sqrt(2 ln(sigma / alpha_min))) ("use opacity to compute a
+ *   tighter 2D extent", Algorithm 1).  tile_w * tile_h must be 64..512 and a multiple of 32.
+ *   newton_iters bounds the fisheye ray inversion (safeguarded Newton). */
+typedef struct {
+  int32_t tile_w, tile_h;
+  float t_min, alpha_min, alpha_max;
+  int32_t rs_iters, newton_iters;
+  float extent_sigma;
+} ut_options;
+
+void ut_default_options(ut_options *opt);
+const char *ut_status_string(ut_status s);
+
+/* Number of CUDA kernels this library has launched in the calling process (all devices,
+ * all threads).  A measurement aid with no counterpart in the paper: benchmarks read it
+ * before and after a step to report how many of the library's kernels the step ran. */
+uint64_t ut_kernel_launch_count(void);
+
+/* UT projection of every particle (Algorithm 1 and Algorithm 2; eq. sigma_points,
+ * weights_1, weights_2, 2d_conic_1, 2d_conic_2).
+ *   Sigma points: mu, mu +- sqrt(3+lambda) s_k R[:,k] (the square root R S of
+ *   Sigma = R S S^T R^T).  Each is projected by the camera; under a rolling shutter
+ *   its time starts at 1/2 and is updated rs_iters times by
+ *   t <- clamp((v - 1/2)/(H-1), 0, 1), then projected once more at that time.
+ *   A particle is culled if any projection is invalid, if sigma < alpha_min, if a
+ *   parameter is not finite, or if its pixel rectangle is empty.
+ * Outputs (device, n entries each; written for every particle):
+ *   mean2d[n][2] = v_mu; cov2d[n][3] = (xx, xy, yy) of Sigma';
+ *   depth[n] = |x_c(mu)| at the mean's shutter time (0 when culled);
+ *   rect[n][4] int16 = (x0, y0, x1, y1) inclusive pixel indices whose centres lie in
+ *   [v - h, v + h], clipped to the image; culled => (0, 0, -1, -1);
+ *   ntiles[n] = number of tiles the rect overlaps (0 when culled).
+ * Errors: UT_ERR_INVALID_ARG for a bad scene / camera / params / options or a NULL
+ * output with n > 0. */
+ut_status ut_project(const ut_scene *scene, const ut_camera *cam, const ut_params *ut, const ut_options *opt,
+                     float *mean2d, float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles,
+                     ut_stream stream);
+
+/* Bytes of scratch memory bin_and_sort needs for n particles and a key capacity. */
+size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt);
+
+/* Duplicate and sort (Sec. 4.3; Table 2 "Duplicate" and "Sort").
+ *   For every particle with ntiles > 0, in increasing index order, and every tile its
+ *   rect overlaps in row-major order, one entry key = (tile << 32) | bits(depth),
+ *   val = particle index, where tile = ty * ceil(W / tile_w) + tx and bits() is the IEEE
+ *   bit pattern of the positive FP32 depth.  Entries are sorted stably by key, so equal
+ *   keys keep increasing particle index.  tile_ranges[t] = {start, end} of tile t's run
+ *   in the sorted list, {0, 0} for an empty tile.
+ * Inputs: depth, rect, ntiles as written by ut_project (n entries, device).
+ * Outputs (device): keys[key_capacity] (may be NULL: the keys are then not written),
+ *   vals[key_capacity], tile_ranges[2 * T], T = ceil(W/tile_w) * ceil(H/tile_h),
+ *   k_out = one device int64 receiving the number of entries K.
+ * Capacity: the call is asynchronous and cannot know K in advance.  If K > key_capacity
+ *   the kernels write K to *k_out, leave keys / vals untouched and set every range to
+ *   {0, 0}; the caller must check *k_out after the stream completes and retry with a
+ *   larger capacity.  key_capacity must be < 2^32.
+ * Workspace: workspace_bytes >= ut_bin_workspace_size(n, key_capacity, cam, opt),
+ *   256-byte aligned, contents need not be initialised. */
+ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                       const ut_camera *cam, const ut_options *opt, void *workspace, size_t workspace_bytes,
+                       int64_t key_capacity, uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges,
+                       int64_t *k_out, ut_stream stream);
+
+/* Front-to-back compositing (eq. QuadratureVolumeRendering) with the particle response
+ * evaluated in 3D at its maximum along the pixel ray (eq. GaussianMaxResponse):
+ *   o_g = S^-1 R^T (o - mu), d_g = S^-1 R^T d, omega^2 = |o_g x d_g|^2 / |d_g|^2,
+ *   alpha = min(alpha_max, sigma exp(-omega^2 / 2)).
+ * Pixel (x, y) considers, in tile order, only particles whose rect contains (x, y);
+ * rays: pinhole d_c = ((x+1/2-cx)/fx, (y+1/2-cy)/fy, 1); fisheye inverts theta_d by a
+ * safeguarded Newton iteration; pixels beyond theta_d(theta_max) are not imaged
+ * (rgb = 0, alpha = 0, t_final = 1).  Rolling shutter: row y uses the pose at y/(H-1).
+ * Inputs: scene, camera, options as for ut_project; rect from ut_project; vals and
+ *   tile_ranges from bin_and_sort (same camera and options).
+ * Outputs (device): rgb[3][H][W] (planar), alpha[H][W] = 1 - T_final,
+ *   t_final[H][W] = T_final, n_used[H][W] = one past the position in vals of the last
+ *   blended particle (0 if none; consumed by composite_backward).
+ * stats (device, nullable): if given, stats[0] += number of (pixel, particle) response
+ *   evaluations (pixel inside the rect, before the pixel stopped) and stats[1] += number
+ *   of blended particles; a measurement aid, NULL in normal use. */
+ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
+                            const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges, float *rgb,
+                            float *alpha, float *t_final, uint32_t *n_used, unsigned long long *stats,
+                            ut_stream stream);
+
+/* Bytes of scratch memory composite_backward needs for n particles. */
+size_t ut_backward_workspace_size(int32_t n);
+
+/* Gradient of a scalar loss L through composite_forward (supplementary Sec. B):
+ *   given dL/drgb[3][H][W] and dL/dalpha[H][W], writes dL/d(parameter) for every
+ *   particle: d_means[n][3], d_log_scales[n][3], d_quats[n][4], d_opacity_logits[n],
+ *   d_sh[n][(deg+1)^2][3] (overwritten, not accumulated).  The projection contributes no
+ *   gradient: rect, depth order and tile membership are piecewise constant (Sec. 4.1).
+ * Inputs: everything composite_forward was given plus its outputs rgb, t_final, n_used.
+ * Workspace: >= ut_backward_workspace_size(n) bytes, 256-byte aligned. */
+ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
+                             const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges,
+                             const float *rgb, const float *t_final, const uint32_t *n_used, const float *d_rgb,
+                             const float *d_alpha, void *workspace, size_t workspace_bytes, float *d_means,
+                             float *d_log_scales, float *d_quats, float *d_opacity_logits, float *d_sh,
+                             ut_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UT3D_H */

@@ -60,7 +60,7 @@ class Options(C.Structure):
 
 class Tol(C.Structure):
     _fields_ = [("eps_px", C.c_double), ("eps_rel", C.c_double), ("depth_ulps", C.c_int32),
-                ("cond_min", C.c_double)]
+                ("cond_min", C.c_double), ("eps_t", C.c_double)]
 
 
 def lib():
@@ -153,6 +153,7 @@ def make_tol(tol: dict | None = None) -> Tol:
     r.eps_rel = float(t.get("eps_rel", 1e-4))
     r.depth_ulps = int(t.get("depth_ulps", 4))
     r.cond_min = float(t.get("cond_min", 0.05))
+    r.eps_t = float(t.get("eps_t", 1e-3))
     return r
 
 

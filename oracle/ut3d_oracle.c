@@ -75,6 +75,7 @@ typedef struct {
   double eps_rel;  /* relative distance of alpha / transmittance / culling to a threshold */
   int32_t depth_ulps; /* depth keys closer than this many FP32 ulps may swap */
   double cond_min; /* fisheye: pixels where d theta_d / d theta is below this are ill-conditioned */
+  double eps_t;    /* relative distance of T (1 - alpha) to t_min */
 } orc_tol;
 
 /* pixel flag bits */
@@ -645,7 +646,7 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
     double alpha = a < op->alpha_max ? a : op->alpha_max;
     double Tn = T * (1.0 - alpha);
-    if (flags && fabs(Tn - op->t_min) < tol->eps_rel * op->t_min) *flags |= ORC_F_TSTOP;
+    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
     if (Tn < op->t_min) break;
     uint32_t bits = orc_f32_bits(x->depth32[i]);
     if (flags && have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) *flags |= ORC_F_DEPTH_TIE;
@@ -732,7 +733,7 @@ void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options
   for (int j = 0; j < nlist; ++j) x.order[j] = (int32_t)list[j];
   x.norder = nlist;
   double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
-  orc_tol tol = {0, 0, 0, 0};
+  orc_tol tol = {0, 0, 0, 0, 0};
   double o[3], d[3], Y[16];
   int valid;
   orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
@@ -770,7 +771,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   /* accumulators: dM (9), dmu (3), dsigma (1) */
   double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 13, sizeof(double));
   memset(d_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
-  orc_tol tol = {0, 0, 0, 0};
+  orc_tol tol = {0, 0, 0, 0, 0};
 #pragma omp parallel
   {
     orc_contrib *rec = (orc_contrib *)malloc(sizeof(orc_contrib) * (size_t)(x.norder > 0 ? x.norder : 1));

@@ -1,0 +1,308 @@
+// abi.cu — the extern "C" entry points declared in include/ut3d.h: host-side validation,
+// camera / UT-weight preparation in FP64, and kernel launches.
+#include <cmath>
+#include <cstring>
+
+#include "ut3d_device.cuh"
+#include "ut3d_internal.h"
+
+#include <atomic>
+
+namespace ut3d {
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+namespace {
+
+bool finite_all(const float *v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+double poly_theta_d(const double k[4], double th) {
+  double t2 = th * th;
+  return th * (1.0 + t2 * (k[0] + t2 * (k[1] + t2 * (k[2] + t2 * k[3]))));
+}
+
+// d theta_d / d theta as a polynomial in u = theta^2: 1 + 3 k1 u + 5 k2 u^2 + 7 k3 u^3 + 9 k4 u^4.
+double dpoly_u(const double k[4], double u) { return 1.0 + u * (3 * k[0] + u * (5 * k[1] + u * (7 * k[2] + u * 9 * k[3]))); }
+
+// Largest imaged angle of the polynomial fisheye: the first sign change of d theta_d / d theta
+// on (0, pi/2], located on a uniform grid in u = theta^2 and refined by bisection; pi/2 if none.
+double fisheye_theta_max(const double k[4]) {
+  const double umax = 0.25 * M_PI * M_PI;
+  const int steps = 4096;
+  double prev_u = 0.0;
+  for (int i = 1; i <= steps; ++i) {
+    double u = umax * i / steps;
+    if (dpoly_u(k, u) <= 0.0) {
+      double lo = prev_u, hi = u;
+      for (int it = 0; it < 100; ++it) {
+        double m = 0.5 * (lo + hi);
+        (dpoly_u(k, m) > 0.0 ? lo : hi) = m;
+      }
+      return std::sqrt(lo);
+    }
+    prev_u = u;
+  }
+  return 0.5 * M_PI;
+}
+
+void quat_rot(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+ut_status make_cam(const ut_camera *c, DevCam &d) {
+  if (!c) return UT_ERR_INVALID_ARG;
+  if (c->model != UT_CAM_PINHOLE && c->model != UT_CAM_FISHEYE) return UT_ERR_INVALID_ARG;
+  if (c->width < 1 || c->height < 1 || c->width > 32767 || c->height > 32767) return UT_ERR_INVALID_ARG;
+  if (c->rolling_shutter != 0 && c->rolling_shutter != 1) return UT_ERR_INVALID_ARG;
+  if (c->rolling_shutter && c->height < 2) return UT_ERR_INVALID_ARG;
+  const float sc[5] = {c->fx, c->fy, c->cx, c->cy, c->near_plane};
+  if (!finite_all(sc, 5) || !finite_all(c->k, 4) || !finite_all(c->q_start, 4) || !finite_all(c->t_start, 3) ||
+      !finite_all(c->q_end, 4) || !finite_all(c->t_end, 3))
+    return UT_ERR_INVALID_ARG;
+  if (!(c->fx > 0) || !(c->fy > 0) || !(c->near_plane > 0)) return UT_ERR_INVALID_ARG;
+  double q0[4], q1[4], n0 = 0, n1 = 0;
+  for (int i = 0; i < 4; ++i) {
+    q0[i] = c->q_start[i];
+    q1[i] = c->q_end[i];
+    n0 += q0[i] * q0[i];
+    n1 += q1[i] * q1[i];
+  }
+  if (!(n0 > 0) || (c->rolling_shutter && !(n1 > 0))) return UT_ERR_INVALID_ARG;
+  n0 = std::sqrt(n0);
+  for (int i = 0; i < 4; ++i) q0[i] /= n0;
+  std::memset(&d, 0, sizeof(d));
+  d.model = c->model;
+  d.W = c->width;
+  d.H = c->height;
+  d.rs = c->rolling_shutter;
+  d.fx = c->fx; d.fy = c->fy; d.cx = c->cx; d.cy = c->cy;
+  d.ifx = (float)(1.0 / c->fx);
+  d.ify = (float)(1.0 / c->fy);
+  d.k1 = c->k[0]; d.k2 = c->k[1]; d.k3 = c->k[2]; d.k4 = c->k[3];
+  double R0[9];
+  quat_rot(q0, R0);
+  for (int i = 0; i < 9; ++i) d.R0[i] = (float)R0[i];
+  for (int i = 0; i < 3; ++i) d.T0[i] = c->t_start[i];
+  for (int j = 0; j < 3; ++j) d.cen[j] = (float)-(R0[j] * c->t_start[0] + R0[3 + j] * c->t_start[1] + R0[6 + j] * c->t_start[2]);
+  d.ax[0] = 1.f;
+  if (c->rolling_shutter) {
+    n1 = std::sqrt(n1);
+    for (int i = 0; i < 4; ++i) q1[i] /= n1;
+    double dot = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2] + q0[3] * q1[3];
+    if (dot < 0)
+      for (int i = 0; i < 4; ++i) q1[i] = -q1[i];
+    // relative rotation q1 * conj(q0): R(t) = Rot(axis, t phi) R0 is the slerp of the two poses
+    double a1 = q1[0], b1 = q1[1], c1 = q1[2], d1 = q1[3];
+    double a2 = q0[0], b2 = -q0[1], c2 = -q0[2], d2 = -q0[3];
+    double rw = a1 * a2 - b1 * b2 - c1 * c2 - d1 * d2;
+    double rx = a1 * b2 + b1 * a2 + c1 * d2 - d1 * c2;
+    double ry = a1 * c2 - b1 * d2 + c1 * a2 + d1 * b2;
+    double rz = a1 * d2 + b1 * c2 - c1 * b2 + d1 * a2;
+    double s = std::sqrt(rx * rx + ry * ry + rz * rz);
+    if (s > 1e-15) {
+      d.phi = (float)(2.0 * std::atan2(s, rw));
+      d.ax[0] = (float)(rx / s);
+      d.ax[1] = (float)(ry / s);
+      d.ax[2] = (float)(rz / s);
+    }
+    for (int i = 0; i < 3; ++i) d.dT[i] = (float)((double)c->t_end[i] - (double)c->t_start[i]);
+    d.inv_hm1 = (float)(1.0 / (c->height - 1));
+  }
+  d.near_plane = c->near_plane;
+  if (c->model == UT_CAM_FISHEYE) {
+    double k[4] = {c->k[0], c->k[1], c->k[2], c->k[3]};
+    double tm = fisheye_theta_max(k);
+    d.theta_max = (float)tm;
+    d.rd_max = (float)poly_theta_d(k, tm);
+  } else {
+    d.theta_max = (float)(0.5 * M_PI);
+    d.rd_max = INFINITY;
+  }
+  return UT_OK;
+}
+
+ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
+  if (!o) return UT_ERR_INVALID_ARG;
+  int area = o->tile_w * o->tile_h;
+  if (o->tile_w < 1 || o->tile_h < 1 || o->tile_w > 512 || o->tile_h > 512 || area < 64 || area > 512 ||
+      area % 32 != 0)
+    return UT_ERR_INVALID_ARG;
+  const float f[4] = {o->t_min, o->alpha_min, o->alpha_max, o->extent_sigma};
+  if (!finite_all(f, 4)) return UT_ERR_INVALID_ARG;
+  if (!(o->t_min >= 0) || !(o->t_min < 1) || !(o->alpha_min > 0) || !(o->alpha_min < 1) || !(o->alpha_max > 0) ||
+      !(o->alpha_max < 1) || !(o->extent_sigma > 0))
+    return UT_ERR_INVALID_ARG;
+  if (o->rs_iters < 0 || o->rs_iters > 64 || o->newton_iters < 1 || o->newton_iters > 64) return UT_ERR_INVALID_ARG;
+  d.tile_w = o->tile_w;
+  d.tile_h = o->tile_h;
+  d.tiles_x = (c->width + o->tile_w - 1) / o->tile_w;
+  d.tiles_y = (c->height + o->tile_h - 1) / o->tile_h;
+  d.t_min = o->t_min;
+  d.alpha_min = o->alpha_min;
+  d.alpha_max = o->alpha_max;
+  d.extent_sigma = o->extent_sigma;
+  d.rs_iters = o->rs_iters;
+  d.newton_iters = o->newton_iters;
+  return UT_OK;
+}
+
+ut_status check_scene(const ut_scene *s, bool need_sh) {
+  if (!s || s->n < 0 || s->sh_degree < 0 || s->sh_degree > 3) return UT_ERR_INVALID_ARG;
+  if (s->n == 0) return UT_OK;
+  if (!s->means || !s->log_scales || !s->quats || !s->opacity_logits || (need_sh && !s->sh)) return UT_ERR_INVALID_ARG;
+  if (!aligned16(s->quats) || (reinterpret_cast<uintptr_t>(s->means) & 3) ||
+      (reinterpret_cast<uintptr_t>(s->log_scales) & 3))
+    return UT_ERR_INVALID_ARG;
+  return UT_OK;
+}
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+}  // namespace
+}  // namespace ut3d
+
+using namespace ut3d;
+
+extern "C" {
+
+void ut_default_options(ut_options *o) {
+  if (!o) return;
+  o->tile_w = 16;
+  o->tile_h = 16;
+  o->t_min = 1e-4f;
+  o->alpha_min = 1.f / 255.f;
+  o->alpha_max = 0.99f;
+  o->rs_iters = 3;
+  o->newton_iters = 12;
+  o->extent_sigma = 3.f;
+}
+
+uint64_t ut_kernel_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
+
+const char *ut_status_string(ut_status s) {
+  switch (s) {
+    case UT_OK: return "ok";
+    case UT_ERR_INVALID_ARG: return "invalid argument";
+    case UT_ERR_CAPACITY: return "capacity exceeded";
+    case UT_ERR_CUDA: return "CUDA error";
+    case UT_ERR_TIMEOUT: return "device wait timed out";
+    case UT_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+ut_status ut_project(const ut_scene *scene, const ut_camera *cam, const ut_params *ut, const ut_options *opt,
+                     float *mean2d, float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles,
+                     ut_stream stream) {
+  ut_status st = check_scene(scene, false);
+  if (st != UT_OK) return st;
+  DevCam dc;
+  if ((st = make_cam(cam, dc)) != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (!ut || !std::isfinite(ut->alpha) || !std::isfinite(ut->beta) || !std::isfinite(ut->kappa))
+    return UT_ERR_INVALID_ARG;
+  double a = ut->alpha, b = ut->beta, k = ut->kappa;
+  double lam = a * a * (3.0 + k) - 3.0;
+  if (!(3.0 + lam > 0)) return UT_ERR_INVALID_ARG;
+  UTWeights w;
+  w.gamma = (float)std::sqrt(3.0 + lam);
+  w.wm0 = (float)(lam / (3.0 + lam));
+  w.wi = (float)(1.0 / (2.0 * (3.0 + lam)));
+  w.wc0 = (float)(lam / (3.0 + lam) + (1.0 - a * a + b));
+  if (scene->n > 0 && (!mean2d || !cov2d || !depth || !rect || !ntiles || !aligned8(mean2d) || !aligned8(rect)))
+    return UT_ERR_INVALID_ARG;
+  return launch_project(scene->n, *scene, dc, dop, w, mean2d, cov2d, depth, rect, ntiles,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt) {
+  if (n < 0 || key_capacity < 0 || !cam || !opt || opt->tile_w < 1 || opt->tile_h < 1) return 0;
+  int tiles = ((cam->width + opt->tile_w - 1) / opt->tile_w) * ((cam->height + opt->tile_h - 1) / opt->tile_h);
+  return bin_workspace_bytes(n, key_capacity, tiles);
+}
+
+ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                       const ut_camera *cam, const ut_options *opt, void *workspace, size_t workspace_bytes,
+                       int64_t key_capacity, uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges,
+                       int64_t *k_out, ut_stream stream) {
+  DevCam dc;
+  ut_status st = make_cam(cam, dc);
+  if (st != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 32)) return UT_ERR_INVALID_ARG;
+  if (n > 0 && (!depth || !rect || !ntiles || !aligned8(rect))) return UT_ERR_INVALID_ARG;
+  if (!tile_ranges || !k_out || (key_capacity > 0 && !vals) || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
+  int tiles = dop.tiles_x * dop.tiles_y;
+  size_t need = bin_workspace_bytes(n, key_capacity, tiles);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return UT_ERR_INVALID_ARG;
+  return launch_bin(n, depth, rect, ntiles, dop, tiles, workspace, key_capacity, keys, vals, tile_ranges, k_out,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
+                            const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges, float *rgb,
+                            float *alpha, float *t_final, uint32_t *n_used, unsigned long long *stats,
+                            ut_stream stream) {
+  ut_status st = check_scene(scene, true);
+  if (st != UT_OK) return st;
+  DevCam dc;
+  if ((st = make_cam(cam, dc)) != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (!tile_ranges || !rgb || !alpha || !t_final || !n_used || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!rect || !aligned8(rect))) return UT_ERR_INVALID_ARG;
+  return launch_composite_fwd(*scene, dc, dop, rect, vals, tile_ranges, rgb, alpha, t_final, n_used, stats,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t ut_backward_workspace_size(int32_t n) { return n < 0 ? 0 : backward_workspace_bytes(n); }
+
+ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
+                             const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges,
+                             const float *rgb, const float *t_final, const uint32_t *n_used, const float *d_rgb,
+                             const float *d_alpha, void *workspace, size_t workspace_bytes, float *d_means,
+                             float *d_log_scales, float *d_quats, float *d_opacity_logits, float *d_sh,
+                             ut_stream stream) {
+  ut_status st = check_scene(scene, true);
+  if (st != UT_OK) return st;
+  DevCam dc;
+  if ((st = make_cam(cam, dc)) != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (!tile_ranges || !rgb || !t_final || !n_used || !d_rgb || !d_alpha || !aligned8(tile_ranges))
+    return UT_ERR_INVALID_ARG;
+  if (scene->n > 0 && (!rect || !aligned8(rect) || !d_means || !d_log_scales || !d_quats || !d_opacity_logits ||
+                       !d_sh))
+    return UT_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < backward_workspace_bytes(scene->n) ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return UT_ERR_INVALID_ARG;
+  return launch_composite_bwd(*scene, dc, dop, rect, vals, tile_ranges, rgb, t_final, n_used, d_rgb, d_alpha,
+                              workspace, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,501 @@
+// composite.cu — tile-based front-to-back compositing with 3D particle evaluation
+// (Sec. 4.2, eq. GaussianMaxResponse; eq. QuadratureVolumeRendering) and its
+// hand-written backward (supplementary Sec. B).
+//
+// One thread block per image tile, one thread per pixel.  The tile's depth-sorted
+// particle list is consumed in batches of kBatch particles: the block gathers each
+// batch's parameters once, activates them (M = S^-1 R^T, sigma, the alpha_min test
+// threshold, packed rect) into shared memory together with their SH coefficients, and
+// every pixel then walks the batch from shared memory.  The block leaves the list as
+// soon as every pixel's transmittance has dropped below t_min.
+//
+// The backward replays the forward IN FORWARD ORDER: the stored rgb and T_final give the
+// suffix sums S_i = C - sum_{j<=i} c_j alpha_j T_j without dividing transmittances,
+// and n_used tells each pixel where the forward stopped.  Per (particle, warp) the 61
+// gradient partials are reduced with a transposing reduce-scatter (31 shuffles per 32
+// values), accumulated across warps in shared memory, and pushed to global memory with
+// one atomic per value per (tile, particle).  A final per-particle kernel maps the
+// accumulated dL/dM, dL/dmu, dL/dsigma onto log-scales, quaternions and logits.
+#include "ut3d_device.cuh"
+#include "ut3d_internal.h"
+
+namespace ut3d {
+namespace {
+
+constexpr int kBatch = 64;
+
+struct SceneArgs {
+  const float *means, *log_scales;
+  const float4 *quats;
+  const float *logits, *sh;
+};
+
+// Staged particle record (4 x float4):
+//   g0 = M00 M01 M02 M10   g1 = M11 M12 M20 M21   g2 = M22 a.x a.y a.z
+//   g3 = sigma, thr = 2 ln(sigma / alpha_min), rect (x0 | y0 << 16), rect (x1 | y1 << 16)
+// where a = M (o - mu) for a global shutter (o fixed) and a = M mu under a rolling shutter.
+template <bool RS>
+__device__ __forceinline__ void stage_particle(const SceneArgs &sc, const DevCam &cam, const DevOpts &op,
+                                               const short4 *rect, uint32_t idx, float4 *g, float4 *aux) {
+  float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
+  float3 ls = make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
+  Particle p;
+  activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
+  short4 r = rect[idx];
+  float3 a;
+  float3 om = make_float3(cam.cen[0] - mu.x, cam.cen[1] - mu.y, cam.cen[2] - mu.z);
+  if (RS) a = mat3_mul(p.M, mu);
+  else a = mat3_mul(p.M, om);
+  float thr = 2.f * logf(p.sigma / op.alpha_min);
+  g[0] = make_float4(p.M[0], p.M[1], p.M[2], p.M[3]);
+  g[1] = make_float4(p.M[4], p.M[5], p.M[6], p.M[7]);
+  g[2] = make_float4(p.M[8], a.x, a.y, a.z);
+  int r0 = ((int)(unsigned short)r.x) | ((int)r.y << 16);
+  int r1 = ((int)(unsigned short)r.z) | ((int)r.w << 16);
+  g[3] = make_float4(p.sigma, thr, __int_as_float(r0), __int_as_float(r1));
+  if (aux) *aux = RS ? make_float4(mu.x, mu.y, mu.z, 0.f) : make_float4(om.x, om.y, om.z, 0.f);
+}
+
+// Response of a staged particle for the ray (o, d) of pixel (px, py).  Returns false if the
+// pixel is outside the particle's rect or sigma rho < alpha_min (tested as
+// |o_g x d_g|^2 > thr |d_g|^2).  Otherwise returns a = sigma exp(-omega^2/2) and the
+// canonical-space ray (o_g, d_g) with |d_g|^2.
+template <bool RS>
+__device__ __forceinline__ bool eval_response(const float4 *g, int px, int py, float3 o, float3 d, float3 &og,
+                                              float3 &dg, float &dd, float &a) {
+  float4 g3 = g[3];
+  int r0 = __float_as_int(g3.z), r1 = __float_as_int(g3.w);
+  if (px < (r0 & 0xffff) || px > (r1 & 0xffff) || py < (r0 >> 16) || py > (r1 >> 16)) return false;
+  float4 g0 = g[0], g1 = g[1], g2 = g[2];
+  dg = make_float3(fmaf(g0.x, d.x, fmaf(g0.y, d.y, g0.z * d.z)), fmaf(g0.w, d.x, fmaf(g1.x, d.y, g1.y * d.z)),
+                   fmaf(g1.z, d.x, fmaf(g1.w, d.y, g2.x * d.z)));
+  if (RS) {
+    og = make_float3(fmaf(g0.x, o.x, fmaf(g0.y, o.y, g0.z * o.z)) - g2.y,
+                     fmaf(g0.w, o.x, fmaf(g1.x, o.y, g1.y * o.z)) - g2.z,
+                     fmaf(g1.z, o.x, fmaf(g1.w, o.y, g2.x * o.z)) - g2.w);
+  } else {
+    og = make_float3(g2.y, g2.z, g2.w);
+  }
+  float3 c = cross3(og, dg);
+  float cc = fmaf(c.x, c.x, fmaf(c.y, c.y, c.z * c.z));
+  dd = fmaf(dg.x, dg.x, fmaf(dg.y, dg.y, dg.z * dg.z));
+  if (!(cc <= g3.y * dd)) return false;
+  a = g3.x * __expf(-0.5f * __fdividef(cc, dd));
+  return true;
+}
+
+template <int DEG>
+__device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op, int px, int py, bool inside,
+                                            float3 &o, float3 &d, float *Y, bool &valid) {
+  valid = inside && pixel_ray(cam, px, py, op.newton_iters, o, d);
+  if (valid) {
+    float in = rsqrtf(dot3(d, d));
+    sh_basis<DEG>(d.x * in, d.y * in, d.z * in, Y);
+  } else {
+    o = d = make_float3(0.f, 0.f, 1.f);
+#pragma unroll
+    for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k) Y[k] = 0.f;
+  }
+}
+
+template <int DEG, bool RS, bool STATS>
+__global__ void __launch_bounds__(512) k_composite_fwd(DevCam cam, DevOpts op, SceneArgs sc,
+                                                       const short4 *__restrict__ rect,
+                                                       const uint32_t *__restrict__ vals,
+                                                       const uint2 *__restrict__ ranges, float *__restrict__ rgb,
+                                                       float *__restrict__ alpha_out, float *__restrict__ tfinal,
+                                                       uint32_t *__restrict__ n_used,
+                                                       unsigned long long *__restrict__ stats) {
+  constexpr int NSH = (DEG + 1) * (DEG + 1);
+  constexpr int NC = NSH * 3;
+  __shared__ float4 s_geo[kBatch][4];
+  __shared__ float s_sh[kBatch * NC];
+  __shared__ uint32_t s_idx[kBatch];
+
+  const int tile = blockIdx.x;
+  const int tx = tile % op.tiles_x, ty = tile / op.tiles_x;
+  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
+  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  const bool inside = px < cam.W && py < cam.H;
+  float3 o, d;
+  float Y[NSH];
+  bool valid;
+  pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  uint32_t last = 0;
+  unsigned long long n_eval = 0, n_blend = 0;
+  bool done = !valid;
+  const uint2 rg = ranges[tile];
+  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+    if (__syncthreads_count(!done) == 0) break;
+    const int nb = min((uint32_t)kBatch, rg.y - start);
+    if (threadIdx.x < nb) s_idx[threadIdx.x] = vals[start + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < nb) stage_particle<RS>(sc, cam, op, rect, s_idx[threadIdx.x], s_geo[threadIdx.x], nullptr);
+    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
+      int b = f / NC;
+      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+    }
+    __syncthreads();
+    if (done) continue;
+    for (int b = 0; b < nb; ++b) {
+      float3 og, dg;
+      float dd, a;
+      if (STATS) {
+        int r0 = __float_as_int(s_geo[b][3].z), r1 = __float_as_int(s_geo[b][3].w);
+        n_eval += !(px < (r0 & 0xffff) || px > (r1 & 0xffff) || py < (r0 >> 16) || py > (r1 >> 16));
+      }
+      if (!eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) continue;
+      float al = fminf(a, op.alpha_max);
+      float Tn = T * (1.f - al);
+      if (Tn < op.t_min) {
+        done = true;
+        break;
+      }
+      if (STATS) ++n_blend;
+      const float *shb = s_sh + b * NC;
+      float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
+#pragma unroll
+      for (int k = 0; k < NSH; ++k) {
+        r0 = fmaf(shb[3 * k], Y[k], r0);
+        r1 = fmaf(shb[3 * k + 1], Y[k], r1);
+        r2 = fmaf(shb[3 * k + 2], Y[k], r2);
+      }
+      float w = al * T;
+      C0 = fmaf(fmaxf(r0, 0.f), w, C0);
+      C1 = fmaf(fmaxf(r1, 0.f), w, C1);
+      C2 = fmaf(fmaxf(r2, 0.f), w, C2);
+      T = Tn;
+      last = start + b + 1;
+    }
+  }
+  if (inside) {
+    size_t pix = (size_t)py * cam.W + px;
+    size_t plane = (size_t)cam.W * cam.H;
+    rgb[pix] = C0;
+    rgb[plane + pix] = C1;
+    rgb[2 * plane + pix] = C2;
+    alpha_out[pix] = valid ? 1.f - T : 0.f;
+    tfinal[pix] = T;
+    n_used[pix] = last;
+  }
+  if (STATS) {
+    for (int o = 16; o >= 1; o >>= 1) {
+      n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
+      n_blend += __shfl_xor_sync(0xffffffffu, n_blend, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats[0], n_eval);
+      atomicAdd(&stats[1], n_blend);
+    }
+  }
+}
+
+// Sum over the 32 lanes of 32 per-lane values; afterwards lane l holds the total of value l.
+__device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16, L = 16; o >= 1; o >>= 1, L >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      float send = up ? v[j] : v[j + L];
+      float keep = up ? v[j + L] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
+// Gradient partial number j of one (pixel, particle) pair:
+//   0..2   v = 2 dL/domega^2 (o_g + tau d_g)             (-> dL/dmu = -M^T sum v)
+//   3..11  v_r x_c with x = o - mu + tau d              (dL/dM, row-major)
+//   12     dL/dsigma
+//   16 + 3k + ch   dL/dc_ch alpha T Y_k                 (dL/dbeta_k,ch)
+template <int NSH>
+__device__ __forceinline__ float grad_value(int j, const float *vv, const float *xx, float dsig, const float *wc,
+                                            const float *Y) {
+  if (j < 3) return vv[j];
+  if (j < 12) return vv[(j - 3) / 3] * xx[(j - 3) % 3];
+  if (j == 12) return dsig;
+  if (j < 16) return 0.f;
+  if (j < 16 + 3 * NSH) return wc[(j - 16) % 3] * Y[(j - 16) / 3];
+  return 0.f;
+}
+
+template <int DEG, bool RS>
+__global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, SceneArgs sc,
+                                                       const short4 *__restrict__ rect,
+                                                       const uint32_t *__restrict__ vals,
+                                                       const uint2 *__restrict__ ranges,
+                                                       const float *__restrict__ rgb,
+                                                       const float *__restrict__ tfinal,
+                                                       const uint32_t *__restrict__ n_used,
+                                                       const float *__restrict__ d_rgb,
+                                                       const float *__restrict__ d_alpha, float *__restrict__ gacc,
+                                                       float *__restrict__ d_sh) {
+  constexpr int NSH = (DEG + 1) * (DEG + 1);
+  constexpr int NC = NSH * 3;
+  constexpr int NV = 16 + NC;                 // used partials
+  constexpr int NCHUNK = (NV + 31) / 32;      // 32-value reduce chunks
+  __shared__ float4 s_geo[kBatch][4];
+  __shared__ float4 s_aux[kBatch];
+  __shared__ float s_sh[kBatch * NC];
+  __shared__ float s_acc[kBatch][NCHUNK * 32];
+  __shared__ uint32_t s_idx[kBatch];
+  __shared__ int s_any[kBatch];
+  __shared__ uint32_t s_end;
+
+  const int tile = blockIdx.x;
+  const int tx = tile % op.tiles_x, ty = tile / op.tiles_x;
+  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
+  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  const int lane = threadIdx.x & 31;
+  const bool inside = px < cam.W && py < cam.H;
+  float3 o, d;
+  float Y[NSH];
+  bool valid;
+  pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+
+  const uint2 rg = ranges[tile];
+  uint32_t my_end = 0;
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gA = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f;
+  if (valid) {
+    size_t pix = (size_t)py * cam.W + px;
+    size_t plane = (size_t)cam.W * cam.H;
+    my_end = n_used[pix];
+    g0 = d_rgb[pix]; g1 = d_rgb[plane + pix]; g2 = d_rgb[2 * plane + pix];
+    gA = d_alpha[pix];
+    Cf0 = rgb[pix]; Cf1 = rgb[plane + pix]; Cf2 = rgb[2 * plane + pix];
+    Tf = tfinal[pix];
+  }
+  if (threadIdx.x == 0) s_end = 0;
+  __syncthreads();
+  if (my_end > rg.x) atomicMax(&s_end, my_end);
+  __syncthreads();
+  const uint32_t block_end = min(s_end, rg.y);
+
+  float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;  // running prefix of the composited colour
+  for (uint32_t start = rg.x; start < block_end; start += kBatch) {
+    const int nb = min((uint32_t)kBatch, block_end - start);
+    __syncthreads();
+    if (threadIdx.x < nb) s_idx[threadIdx.x] = vals[start + threadIdx.x];
+    for (int f = threadIdx.x; f < kBatch * NCHUNK * 32; f += blockDim.x) (&s_acc[0][0])[f] = 0.f;
+    if (threadIdx.x < kBatch) s_any[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x < nb)
+      stage_particle<RS>(sc, cam, op, rect, s_idx[threadIdx.x], s_geo[threadIdx.x], &s_aux[threadIdx.x]);
+    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
+      int b = f / NC;
+      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+    }
+    __syncthreads();
+    for (int b = 0; b < nb; ++b) {
+      bool contrib = false;
+      float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
+      float3 og, dg;
+      float dd, a;
+      if (start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
+        contrib = true;
+        float al = fminf(a, op.alpha_max);
+        const float *shb = s_sh + b * NC;
+        float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k) {
+          r0 = fmaf(shb[3 * k], Y[k], r0);
+          r1 = fmaf(shb[3 * k + 1], Y[k], r1);
+          r2 = fmaf(shb[3 * k + 2], Y[k], r2);
+        }
+        float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
+        float w = al * T;
+        A0 = fmaf(c0, w, A0);
+        A1 = fmaf(c1, w, A1);
+        A2 = fmaf(c2, w, A2);
+        float inv = 1.f / (1.f - al);
+        // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
+        float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
+                    g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
+        wc[0] = r0 > 0.f ? g0 * w : 0.f;
+        wc[1] = r1 > 0.f ? g1 * w : 0.f;
+        wc[2] = r2 > 0.f ? g2 * w : 0.f;
+        T = T * (1.f - al);
+        float da = a > op.alpha_max ? 0.f : dal;
+        float sigma = s_geo[b][3].x;
+        dsig = da * a / sigma;
+        float dw2 = -0.5f * a * da;
+        float tau = -dot3(og, dg) / dd;
+        float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
+        vv[0] = 2.f * dw2 * pp.x;
+        vv[1] = 2.f * dw2 * pp.y;
+        vv[2] = 2.f * dw2 * pp.z;
+        float4 ax = s_aux[b];
+        if (RS) {
+          xx[0] = fmaf(tau, d.x, o.x - ax.x);
+          xx[1] = fmaf(tau, d.y, o.y - ax.y);
+          xx[2] = fmaf(tau, d.z, o.z - ax.z);
+        } else {
+          xx[0] = fmaf(tau, d.x, ax.x);
+          xx[1] = fmaf(tau, d.y, ax.y);
+          xx[2] = fmaf(tau, d.z, ax.z);
+        }
+      }
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+#pragma unroll
+      for (int ch = 0; ch < NCHUNK; ++ch) {
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = grad_value<NSH>(ch * 32 + j, vv, xx, dsig, wc, Y);
+        warp_reduce_scatter32(v, lane);
+        atomicAdd(&s_acc[b][ch * 32 + lane], v[0]);
+      }
+      if (lane == 0) s_any[b] = 1;
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < nb * NCHUNK * 32; f += blockDim.x) {
+      int b = f / (NCHUNK * 32), j = f - b * (NCHUNK * 32);
+      if (!s_any[b]) continue;
+      uint32_t idx = s_idx[b];
+      float v = s_acc[b][j];
+      if (j < 13) atomicAdd(&gacc[(size_t)idx * 16 + j], v);
+      else if (j >= 16 && j < NV) atomicAdd(&d_sh[(size_t)idx * NC + (j - 16)], v);
+    }
+  }
+}
+
+// d(rotation matrix)/d(unit quaternion) contracted with G = dL/dR (row-major).
+__device__ __forceinline__ void rot_grad(const float *q, const float *G, float *gq) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  gq[0] = 2.f * (x * (G[7] - G[5]) + y * (G[2] - G[6]) + z * (G[3] - G[1]));
+  gq[1] = 2.f * (-2.f * x * (G[4] + G[8]) + y * (G[1] + G[3]) + z * (G[2] + G[6]) + w * (G[7] - G[5]));
+  gq[2] = 2.f * (x * (G[1] + G[3]) - 2.f * y * (G[0] + G[8]) + z * (G[5] + G[7]) + w * (G[2] - G[6]));
+  gq[3] = 2.f * (x * (G[2] + G[6]) + y * (G[5] + G[7]) - 2.f * z * (G[0] + G[4]) + w * (G[3] - G[1]));
+}
+
+__global__ void k_finalize(int n, SceneArgs sc, const float *__restrict__ gacc, float *__restrict__ d_means,
+                           float *__restrict__ d_ls, float *__restrict__ d_q, float *__restrict__ d_logit) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float3 mu = make_float3(sc.means[3 * i], sc.means[3 * i + 1], sc.means[3 * i + 2]);
+    float3 ls = make_float3(sc.log_scales[3 * i], sc.log_scales[3 * i + 1], sc.log_scales[3 * i + 2]);
+    Particle p;
+    bool ok = activate(mu, ls, sc.quats[i], sc.logits[i], p);
+    const float *A = gacc + (size_t)i * 16;
+    float out_m[3] = {0.f, 0.f, 0.f}, out_s[3] = {0.f, 0.f, 0.f}, out_q[4] = {0.f, 0.f, 0.f, 0.f}, out_l = 0.f;
+    if (ok) {
+      float v0 = A[0], v1 = A[1], v2 = A[2];
+      for (int j = 0; j < 3; ++j) out_m[j] = -(p.M[j] * v0 + p.M[3 + j] * v1 + p.M[6 + j] * v2);
+      float G[9];
+      for (int k = 0; k < 3; ++k) {
+        float acc = 0.f;
+        for (int j = 0; j < 3; ++j) {
+          float dm = A[3 + 3 * k + j];
+          acc = fmaf(dm, p.M[3 * k + j], acc);
+          G[3 * j + k] = dm / p.s[k];
+        }
+        out_s[k] = -acc;
+      }
+      float gq[4];
+      rot_grad(p.q, G, gq);
+      float dot = gq[0] * p.q[0] + gq[1] * p.q[1] + gq[2] * p.q[2] + gq[3] * p.q[3];
+      for (int j = 0; j < 4; ++j) out_q[j] = (gq[j] - p.q[j] * dot) / p.qn;
+      out_l = A[12] * p.sigma * (1.f - p.sigma);
+    }
+    for (int j = 0; j < 3; ++j) {
+      d_means[3 * i + j] = out_m[j];
+      d_ls[3 * i + j] = out_s[j];
+    }
+    for (int j = 0; j < 4; ++j) d_q[4 * i + j] = out_q[j];
+    d_logit[i] = out_l;
+  }
+}
+
+template <int DEG, bool RS>
+void fwd_launch(int blocks, int threads, const DevCam &cam, const DevOpts &op, const SceneArgs &sc,
+                const int16_t *rect, const uint32_t *vals, const uint32_t *ranges, float *rgb, float *alpha,
+                float *tf, uint32_t *nu, unsigned long long *stats, cudaStream_t s) {
+  if (stats)
+    k_composite_fwd<DEG, RS, true><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect),
+                                                              vals, reinterpret_cast<const uint2 *>(ranges), rgb,
+                                                              alpha, tf, nu, stats);
+  else
+    k_composite_fwd<DEG, RS, false><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect),
+                                                               vals, reinterpret_cast<const uint2 *>(ranges), rgb,
+                                                               alpha, tf, nu, nullptr);
+}
+
+template <int DEG, bool RS>
+void bwd_launch(int blocks, int threads, const DevCam &cam, const DevOpts &op, const SceneArgs &sc,
+                const int16_t *rect, const uint32_t *vals, const uint32_t *ranges, const float *rgb,
+                const float *tf, const uint32_t *nu, const float *drgb, const float *dal, float *gacc, float *dsh,
+                cudaStream_t s) {
+  k_composite_bwd<DEG, RS><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect), vals,
+                                                      reinterpret_cast<const uint2 *>(ranges), rgb, tf, nu, drgb,
+                                                      dal, gacc, dsh);
+}
+
+SceneArgs scene_args(const ut_scene &sc) {
+  return SceneArgs{sc.means, sc.log_scales, reinterpret_cast<const float4 *>(sc.quats), sc.opacity_logits, sc.sh};
+}
+
+}  // namespace
+
+ut_status launch_composite_fwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
+                               const uint32_t *vals, const uint32_t *ranges, float *rgb, float *alpha,
+                               float *t_final, uint32_t *n_used, unsigned long long *stats, cudaStream_t s) {
+  int blocks = op.tiles_x * op.tiles_y;
+  int threads = op.tile_w * op.tile_h;
+  SceneArgs a = scene_args(sc);
+  const bool rs = cam.rs != 0;
+#define UT3D_FWD(D)                                                                                 \
+  (rs ? fwd_launch<D, true>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, alpha, t_final, n_used, stats, s) \
+      : fwd_launch<D, false>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, alpha, t_final, n_used, stats, s))
+  switch (sc.sh_degree) {
+    case 0: UT3D_FWD(0); break;
+    case 1: UT3D_FWD(1); break;
+    case 2: UT3D_FWD(2); break;
+    default: UT3D_FWD(3); break;
+  }
+#undef UT3D_FWD
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+}
+
+size_t backward_workspace_bytes(int n) { return align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1)); }
+
+ut_status launch_composite_bwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
+                               const uint32_t *vals, const uint32_t *ranges, const float *rgb, const float *t_final,
+                               const uint32_t *n_used, const float *d_rgb, const float *d_alpha, void *ws,
+                               float *d_means, float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
+                               cudaStream_t s) {
+  const int n = sc.n;
+  const int nc = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
+  float *gacc = static_cast<float *>(ws);
+  if (n > 0) {
+    if (cudaMemsetAsync(gacc, 0, sizeof(float) * 16 * (size_t)n, s) != cudaSuccess) return UT_ERR_CUDA;
+    if (cudaMemsetAsync(d_sh, 0, sizeof(float) * (size_t)nc * n, s) != cudaSuccess) return UT_ERR_CUDA;
+  }
+  int blocks = op.tiles_x * op.tiles_y;
+  int threads = op.tile_w * op.tile_h;
+  SceneArgs a = scene_args(sc);
+  const bool rs = cam.rs != 0;
+#define UT3D_BWD(D)                                                                                           \
+  (rs ? bwd_launch<D, true>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, t_final, n_used, d_rgb, d_alpha, \
+                            gacc, d_sh, s)                                                                    \
+      : bwd_launch<D, false>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, t_final, n_used, d_rgb,     \
+                             d_alpha, gacc, d_sh, s))
+  switch (sc.sh_degree) {
+    case 0: UT3D_BWD(0); break;
+    case 1: UT3D_BWD(1); break;
+    case 2: UT3D_BWD(2); break;
+    default: UT3D_BWD(3); break;
+  }
+#undef UT3D_BWD
+  count_launches(1);
+  if (n > 0) {
+    int g = (n + 255) / 256;
+    int cap = device_sm_count() * 8;
+    k_finalize<<<g < cap ? g : cap, 256, 0, s>>>(n, a, gacc, d_means, d_log_scales, d_quats, d_logits);
+    count_launches(1);
+  }
+  return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+}
+
+}  // namespace ut3d

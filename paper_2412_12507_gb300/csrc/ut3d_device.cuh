@@ -1,0 +1,239 @@
+// ut3d_device.cuh — device-side building blocks of the 3DGUT hot path (internal).
+//
+// Camera model g(x), pixel rays, particle activation and the real SH basis, all FP32.
+// Shared by the projection, compositing and backward kernels so that every kernel
+// takes the same decisions from the same arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ut3d.h"
+
+namespace ut3d {
+
+// Camera as the kernels see it: the host converts ut_camera once per call
+// (rotation matrices, rolling-shutter relative rotation, fisheye limits) in FP64.
+struct DevCam {
+  int model, W, H, rs;
+  float fx, fy, cx, cy, ifx, ify;
+  float k1, k2, k3, k4;
+  float R0[9];    // world->camera rotation at t = 0 (row-major)
+  float T0[3];    // translation at t = 0
+  float dT[3];    // t_end - t_start
+  float ax[3];    // axis of the rotation taking the start pose to the end pose
+  float phi;      // its angle (0 for a global shutter)
+  float near_plane;
+  float theta_max;  // fisheye: largest imaged angle
+  float rd_max;     // fisheye: theta_d(theta_max), the imaged radius in normalised units
+  float inv_hm1;    // 1 / (H - 1) (rolling shutter row -> time)
+  float cen[3];     // camera centre -R0^T T0 at t = 0 (the ray origin of a global shutter)
+};
+
+struct DevOpts {
+  int tile_w, tile_h, tiles_x, tiles_y;
+  float t_min, alpha_min, alpha_max, extent_sigma;
+  int rs_iters, newton_iters;
+};
+
+__device__ __forceinline__ float3 mat3_mul(const float *R, float3 v) {
+  return make_float3(fmaf(R[0], v.x, fmaf(R[1], v.y, R[2] * v.z)), fmaf(R[3], v.x, fmaf(R[4], v.y, R[5] * v.z)),
+                     fmaf(R[6], v.x, fmaf(R[7], v.y, R[8] * v.z)));
+}
+
+__device__ __forceinline__ float3 mat3_tmul(const float *R, float3 v) {  // R^T v
+  return make_float3(fmaf(R[0], v.x, fmaf(R[3], v.y, R[6] * v.z)), fmaf(R[1], v.x, fmaf(R[4], v.y, R[7] * v.z)),
+                     fmaf(R[2], v.x, fmaf(R[5], v.y, R[8] * v.z)));
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+
+// Rodrigues rotation of y by angle th about the unit axis a.
+__device__ __forceinline__ float3 rotate_axis(const float *a, float3 y, float th) {
+  float s, c;
+  sincosf(th, &s, &c);
+  float ad = a[0] * y.x + a[1] * y.y + a[2] * y.z;
+  float3 axy = make_float3(a[1] * y.z - a[2] * y.y, a[2] * y.x - a[0] * y.z, a[0] * y.y - a[1] * y.x);
+  float oc = (1.f - c) * ad;
+  return make_float3(fmaf(y.x, c, fmaf(axy.x, s, a[0] * oc)), fmaf(y.y, c, fmaf(axy.y, s, a[1] * oc)),
+                     fmaf(y.z, c, fmaf(axy.z, s, a[2] * oc)));
+}
+
+// x_c(t) for a point whose start-pose camera coordinates rotated part is y = R0 x.
+__device__ __forceinline__ float3 cam_point_at(const DevCam &c, float3 y, float t) {
+  float3 r = c.rs ? rotate_axis(c.ax, y, t * c.phi) : y;
+  return make_float3(r.x + fmaf(t, c.dT[0], c.T0[0]), r.y + fmaf(t, c.dT[1], c.T0[1]),
+                     r.z + fmaf(t, c.dT[2], c.T0[2]));
+}
+
+__device__ __forceinline__ float theta_d_poly(const DevCam &c, float th) {
+  float t2 = th * th;
+  return th * fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, c.k4, c.k3), c.k2), c.k1), 1.f);
+}
+
+__device__ __forceinline__ float theta_d_prime(const DevCam &c, float th) {
+  float t2 = th * th;
+  return fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 9.f * c.k4, 7.f * c.k3), 5.f * c.k2), 3.f * c.k1), 1.f);
+}
+
+// g(x_c): camera-space point to pixel coordinates; returns false when not imaged.
+__device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &uv) {
+  if (c.model == UT_CAM_PINHOLE) {
+    float iz = 1.f / p.z;
+    uv.x = fmaf(c.fx * p.x, iz, c.cx);
+    uv.y = fmaf(c.fy * p.y, iz, c.cy);
+    return p.z > c.near_plane;
+  }
+  float r2 = fmaf(p.x, p.x, p.y * p.y);
+  float rho = sqrtf(r2);
+  float r3 = sqrtf(fmaf(p.z, p.z, r2));
+  float th = atan2f(rho, p.z);
+  float s = rho > 0.f ? theta_d_poly(c, th) / rho : 1.f / p.z;
+  uv.x = fmaf(c.fx * s, p.x, c.cx);
+  uv.y = fmaf(c.fy * s, p.y, c.cy);
+  return (r3 > c.near_plane) && (th <= c.theta_max);
+}
+
+// Projection of a world point with the rolling-shutter time fixed point
+// (t = 1/2, rs_iters updates t <- clamp((v - 1/2)/(H-1)), final projection).
+// y = R0 x.  Returns validity of every projection taken; t_out = the final time.
+__device__ __forceinline__ bool project_world(const DevCam &c, int rs_iters, float3 y, float2 &uv, float &t_out) {
+  bool ok = true;
+  float t = 0.f;
+  if (c.rs) {
+    t = 0.5f;
+    for (int it = 0; it < rs_iters; ++it) {
+      ok &= cam_project(c, cam_point_at(c, y, t), uv);
+      t = fminf(fmaxf((uv.y - 0.5f) * c.inv_hm1, 0.f), 1.f);
+    }
+  }
+  ok &= cam_project(c, cam_point_at(c, y, t), uv);
+  t_out = t;
+  return ok;
+}
+
+// World ray of pixel (px, py) (integer indices; the ray goes through the pixel centre).
+// Returns false for a fisheye pixel outside the imaged disc.
+__device__ __forceinline__ bool pixel_ray(const DevCam &c, int px, int py, int newton_iters, float3 &o, float3 &d) {
+  float mx = (px + 0.5f - c.cx) * c.ifx;
+  float my = (py + 0.5f - c.cy) * c.ify;
+  float3 dc;
+  if (c.model == UT_CAM_PINHOLE) {
+    dc = make_float3(mx, my, 1.f);
+  } else {
+    float rd = sqrtf(fmaf(mx, mx, my * my));
+    if (!(rd <= c.rd_max)) return false;
+    // safeguarded Newton for theta_d(theta) = rd on the increasing branch [0, theta_max]
+    float lo = 0.f, hi = c.theta_max;
+    float th = fminf(rd, c.theta_max);
+    for (int it = 0; it < newton_iters; ++it) {
+      float f = theta_d_poly(c, th) - rd;
+      if (f > 0.f) hi = th; else lo = th;
+      float fp = theta_d_prime(c, th);
+      float nt = th - f / fp;
+      if (!(nt > lo && nt < hi)) nt = 0.5f * (lo + hi);
+      if (nt == th) break;
+      th = nt;
+    }
+    float s, co;
+    sincosf(th, &s, &co);
+    if (rd > 0.f) {
+      float k = s / rd;
+      dc = make_float3(k * mx, k * my, co);
+    } else {
+      dc = make_float3(0.f, 0.f, 1.f);
+    }
+  }
+  float t = c.rs ? py * c.inv_hm1 : 0.f;
+  // pose at the row time: R(t) = Rot(ax, t phi) R0, T(t) = T0 + t dT; camera centre o = -R^T T
+  float3 Tt = make_float3(fmaf(t, c.dT[0], c.T0[0]), fmaf(t, c.dT[1], c.T0[1]), fmaf(t, c.dT[2], c.T0[2]));
+  if (c.rs) {
+    // R(t)^T v = R0^T Rot(ax, -t phi) v
+    float3 mT = rotate_axis(c.ax, make_float3(-Tt.x, -Tt.y, -Tt.z), -t * c.phi);
+    float3 dr = rotate_axis(c.ax, dc, -t * c.phi);
+    o = mat3_tmul(c.R0, mT);
+    d = mat3_tmul(c.R0, dr);
+  } else {
+    o = mat3_tmul(c.R0, make_float3(-Tt.x, -Tt.y, -Tt.z));
+    d = mat3_tmul(c.R0, dc);
+  }
+  return true;
+}
+
+// Real spherical harmonics with the Condon-Shortley phase, orthonormal, degrees 0..DEG,
+// index l*l + l + m, at the unit direction (x, y, z).  The constants are
+// sqrt(2) K_l^|m| times the constant factor of P_l^|m| / (1 - z^2)^{|m|/2}, with
+// K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+  Y[0] = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+  if (DEG >= 1) {
+    const float c1 = 0.4886025119029199f;  // sqrt(3 / (4 pi))
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+  }
+  if (DEG >= 2) {
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 1.0925484305920792f * x * y;                 // 3 sqrt(5 / (12 pi)) xy
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);  // sqrt(5 / (16 pi)) (3z^2 - 1)
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.5462742152960396f * (xx - yy);             // 3 sqrt(5 / (48 pi))
+    if (DEG >= 3) {
+      Y[9] = -0.5900435899266435f * y * (3.f * xx - yy);   // 15 sqrt(7 / (1440 pi))
+      Y[10] = 2.890611442640554f * x * y * z;              // 30 sqrt(7 / (240 pi))
+      Y[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);  // 1.5 sqrt(7 / (24 pi))
+      Y[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);  // sqrt(7 / (16 pi))
+      Y[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
+      Y[14] = 1.445305721320277f * z * (xx - yy);           // 15 sqrt(7 / (240 pi))
+      Y[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
+    }
+  }
+}
+
+// Activated particle parameters: s = exp(log_s), sigma = sigmoid(logit), unit quaternion,
+// R(q), M = S^-1 R^T.  Returns false for non-finite parameters or a zero quaternion.
+struct Particle {
+  float3 mu;
+  float s[3];
+  float q[4];   // normalised
+  float qn;     // |q| before normalisation
+  float R[9];
+  float M[9];
+  float sigma;
+};
+
+__device__ __forceinline__ void quat_to_rot(const float *q, float *R) {
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ bool activate(float3 mu, float3 ls, float4 q4, float logit, Particle &p) {
+  p.mu = mu;
+  p.s[0] = expf(ls.x); p.s[1] = expf(ls.y); p.s[2] = expf(ls.z);
+  float qq = fmaf(q4.x, q4.x, fmaf(q4.y, q4.y, fmaf(q4.z, q4.z, q4.w * q4.w)));
+  p.qn = sqrtf(qq);
+  float iq = 1.f / p.qn;
+  p.q[0] = q4.x * iq; p.q[1] = q4.y * iq; p.q[2] = q4.z * iq; p.q[3] = q4.w * iq;
+  quat_to_rot(p.q, p.R);
+  for (int k = 0; k < 3; ++k) {
+    float is = 1.f / p.s[k];
+    p.M[3 * k + 0] = p.R[0 + k] * is;
+    p.M[3 * k + 1] = p.R[3 + k] * is;
+    p.M[3 * k + 2] = p.R[6 + k] * is;
+  }
+  p.sigma = 1.f / (1.f + expf(-logit));
+  bool ok = isfinite(mu.x) && isfinite(mu.y) && isfinite(mu.z) && isfinite(logit) && qq > 0.f && isfinite(qq);
+  ok = ok && p.s[0] > 0.f && p.s[1] > 0.f && p.s[2] > 0.f && isfinite(p.s[0]) && isfinite(p.s[1]) &&
+       isfinite(p.s[2]);
+  return ok;
+}
+
+}  // namespace ut3d

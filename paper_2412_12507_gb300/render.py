@@ -1,0 +1,242 @@
+"""PyTorch-facing wrapper of the 3DGUT C ABI: device memory, streams and autograd.
+
+PyTorch supplies device buffers and the current CUDA stream; every step of the hot path
+(projection, binning / sorting, compositing, backward) runs in libut3d.so's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import torch
+
+from . import abi
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class Scene:
+    """Particle parameters as contiguous FP32 CUDA tensors (Sec. 3)."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_arrays(d: dict, device="cuda") -> "Scene":
+        f = lambda k: torch.as_tensor(d[k], dtype=torch.float32).contiguous().to(device)  # noqa: E731
+        n = f("means").reshape(-1, 3).shape[0]
+        deg = int(d["sh_degree"])
+        return Scene(f("means").reshape(n, 3), f("log_scales").reshape(n, 3), f("quats").reshape(n, 4),
+                     f("opacity_logits").reshape(n), f("sh").reshape(n, (deg + 1) ** 2, 3).contiguous(), deg)
+
+    def struct(self) -> abi.UtScene:
+        return abi.make_scene(self.means, self.log_scales, self.quats, self.opacity_logits, self.sh, self.sh_degree)
+
+
+@dataclass
+class Projection:
+    mean2d: torch.Tensor
+    cov2d: torch.Tensor
+    depth: torch.Tensor
+    rect: torch.Tensor
+    ntiles: torch.Tensor
+
+
+@dataclass
+class Binning:
+    vals: torch.Tensor
+    ranges: torch.Tensor
+    k_dev: torch.Tensor
+    keys: torch.Tensor | None = None
+    capacity: int = 0
+
+    def count(self) -> int:
+        return int(self.k_dev.item())
+
+
+def project(scene: Scene, cam: dict, opts: dict | None = None, out: Projection | None = None) -> Projection:
+    """ut_project: UT projection of every particle (Algorithms 1-2)."""
+    n = scene.n
+    dev = scene.means.device
+    if out is None:
+        out = Projection(torch.empty((n, 2), dtype=torch.float32, device=dev),
+                         torch.empty((n, 3), dtype=torch.float32, device=dev),
+                         torch.empty(n, dtype=torch.float32, device=dev),
+                         torch.empty((n, 4), dtype=torch.int16, device=dev),
+                         torch.empty(n, dtype=torch.int32, device=dev))
+    c, o, u, s = abi.make_camera(cam), abi.make_options(opts), abi.make_params(opts), scene.struct()
+    st = abi.lib().ut_project(C.byref(s), C.byref(c), C.byref(u), C.byref(o), _ptr(out.mean2d), _ptr(out.cov2d),
+                              _ptr(out.depth), _ptr(out.rect), _ptr(out.ntiles), _stream())
+    abi.check("ut_project", st)
+    return out
+
+
+def tile_count(cam: dict, opts: dict | None = None) -> int:
+    o = abi.make_options(opts)
+    return -(-int(cam["width"]) // o.tile_w) * -(-int(cam["height"]) // o.tile_h)
+
+
+class Workspace:
+    """Grow-only device scratch buffer (uint8), 256-byte aligned."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != torch.device(device):
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        p = self.buf.data_ptr()
+        off = (-p) % 256
+        return self.buf[off:off + nbytes]
+
+
+def bin_and_sort(proj: Projection, cam: dict, opts: dict | None, capacity: int, want_keys: bool = False,
+                 ws: Workspace | None = None, out: Binning | None = None) -> Binning:
+    """bin_and_sort: duplicate (tile | depth) keys, stable sort, per-tile ranges (Sec. 4.3).
+
+    Asynchronous: if the true key count exceeds `capacity`, out.count() reports it after the
+    stream completes and the ranges are all empty (the caller retries)."""
+    n = int(proj.depth.shape[0])
+    dev = proj.depth.device
+    c, o = abi.make_camera(cam), abi.make_options(opts)
+    T = tile_count(cam, opts)
+    capacity = int(max(capacity, 1))
+    if out is None or out.capacity < capacity or (want_keys and out.keys is None):
+        out = Binning(torch.empty(capacity, dtype=torch.int32, device=dev),
+                      torch.empty((T, 2), dtype=torch.int32, device=dev),
+                      torch.zeros(1, dtype=torch.int64, device=dev),
+                      torch.empty(capacity, dtype=torch.int64, device=dev) if want_keys else None, capacity)
+    ws = ws or Workspace()
+    nbytes = abi.lib().ut_bin_workspace_size(n, out.capacity, C.byref(c), C.byref(o))
+    w = ws.get(nbytes, dev)
+    st = abi.lib().bin_and_sort(n, _ptr(proj.depth), _ptr(proj.rect), _ptr(proj.ntiles), C.byref(c), C.byref(o),
+                                _ptr(w), w.numel(), out.capacity, _ptr(out.keys) if want_keys else None,
+                                _ptr(out.vals), _ptr(out.ranges), _ptr(out.k_dev), _stream())
+    abi.check("bin_and_sort", st)
+    return out
+
+
+@dataclass
+class Frame:
+    rgb: torch.Tensor
+    alpha: torch.Tensor
+    t_final: torch.Tensor
+    n_used: torch.Tensor
+
+
+def composite_forward(scene: Scene, cam: dict, opts: dict | None, proj: Projection, binning: Binning,
+                      out: Frame | None = None, stats: torch.Tensor | None = None) -> Frame:
+    """composite_forward: front-to-back compositing with 3D max-response evaluation."""
+    W, H = int(cam["width"]), int(cam["height"])
+    dev = scene.means.device
+    if out is None:
+        out = Frame(torch.empty((3, H, W), dtype=torch.float32, device=dev),
+                    torch.empty((H, W), dtype=torch.float32, device=dev),
+                    torch.empty((H, W), dtype=torch.float32, device=dev),
+                    torch.empty((H, W), dtype=torch.int32, device=dev))
+    c, o, s = abi.make_camera(cam), abi.make_options(opts), scene.struct()
+    st = abi.lib().composite_forward(C.byref(s), C.byref(c), C.byref(o), _ptr(proj.rect), _ptr(binning.vals),
+                                     _ptr(binning.ranges), _ptr(out.rgb), _ptr(out.alpha), _ptr(out.t_final),
+                                     _ptr(out.n_used), _ptr(stats), _stream())
+    abi.check("composite_forward", st)
+    return out
+
+
+def composite_backward(scene: Scene, cam: dict, opts: dict | None, proj: Projection, binning: Binning,
+                       frame: Frame, d_rgb: torch.Tensor, d_alpha: torch.Tensor, ws: Workspace | None = None):
+    """composite_backward: gradients of the loss w.r.t. every particle parameter."""
+    n = scene.n
+    dev = scene.means.device
+    grads = dict(means=torch.empty_like(scene.means), log_scales=torch.empty_like(scene.log_scales),
+                 quats=torch.empty_like(scene.quats), opacity_logits=torch.empty_like(scene.opacity_logits),
+                 sh=torch.empty_like(scene.sh))
+    ws = ws or Workspace()
+    w = ws.get(abi.lib().ut_backward_workspace_size(n), dev)
+    c, o, s = abi.make_camera(cam), abi.make_options(opts), scene.struct()
+    d_rgb = d_rgb.contiguous()
+    d_alpha = d_alpha.contiguous()
+    st = abi.lib().composite_backward(C.byref(s), C.byref(c), C.byref(o), _ptr(proj.rect), _ptr(binning.vals),
+                                      _ptr(binning.ranges), _ptr(frame.rgb), _ptr(frame.t_final),
+                                      _ptr(frame.n_used), _ptr(d_rgb), _ptr(d_alpha), _ptr(w), w.numel(),
+                                      _ptr(grads["means"]), _ptr(grads["log_scales"]), _ptr(grads["quats"]),
+                                      _ptr(grads["opacity_logits"]), _ptr(grads["sh"]), _stream())
+    abi.check("composite_backward", st)
+    return grads
+
+
+@dataclass
+class Renderer:
+    """Renders one camera repeatedly, keeping workspaces and a key capacity that grows on demand."""
+    cam: dict
+    opts: dict | None = None
+    capacity: int = 1 << 20
+    growth: float = 1.25
+    ws: Workspace = field(default_factory=Workspace)
+    bws: Workspace = field(default_factory=Workspace)
+    binning: Binning | None = None
+    proj: Projection | None = None
+    frame: Frame | None = None
+
+    def forward(self, scene: Scene, sync_check: bool = True):
+        self.proj = project(scene, self.cam, self.opts, self.proj if self.proj is not None and
+                            self.proj.depth.shape[0] == scene.n else None)
+        while True:
+            self.binning = bin_and_sort(self.proj, self.cam, self.opts, self.capacity, ws=self.ws,
+                                        out=self.binning)
+            if not sync_check:
+                break
+            K = self.binning.count()
+            if K <= self.binning.capacity:
+                break
+            self.capacity = int(K * self.growth) + 1
+        self.frame = composite_forward(scene, self.cam, self.opts, self.proj, self.binning, self.frame)
+        return self.frame
+
+    def backward(self, scene: Scene, d_rgb: torch.Tensor, d_alpha: torch.Tensor):
+        return composite_backward(scene, self.cam, self.opts, self.proj, self.binning, self.frame, d_rgb, d_alpha,
+                                  self.bws)
+
+
+class RenderFunction(torch.autograd.Function):
+    """torch.autograd.Function over the C ABI: (means, log_scales, quats, logits, sh) -> (rgb, alpha)."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, renderer: Renderer, sh_degree: int):
+        scene = Scene(means.detach().contiguous(), log_scales.detach().contiguous(), quats.detach().contiguous(),
+                      opacity_logits.detach().contiguous(), sh.detach().contiguous(), sh_degree)
+        frame = renderer.forward(scene)
+        ctx.renderer = renderer
+        ctx.scene = scene
+        ctx.proj, ctx.binning = renderer.proj, renderer.binning
+        ctx.frame = Frame(frame.rgb.clone(), frame.alpha.clone(), frame.t_final.clone(), frame.n_used.clone())
+        return ctx.frame.rgb.clone(), ctx.frame.alpha.clone()
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_alpha):
+        r = ctx.renderer
+        if d_rgb is None:
+            d_rgb = torch.zeros_like(ctx.frame.rgb)
+        if d_alpha is None:
+            d_alpha = torch.zeros_like(ctx.frame.alpha)
+        g = composite_backward(ctx.scene, r.cam, r.opts, ctx.proj, ctx.binning, ctx.frame, d_rgb, d_alpha, r.bws)
+        return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None
+
+
+def render(means, log_scales, quats, opacity_logits, sh, sh_degree: int, renderer: Renderer):
+    """Differentiable render through the C ABI; returns (rgb[3,H,W], alpha[H,W])."""
+    return RenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, sh_degree)

@@ -124,18 +124,22 @@ def camera(model, width, height, fx=None, fy=None, cx=None, cy=None, k=(0, 0, 0,
         fx = width / math.pi if model == "fisheye" else float(width)
     if fy is None:
         fy = fx
-    return dict(model=model, width=int(width), height=int(height), fx=float(fx), fy=float(fy),
-                cx=float(width / 2 if cx is None else cx), cy=float(height / 2 if cy is None else cy),
-                k=[float(v) for v in k], q_start=[float(v) for v in q], t_start=[float(v) for v in t],
-                q_end=[float(v) for v in (q if q_end is None else q_end)],
-                t_end=[float(v) for v in (t if t_end is None else t_end)],
-                rolling_shutter=int(rolling_shutter), near_plane=float(near_plane))
+    f = lambda v: float(np.float32(v))  # noqa: E731  (FP32 values: both sides see identical numbers)
+    return dict(model=model, width=int(width), height=int(height), fx=f(fx), fy=f(fy),
+                cx=f(width / 2 if cx is None else cx), cy=f(height / 2 if cy is None else cy),
+                k=[f(v) for v in k], q_start=[f(v) for v in q], t_start=[f(v) for v in t],
+                q_end=[f(v) for v in (q if q_end is None else q_end)],
+                t_end=[f(v) for v in (t if t_end is None else t_end)],
+                rolling_shutter=int(rolling_shutter), near_plane=f(near_plane))
 
 
 def options(**kw):
     o = dict(tile_w=16, tile_h=16, t_min=1e-4, alpha_min=1.0 / 255.0, alpha_max=0.99, rs_iters=3,
              newton_iters=12, ut_alpha=1.0, ut_beta=2.0, ut_kappa=0.0, extent_sigma=3.0)
     o.update(kw)
+    # FP32 values: both sides see identical thresholds
+    for k in ("t_min", "alpha_min", "alpha_max", "ut_alpha", "ut_beta", "ut_kappa", "extent_sigma"):
+        o[k] = float(np.float32(o[k]))
     return o
 
 

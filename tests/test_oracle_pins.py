@@ -68,6 +68,8 @@ def test_ut_exact_for_affine_camera(orc, ut):
     qc = synth._rot_to_quat(Rc)
     tc = np.array([0.2, -0.1, 1.5])
     cam = synth.camera("ortho", 100, 80, fx=37.0, fy=29.0, cx=41.0, cy=33.0, q=qc, t=tc)
+    # the camera carries FP32-rounded pose numbers: use exactly those
+    Rc, tc = rot(cam["q_start"]), np.array(cam["t_start"])
     for _ in range(10):
         mu = rng.uniform(-1, 1, 3)
         R = rot(rng.standard_normal(4))
@@ -329,11 +331,13 @@ def test_opaque_particle_gives_clamped_alpha(orc):
     beta = (c - 0.5) * 2 * math.sqrt(math.pi)
     sc = one_scene([0.0, 0.0, 2.0], [1.0, 1.0, 1.0], [1, 0, 0, 0], 12.0, [beta])
     proj = dict(rect=np.array([[0, 0, 7, 7]], np.int32), depth32=np.array([2.0], np.float32))
-    out = orc.render(sc, cam, synth.options(), proj=proj, pixels=([3, 4], [3, 4]))
+    op = synth.options()
+    amax = op["alpha_max"]  # 0.99 as an FP32 number
+    out = orc.render(sc, cam, op, proj=proj, pixels=([3, 4], [3, 4]))
     for q in range(2):
-        assert np.allclose(out["rgb"][q], 0.99 * np.float32(beta).astype(float) / (2 * math.sqrt(math.pi)) + 0.99 * 0.5,
+        assert np.allclose(out["rgb"][q], amax * np.float32(beta).astype(float) / (2 * math.sqrt(math.pi)) + amax * 0.5,
                            atol=1e-12)
-        assert abs(out["alpha"][q] - 0.99) < 1e-15
+        assert abs(out["alpha"][q] - amax) < 1e-15
 
 
 def test_two_particles_quadrature_closed_form(orc):
