@@ -171,10 +171,11 @@ static double orc_theta_inverse(const double k[4], double theta_max, double rd) 
   double th = rd < theta_max ? rd : theta_max;
   for (int it = 0; it < 200; ++it) {
     double f = orc_theta_d(k, th) - rd;
+    if (f == 0.0) break; /* exact root */
     if (f > 0) b = th; else a = th;
     double fp = orc_theta_d_prime(k, th);
     double nt = fp > 0 ? th - f / fp : 0.5 * (a + b);
-    if (!(nt > a && nt < b)) nt = 0.5 * (a + b);
+    if (!(nt >= a && nt <= b)) nt = 0.5 * (a + b); /* Newton left the bracket: bisect */
     if (fabs(nt - th) < 1e-16 * (1.0 + th)) { th = nt; break; }
     th = nt;
     if (b - a < 1e-17) break;
@@ -435,8 +436,9 @@ void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op
         /* a near-valid particle: estimate its footprint anyway so that pixels under it get flagged */
         orc_camera c2 = *c;
         c2.near_plane = 1e-9;
-        double th2 = 0.5 * ORC_PI;
-        if (orc_ut_estimate(&c2, th2 > theta_max ? th2 : theta_max, op->rs_iters, op->ut_alpha, op->ut_beta,
+        /* the polynomial fisheye extends to the whole sphere but the pole behind the camera */
+        double th2 = c->model == 1 ? ORC_PI : theta_max;
+        if (orc_ut_estimate(&c2, th2, op->rs_iters, op->ut_alpha, op->ut_beta,
                             op->ut_kappa, p.mu, p.R, p.s, vmu, cov, NULL, NULL)) {
           double k = op->extent_sigma;
           double hx = k * sqrt(cov[0]), hy = k * sqrt(cov[2]);

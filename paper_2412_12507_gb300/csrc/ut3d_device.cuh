@@ -132,10 +132,11 @@ __device__ __forceinline__ bool pixel_ray(const DevCam &c, int px, int py, int n
     float th = fminf(rd, c.theta_max);
     for (int it = 0; it < newton_iters; ++it) {
       float f = theta_d_poly(c, th) - rd;
+      if (f == 0.f) break;
       if (f > 0.f) hi = th; else lo = th;
       float fp = theta_d_prime(c, th);
       float nt = th - f / fp;
-      if (!(nt > lo && nt < hi)) nt = 0.5f * (lo + hi);
+      if (!(nt >= lo && nt <= hi)) nt = 0.5f * (lo + hi);  // Newton left the bracket: bisect
       if (nt == th) break;
       th = nt;
     }

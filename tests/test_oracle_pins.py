@@ -170,6 +170,29 @@ def test_fisheye_equidistant_closed_form(orc):
         assert abs(math.atan2(uv[1] - 300, uv[0] - 400) - math.atan2(x[1], x[0])) < 1e-9
 
 
+@pytest.mark.parametrize("k", [[0, 0, 0, 0], [0.03, -0.01, 0.004, -0.001], [-0.05, -0.04, 0.03, -0.05]])
+def test_fisheye_ray_inverts_the_distortion(orc, k):
+    """The pixel ray's angle theta from the optical axis solves theta_d(theta) = r_d; for k = 0
+    (equidistant) theta = r_d exactly, which starts the root search on an exact root."""
+    cam = synth.camera("fisheye", 640, 480, fx=200.0, fy=200.0, k=k)
+    kk = np.array(cam["k"])
+    tm = orc.theta_max(kk)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        px, py = rng.uniform(0, 640), rng.uniform(0, 480)
+        rd = math.hypot((px - 320) / 200, (py - 240) / 200)
+        ok, o, d = orc.pixel_ray(cam, px, py)
+        th_lim = tm * (1 + kk[0] * tm**2 + kk[1] * tm**4 + kk[2] * tm**6 + kk[3] * tm**8)
+        assert ok == (rd <= th_lim)
+        if not ok:
+            continue
+        th = math.acos(d[2] / np.linalg.norm(d))
+        td = th * (1 + kk[0] * th**2 + kk[1] * th**4 + kk[2] * th**6 + kk[3] * th**8)
+        assert abs(td - rd) < 1e-12, (td, rd)
+        if not any(k):
+            assert abs(th - rd) < 1e-13
+
+
 def test_theta_max_is_first_root_of_derivative(orc):
     assert abs(orc.theta_max([0, 0, 0, 0]) - math.pi / 2) < 1e-15
     # strongly negative distortion: d theta_d / d theta turns over before pi/2
