@@ -24,8 +24,9 @@ _lib = None
 F_RECT_EDGE, F_ALPHA_MIN, F_TSTOP, F_DEPTH_TIE = 1, 2, 4, 8
 F_CULL_TIE, F_PIXEL_EDGE, F_ILL_COND, F_ALPHA_MAX, F_INVALID_PIXEL = 16, 32, 64, 128, 256
 # flags that can change the forward result between an FP32 and an FP64 evaluation
-F_FORWARD_TIES = (F_RECT_EDGE | F_ALPHA_MIN | F_TSTOP | F_DEPTH_TIE | F_CULL_TIE | F_PIXEL_EDGE
-                  | F_ILL_COND)
+# (depth-tied pairs and stop-threshold ties are not in this set: their effect is bounded by the
+# per-pixel slack / aslack that render() returns)
+F_FORWARD_TIES = (F_RECT_EDGE | F_ALPHA_MIN | F_DEPTH_TIE | F_CULL_TIE | F_PIXEL_EDGE | F_ILL_COND)
 
 
 def build(force: bool = False) -> str:
@@ -85,7 +86,7 @@ def lib():
         L.orc_count_keys.argtypes = [C.c_int, P, C.c_int, C.c_int]
         L.orc_bin.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_render.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), C.POINTER(Tol),
-                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P]
+                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, P]
         L.orc_render_list.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P,
                                       C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_backward.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P, C.c_int,
@@ -250,7 +251,7 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
 
     proj: output of project() (or a dict with rect / depth32 and optionally edges / tie,
     e.g. synthetic arrays).  Returns rgb[P,3], alpha[P], tfinal[P], nblend[P], flags[P],
-    and px, py."""
+    slack (the colour change depth-tied pairs can cause when reordered), and px, py."""
     S = _SceneArrays(scene)
     if proj is None:
         proj = project(scene, cam, opts, tol)
@@ -267,11 +268,12 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
     edges = _f64(proj["edges"]).reshape(-1, 4) if proj.get("edges") is not None else None
     tie = _i32(proj["tie"]) if proj.get("tie") is not None else None
     out = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), tfinal=np.zeros(P), nblend=np.zeros(P, np.int32),
-               flags=np.zeros(P, np.int32), px=px, py=py)
+               flags=np.zeros(P, np.int32), slack=np.zeros(P), aslack=np.zeros(P), px=px, py=py)
     c, o, t = make_camera(cam), make_options(opts), make_tol(tol)
     lib().orc_render(C.byref(S.s), C.byref(c), C.byref(o), C.byref(t), _p(rect), _p(depth32), _p(edges),
                      _p(tie), P, _p(px), _p(py), int(no_rect), _p(out["rgb"]), _p(out["alpha"]),
-                     _p(out["tfinal"]), _p(out["nblend"]), _p(out["flags"]))
+                     _p(out["tfinal"]), _p(out["nblend"]), _p(out["flags"]), _p(out["slack"]),
+                     _p(out["aslack"]))
     return out
 
 

@@ -605,14 +605,21 @@ typedef struct {
 
 /* Composites one pixel ray over the particles in `order` (eq. QuadratureVolumeRendering with
  * alpha_i = sigma_i rho_i at tau_max).  Returns the number of blended particles; fills rgb, T.
- * When `rec` is given, records every blended particle (up to cap). */
+ * When `rec` is given, records every blended particle (up to cap).
+ * Depth near-ties: two consecutive blended particles whose FP32 depth keys are within
+ * depth_ulps may legitimately come in either order from an FP32 depth; swapping them changes
+ * the colour by exactly T_i alpha_i alpha_j (c_j - c_i), which is added to *slack.  Three or more
+ * in a row set ORC_F_DEPTH_TIE instead.  A transmittance T (1 - alpha) within eps_t of t_min may
+ * stop one particle earlier or later: its T alpha c is added to *slack and T alpha to *aslack. */
 static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_options *op, const orc_tol *tol,
                              int px, int py, const double o[3], const double d[3], const double *Y, double rgb[3],
-                             double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect) {
+                             double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect, double *slack,
+                             double *aslack) {
   double T = 1.0;
   int nb = 0;
   uint32_t last_bits = 0;
-  int have_last = 0;
+  int have_last = 0, last_tie = 0;
+  double last_alpha = 0.0, last_T = 1.0, last_col[3] = {0, 0, 0};
   rgb[0] = rgb[1] = rgb[2] = 0.0;
   for (int j = 0; j < x->norder; ++j) {
     int i = x->order[j];
@@ -648,20 +655,37 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
     double alpha = a < op->alpha_max ? a : op->alpha_max;
     double Tn = T * (1.0 - alpha);
-    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
-    if (Tn < op->t_min) break;
-    uint32_t bits = orc_f32_bits(x->depth32[i]);
-    if (flags && have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) *flags |= ORC_F_DEPTH_TIE;
-    last_bits = bits; have_last = 1;
     const float *beta = sc->sh + (size_t)i * x->nsh * 3;
-    double raw[3], col[3];
+    double raw[3], col[3], cmax = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
       double s = 0.5;
       for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Y[kk];
       raw[ch] = s;
       col[ch] = s > 0.0 ? s : 0.0;
-      rgb[ch] += col[ch] * alpha * T;
+      cmax = fmax(cmax, col[ch]);
     }
+    if (fabs(Tn - op->t_min) < tol->eps_t * op->t_min) {
+      /* the stop decision may flip: this one particle is blended or not (and at most one more
+       * after it, whose T is already below t_min) */
+      if (flags) *flags |= ORC_F_TSTOP;
+      if (slack) *slack += T * alpha * cmax;
+      if (aslack) *aslack += T * alpha;
+    }
+    if (Tn < op->t_min) break;
+    uint32_t bits = orc_f32_bits(x->depth32[i]);
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] += col[ch] * alpha * T;
+    if (have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) {
+      if (flags && last_tie) *flags |= ORC_F_DEPTH_TIE;
+      double dc = 0.0;
+      for (int ch = 0; ch < 3; ++ch) dc = fmax(dc, fabs(col[ch] - last_col[ch]));
+      if (slack) *slack += last_T * last_alpha * alpha * dc;
+      last_tie = 1;
+    } else {
+      last_tie = 0;
+    }
+    last_bits = bits; have_last = 1;
+    last_alpha = alpha; last_T = T;
+    for (int ch = 0; ch < 3; ++ch) last_col[ch] = col[ch];
     if (rec && nb < cap) {
       orc_contrib *c = &rec[nb];
       c->i = i; c->alpha = alpha; c->a = a; c->T = T; c->rho = rho; c->tau = tau;
@@ -690,11 +714,13 @@ static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int 
  * rect / depth32 / valid come from orc_project or are given directly (synthetic).
  * edges / tie may be NULL (then no near-tie flags of those kinds).  no_rect != 0 evaluates
  * every particle at every pixel (culling disabled).
- * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags. */
+ * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags, and slack / aslack =
+ * the largest colour / opacity change that FP32 depth ties and stop-threshold ties can cause
+ * (see orc_composite_ray). */
 void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
                 const int32_t *rect, const float *depth32, const double *edges, const int32_t *tie, int npix,
                 const int32_t *pix_x, const int32_t *pix_y, int no_rect, double *rgb, double *alpha,
-                double *tfinal, int32_t *nblend, int32_t *flags) {
+                double *tfinal, int32_t *nblend, int32_t *flags, double *slack, double *aslack) {
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, edges, tie);
   double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
@@ -707,7 +733,7 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     orc_pixel_setup(c, theta_max, x.deg, px, py, tol, o, d, Y, &valid, &fl);
     if (!valid) {
       rgb[3 * q] = rgb[3 * q + 1] = rgb[3 * q + 2] = 0.0;
-      alpha[q] = 0.0; tfinal[q] = 1.0; nblend[q] = 0; flags[q] = fl;
+      alpha[q] = 0.0; tfinal[q] = 1.0; nblend[q] = 0; flags[q] = fl; slack[q] = 0.0; aslack[q] = 0.0;
       continue;
     }
     for (int t = 0; t < x.ntie; ++t) {
@@ -717,7 +743,10 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
         fl |= ORC_F_CULL_TIE;
     }
     double T;
-    nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect);
+    slack[q] = 0.0;
+    aslack[q] = 0.0;
+    nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect,
+                                  &slack[q], &aslack[q]);
     alpha[q] = 1.0 - T;
     tfinal[q] = T;
     flags[q] = fl;
@@ -740,7 +769,7 @@ void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options
   int valid;
   orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
   if (!valid) { rgb[0] = rgb[1] = rgb[2] = 0; *tfinal = 1.0; }
-  else orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, tfinal, NULL, NULL, 0, 0);
+  else orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, tfinal, NULL, NULL, 0, 0, NULL, NULL);
   orc_ctx_free(&x);
 }
 
@@ -785,7 +814,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
       orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
       if (!valid) continue;
       double rgb[3], Tf;
-      int nb = orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0);
+      int nb = orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL, NULL);
       const double *g = g_rgb + 3 * q;
       double gA = g_alpha[q];
       double S[3] = {0, 0, 0}; /* sum over later blended particles of c alpha T */

@@ -46,9 +46,12 @@ def compare_frame(frame, ref, tol=RGB_TOL):
     """Max |rgb - oracle| and |alpha - oracle| over pixels without a forward near-tie flag."""
     got_rgb, got_a, _ = frame_at(frame, ref["px"], ref["py"])
     flagged = (ref["flags"] & oracle.F_FORWARD_TIES) != 0
-    err = np.maximum(np.abs(got_rgb - ref["rgb"]).max(axis=1), np.abs(got_a - ref["alpha"]))
+    # reordering depth-tied pairs changes the colour by at most the oracle's slack
+    err = np.maximum(np.abs(got_rgb - ref["rgb"]).max(axis=1) - ref["slack"],
+                     np.abs(got_a - ref["alpha"]) - ref["aslack"])
     ok = ~flagged
     return dict(max_err=float(err[ok].max()) if ok.any() else 0.0, n=int(err.size), n_flagged=int(flagged.sum()),
+                n_slack=int((ref["slack"] > 0).sum()),
                 n_bad=int((err[ok] > tol).sum()), max_err_flagged=float(err[flagged].max()) if flagged.any() else 0.0)
 
 

@@ -71,6 +71,11 @@ def test_projection_matches_oracle(name):
     assert np.max(np.abs(c2 - ref["cov2d"][both]).max(1) / (scale + 1e-6)) < 2e-4
     dep = to_np(p.depth)[both]
     assert np.max(np.abs(dep - ref["depth"][both]) / ref["depth"][both]) < 2e-6
+    print(name, "mean2d err", np.max(np.abs(m2 - ref["mean2d"][both])), "cov rel err",
+          np.max(np.abs(c2 - ref["cov2d"][both]).max(1) / (scale + 1e-6)),
+          "depth ulps", np.max(np.abs(dep.view(np.int32).astype(np.int64) -
+                                      ref["depth32"][both].view(np.int32).astype(np.int64))),
+          "cull mismatches", int(mism.sum()))
     # rects: identical except edges the oracle places within eps of an integer
     diff = rect[both] != ref["rect"][both]
     eb = e[both][:, [0, 2, 1, 3]]  # x0, y0, x1, y1 order of rect
