@@ -47,6 +47,8 @@ def workload(name):
     from paper_2412_12507_gb300 import synth
     if name == "rs_fisheye_1m_1080p":
         return synth.rs_fisheye(seed=2, n=1_000_000, width=1920, height=1080, deg=3)
+    if name == "rs_fisheye_300k_1080p":
+        return synth.rs_fisheye(seed=2, n=300_000, width=1920, height=1080, deg=3)
     if name == "fisheye_shell_100k_720p":
         return synth.fisheye_shell(seed=1, n=100_000, width=1280, height=720)
     if name == "pinhole_1k_64":
