@@ -159,6 +159,25 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
                        int64_t key_capacity, uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges,
                        int64_t *k_out, ut_stream stream);
 
+/* bin_and_sort without caller scratch memory (the paper has no counterpart: this is a
+ * deployment convenience).  For callers that cannot allocate device memory or hand the
+ * library a workspace, e.g. a plugin inside a host application that owns all device memory
+ * through its own pool, or a real-time frame loop that must never enter the CUDA allocator.
+ * Same inputs, outputs, asynchrony and capacity contract as bin_and_sort; the scratch comes
+ * from a fixed array of UT_BIN_STATIC_SCRATCH_BYTES (32 MiB) compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - Returns UT_ERR_CAPACITY, launching nothing, when
+ *     ut_bin_workspace_size(n, key_capacity, cam, opt) > UT_BIN_STATIC_SCRATCH_BYTES
+ *     (for example n = 100k particles with key_capacity = 2M fits).
+ *   - The first call on each device looks up the array's device address (once per device,
+ *     with that device current); make that first call before capturing any stream.
+ *   - Allocates nothing.  All calls share the one array and it keeps the last call's
+ *     contents; calls whose work overlaps on the GPU race on it: order them (one stream). */
+#define UT_BIN_STATIC_SCRATCH_BYTES (32u << 20)
+ut_status bin_and_sort_static(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                              const ut_camera *cam, const ut_options *opt, int64_t key_capacity, uint64_t *keys,
+                              uint32_t *vals, uint32_t *tile_ranges, int64_t *k_out, ut_stream stream);
+
 /* Front-to-back compositing (eq. QuadratureVolumeRendering) with the particle response
  * evaluated in 3D at its maximum along the pixel ray (eq. GaussianMaxResponse):
  *   o_g = S^-1 R^T (o - mu), d_g = S^-1 R^T d, omega^2 = |o_g x d_g|^2 / |d_g|^2,

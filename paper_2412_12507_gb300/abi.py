@@ -55,6 +55,8 @@ SIGNATURES = {
     "ut_bin_workspace_size": (C.c_size_t, [C.c_int32, C.c_int64, C.POINTER(UtCamera), C.POINTER(UtOptions)]),
     "bin_and_sort": (C.c_int, [C.c_int32, _P, _P, _P, C.POINTER(UtCamera), C.POINTER(UtOptions), _P, C.c_size_t,
                                C.c_int64, _P, _P, _P, _P, _P]),
+    "bin_and_sort_static": (C.c_int, [C.c_int32, _P, _P, _P, C.POINTER(UtCamera), C.POINTER(UtOptions), C.c_int64,
+                                      _P, _P, _P, _P, _P]),
     "composite_forward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,
                                     _P, _P, _P, _P, _P]),
     "ut_backward_workspace_size": (C.c_size_t, [C.c_int32]),
