@@ -216,6 +216,61 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
                              float *d_log_scales, float *d_quats, float *d_opacity_logits, float *d_sh,
                              ut_stream stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Batches of views: one launch sequence renders several (scene, camera) views at once — the
+ * multi-view training step and the unit of work of the serving loop.  The method per view is
+ * exactly that of ut_project + bin_and_sort + composite_forward (the single-view calls are
+ * the batch of one view); particles of all views are projected in one kernel, all their
+ * (tile, particle) entries are sorted together (tile ids are global over the batch), and
+ * one compositing kernel covers every tile of every view.
+ * ------------------------------------------------------------------------------------------ */
+#define UT_MAX_BATCH_VIEWS 32
+#define UT_MAX_BATCH_SCENES 8
+
+/* One view of a batch.  rgb[3][H][W] and alpha[H][W] (device) are written by render_batch;
+ * t_final[H][W] and n_used[H][W] are written when non-NULL and are required by
+ * render_batch_backward, which also reads d_rgb[3][H][W] and d_alpha[H][W]. */
+typedef struct {
+  int32_t scene; /* index into the scenes array */
+  ut_camera camera;
+  float *rgb, *alpha, *t_final;
+  uint32_t *n_used;
+  const float *d_rgb, *d_alpha;
+} ut_view;
+
+/* Bytes of scratch render_batch needs; the same buffer, untouched, feeds render_batch_backward.
+ * Returns 0 for invalid arguments. */
+size_t ut_batch_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                               const ut_options *opt, int64_t key_capacity);
+
+/* Forward render of n_views (1..UT_MAX_BATCH_VIEWS) views of n_scenes (1..UT_MAX_BATCH_SCENES)
+ * scenes (all with the same sh_degree), with the UT projection, binning and compositing defined
+ * by ut_project, bin_and_sort and composite_forward.  key_capacity bounds the total number of
+ * (tile, particle) entries of the batch; *k_out (device int64) receives that total, and if it
+ * exceeds key_capacity every view's image is left black (all ranges empty): check *k_out after
+ * the stream completes and retry with a larger capacity (and workspace).  Asynchronous on
+ * `stream`; allocates nothing. */
+ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                       const ut_params *ut, const ut_options *opt, void *workspace, size_t workspace_bytes,
+                       int64_t key_capacity, int64_t *k_out, ut_stream stream);
+
+/* Per-scene gradient outputs of render_batch_backward (device, layouts as composite_backward). */
+typedef struct {
+  float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_sh;
+} ut_scene_grads;
+
+/* Bytes of accumulator scratch render_batch_backward needs for these scenes. */
+size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes);
+
+/* Gradient of a loss through render_batch (supplementary Sec. B): every view's d_rgb / d_alpha
+ * is propagated into its scene's parameters; gradients of views sharing a scene add up.
+ * workspace / key_capacity must be the buffer and capacity render_batch used, unchanged since;
+ * views must carry the t_final and n_used render_batch wrote.  grads[n_scenes] are overwritten. */
+ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                                const ut_options *opt, const void *workspace, size_t workspace_bytes,
+                                int64_t key_capacity, void *grad_workspace, size_t grad_workspace_bytes,
+                                const ut_scene_grads *grads, ut_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,8 +44,22 @@ class UtOptions(C.Structure):
                 ("extent_sigma", C.c_float)]
 
 
+class UtView(C.Structure):
+    _fields_ = [("scene", C.c_int32), ("camera", UtCamera), ("rgb", C.c_void_p), ("alpha", C.c_void_p),
+                ("t_final", C.c_void_p), ("n_used", C.c_void_p), ("d_rgb", C.c_void_p), ("d_alpha", C.c_void_p)]
+
+
+class UtSceneGrads(C.Structure):
+    _fields_ = [("d_means", C.c_void_p), ("d_log_scales", C.c_void_p), ("d_quats", C.c_void_p),
+                ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
+
+
+MAX_BATCH_VIEWS = 32
+MAX_BATCH_SCENES = 8
+
 # every exported symbol of include/ut3d.h, with its ctypes signature
 _P = C.c_void_p
+_SC, _VW = C.POINTER(UtScene), C.POINTER(UtView)
 SIGNATURES = {
     "ut_default_options": (None, [C.POINTER(UtOptions)]),
     "ut_status_string": (C.c_char_p, [C.c_int]),
@@ -60,6 +74,12 @@ SIGNATURES = {
     "composite_forward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,
                                     _P, _P, _P, _P, _P]),
     "ut_backward_workspace_size": (C.c_size_t, [C.c_int32]),
+    "ut_batch_workspace_size": (C.c_size_t, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtOptions), C.c_int64]),
+    "render_batch": (C.c_int, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtParams), C.POINTER(UtOptions), _P,
+                               C.c_size_t, C.c_int64, _P, _P]),
+    "ut_batch_backward_workspace_size": (C.c_size_t, [_SC, C.c_int32]),
+    "render_batch_backward": (C.c_int, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtOptions), _P, C.c_size_t,
+                                        C.c_int64, _P, C.c_size_t, C.POINTER(UtSceneGrads), _P]),
     "composite_backward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,
                                      _P, _P, _P, _P, _P, C.c_size_t, _P, _P, _P, _P, _P, _P]),
 }

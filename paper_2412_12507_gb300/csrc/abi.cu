@@ -179,6 +179,117 @@ ut_status check_scene(const ut_scene *s, bool need_sh) {
 
 bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
+DevScene scene_desc(const ut_scene &s) {
+  DevScene d;
+  std::memset(&d, 0, sizeof(d));
+  d.means = s.means;
+  d.log_scales = s.log_scales;
+  d.quats = reinterpret_cast<const float4 *>(s.quats);
+  d.logits = s.opacity_logits;
+  d.sh = s.sh;
+  d.n = s.n;
+  d.deg = s.sh_degree;
+  const int nc = 3 * (s.sh_degree + 1) * (s.sh_degree + 1);
+  d.sh_vec = (nc % 4 == 0) && aligned16(s.sh);
+  return d;
+}
+
+// A batch of one view of one scene (the single-view entry points).
+void single_view(BatchDesc &bd, const DevCam &cam, const DevOpts &op, const ut_scene *scene, int n) {
+  std::memset(&bd, 0, sizeof(bd));
+  bd.nv = 1;
+  bd.ns = 1;
+  bd.total_particles = n;
+  bd.total_tiles = op.tiles_x * op.tiles_y;
+  bd.v[0].cam = cam;
+  bd.v[0].n = n;
+  bd.v[0].tiles_x = op.tiles_x;
+  bd.v[0].tiles_y = op.tiles_y;
+  if (scene) bd.s[0] = scene_desc(*scene);
+  bd.s[0].n = n;
+}
+
+ut_status make_weights(const ut_params *ut, UTWeights &w) {
+  if (!ut || !std::isfinite(ut->alpha) || !std::isfinite(ut->beta) || !std::isfinite(ut->kappa))
+    return UT_ERR_INVALID_ARG;
+  double a = ut->alpha, b = ut->beta, k = ut->kappa;
+  double lam = a * a * (3.0 + k) - 3.0;
+  if (!(3.0 + lam > 0)) return UT_ERR_INVALID_ARG;
+  w.gamma = (float)std::sqrt(3.0 + lam);
+  w.wm0 = (float)(lam / (3.0 + lam));
+  w.wi = (float)(1.0 / (2.0 * (3.0 + lam)));
+  w.wc0 = (float)(lam / (3.0 + lam) + (1.0 - a * a + b));
+  return UT_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+// Validates a batch and fills its descriptor (flattened particle / tile offsets).
+ut_status make_batch(const ut_scene *scenes, int ns, const ut_view *views, int nv, const ut_options *opt,
+                     BatchDesc &bd, DevOpts &dop) {
+  if (!scenes || !views || ns < 1 || ns > kMaxScenes || nv < 1 || nv > kMaxViews || !opt) return UT_ERR_INVALID_ARG;
+  std::memset(&bd, 0, sizeof(bd));
+  for (int s = 0; s < ns; ++s) {
+    ut_status st = check_scene(&scenes[s], true);
+    if (st != UT_OK) return st;
+    if (scenes[s].sh_degree != scenes[0].sh_degree) return UT_ERR_INVALID_ARG;
+    bd.s[s] = scene_desc(scenes[s]);
+  }
+  bd.ns = ns;
+  bd.nv = nv;
+  long long part = 0, tiles = 0;
+  for (int v = 0; v < nv; ++v) {
+    const ut_view &vw = views[v];
+    if (vw.scene < 0 || vw.scene >= ns || !vw.rgb || !vw.alpha) return UT_ERR_INVALID_ARG;
+    DevView &d = bd.v[v];
+    ut_status st = make_cam(&vw.camera, d.cam);
+    if (st != UT_OK) return st;
+    DevOpts o;
+    if ((st = make_opts(opt, &vw.camera, o)) != UT_OK) return st;
+    if (v == 0) dop = o;
+    d.scene = vw.scene;
+    d.n = scenes[vw.scene].n;
+    d.part_off = (int)part;
+    d.tile_off = (int)tiles;
+    d.tiles_x = o.tiles_x;
+    d.tiles_y = o.tiles_y;
+    d.rgb = vw.rgb;
+    d.alpha = vw.alpha;
+    d.tfinal = vw.t_final;
+    d.n_used = vw.n_used;
+    d.d_rgb = vw.d_rgb;
+    d.d_alpha = vw.d_alpha;
+    part += d.n;
+    tiles += (long long)o.tiles_x * o.tiles_y;
+  }
+  if (part >= (1ll << 31) || tiles >= (1ll << 31)) return UT_ERR_INVALID_ARG;
+  bd.total_particles = (int)part;
+  bd.total_tiles = (int)tiles;
+  return UT_OK;
+}
+
+// Layout of the render_batch workspace: projection of every flattened entry, ranges of every
+// global tile, the sorted values, then bin_and_sort's own scratch.
+struct BatchLayout {
+  size_t mean2d, cov2d, depth, rect, ntiles, ranges, vals, bin, total;
+};
+
+BatchLayout batch_layout(long long part, long long tiles, long long cap) {
+  BatchLayout L;
+  size_t off = 0;
+  size_t p = (size_t)(part > 0 ? part : 1), t = (size_t)(tiles > 0 ? tiles : 1), c = (size_t)(cap > 0 ? cap : 1);
+  L.mean2d = off; off += align256(p * 8);
+  L.cov2d = off; off += align256(p * 12);
+  L.depth = off; off += align256(p * 4);
+  L.rect = off; off += align256(p * 8);
+  L.ntiles = off; off += align256(p * 4);
+  L.ranges = off; off += align256(t * 8);
+  L.vals = off; off += align256(c * 4);
+  L.bin = off; off += bin_workspace_bytes((int)p, (int64_t)c, (int)t);
+  L.total = off;
+  return L;
+}
+
 }  // namespace
 }  // namespace ut3d
 
@@ -221,20 +332,13 @@ ut_status ut_project(const ut_scene *scene, const ut_camera *cam, const ut_param
   if ((st = make_cam(cam, dc)) != UT_OK) return st;
   DevOpts dop;
   if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
-  if (!ut || !std::isfinite(ut->alpha) || !std::isfinite(ut->beta) || !std::isfinite(ut->kappa))
-    return UT_ERR_INVALID_ARG;
-  double a = ut->alpha, b = ut->beta, k = ut->kappa;
-  double lam = a * a * (3.0 + k) - 3.0;
-  if (!(3.0 + lam > 0)) return UT_ERR_INVALID_ARG;
   UTWeights w;
-  w.gamma = (float)std::sqrt(3.0 + lam);
-  w.wm0 = (float)(lam / (3.0 + lam));
-  w.wi = (float)(1.0 / (2.0 * (3.0 + lam)));
-  w.wc0 = (float)(lam / (3.0 + lam) + (1.0 - a * a + b));
+  if ((st = make_weights(ut, w)) != UT_OK) return st;
   if (scene->n > 0 && (!mean2d || !cov2d || !depth || !rect || !ntiles || !aligned8(mean2d) || !aligned8(rect)))
     return UT_ERR_INVALID_ARG;
-  return launch_project(scene->n, *scene, dc, dop, w, mean2d, cov2d, depth, rect, ntiles,
-                        reinterpret_cast<cudaStream_t>(stream));
+  BatchDesc bd;
+  single_view(bd, dc, dop, scene, scene->n);
+  return launch_project(bd, dop, w, mean2d, cov2d, depth, rect, ntiles, reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt) {
@@ -258,7 +362,9 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
   int tiles = dop.tiles_x * dop.tiles_y;
   size_t need = bin_workspace_bytes(n, key_capacity, tiles);
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return UT_ERR_INVALID_ARG;
-  return launch_bin(n, depth, rect, ntiles, dop, tiles, workspace, key_capacity, keys, vals, tile_ranges, k_out,
+  BatchDesc bd;
+  single_view(bd, dc, dop, nullptr, n);
+  return launch_bin(bd, depth, rect, ntiles, dop, workspace, key_capacity, keys, vals, tile_ranges, k_out,
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -274,8 +380,13 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
   if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
   if (!tile_ranges || !rgb || !alpha || !t_final || !n_used || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
   if (scene->n > 0 && (!rect || !aligned8(rect))) return UT_ERR_INVALID_ARG;
-  return launch_composite_fwd(*scene, dc, dop, rect, vals, tile_ranges, rgb, alpha, t_final, n_used, stats,
-                              reinterpret_cast<cudaStream_t>(stream));
+  BatchDesc bd;
+  single_view(bd, dc, dop, scene, scene->n);
+  bd.v[0].rgb = rgb;
+  bd.v[0].alpha = alpha;
+  bd.v[0].tfinal = t_final;
+  bd.v[0].n_used = n_used;
+  return launch_composite_fwd(bd, dop, rect, vals, tile_ranges, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t ut_backward_workspace_size(int32_t n) { return n < 0 ? 0 : backward_workspace_bytes(n); }
@@ -300,8 +411,107 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
   if (!workspace || workspace_bytes < backward_workspace_bytes(scene->n) ||
       (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
-  return launch_composite_bwd(*scene, dc, dop, rect, vals, tile_ranges, rgb, t_final, n_used, d_rgb, d_alpha,
-                              workspace, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+  BatchDesc bd;
+  single_view(bd, dc, dop, scene, scene->n);
+  DevView &v = bd.v[0];
+  v.rgb = const_cast<float *>(rgb);
+  v.tfinal = const_cast<float *>(t_final);
+  v.n_used = const_cast<uint32_t *>(n_used);
+  v.d_rgb = d_rgb;
+  v.d_alpha = d_alpha;
+  DevScene &s = bd.s[0];
+  s.gacc = static_cast<float *>(workspace);
+  s.d_means = d_means;
+  s.d_log_scales = d_log_scales;
+  s.d_quats = d_quats;
+  s.d_logits = d_opacity_logits;
+  s.d_sh = d_sh;
+  s.grad_off = 0;
+  return launch_composite_bwd(bd, dop, rect, vals, tile_ranges, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t ut_batch_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                               const ut_options *opt, int64_t key_capacity) {
+  BatchDesc bd;
+  DevOpts dop;
+  if (key_capacity < 0 || make_batch(scenes, n_scenes, views, n_views, opt, bd, dop) != UT_OK) return 0;
+  return batch_layout(bd.total_particles, bd.total_tiles, key_capacity).total;
+}
+
+ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                       const ut_params *ut, const ut_options *opt, void *workspace, size_t workspace_bytes,
+                       int64_t key_capacity, int64_t *k_out, ut_stream stream) {
+  BatchDesc bd;
+  DevOpts dop;
+  ut_status st = make_batch(scenes, n_scenes, views, n_views, opt, bd, dop);
+  if (st != UT_OK) return st;
+  UTWeights w;
+  if ((st = make_weights(ut, w)) != UT_OK) return st;
+  if (key_capacity < 0 || key_capacity >= (int64_t(1) << 32) || !k_out) return UT_ERR_INVALID_ARG;
+  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, key_capacity);
+  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return UT_ERR_INVALID_ARG;
+  char *ws = static_cast<char *>(workspace);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float *depth = reinterpret_cast<float *>(ws + L.depth);
+  int16_t *rect = reinterpret_cast<int16_t *>(ws + L.rect);
+  uint32_t *ntiles = reinterpret_cast<uint32_t *>(ws + L.ntiles);
+  uint32_t *ranges = reinterpret_cast<uint32_t *>(ws + L.ranges);
+  uint32_t *vals = reinterpret_cast<uint32_t *>(ws + L.vals);
+  if ((st = launch_project(bd, dop, w, reinterpret_cast<float *>(ws + L.mean2d), reinterpret_cast<float *>(ws + L.cov2d),
+                           depth, rect, ntiles, s)) != UT_OK)
+    return st;
+  if ((st = launch_bin(bd, depth, rect, ntiles, dop, ws + L.bin, key_capacity, nullptr, vals, ranges, k_out, s)) !=
+      UT_OK)
+    return st;
+  return launch_composite_fwd(bd, dop, rect, vals, ranges, nullptr, s);
+}
+
+size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes) {
+  if (!scenes || n_scenes < 1 || n_scenes > kMaxScenes) return 0;
+  size_t total = 0;
+  for (int k = 0; k < n_scenes; ++k) total += backward_workspace_bytes(scenes[k].n);
+  return total;
+}
+
+ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
+                                const ut_options *opt, const void *workspace, size_t workspace_bytes,
+                                int64_t key_capacity, void *grad_workspace, size_t grad_workspace_bytes,
+                                const ut_scene_grads *grads, ut_stream stream) {
+  BatchDesc bd;
+  DevOpts dop;
+  ut_status st = make_batch(scenes, n_scenes, views, n_views, opt, bd, dop);
+  if (st != UT_OK) return st;
+  for (int v = 0; v < n_views; ++v)
+    if (!views[v].t_final || !views[v].n_used || !views[v].d_rgb || !views[v].d_alpha) return UT_ERR_INVALID_ARG;
+  if (key_capacity < 0 || key_capacity >= (int64_t(1) << 32) || !grads) return UT_ERR_INVALID_ARG;
+  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, key_capacity);
+  if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return UT_ERR_INVALID_ARG;
+  if (!grad_workspace || grad_workspace_bytes < ut_batch_backward_workspace_size(scenes, n_scenes) ||
+      (reinterpret_cast<uintptr_t>(grad_workspace) & 255))
+    return UT_ERR_INVALID_ARG;
+  char *gw = static_cast<char *>(grad_workspace);
+  int goff = 0;
+  for (int k = 0; k < n_scenes; ++k) {
+    const ut_scene_grads &g = grads[k];
+    if (scenes[k].n > 0 && (!g.d_means || !g.d_log_scales || !g.d_quats || !g.d_opacity_logits || !g.d_sh))
+      return UT_ERR_INVALID_ARG;
+    DevScene &s = bd.s[k];
+    s.gacc = reinterpret_cast<float *>(gw);
+    gw += backward_workspace_bytes(scenes[k].n);
+    s.d_means = g.d_means;
+    s.d_log_scales = g.d_log_scales;
+    s.d_quats = g.d_quats;
+    s.d_logits = g.d_opacity_logits;
+    s.d_sh = g.d_sh;
+    s.grad_off = goff;
+    goff += scenes[k].n;
+  }
+  const char *ws = static_cast<const char *>(workspace);
+  return launch_composite_bwd(bd, dop, reinterpret_cast<const int16_t *>(ws + L.rect),
+                              reinterpret_cast<const uint32_t *>(ws + L.vals),
+                              reinterpret_cast<const uint32_t *>(ws + L.ranges),
                               reinterpret_cast<cudaStream_t>(stream));
 }
 

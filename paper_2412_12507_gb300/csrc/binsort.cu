@@ -300,14 +300,17 @@ __global__ void k_write_kout(const u64 *__restrict__ total, int64_t *__restrict_
 // One block per 256 consecutive particles of the depth order: the block's output span
 // [offs[first], offs[last+1]) is filled by consecutive threads (coalesced), each finding its
 // particle by binary search over the block's 257 offsets.
-__global__ void __launch_bounds__(kThreads) k_emit(int n, const uint32_t *__restrict__ order,
+// Entries of a batch: `order` holds flattened (view, particle) indices; the emitted key is
+// the global tile id (view's tile offset + row-major tile in the view) and the value is the
+// particle index within its scene.
+__global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ BatchDesc bd, int n,
+                                                   const uint32_t *__restrict__ order,
                                                    const uint32_t *__restrict__ offs, const short4 *__restrict__ rect,
                                                    const u64 *__restrict__ total, u64 cap, int tile_w, int tile_h,
-                                                   int tiles_x, uint32_t *__restrict__ tkeys,
-                                                   uint32_t *__restrict__ vals) {
+                                                   uint32_t *__restrict__ tkeys, uint32_t *__restrict__ vals) {
   __shared__ uint32_t s_off[kThreads + 1];
   __shared__ uint32_t s_idx[kThreads];
-  __shared__ int s_tx0[kThreads], s_ty0[kThreads], s_tw[kThreads];
+  __shared__ int s_tx0[kThreads], s_ty0[kThreads], s_tw[kThreads], s_tx[kThreads];
   const u64 K = *total;
   if (K > cap) return;
   const int first = blockIdx.x * kThreads;
@@ -315,13 +318,16 @@ __global__ void __launch_bounds__(kThreads) k_emit(int n, const uint32_t *__rest
   const int cnt = min(kThreads, n - first);
   const int t = threadIdx.x;
   if (t < cnt) {
-    uint32_t idx = order[first + t];
-    short4 r = rect[idx];
+    uint32_t g = order[first + t];
+    short4 r = rect[g];
+    const int v = view_of_particle(bd, (int)g);
     s_off[t] = offs[first + t];
-    s_idx[t] = idx;
+    s_idx[t] = g - (uint32_t)bd.v[v].part_off;
     int tx0 = r.x / tile_w, tx1 = r.z / tile_w, ty0 = r.y / tile_h;
-    s_tx0[t] = tx0;
+    // fold the view's tile offset into the start tile: tile = base + ty * tiles_x + tx
+    s_tx0[t] = bd.v[v].tile_off + tx0;
     s_ty0[t] = ty0;
+    s_tx[t] = bd.v[v].tiles_x;
     s_tw[t] = max(tx1 - tx0 + 1, 1);
   }
   if (t == 0) s_off[cnt] = (first + cnt < n) ? offs[first + cnt] : (uint32_t)K;
@@ -337,19 +343,23 @@ __global__ void __launch_bounds__(kThreads) k_emit(int n, const uint32_t *__rest
     int w = s_tw[lo];
     int ty = (int)(local / (uint32_t)w);
     int tx = (int)(local - (uint32_t)(ty * w));
-    tkeys[p] = (uint32_t)((s_ty0[lo] + ty) * tiles_x + s_tx0[lo] + tx);
+    tkeys[p] = (uint32_t)((s_ty0[lo] + ty) * s_tx[lo] + s_tx0[lo] + tx);
     vals[p] = s_idx[lo];
   }
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals, Count cnt,
-                         const float *__restrict__ depth, uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys) {
+__global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *__restrict__ tkeys,
+                         const uint32_t *__restrict__ vals, Count cnt, const float *__restrict__ depth,
+                         uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys) {
   const uint32_t K = cnt.get();
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < K; p += gridDim.x * blockDim.x) {
     uint32_t t = tkeys[p];
     if (p == 0 || tkeys[p - 1] != t) ranges[2 * t] = p;
     if (p == K - 1 || tkeys[p + 1] != t) ranges[2 * t + 1] = p + 1;
-    if (keys) keys[p] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(depth[vals[p]]);
+    if (keys) {
+      const int v = view_of_tile(bd, (int)t);
+      keys[p] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(depth[bd.v[v].part_off + vals[p]]);
+    }
   }
 }
 
@@ -454,9 +464,11 @@ int bits_for(int tiles) {
 
 size_t bin_workspace_bytes(int n, int64_t cap, int /*tiles*/) { return carve_bytes(n, cap); }
 
-ut_status launch_bin(int n, const float *depth, const int16_t *rect, const uint32_t *ntiles, const DevOpts &op,
-                     int tiles, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
+ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                     const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                      int64_t *k_out, cudaStream_t s) {
+  const int n = bd.total_particles;
+  const int tiles = bd.total_tiles;
   Buffers b = carve(ws, n, cap);
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, s) != cudaSuccess) return UT_ERR_CUDA;
   if (cudaMemsetAsync(b.total, 0, sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
@@ -475,14 +487,13 @@ ut_status launch_bin(int n, const float *depth, const int16_t *rect, const uint3
     uint32_t *tv[2];
     tv[passes & 1] = vals;
     tv[(passes & 1) ^ 1] = b.valt;
-    k_emit<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(n, b.dv[r], b.offs,
+    k_emit<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs,
                                                               reinterpret_cast<const short4 *>(rect), b.total,
-                                                              (u64)cap, op.tile_w, op.tile_h, op.tiles_x, b.tk[0],
-                                                              tv[0]);
+                                                              (u64)cap, op.tile_w, op.tile_h, b.tk[0], tv[0]);
     count_launches(1);
     Count ck{b.total, (u64)cap, 0};
     int rr = radix_sort(b.tk, tv, ck, (u64)cap, tb, b.spine, b.chunk, s);
-    k_ranges<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(b.tk[rr], tv[rr], ck, depth, ranges, keys);
+    k_ranges<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(bd, b.tk[rr], tv[rr], ck, depth, ranges, keys);
     count_launches(1);
   }
   k_write_kout<<<1, 1, 0, s>>>(b.total, k_out);

@@ -1,13 +1,13 @@
 // composite.cu — tile-based front-to-back compositing with 3D particle evaluation
 // (Sec. 4.2, eq. GaussianMaxResponse; eq. QuadratureVolumeRendering) and its
-// hand-written backward (supplementary Sec. B).
+// hand-written backward (supplementary Sec. B), for a batch of views.
 //
-// One thread block per image tile, one thread per pixel.  The tile's depth-sorted
-// particle list is consumed in batches of kBatch particles: the block gathers each
-// batch's parameters once, activates them (M = S^-1 R^T, sigma, the alpha_min test
-// threshold, packed rect) into shared memory together with their SH coefficients, and
-// every pixel then walks the batch from shared memory.  The block leaves the list as
-// soon as every pixel's transmittance has dropped below t_min.
+// One thread block per image tile (global tile ids over all views of the batch), one thread
+// per pixel.  The tile's depth-sorted particle list is consumed in batches of kBatch
+// particles: the block gathers each batch's parameters once, activates them (M = S^-1 R^T,
+// sigma, the alpha_min test threshold, packed rect) into shared memory together with their
+// SH coefficients, and every pixel then walks the batch from shared memory.  The block
+// leaves the list as soon as every pixel's transmittance has dropped below t_min.
 //
 // The backward replays the forward IN FORWARD ORDER: the stored rgb and T_final give the
 // suffix sums S_i = C - sum_{j<=i} c_j alpha_j T_j without dividing transmittances,
@@ -16,6 +16,9 @@
 // values), accumulated across warps in shared memory, and pushed to global memory with
 // one atomic per value per (tile, particle).  A final per-particle kernel maps the
 // accumulated dL/dM, dL/dmu, dL/dsigma onto log-scales, quaternions and logits.
+//
+// Template RS selects the general ray-origin path (per-pixel origin, needed when any view
+// has a rolling shutter); without it the origin is the camera centre of the view.
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -24,24 +27,18 @@ namespace {
 
 constexpr int kBatch = 64;
 
-struct SceneArgs {
-  const float *means, *log_scales;
-  const float4 *quats;
-  const float *logits, *sh;
-};
-
 // Staged particle record (4 x float4):
 //   g0 = M00 M01 M02 M10   g1 = M11 M12 M20 M21   g2 = M22 a.x a.y a.z
 //   g3 = sigma, thr = 2 ln(sigma / alpha_min), rect (x0 | y0 << 16), rect (x1 | y1 << 16)
-// where a = M (o - mu) for a global shutter (o fixed) and a = M mu under a rolling shutter.
+// where a = M (o - mu) with o the camera centre (RS = false) or a = M mu (RS = true).
+// aux (backward only) = o - mu (RS = false) or mu (RS = true).
 template <bool RS>
-__device__ __forceinline__ void stage_particle(const SceneArgs &sc, const DevCam &cam, const DevOpts &op,
-                                               const short4 *rect, uint32_t idx, float4 *g, float4 *aux) {
+__device__ __forceinline__ void stage_particle(const DevScene &sc, const DevCam &cam, const DevOpts &op, short4 r,
+                                               uint32_t idx, float4 *g, float4 *aux) {
   float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
   float3 ls = make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
   Particle p;
   activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
-  short4 r = rect[idx];
   float3 a;
   float3 om = make_float3(cam.cen[0] - mu.x, cam.cen[1] - mu.y, cam.cen[2] - mu.z);
   if (RS) a = mat3_mul(p.M, mu);
@@ -54,6 +51,61 @@ __device__ __forceinline__ void stage_particle(const SceneArgs &sc, const DevCam
   int r1 = ((int)(unsigned short)r.z) | ((int)r.w << 16);
   g[3] = make_float4(p.sigma, thr, __int_as_float(r0), __int_as_float(r1));
   if (aux) *aux = RS ? make_float4(mu.x, mu.y, mu.z, 0.f) : make_float4(om.x, om.y, om.z, 0.f);
+}
+
+// SH coefficients of the batch's particles into shared memory (float4 when aligned).
+template <int NC>
+__device__ __forceinline__ void stage_sh(const DevScene &sc, const uint32_t *s_idx, int nb, float *s_sh) {
+  if constexpr (NC % 4 == 0) {
+    if (!sc.sh_vec) {
+      for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
+        int b = f / NC;
+        s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+      }
+      return;
+    }
+    constexpr int N4 = NC / 4;
+    const float4 *src = reinterpret_cast<const float4 *>(sc.sh);
+    float4 *dst = reinterpret_cast<float4 *>(s_sh);
+    for (int f = threadIdx.x; f < nb * N4; f += blockDim.x) {
+      int b = f / N4;
+      dst[f] = src[(size_t)s_idx[b] * N4 + (f - b * N4)];
+    }
+  } else {
+    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
+      int b = f / NC;
+      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+    }
+  }
+}
+
+// Raw colour sum_k beta_k,ch Y_k + 1/2 of one staged particle (before the clamp at 0).
+template <int NSH>
+__device__ __forceinline__ void sh_colour(const float *shb, const float *Y, float &r0, float &r1, float &r2) {
+  constexpr int NC = NSH * 3;
+  r0 = 0.5f; r1 = 0.5f; r2 = 0.5f;
+  if constexpr (NC % 4 == 0) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(shb);
+#pragma unroll
+    for (int j = 0; j < NC / 4; ++j) {
+      float4 c = s4[j];
+      const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int idx = 4 * j + e, k = idx / 3, ch = idx % 3;
+        if (ch == 0) r0 = fmaf(cv[e], Y[k], r0);
+        else if (ch == 1) r1 = fmaf(cv[e], Y[k], r1);
+        else r2 = fmaf(cv[e], Y[k], r2);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NSH; ++k) {
+      r0 = fmaf(shb[3 * k], Y[k], r0);
+      r1 = fmaf(shb[3 * k + 1], Y[k], r1);
+      r2 = fmaf(shb[3 * k + 2], Y[k], r2);
+    }
+  }
 }
 
 // Response of a staged particle for the ray (o, d) of pixel (px, py).  Returns false if the
@@ -99,21 +151,23 @@ __device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op
 }
 
 template <int DEG, bool RS, bool STATS>
-__global__ void __launch_bounds__(512) k_composite_fwd(DevCam cam, DevOpts op, SceneArgs sc,
+__global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
-                                                       const uint2 *__restrict__ ranges, float *__restrict__ rgb,
-                                                       float *__restrict__ alpha_out, float *__restrict__ tfinal,
-                                                       uint32_t *__restrict__ n_used,
+                                                       const uint2 *__restrict__ ranges,
                                                        unsigned long long *__restrict__ stats) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
   __shared__ float4 s_geo[kBatch][4];
-  __shared__ float s_sh[kBatch * NC];
+  __shared__ __align__(16) float s_sh[kBatch * NC];
   __shared__ uint32_t s_idx[kBatch];
 
   const int tile = blockIdx.x;
-  const int tx = tile % op.tiles_x, ty = tile / op.tiles_x;
+  const DevView &view = bd.v[view_of_tile(bd, tile)];
+  const DevScene &sc = bd.s[view.scene];
+  const DevCam &cam = view.cam;
+  const int lt = tile - view.tile_off;
+  const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
   const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
   const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
   const bool inside = px < cam.W && py < cam.H;
@@ -132,11 +186,11 @@ __global__ void __launch_bounds__(512) k_composite_fwd(DevCam cam, DevOpts op, S
     const int nb = min((uint32_t)kBatch, rg.y - start);
     if (threadIdx.x < nb) s_idx[threadIdx.x] = vals[start + threadIdx.x];
     __syncthreads();
-    if (threadIdx.x < nb) stage_particle<RS>(sc, cam, op, rect, s_idx[threadIdx.x], s_geo[threadIdx.x], nullptr);
-    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
-      int b = f / NC;
-      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+    if (threadIdx.x < nb) {
+      uint32_t idx = s_idx[threadIdx.x];
+      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[threadIdx.x], nullptr);
     }
+    stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
     if (done) continue;
     for (int b = 0; b < nb; ++b) {
@@ -154,14 +208,8 @@ __global__ void __launch_bounds__(512) k_composite_fwd(DevCam cam, DevOpts op, S
         break;
       }
       if (STATS) ++n_blend;
-      const float *shb = s_sh + b * NC;
-      float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
-#pragma unroll
-      for (int k = 0; k < NSH; ++k) {
-        r0 = fmaf(shb[3 * k], Y[k], r0);
-        r1 = fmaf(shb[3 * k + 1], Y[k], r1);
-        r2 = fmaf(shb[3 * k + 2], Y[k], r2);
-      }
+      float r0, r1, r2;
+      sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
       float w = al * T;
       C0 = fmaf(fmaxf(r0, 0.f), w, C0);
       C1 = fmaf(fmaxf(r1, 0.f), w, C1);
@@ -173,17 +221,17 @@ __global__ void __launch_bounds__(512) k_composite_fwd(DevCam cam, DevOpts op, S
   if (inside) {
     size_t pix = (size_t)py * cam.W + px;
     size_t plane = (size_t)cam.W * cam.H;
-    rgb[pix] = C0;
-    rgb[plane + pix] = C1;
-    rgb[2 * plane + pix] = C2;
-    alpha_out[pix] = valid ? 1.f - T : 0.f;
-    tfinal[pix] = T;
-    n_used[pix] = last;
+    view.rgb[pix] = C0;
+    view.rgb[plane + pix] = C1;
+    view.rgb[2 * plane + pix] = C2;
+    view.alpha[pix] = valid ? 1.f - T : 0.f;
+    if (view.tfinal) view.tfinal[pix] = T;
+    if (view.n_used) view.n_used[pix] = last;
   }
   if (STATS) {
-    for (int o = 16; o >= 1; o >>= 1) {
-      n_eval += __shfl_xor_sync(0xffffffffu, n_eval, o);
-      n_blend += __shfl_xor_sync(0xffffffffu, n_blend, o);
+    for (int s = 16; s >= 1; s >>= 1) {
+      n_eval += __shfl_xor_sync(0xffffffffu, n_eval, s);
+      n_blend += __shfl_xor_sync(0xffffffffu, n_blend, s);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&stats[0], n_eval);
@@ -223,30 +271,28 @@ __device__ __forceinline__ float grad_value(int j, const float *vv, const float 
 }
 
 template <int DEG, bool RS>
-__global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, SceneArgs sc,
+__global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
-                                                       const uint2 *__restrict__ ranges,
-                                                       const float *__restrict__ rgb,
-                                                       const float *__restrict__ tfinal,
-                                                       const uint32_t *__restrict__ n_used,
-                                                       const float *__restrict__ d_rgb,
-                                                       const float *__restrict__ d_alpha, float *__restrict__ gacc,
-                                                       float *__restrict__ d_sh) {
+                                                       const uint2 *__restrict__ ranges) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
   constexpr int NV = 16 + NC;                 // used partials
   constexpr int NCHUNK = (NV + 31) / 32;      // 32-value reduce chunks
   __shared__ float4 s_geo[kBatch][4];
   __shared__ float4 s_aux[kBatch];
-  __shared__ float s_sh[kBatch * NC];
+  __shared__ __align__(16) float s_sh[kBatch * NC];
   __shared__ float s_acc[kBatch][NCHUNK * 32];
   __shared__ uint32_t s_idx[kBatch];
   __shared__ int s_any[kBatch];
   __shared__ uint32_t s_end;
 
   const int tile = blockIdx.x;
-  const int tx = tile % op.tiles_x, ty = tile / op.tiles_x;
+  const DevView &view = bd.v[view_of_tile(bd, tile)];
+  const DevScene &sc = bd.s[view.scene];
+  const DevCam &cam = view.cam;
+  const int lt = tile - view.tile_off;
+  const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
   const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
   const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
   const int lane = threadIdx.x & 31;
@@ -262,11 +308,11 @@ __global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, S
   if (valid) {
     size_t pix = (size_t)py * cam.W + px;
     size_t plane = (size_t)cam.W * cam.H;
-    my_end = n_used[pix];
-    g0 = d_rgb[pix]; g1 = d_rgb[plane + pix]; g2 = d_rgb[2 * plane + pix];
-    gA = d_alpha[pix];
-    Cf0 = rgb[pix]; Cf1 = rgb[plane + pix]; Cf2 = rgb[2 * plane + pix];
-    Tf = tfinal[pix];
+    my_end = view.n_used[pix];
+    g0 = view.d_rgb[pix]; g1 = view.d_rgb[plane + pix]; g2 = view.d_rgb[2 * plane + pix];
+    gA = view.d_alpha[pix];
+    Cf0 = view.rgb[pix]; Cf1 = view.rgb[plane + pix]; Cf2 = view.rgb[2 * plane + pix];
+    Tf = view.tfinal[pix];
   }
   if (threadIdx.x == 0) s_end = 0;
   __syncthreads();
@@ -282,12 +328,11 @@ __global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, S
     for (int f = threadIdx.x; f < kBatch * NCHUNK * 32; f += blockDim.x) (&s_acc[0][0])[f] = 0.f;
     if (threadIdx.x < kBatch) s_any[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x < nb)
-      stage_particle<RS>(sc, cam, op, rect, s_idx[threadIdx.x], s_geo[threadIdx.x], &s_aux[threadIdx.x]);
-    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
-      int b = f / NC;
-      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
+    if (threadIdx.x < nb) {
+      uint32_t idx = s_idx[threadIdx.x];
+      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[threadIdx.x], &s_aux[threadIdx.x]);
     }
+    stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
     for (int b = 0; b < nb; ++b) {
       bool contrib = false;
@@ -297,14 +342,8 @@ __global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, S
       if (start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
         contrib = true;
         float al = fminf(a, op.alpha_max);
-        const float *shb = s_sh + b * NC;
-        float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
-#pragma unroll
-        for (int k = 0; k < NSH; ++k) {
-          r0 = fmaf(shb[3 * k], Y[k], r0);
-          r1 = fmaf(shb[3 * k + 1], Y[k], r1);
-          r2 = fmaf(shb[3 * k + 2], Y[k], r2);
-        }
+        float r0, r1, r2;
+        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
         float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
         float w = al * T;
         A0 = fmaf(c0, w, A0);
@@ -355,8 +394,8 @@ __global__ void __launch_bounds__(512) k_composite_bwd(DevCam cam, DevOpts op, S
       if (!s_any[b]) continue;
       uint32_t idx = s_idx[b];
       float v = s_acc[b][j];
-      if (j < 13) atomicAdd(&gacc[(size_t)idx * 16 + j], v);
-      else if (j >= 16 && j < NV) atomicAdd(&d_sh[(size_t)idx * NC + (j - 16)], v);
+      if (j < 13) atomicAdd(&sc.gacc[(size_t)idx * 16 + j], v);
+      else if (j >= 16 && j < NV) atomicAdd(&sc.d_sh[(size_t)idx * NC + (j - 16)], v);
     }
   }
 }
@@ -370,14 +409,16 @@ __device__ __forceinline__ void rot_grad(const float *q, const float *G, float *
   gq[3] = 2.f * (x * (G[2] + G[6]) + y * (G[5] + G[7]) - 2.f * z * (G[0] + G[4]) + w * (G[3] - G[1]));
 }
 
-__global__ void k_finalize(int n, SceneArgs sc, const float *__restrict__ gacc, float *__restrict__ d_means,
-                           float *__restrict__ d_ls, float *__restrict__ d_q, float *__restrict__ d_logit) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// Per particle of every scene in the batch: dL/dM, sum v, dL/dsigma -> parameter gradients.
+__global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    const DevScene &sc = bd.s[scene_of_grad(bd, g)];
+    const int i = g - sc.grad_off;
     float3 mu = make_float3(sc.means[3 * i], sc.means[3 * i + 1], sc.means[3 * i + 2]);
     float3 ls = make_float3(sc.log_scales[3 * i], sc.log_scales[3 * i + 1], sc.log_scales[3 * i + 2]);
     Particle p;
     bool ok = activate(mu, ls, sc.quats[i], sc.logits[i], p);
-    const float *A = gacc + (size_t)i * 16;
+    const float *A = sc.gacc + (size_t)i * 16;
     float out_m[3] = {0.f, 0.f, 0.f}, out_s[3] = {0.f, 0.f, 0.f}, out_q[4] = {0.f, 0.f, 0.f, 0.f}, out_l = 0.f;
     if (ok) {
       float v0 = A[0], v1 = A[1], v2 = A[2];
@@ -399,55 +440,50 @@ __global__ void k_finalize(int n, SceneArgs sc, const float *__restrict__ gacc, 
       out_l = A[12] * p.sigma * (1.f - p.sigma);
     }
     for (int j = 0; j < 3; ++j) {
-      d_means[3 * i + j] = out_m[j];
-      d_ls[3 * i + j] = out_s[j];
+      sc.d_means[3 * i + j] = out_m[j];
+      sc.d_log_scales[3 * i + j] = out_s[j];
     }
-    for (int j = 0; j < 4; ++j) d_q[4 * i + j] = out_q[j];
-    d_logit[i] = out_l;
+    for (int j = 0; j < 4; ++j) sc.d_quats[4 * i + j] = out_q[j];
+    sc.d_logits[i] = out_l;
   }
 }
 
 template <int DEG, bool RS>
-void fwd_launch(int blocks, int threads, const DevCam &cam, const DevOpts &op, const SceneArgs &sc,
-                const int16_t *rect, const uint32_t *vals, const uint32_t *ranges, float *rgb, float *alpha,
-                float *tf, uint32_t *nu, unsigned long long *stats, cudaStream_t s) {
+void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                const uint32_t *ranges, unsigned long long *stats, cudaStream_t s) {
+  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
   if (stats)
-    k_composite_fwd<DEG, RS, true><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect),
-                                                              vals, reinterpret_cast<const uint2 *>(ranges), rgb,
-                                                              alpha, tf, nu, stats);
+    k_composite_fwd<DEG, RS, true><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
+                                                              reinterpret_cast<const uint2 *>(ranges), stats);
   else
-    k_composite_fwd<DEG, RS, false><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect),
-                                                               vals, reinterpret_cast<const uint2 *>(ranges), rgb,
-                                                               alpha, tf, nu, nullptr);
+    k_composite_fwd<DEG, RS, false><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
+                                                               reinterpret_cast<const uint2 *>(ranges), nullptr);
 }
 
 template <int DEG, bool RS>
-void bwd_launch(int blocks, int threads, const DevCam &cam, const DevOpts &op, const SceneArgs &sc,
-                const int16_t *rect, const uint32_t *vals, const uint32_t *ranges, const float *rgb,
-                const float *tf, const uint32_t *nu, const float *drgb, const float *dal, float *gacc, float *dsh,
-                cudaStream_t s) {
-  k_composite_bwd<DEG, RS><<<blocks, threads, 0, s>>>(cam, op, sc, reinterpret_cast<const short4 *>(rect), vals,
-                                                      reinterpret_cast<const uint2 *>(ranges), rgb, tf, nu, drgb,
-                                                      dal, gacc, dsh);
+void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                const uint32_t *ranges, cudaStream_t s) {
+  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
+  k_composite_bwd<DEG, RS><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
+                                                      reinterpret_cast<const uint2 *>(ranges));
 }
 
-SceneArgs scene_args(const ut_scene &sc) {
-  return SceneArgs{sc.means, sc.log_scales, reinterpret_cast<const float4 *>(sc.quats), sc.opacity_logits, sc.sh};
+bool any_rs(const BatchDesc &bd) {
+  for (int v = 0; v < bd.nv; ++v)
+    if (bd.v[v].cam.rs) return true;
+  return false;
 }
 
 }  // namespace
 
-ut_status launch_composite_fwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
-                               const uint32_t *vals, const uint32_t *ranges, float *rgb, float *alpha,
-                               float *t_final, uint32_t *n_used, unsigned long long *stats, cudaStream_t s) {
-  int blocks = op.tiles_x * op.tiles_y;
-  int threads = op.tile_w * op.tile_h;
-  SceneArgs a = scene_args(sc);
-  const bool rs = cam.rs != 0;
-#define UT3D_FWD(D)                                                                                 \
-  (rs ? fwd_launch<D, true>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, alpha, t_final, n_used, stats, s) \
-      : fwd_launch<D, false>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, alpha, t_final, n_used, stats, s))
-  switch (sc.sh_degree) {
+ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                               const uint32_t *ranges, unsigned long long *stats, cudaStream_t s) {
+  if (bd.total_tiles == 0) return UT_OK;
+  const bool rs = any_rs(bd);
+#define UT3D_FWD(D)                                                 \
+  (rs ? fwd_launch<D, true>(bd, op, rect, vals, ranges, stats, s) \
+      : fwd_launch<D, false>(bd, op, rect, vals, ranges, stats, s))
+  switch (bd.s[0].deg) {
     case 0: UT3D_FWD(0); break;
     case 1: UT3D_FWD(1); break;
     case 2: UT3D_FWD(2); break;
@@ -460,39 +496,35 @@ ut_status launch_composite_fwd(const ut_scene &sc, const DevCam &cam, const DevO
 
 size_t backward_workspace_bytes(int n) { return align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1)); }
 
-ut_status launch_composite_bwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
-                               const uint32_t *vals, const uint32_t *ranges, const float *rgb, const float *t_final,
-                               const uint32_t *n_used, const float *d_rgb, const float *d_alpha, void *ws,
-                               float *d_means, float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
-                               cudaStream_t s) {
-  const int n = sc.n;
-  const int nc = 3 * (sc.sh_degree + 1) * (sc.sh_degree + 1);
-  float *gacc = static_cast<float *>(ws);
-  if (n > 0) {
-    if (cudaMemsetAsync(gacc, 0, sizeof(float) * 16 * (size_t)n, s) != cudaSuccess) return UT_ERR_CUDA;
-    if (cudaMemsetAsync(d_sh, 0, sizeof(float) * (size_t)nc * n, s) != cudaSuccess) return UT_ERR_CUDA;
+// Clears the scenes' accumulators and d_sh, runs the backward over every tile, then finalize.
+ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                               const uint32_t *ranges, cudaStream_t s) {
+  int total = 0;
+  for (int k = 0; k < bd.ns; ++k) {
+    const DevScene &sc = bd.s[k];
+    if (sc.n <= 0) continue;
+    const size_t nc = 3 * (size_t)(sc.deg + 1) * (sc.deg + 1);
+    if (cudaMemsetAsync(sc.gacc, 0, sizeof(float) * 16 * (size_t)sc.n, s) != cudaSuccess) return UT_ERR_CUDA;
+    if (cudaMemsetAsync(sc.d_sh, 0, sizeof(float) * nc * sc.n, s) != cudaSuccess) return UT_ERR_CUDA;
+    total = sc.grad_off + sc.n > total ? sc.grad_off + sc.n : total;
   }
-  int blocks = op.tiles_x * op.tiles_y;
-  int threads = op.tile_w * op.tile_h;
-  SceneArgs a = scene_args(sc);
-  const bool rs = cam.rs != 0;
-#define UT3D_BWD(D)                                                                                           \
-  (rs ? bwd_launch<D, true>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, t_final, n_used, d_rgb, d_alpha, \
-                            gacc, d_sh, s)                                                                    \
-      : bwd_launch<D, false>(blocks, threads, cam, op, a, rect, vals, ranges, rgb, t_final, n_used, d_rgb,     \
-                             d_alpha, gacc, d_sh, s))
-  switch (sc.sh_degree) {
-    case 0: UT3D_BWD(0); break;
-    case 1: UT3D_BWD(1); break;
-    case 2: UT3D_BWD(2); break;
-    default: UT3D_BWD(3); break;
-  }
+  if (bd.total_tiles > 0) {
+    const bool rs = any_rs(bd);
+#define UT3D_BWD(D) \
+  (rs ? bwd_launch<D, true>(bd, op, rect, vals, ranges, s) : bwd_launch<D, false>(bd, op, rect, vals, ranges, s))
+    switch (bd.s[0].deg) {
+      case 0: UT3D_BWD(0); break;
+      case 1: UT3D_BWD(1); break;
+      case 2: UT3D_BWD(2); break;
+      default: UT3D_BWD(3); break;
+    }
 #undef UT3D_BWD
-  count_launches(1);
-  if (n > 0) {
-    int g = (n + 255) / 256;
+    count_launches(1);
+  }
+  if (total > 0) {
+    int g = (total + 255) / 256;
     int cap = device_sm_count() * 8;
-    k_finalize<<<g < cap ? g : cap, 256, 0, s>>>(n, a, gacc, d_means, d_log_scales, d_quats, d_logits);
+    k_finalize<<<g < cap ? g : cap, 256, 0, s>>>(bd, total);
     count_launches(1);
   }
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;

@@ -1,12 +1,12 @@
 // project.cu — Unscented-Transform projection of every particle (Sec. 4.1; Algorithms 1-2).
 //
-// One thread per particle, one warp per 32 consecutive particles.  The warp loads its
-// 32 twelve-byte records (means, log-scales) as 24 aligned float4 through shared
-// memory and writes the twelve-byte covariance records back the same way, so every
-// global access of the kernel is a coalesced vector access.  The 7 sigma points are
-// projected through the camera (with the rolling-shutter time fixed point), and the
-// weighted mean / covariance, depth, opacity-tightened rectangle and tile count are
-// written out.
+// One thread per (view, particle) entry of the flattened batch, one warp per 32
+// consecutive entries.  When a warp's 32 entries belong to one view, the warp loads its 32
+// twelve-byte records (means, log-scales) as 24 aligned float4 through shared memory and
+// writes the twelve-byte covariance records back the same way, so the global accesses are
+// coalesced vector accesses.  The 7 sigma points are projected through the view's camera
+// (with the rolling-shutter time fixed point), and the weighted mean / covariance, depth,
+// opacity-tightened rectangle and tile count are written out.
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -16,38 +16,48 @@ namespace {
 
 constexpr int kWarps = 8;
 
-__global__ void __launch_bounds__(kWarps * 32) k_project(int n, const float *__restrict__ means,
-                                                         const float *__restrict__ log_scales,
-                                                         const float4 *__restrict__ quats,
-                                                         const float *__restrict__ logits, DevCam cam, DevOpts op,
-                                                         UTWeights w, int vec_ok, float2 *__restrict__ mean2d,
-                                                         float *__restrict__ cov2d, float *__restrict__ depth,
-                                                         short4 *__restrict__ rect, uint32_t *__restrict__ ntiles) {
+__global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__ BatchDesc bd, DevOpts op, UTWeights w,
+                                                         float2 *__restrict__ mean2d, float *__restrict__ cov2d,
+                                                         float *__restrict__ depth, short4 *__restrict__ rect,
+                                                         uint32_t *__restrict__ ntiles) {
   __shared__ float4 s_stage[kWarps][24];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = bd.total_particles;
   const int base = (blockIdx.x * kWarps + warp) * 32;
   if (base >= n) return;  // warp-uniform
-  const int i = base + lane;
-  const bool full = vec_ok && (base + 32 <= n);
-  const bool live = i < n;
+  const int g = base + lane;
+  const bool live = g < n;
+  const int vi = view_of_particle(bd, live ? g : n - 1);
+  const DevView &view = bd.v[vi];
+  const DevScene &sc = bd.s[view.scene];
+  const int i = (live ? g : n - 1) - view.part_off;
+  // vector path: all 32 entries in this view, 16-byte aligned records
+  const int v_last = __shfl_sync(0xffffffffu, vi, 31);
+  const int v_first = __shfl_sync(0xffffffffu, vi, 0);
+  const int i0 = __shfl_sync(0xffffffffu, i, 0);
+  const bool full = (base + 32 <= n) && v_first == v_last && ((i0 & 3) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(sc.means) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(sc.log_scales) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(cov2d) & 15) == 0);
   float *st = reinterpret_cast<float *>(s_stage[warp]);
 
-  float3 mu = make_float3(0.f, 0.f, 0.f), ls = make_float3(0.f, 0.f, 0.f);
+  float3 mu, ls;
   if (full) {
-    if (lane < 24) s_stage[warp][lane] = reinterpret_cast<const float4 *>(means + 3 * (size_t)base)[lane];
+    if (lane < 24) s_stage[warp][lane] = reinterpret_cast<const float4 *>(sc.means + 3 * (size_t)i0)[lane];
     __syncwarp();
     mu = make_float3(st[3 * lane], st[3 * lane + 1], st[3 * lane + 2]);
     __syncwarp();
-    if (lane < 24) s_stage[warp][lane] = reinterpret_cast<const float4 *>(log_scales + 3 * (size_t)base)[lane];
+    if (lane < 24) s_stage[warp][lane] = reinterpret_cast<const float4 *>(sc.log_scales + 3 * (size_t)i0)[lane];
     __syncwarp();
     ls = make_float3(st[3 * lane], st[3 * lane + 1], st[3 * lane + 2]);
     __syncwarp();
-  } else if (live) {
-    mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
-    ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
+  } else {
+    mu = make_float3(sc.means[3 * i], sc.means[3 * i + 1], sc.means[3 * i + 2]);
+    ls = make_float3(sc.log_scales[3 * i], sc.log_scales[3 * i + 1], sc.log_scales[3 * i + 2]);
   }
-  float4 q4 = live ? quats[i] : make_float4(1.f, 0.f, 0.f, 0.f);
-  float logit = live ? logits[i] : 0.f;
+  const float4 q4 = sc.quats[i];
+  const float logit = sc.logits[i];
+  const DevCam cam = view.cam;
 
   Particle p;
   bool ok = live && activate(mu, ls, q4, logit, p);
@@ -60,8 +70,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(int n, const float *__r
   ok = ok & project_world(cam, op.rs_iters, y0, v[0], t_mu);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float g = w.gamma * p.s[k];
-    float3 col = make_float3(g * p.R[k], g * p.R[3 + k], g * p.R[6 + k]);
+    float gs = w.gamma * p.s[k];
+    float3 col = make_float3(gs * p.R[k], gs * p.R[3 + k], gs * p.R[6 + k]);
     float3 dy = mat3_mul(cam.R0, col);
     float tt;
     ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v[1 + k], tt);
@@ -112,29 +122,26 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(int n, const float *__r
     __syncwarp();
     if (lane < 24) reinterpret_cast<float4 *>(cov2d + 3 * (size_t)base)[lane] = s_stage[warp][lane];
   } else if (live) {
-    cov2d[3 * i] = cxx;
-    cov2d[3 * i + 1] = cxy;
-    cov2d[3 * i + 2] = cyy;
+    cov2d[3 * (size_t)g] = cxx;
+    cov2d[3 * (size_t)g + 1] = cxy;
+    cov2d[3 * (size_t)g + 2] = cyy;
   }
   if (live) {
-    mean2d[i] = vm;
-    depth[i] = dep;
-    rect[i] = r;
-    ntiles[i] = nt;
+    mean2d[g] = vm;
+    depth[g] = dep;
+    rect[g] = r;
+    ntiles[g] = nt;
   }
 }
 
 }  // namespace
 
-ut_status launch_project(int n, const ut_scene &sc, const DevCam &cam, const DevOpts &op, const UTWeights &w,
-                         float *mean2d, float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles,
-                         cudaStream_t stream) {
+ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights &w, float *mean2d, float *cov2d,
+                         float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream) {
+  const int n = bd.total_particles;
   if (n == 0) return UT_OK;
-  int vec_ok = aligned16(sc.means) && aligned16(sc.log_scales) && aligned16(cov2d);
   int blocks = (n + kWarps * 32 - 1) / (kWarps * 32);
-  k_project<<<blocks, kWarps * 32, 0, stream>>>(n, sc.means, sc.log_scales, reinterpret_cast<const float4 *>(sc.quats),
-                                                sc.opacity_logits, cam, op, w, vec_ok,
-                                                reinterpret_cast<float2 *>(mean2d), cov2d, depth,
+  k_project<<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d, depth,
                                                 reinterpret_cast<short4 *>(rect), ntiles);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;

@@ -36,6 +36,74 @@ struct DevOpts {
   int rs_iters, newton_iters;
 };
 
+// ---------------------------------------------------------------- batches of views
+//
+// Every kernel works on a batch of V views (a camera looking at one of S scenes).  The
+// particles of all views are flattened (view v owns entries [part_off, part_off + n) of the
+// projection arrays) and so are the tiles (view v owns global tiles [tile_off, tile_off +
+// tiles_x * tiles_y)).  The descriptor travels as a __grid_constant__ kernel parameter, so a
+// batch needs no host-to-device copy.  A single-view call is the batch V = S = 1.
+constexpr int kMaxViews = 32;
+constexpr int kMaxScenes = 8;
+
+struct DevView {
+  DevCam cam;
+  int scene;
+  int part_off, n;             // flattened particle range of this view
+  int tile_off, tiles_x, tiles_y;
+  float *rgb, *alpha, *tfinal;  // outputs ([3][H][W], [H][W], [H][W]); tfinal may be null
+  uint32_t *n_used;             // [H][W], may be null
+  const float *d_rgb, *d_alpha; // backward inputs
+};
+
+struct DevScene {
+  const float *means, *log_scales;
+  const float4 *quats;
+  const float *logits, *sh;
+  int n, deg;
+  float *gacc;                  // backward accumulators [n][16]
+  float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
+  int grad_off;                 // flattened offset of this scene in finalize's range
+  int sh_vec;                   // sh is 16-byte aligned and (deg+1)^2 * 3 is a multiple of 4
+};
+
+struct BatchDesc {
+  int nv, ns;
+  int total_particles, total_tiles;
+  DevView v[kMaxViews];
+  DevScene s[kMaxScenes];
+};
+
+// View owning flattened particle g (views are sorted by part_off).
+__device__ __forceinline__ int view_of_particle(const BatchDesc &b, int g) {
+  int lo = 0, hi = b.nv - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.v[mid].part_off <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// View owning global tile t.
+__device__ __forceinline__ int view_of_tile(const BatchDesc &b, int t) {
+  int lo = 0, hi = b.nv - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.v[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Scene owning flattened gradient index g (scenes are sorted by grad_off).
+__device__ __forceinline__ int scene_of_grad(const BatchDesc &b, int g) {
+  int lo = 0, hi = b.ns - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.s[mid].grad_off <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ float3 mat3_mul(const float *R, float3 v) {
   return make_float3(fmaf(R[0], v.x, fmaf(R[1], v.y, R[2] * v.z)), fmaf(R[3], v.x, fmaf(R[4], v.y, R[5] * v.z)),
                      fmaf(R[6], v.x, fmaf(R[7], v.y, R[8] * v.z)));

@@ -9,8 +9,8 @@
 
 namespace ut3d {
 
-struct DevCam;
 struct DevOpts;
+struct BatchDesc;
 
 // Unscented-Transform spread and weights (eq. weights_1/2), computed on the host in FP64.
 struct UTWeights {
@@ -21,32 +21,31 @@ struct UTWeights {
 };
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Process-wide count of kernel launches (ut_kernel_launch_count); every launch site adds to it.
 void count_launches(int k);
-inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // SM count of the current device (cached per device).
 int device_sm_count();
 
-ut_status launch_project(int n, const ut_scene &sc, const DevCam &cam, const DevOpts &op, const UTWeights &w,
-                         float *mean2d, float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles,
-                         cudaStream_t stream);
+// Projection of every flattened (view, particle) entry of the batch.
+ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights &w, float *mean2d, float *cov2d,
+                         float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream);
 
+// Duplicate + sort + ranges over the batch's flattened entries and global tiles.
 size_t bin_workspace_bytes(int n, int64_t cap, int tiles);
-ut_status launch_bin(int n, const float *depth, const int16_t *rect, const uint32_t *ntiles, const DevOpts &op,
-                     int tiles, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
+ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                     const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                      int64_t *k_out, cudaStream_t stream);
 
-ut_status launch_composite_fwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
-                               const uint32_t *vals, const uint32_t *ranges, float *rgb, float *alpha,
-                               float *t_final, uint32_t *n_used, unsigned long long *stats, cudaStream_t stream);
+// Compositing of every global tile of the batch into the views' outputs.
+ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                               const uint32_t *ranges, unsigned long long *stats, cudaStream_t stream);
 
+// Backward of the batch into the scenes' gradient outputs (accumulators cleared here).
 size_t backward_workspace_bytes(int n);
-ut_status launch_composite_bwd(const ut_scene &sc, const DevCam &cam, const DevOpts &op, const int16_t *rect,
-                               const uint32_t *vals, const uint32_t *ranges, const float *rgb, const float *t_final,
-                               const uint32_t *n_used, const float *d_rgb, const float *d_alpha, void *ws,
-                               float *d_means, float *d_log_scales, float *d_quats, float *d_logits, float *d_sh,
-                               cudaStream_t stream);
+ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                               const uint32_t *ranges, cudaStream_t stream);
 
 }  // namespace ut3d

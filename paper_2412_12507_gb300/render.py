@@ -240,3 +240,120 @@ class RenderFunction(torch.autograd.Function):
 def render(means, log_scales, quats, opacity_logits, sh, sh_degree: int, renderer: Renderer):
     """Differentiable render through the C ABI; returns (rgb[3,H,W], alpha[H,W])."""
     return RenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, sh_degree)
+
+
+# ---------------------------------------------------------------- batches of views
+
+def _frame_for(cam: dict, dev, grad: bool) -> Frame:
+    W, H = int(cam["width"]), int(cam["height"])
+    return Frame(torch.empty((3, H, W), dtype=torch.float32, device=dev),
+                 torch.empty((H, W), dtype=torch.float32, device=dev),
+                 torch.empty((H, W), dtype=torch.float32, device=dev) if grad else None,
+                 torch.empty((H, W), dtype=torch.int32, device=dev) if grad else None)
+
+
+@dataclass
+class BatchRenderer:
+    """render_batch / render_batch_backward: several (scene, camera) views in one launch
+    sequence.  views = list of (scene index, camera dict)."""
+    scenes: list
+    opts: dict | None = None
+    capacity: int = 1 << 20
+    growth: float = 1.25
+    ws: Workspace = field(default_factory=Workspace)
+    gws: Workspace = field(default_factory=Workspace)
+    k_dev: torch.Tensor | None = None
+    last: tuple | None = None
+
+    def _structs(self, views, frames, d_rgb=None, d_alpha=None):
+        sc = (abi.UtScene * len(self.scenes))(*[s.struct() for s in self.scenes])
+        vw = (abi.UtView * len(views))()
+        for j, ((si, cam), f) in enumerate(zip(views, frames)):
+            v = vw[j]
+            v.scene = int(si)
+            v.camera = abi.make_camera(cam)
+            v.rgb, v.alpha = _ptr(f.rgb), _ptr(f.alpha)
+            v.t_final, v.n_used = _ptr(f.t_final), _ptr(f.n_used)
+            if d_rgb is not None:
+                v.d_rgb, v.d_alpha = _ptr(d_rgb[j]), _ptr(d_alpha[j])
+        return sc, vw
+
+    def forward(self, views, frames=None, grad: bool = False, sync_check: bool = True):
+        """Renders every view; returns its Frame list (t_final / n_used kept when grad)."""
+        dev = self.scenes[0].means.device
+        if frames is None:
+            frames = [_frame_for(cam, dev, grad) for _, cam in views]
+        if self.k_dev is None:
+            self.k_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        o, u = abi.make_options(self.opts), abi.make_params(self.opts)
+        L = abi.lib()
+        while True:
+            sc, vw = self._structs(views, frames)
+            nbytes = L.ut_batch_workspace_size(sc, len(self.scenes), vw, len(views), C.byref(o), self.capacity)
+            if nbytes == 0:
+                raise abi.UtError("ut_batch_workspace_size", abi.UT_ERR_INVALID_ARG, "invalid batch")
+            w = self.ws.get(nbytes, dev)
+            st = L.render_batch(sc, len(self.scenes), vw, len(views), C.byref(u), C.byref(o), _ptr(w), w.numel(),
+                                self.capacity, _ptr(self.k_dev), _stream())
+            abi.check("render_batch", st)
+            if not sync_check:
+                break
+            K = int(self.k_dev.item())
+            if K <= self.capacity:
+                break
+            self.capacity = int(K * self.growth) + 1
+        self.last = (views, frames, w, self.capacity)
+        return frames
+
+    def backward(self, d_rgb, d_alpha):
+        """Gradients of every scene for the views of the last forward; d_rgb / d_alpha: per view."""
+        views, frames, w, cap = self.last
+        dev = self.scenes[0].means.device
+        d_rgb = [t.contiguous() for t in d_rgb]
+        d_alpha = [t.contiguous() for t in d_alpha]
+        grads = [dict(means=torch.empty_like(s.means), log_scales=torch.empty_like(s.log_scales),
+                      quats=torch.empty_like(s.quats), opacity_logits=torch.empty_like(s.opacity_logits),
+                      sh=torch.empty_like(s.sh)) for s in self.scenes]
+        gs = (abi.UtSceneGrads * len(self.scenes))(*[
+            abi.UtSceneGrads(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logits"]),
+                             _ptr(g["sh"])) for g in grads])
+        sc, vw = self._structs(views, frames, d_rgb, d_alpha)
+        L = abi.lib()
+        gw = self.gws.get(L.ut_batch_backward_workspace_size(sc, len(self.scenes)), dev)
+        o = abi.make_options(self.opts)
+        st = L.render_batch_backward(sc, len(self.scenes), vw, len(views), C.byref(o), _ptr(w), w.numel(), cap,
+                                     _ptr(gw), gw.numel(), gs, _stream())
+        abi.check("render_batch_backward", st)
+        return grads
+
+
+class MultiViewRenderFunction(torch.autograd.Function):
+    """One scene rendered from several cameras in one batch: (params) -> (rgb_0, alpha_0, rgb_1, ...)."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, renderer: BatchRenderer, cams, sh_degree: int):
+        scene = Scene(means.detach().contiguous(), log_scales.detach().contiguous(), quats.detach().contiguous(),
+                      opacity_logits.detach().contiguous(), sh.detach().contiguous(), sh_degree)
+        renderer.scenes = [scene]
+        views = [(0, c) for c in cams]
+        frames = renderer.forward(views, grad=True)
+        ctx.renderer = renderer
+        out = []
+        for f in frames:
+            out += [f.rgb, f.alpha]
+        return tuple(t.clone() for t in out)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        r = ctx.renderer
+        views, frames = r.last[0], r.last[1]
+        d_rgb = [g if g is not None else torch.zeros_like(f.rgb) for g, f in zip(grads[0::2], frames)]
+        d_alpha = [g if g is not None else torch.zeros_like(f.alpha) for g, f in zip(grads[1::2], frames)]
+        g = r.backward(d_rgb, d_alpha)[0]
+        return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None, None
+
+
+def render_views(means, log_scales, quats, opacity_logits, sh, sh_degree: int, cams, renderer: BatchRenderer):
+    """Differentiable multi-view render of one scene in one batch; returns [(rgb, alpha)] per camera."""
+    out = MultiViewRenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, cams, sh_degree)
+    return [(out[2 * j], out[2 * j + 1]) for j in range(len(cams))]

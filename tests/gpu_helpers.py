@@ -39,7 +39,8 @@ def to_np(t):
 
 def frame_at(frame, px, py):
     rgb = to_np(frame.rgb)
-    return rgb[:, py, px].T, to_np(frame.alpha)[py, px], to_np(frame.t_final)[py, px]
+    tf = to_np(frame.t_final)[py, px] if frame.t_final is not None else None
+    return rgb[:, py, px].T, to_np(frame.alpha)[py, px], tf
 
 
 def compare_frame(frame, ref, tol=RGB_TOL):

@@ -1,0 +1,171 @@
+"""Batches of views (render_batch / render_batch_backward) through the C ABI.
+
+A batch must render every view exactly as the single-view path does (the single-view calls
+are the batch of one view), match the FP64 oracle view by view, and propagate the gradients
+of all views into their scenes (views sharing a scene add up).
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_helpers import TOL, compare_frame, to_np  # noqa: E402
+from paper_2412_12507_gb300 import abi, render, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2412_12507_gb300 import build
+    build.build()
+    abi.lib()
+
+
+def _scenes():
+    a = synth.scene_shell(6000, 41, radius=3.0, radial_std=0.2, log_s=(-3.5, 0.5), logit_std=1.0, deg=3)
+    b = synth.scene_cube(4000, 42, log_s=(-3.0, 0.4), deg=3)
+    return [a, b]
+
+
+def _cams():
+    qe, te = synth.rs_end_pose(0.05, 2.0)
+    q1, t1 = synth.look_at_pose([0.5, -0.3, -2.5])
+    return [
+        (1, synth.camera("pinhole", 160, 96, fx=140.0, fy=140.0)),
+        (0, synth.camera("fisheye", 200, 150, k=[0.01, -0.02, 0.005, 0.0])),
+        (1, synth.camera("fisheye", 176, 99, k=[0.02, 0.01, -0.004, 0.001], q_end=qe, t_end=te, rolling_shutter=1)),
+        (0, synth.camera("pinhole", 128, 128, fx=100.0, fy=100.0, q=q1, t=t1)),
+        (1, synth.camera("pinhole", 64, 48, fx=60.0, fy=60.0)),
+    ]
+
+
+def _single(scene_np, cam, op):
+    scene = render.Scene.from_arrays(scene_np)
+    r = render.Renderer(cam, op, capacity=1 << 12)
+    f = r.forward(scene)
+    torch.cuda.synchronize()
+    return f
+
+
+def test_global_shutter_batch_is_bit_identical_to_single_views():
+    """All-global-shutter batch: same kernels, same per-pixel particle sequence -> identical bits."""
+    scenes_np = _scenes()
+    op = synth.options()
+    views = [v for v in _cams() if not v[1]["rolling_shutter"]]
+    br = render.BatchRenderer([render.Scene.from_arrays(s) for s in scenes_np], op, capacity=1 << 12)
+    frames = br.forward(views)
+    torch.cuda.synchronize()
+    for (si, cam), f in zip(views, frames):
+        g = _single(scenes_np[si], cam, op)
+        assert torch.equal(f.rgb, g.rgb) and torch.equal(f.alpha, g.alpha)
+
+
+def test_mixed_batch_matches_single_views_and_oracle():
+    scenes_np = _scenes()
+    op = synth.options()
+    views = _cams()
+    br = render.BatchRenderer([render.Scene.from_arrays(s) for s in scenes_np], op, capacity=1 << 12)
+    frames = br.forward(views)
+    torch.cuda.synchronize()
+    assert br.capacity >= int(br.k_dev.item())
+    for (si, cam), f in zip(views, frames):
+        g = _single(scenes_np[si], cam, op)
+        # views of a batch with a rolling-shutter member take the general ray-origin path
+        assert torch.max(torch.abs(f.rgb - g.rgb)).item() < 2e-5
+        ref = oracle.render(scenes_np[si], cam, op, proj=oracle.project(scenes_np[si], cam, op, TOL), tol=TOL)
+        r = compare_frame(f, ref)
+        assert r["n_bad"] == 0, (cam["model"], r)
+        assert r["n_flagged"] <= 0.03 * r["n"], r
+
+
+def test_batch_capacity_overflow_is_reported_and_retried():
+    scenes_np = _scenes()
+    op = synth.options()
+    views = _cams()[:2]
+    br = render.BatchRenderer([render.Scene.from_arrays(s) for s in scenes_np], op, capacity=16)
+    frames = br.forward(views, sync_check=False)
+    torch.cuda.synchronize()
+    K = int(br.k_dev.item())
+    assert K > 16
+    assert not any(to_np(f.rgb).any() for f in frames)  # overflowing batch renders nothing
+    frames = br.forward(views)  # grows the capacity and retries
+    torch.cuda.synchronize()
+    assert br.capacity >= K and any(to_np(f.rgb).any() for f in frames)
+
+
+def test_batch_validation():
+    scenes_np = _scenes()
+    op = synth.options()
+    sc = [render.Scene.from_arrays(s) for s in scenes_np]
+    br = render.BatchRenderer(sc, op)
+    views = [(0, synth.camera("pinhole", 32, 32, fx=30.0))] * (abi.MAX_BATCH_VIEWS + 1)
+    with pytest.raises(abi.UtError):
+        br.forward(views)
+    with pytest.raises(abi.UtError):
+        br.forward([(5, synth.camera("pinhole", 32, 32, fx=30.0))])
+    mixed = [sc[0], render.Scene.from_arrays(synth.scene_cube(100, 1, deg=1))]
+    with pytest.raises(abi.UtError):
+        render.BatchRenderer(mixed, op).forward([(0, synth.camera("pinhole", 32, 32, fx=30.0))])
+
+
+def test_batch_backward_sums_views_of_a_scene():
+    """Three views of one scene plus one of another: each scene's gradient equals the sum of
+    its views' single-view gradients and the FP64 oracle's."""
+    scenes_np = _scenes()
+    op = synth.options()
+    views = [_cams()[k] for k in (0, 2, 4, 1)]  # scene 1 three times, scene 0 once
+    br = render.BatchRenderer([render.Scene.from_arrays(s) for s in scenes_np], op, capacity=1 << 12)
+    frames = br.forward(views, grad=True)
+    rng = np.random.default_rng(5)
+    d_rgb, d_a, refs = [], [], [dict(), dict()]
+    for (si, cam), f in zip(views, frames):
+        H, W = cam["height"], cam["width"]
+        pr = oracle.project(scenes_np[si], cam, op, TOL)
+        rf = oracle.render(scenes_np[si], cam, op, proj=pr, tol=TOL)
+        keep = (rf["flags"] & (oracle.F_FORWARD_TIES | oracle.F_ALPHA_MAX | oracle.F_TSTOP)) == 0
+        w_rgb = rng.standard_normal((H * W, 3)) * keep[:, None]
+        w_a = rng.standard_normal(H * W) * keep
+        d_rgb.append(torch.as_tensor(w_rgb.T.reshape(3, H, W).astype(np.float32)).cuda())
+        d_a.append(torch.as_tensor(w_a.reshape(H, W).astype(np.float32)).cuda())
+        g = oracle.backward(scenes_np[si], cam, op, pr, (rf["px"], rf["py"]), w_rgb, w_a)
+        for k, v in g.items():
+            refs[si][k] = refs[si].get(k, 0) + v
+    grads = br.backward(d_rgb, d_a)
+    torch.cuda.synchronize()
+    for si in (0, 1):
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            got = to_np(grads[si][k]).astype(np.float64).reshape(-1)
+            ref = refs[si][k].reshape(-1)
+            e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            assert e < 1e-3, (si, k, e)
+
+
+def test_multiview_autograd_matches_batch_backward():
+    scene_np = _scenes()[1]
+    op = synth.options()
+    cams = [c for s, c in _cams() if s == 1]
+    scene = render.Scene.from_arrays(scene_np)
+    leaves = [t.clone().requires_grad_(True) for t in (scene.means, scene.log_scales, scene.quats,
+                                                        scene.opacity_logits, scene.sh)]
+    br = render.BatchRenderer([scene], op, capacity=1 << 12)
+    outs = render.render_views(*leaves, scene.sh_degree, cams, br)
+    loss = sum((rgb ** 2).sum() + alpha.sum() for rgb, alpha in outs)
+    loss.backward()
+    torch.cuda.synchronize()
+    # same gradient via single-view autograd calls, summed
+    tot = [torch.zeros_like(t) for t in leaves]
+    for cam in cams:
+        ls = [t.detach().clone().requires_grad_(True) for t in leaves]
+        rgb, alpha = render.render(*ls, scene.sh_degree, render.Renderer(cam, op, capacity=1 << 12))
+        ((rgb ** 2).sum() + alpha.sum()).backward()
+        for a, b in zip(tot, ls):
+            a += b.grad
+    for a, b in zip(leaves, tot):
+        e = (torch.linalg.norm(a.grad - b) / torch.linalg.norm(b)).item()
+        assert e < 1e-4, e
