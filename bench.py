@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--workload", default="rs_fisheye_1m_1080p")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle's CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="measured serving requests (0: skip)")
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests / s")
+    ap.add_argument("--serve-arena-gb", type=float, default=64.0)
     return ap.parse_args()
 
 
@@ -170,6 +174,102 @@ def run_reference(args):
 
 
 METRIC = "Mpix/s fwd & fwd+bwd ms/view, 1M Gaussians fisheye 1080p; serve p50/p99 ms"
+
+
+# ---------------------------------------------------------------- serving workload
+
+def serving_requests(n, rate, seed=4):
+    """Poisson arrivals at `rate` req/s; each request picks a scene U{4}, a camera model
+    U{pinhole, fisheye, rolling-shutter fisheye} and a resolution U{640x480, 1280x720,
+    1920x1080, 3840x2160}, posed on a radius-4 orbit around the scenes."""
+    from paper_2412_12507_gb300 import synth
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    res = [(640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+    specs, scenes = [], []
+    for _ in range(n):
+        m = int(rng.integers(3))
+        W, H = res[int(rng.integers(4))]
+        specs.append(("pinhole" if m == 0 else "fisheye", W, H, int(m == 2)))
+        scenes.append(int(rng.integers(4)))
+    cams = synth.orbit_cameras(seed, specs)
+    return [(float(t[j]), scenes[j], cams[j]) for j in range(n)]
+
+
+def serving_scenes(dev, sizes=(200_000, 1_000_000, 3_000_000, 6_000_000)):
+    """Four resident scenes generated like the 1M workload (box of side 2 at the origin,
+    log-scales N(-3, 0.5), SH degree 3)."""
+    from paper_2412_12507_gb300 import render, synth
+    return [render.Scene.from_arrays(synth.scene_cube(n, 10 + j, log_s=(-3.0, 0.5), deg=3, lo=(-1, -1, -1),
+                                                      hi=(1, 1, 1)), dev) for j, n in enumerate(sizes)]
+
+
+def run_serving(scenes, opts, reqs, n_warm, arena_bytes, max_batch_views=8, max_in_flight=3, use_graphs=True):
+    """Replays the arrival trace against the library's server; returns latencies (ms) and the
+    wall time of the measured part."""
+    import torch
+
+    from paper_2412_12507_gb300 import render
+    srv = render.Server(scenes, opts, arena_bytes=arena_bytes, max_batch_views=max_batch_views,
+                        max_in_flight=max_in_flight, use_graphs=use_graphs)
+    ids = [None] * len(reqs)
+    lag = [0.0] * len(reqs)
+    lat = [0.0] * len(reqs)
+    t_done = [0.0] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for j, (ta, s, cam) in enumerate(reqs):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= ta:
+                    break
+                time.sleep(min(0.0005, ta - now))
+            ids[j] = srv.submit(s, cam)
+            lag[j] = (time.perf_counter() - t0) - ta
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    for j in range(len(reqs)):
+        while ids[j] is None:
+            time.sleep(0.0001)
+        out = srv.wait(ids[j], 600_000)
+        if out is None:
+            raise SystemExit("serving: a request did not complete")
+        lat[j] = out[2] + 1e3 * lag[j]
+        t_done[j] = time.perf_counter() - t0
+        srv.release(ids[j])
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+    meas = slice(n_warm, len(reqs))
+    wall = max(t_done[meas]) - reqs[n_warm][0]
+    return np.array(lat[meas]), wall, stats
+
+
+def run_plain(scenes, opts, reqs, n_warm):
+    """The same trace through one plain single-view render call per request, in arrival order."""
+    import torch
+
+    from paper_2412_12507_gb300 import render
+    ws, caps = render.Workspace(), {}
+    lat, t_done = [], []
+    t0 = time.perf_counter()
+    for j, (ta, s, cam) in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        key = (s, cam["model"], cam["width"], cam["height"])
+        r = render.Renderer(cam, opts, capacity=caps.get(key, 1 << 20), ws=ws)
+        r.forward(scenes[s])
+        torch.cuda.synchronize()
+        caps[key] = max(caps.get(key, 0), r.capacity)
+        t = time.perf_counter() - t0
+        lat.append(1e3 * (t - ta))
+        t_done.append(t)
+    meas = slice(n_warm, len(reqs))
+    return np.array(lat[meas]), max(t_done[meas]) - reqs[n_warm][0]
 
 
 # ---------------------------------------------------------------- our arm
@@ -321,6 +421,22 @@ def run_ours(args):
 
     e2e_ms = timed(e2e_step, max(3, args.steps // 2), 2)
 
+    serve = None
+    if args.serve_requests > 0:
+        sc_list = serving_scenes(dev)
+        reqs = serving_requests(args.serve_warmup + args.serve_requests, args.serve_rate)
+        pix = sum(c["width"] * c["height"] for _, _, c in reqs[args.serve_warmup:])
+        lat_s, wall_s, st = run_serving(sc_list, op, reqs, args.serve_warmup, int(args.serve_arena_gb * (1 << 30)))
+        lat_p, wall_p = run_plain(sc_list, op, reqs, args.serve_warmup)
+        serve = {"requests": args.serve_requests, "warmup_requests": args.serve_warmup, "rate_req_s": args.serve_rate,
+                 "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+                 "mean_ms": float(lat_s.mean()), "mpix_s": pix / wall_s / 1e6,
+                 "plain_p50_ms": float(np.percentile(lat_p, 50)), "plain_p99_ms": float(np.percentile(lat_p, 99)),
+                 "plain_mpix_s": pix / wall_p / 1e6, "offered_mpix_s": pix / (reqs[-1][0] - reqs[args.serve_warmup][0]) / 1e6,
+                 "server": st, "scenes": [s.n for s in sc_list]}
+        del sc_list
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         f_s, desc, thr = oracle_frame_time(case, args.cpu_seconds)
@@ -342,6 +458,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
             "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -271,6 +271,61 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
                                 int64_t key_capacity, void *grad_workspace, size_t grad_workspace_bytes,
                                 const ut_scene_grads *grads, ut_stream stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: a device-resident request loop (no counterpart in the paper; the paper renders one
+ * image at a time).  Scenes stay resident (caller-owned device memory).  Requests (scene,
+ * camera) are submitted from any host thread and return immediately; a worker thread admits
+ * pending requests as memory in the caller's device arena frees up (each request needs its
+ * output image; each batch its render_batch workspace), groups up to max_batch_views of them
+ * into one render_batch launch sequence (optionally captured and replayed as a CUDA graph),
+ * and keeps up to max_in_flight batches on the GPU at once on separate streams, so requests
+ * that arrive while others render overlap with them on the device.  Completion is detected
+ * with CUDA events polled on the host; no kernel waits on anything.  A batch whose key count
+ * overflowed its capacity is re-run with a larger capacity before its requests complete.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct ut_server ut_server;
+
+typedef struct {
+  int32_t max_batch_views; /* 1..UT_MAX_BATCH_VIEWS views per launch sequence */
+  int32_t max_in_flight;   /* 1..8 batches concurrently on the GPU (one stream each) */
+  int32_t use_graphs;      /* 1: capture each batch's launches and replay them as a CUDA graph */
+  float key_headroom;      /* key capacity = headroom x (estimated keys); >= 1, e.g. 1.3 */
+  ut_options options;      /* renderer knobs shared by all requests */
+  ut_params ut;            /* UT parameters shared by all requests */
+} ut_server_config;
+
+/* Creates a server over n_scenes resident scenes (1..UT_MAX_BATCH_SCENES, same sh_degree; the
+ * arrays must stay valid until ut_server_destroy) and a caller-owned device arena of
+ * arena_bytes (256-byte aligned) from which it carves outputs and workspaces.  Starts the
+ * worker thread.  The calling thread's current device is the server's device. */
+ut_status ut_server_create(const ut_server_config *cfg, const ut_scene *scenes, int32_t n_scenes, void *arena,
+                           size_t arena_bytes, ut_server **out);
+
+/* Queues a request; *id identifies it.  UT_ERR_CAPACITY if the request alone can never fit
+ * the arena. */
+ut_status ut_server_submit(ut_server *s, int32_t scene, const ut_camera *cam, uint64_t *id);
+
+/* Waits up to timeout_ms (0 = just poll) for request id.  On completion sets *done = 1 and
+ * returns device pointers to its rgb[3][H][W] and alpha[H][W] (valid until released) and its
+ * latency in ms from submission to completion; otherwise *done = 0 (UT_ERR_TIMEOUT only if
+ * timeout_ms > 0 elapsed).  Errors of the request's batch are reported here. */
+ut_status ut_server_wait(ut_server *s, uint64_t id, int32_t timeout_ms, int32_t *done, const float **rgb,
+                         const float **alpha, double *latency_ms);
+
+/* Releases a completed request's output memory back to the arena. */
+ut_status ut_server_release(ut_server *s, uint64_t id);
+
+/* Counters since creation: completed requests, batches launched, key-capacity retries, graph
+ * replays, graph (re)instantiations. */
+typedef struct {
+  uint64_t completed, batches, retries, graph_launches, graph_instantiations;
+} ut_server_stats;
+ut_status ut_server_get_stats(ut_server *s, ut_server_stats *stats);
+
+/* Stops the worker after the batches in flight complete (bounded wait) and frees host state.
+ * Pending requests are dropped.  The arena is the caller's to free. */
+ut_status ut_server_destroy(ut_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,16 @@ class UtSceneGrads(C.Structure):
                 ("d_opacity_logits", C.c_void_p), ("d_sh", C.c_void_p)]
 
 
+class UtServerConfig(C.Structure):
+    _fields_ = [("max_batch_views", C.c_int32), ("max_in_flight", C.c_int32), ("use_graphs", C.c_int32),
+                ("key_headroom", C.c_float), ("options", UtOptions), ("ut", UtParams)]
+
+
+class UtServerStats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("batches", C.c_uint64), ("retries", C.c_uint64),
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
+
+
 MAX_BATCH_VIEWS = 32
 MAX_BATCH_SCENES = 8
 
@@ -78,6 +88,14 @@ SIGNATURES = {
     "render_batch": (C.c_int, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtParams), C.POINTER(UtOptions), _P,
                                C.c_size_t, C.c_int64, _P, _P]),
     "ut_batch_backward_workspace_size": (C.c_size_t, [_SC, C.c_int32]),
+    "ut_server_create": (C.c_int, [C.POINTER(UtServerConfig), _SC, C.c_int32, _P, C.c_size_t,
+                                   C.POINTER(C.c_void_p)]),
+    "ut_server_submit": (C.c_int, [_P, C.c_int32, C.POINTER(UtCamera), C.POINTER(C.c_uint64)]),
+    "ut_server_wait": (C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_void_p),
+                                 C.POINTER(C.c_void_p), C.POINTER(C.c_double)]),
+    "ut_server_release": (C.c_int, [_P, C.c_uint64]),
+    "ut_server_get_stats": (C.c_int, [_P, C.POINTER(UtServerStats)]),
+    "ut_server_destroy": (C.c_int, [_P]),
     "render_batch_backward": (C.c_int, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtOptions), _P, C.c_size_t,
                                         C.c_int64, _P, C.c_size_t, C.POINTER(UtSceneGrads), _P]),
     "composite_backward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,

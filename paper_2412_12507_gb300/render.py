@@ -357,3 +357,73 @@ def render_views(means, log_scales, quats, opacity_logits, sh, sh_degree: int, c
     """Differentiable multi-view render of one scene in one batch; returns [(rgb, alpha)] per camera."""
     out = MultiViewRenderFunction.apply(means, log_scales, quats, opacity_logits, sh, renderer, cams, sh_degree)
     return [(out[2 * j], out[2 * j + 1]) for j in range(len(cams))]
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """The library's request loop (ut_server_*): resident scenes, requests submitted from the
+    host, admitted by the budget of a device arena, batched into render_batch launches on
+    several streams.  Results are views into the arena, valid until released."""
+
+    def __init__(self, scenes: list, opts: dict | None = None, arena_bytes: int = 1 << 32,
+                 max_batch_views: int = 8, max_in_flight: int = 2, use_graphs: bool = True,
+                 key_headroom: float = 1.3):
+        self.scenes = scenes
+        dev = scenes[0].means.device
+        self.arena_buf = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device=dev)
+        off = (-self.arena_buf.data_ptr()) % 256
+        self.arena = self.arena_buf[off:off + int(arena_bytes)]
+        cfg = abi.UtServerConfig(int(max_batch_views), int(max_in_flight), int(use_graphs), float(key_headroom),
+                                 abi.make_options(opts), abi.make_params(opts))
+        self._sc = (abi.UtScene * len(scenes))(*[s.struct() for s in scenes])
+        h = C.c_void_p()
+        torch.cuda.synchronize()  # scenes and arena must exist before the worker uses them
+        abi.check("ut_server_create", abi.lib().ut_server_create(C.byref(cfg), self._sc, len(scenes),
+                                                                 _ptr(self.arena), int(arena_bytes), C.byref(h)))
+        self.h = h
+        self.cams = {}
+
+    def submit(self, scene: int, cam: dict) -> int:
+        rid = C.c_uint64()
+        c = abi.make_camera(cam)
+        abi.check("ut_server_submit", abi.lib().ut_server_submit(self.h, int(scene), C.byref(c), C.byref(rid)))
+        self.cams[rid.value] = cam
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 10_000):
+        """Returns (rgb[3,H,W], alpha[H,W], latency_ms) views into the arena, or None if not done."""
+        done, rgb, alpha, lat = C.c_int32(), C.c_void_p(), C.c_void_p(), C.c_double()
+        st = abi.lib().ut_server_wait(self.h, int(rid), int(timeout_ms), C.byref(done), C.byref(rgb),
+                                      C.byref(alpha), C.byref(lat))
+        if st == abi.UT_ERR_TIMEOUT:
+            return None
+        abi.check("ut_server_wait", st)
+        if not done.value:
+            return None
+        cam = self.cams[rid]
+        W, H = int(cam["width"]), int(cam["height"])
+        base = self.arena.data_ptr()
+        o = rgb.value - base
+        img = self.arena[o:o + 16 * W * H].view(torch.float32)
+        return img[:3 * W * H].view(3, H, W), img[3 * W * H:].view(H, W), lat.value
+
+    def release(self, rid: int):
+        abi.check("ut_server_release", abi.lib().ut_server_release(self.h, int(rid)))
+        self.cams.pop(rid, None)
+
+    def stats(self) -> dict:
+        s = abi.UtServerStats()
+        abi.check("ut_server_get_stats", abi.lib().ut_server_get_stats(self.h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in abi.UtServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            abi.check("ut_server_destroy", abi.lib().ut_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
