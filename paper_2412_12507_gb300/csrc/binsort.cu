@@ -11,9 +11,9 @@
 // while step 2 moves 8 bytes per entry per pass over ceil(log2 T / 8) passes instead of
 // 12 bytes over ceil((32 + log2 T) / 8) passes.
 //
-// The radix sort is the project's own: per 8-bit digit pass an upsweep (block digit
-// histograms, warp-aggregated shared-memory atomics), a digit-major exclusive scan, and a
-// downsweep that ranks keys stably in shared memory (__match_any_sync per 32-key group,
+// The radix sort is the project's own: per 8-bit digit pass an upsweep (per-warp shared
+// histograms fed by uint4 key loads), a digit-major exclusive scan, and a downsweep that
+// ranks keys stably in shared memory (same-digit lanes found with 8 ballots per 32-key group,
 // per-warp running digit counters) and writes them out digit-grouped for coalescing.
 // No kernel waits on another block, so nothing in here can spin.
 #include "ut3d_device.cuh"
@@ -25,7 +25,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kIPT = 16;
-constexpr int kTile = kThreads * kIPT;  // keys per radix / scan tile
+constexpr int kTile = kThreads * kIPT;  // keys per scan tile
+constexpr int kRIPT = 8;                 // keys per thread in a radix tile
+constexpr int kRTile = kThreads * kRIPT; // keys per radix tile (upsweep and downsweep agree)
 constexpr int kRadixBits = 8;
 
 typedef unsigned long long u64;
@@ -49,7 +51,7 @@ struct SpineLen {
   int nd;
   __device__ __forceinline__ uint32_t get() const {
     uint32_t k = c.get();
-    return (uint32_t)nd * ((k + kTile - 1) / kTile);
+    return (uint32_t)nd * ((k + kRTile - 1) / kRTile);
   }
 };
 
@@ -177,26 +179,52 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint
 
 // ---------------------------------------------------------------- radix sort passes
 
+
+// Lanes of this warp whose 8-bit digit equals mine, from 8 ballots (one per digit bit).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int bit = 0; bit < 8; ++bit) {
+    const bool one = (d >> bit) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, one);
+    peers &= one ? bal : ~bal;
+  }
+  return peers;
+}
+
+// Per radix tile, the count of each digit (digit-major layout counts[d * nb + b]).  Keys are
+// read as uint4; every warp counts into its own shared histogram.
 __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t *__restrict__ keys, Count cnt, int shift,
                                                             uint32_t mask, uint32_t *__restrict__ counts) {
-  __shared__ uint32_t s_hist[256];
+  __shared__ uint32_t s_wh[kWarps][256];
   const uint32_t n = cnt.get();
-  const uint32_t nb = (n + kTile - 1) / kTile;
-  const int lane = threadIdx.x & 31;
+  const uint32_t nb = (n + kRTile - 1) / kRTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *wh = s_wh[warp];
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    s_hist[threadIdx.x] = 0;
-    __syncthreads();
-    uint32_t base = b * kTile;
-#pragma unroll 4
-    for (int i = 0; i < kIPT; ++i) {
-      uint32_t p = base + i * kThreads + threadIdx.x;
-      bool valid = p < n;
-      uint32_t d = valid ? (keys[p] >> shift) & mask : 0xffffffffu;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_hist[d], (uint32_t)__popc(peers));
+    for (int d = lane; d < 256; d += 32) wh[d] = 0;
+    __syncwarp();
+    const uint32_t base = b * kRTile;
+    if (base + kRTile <= n) {
+      const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+      for (int i = 0; i < kRIPT / 4; ++i) {
+        uint4 q = k4[i * kThreads + threadIdx.x];
+        atomicAdd(&wh[(q.x >> shift) & mask], 1u);
+        atomicAdd(&wh[(q.y >> shift) & mask], 1u);
+        atomicAdd(&wh[(q.z >> shift) & mask], 1u);
+        atomicAdd(&wh[(q.w >> shift) & mask], 1u);
+      }
+    } else {
+      for (uint32_t p = base + threadIdx.x; p < n; p += kThreads) atomicAdd(&wh[(keys[p] >> shift) & mask], 1u);
     }
     __syncthreads();
-    if (threadIdx.x <= mask) counts[(size_t)threadIdx.x * nb + b] = s_hist[threadIdx.x];
+    if (threadIdx.x <= mask) {
+      uint32_t s = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) s += s_wh[w][threadIdx.x];
+      counts[(size_t)threadIdx.x * nb + b] = s;
+    }
     __syncthreads();
   }
 }
@@ -206,23 +234,23 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
                                                               uint32_t *__restrict__ keys_out,
                                                               uint32_t *__restrict__ vals_out, Count cnt, int shift,
                                                               uint32_t mask, const uint32_t *__restrict__ offsets) {
-  __shared__ uint32_t s_k[kTile];
-  __shared__ uint32_t s_v[kTile];
+  __shared__ uint32_t s_k[kRTile];
+  __shared__ uint32_t s_v[kRTile];
   __shared__ uint32_t s_whist[kWarps][256];
   __shared__ uint32_t s_dstart[256];
   __shared__ uint32_t s_goff[256];
   __shared__ u64 s_warp[kWarps + 1];
   const uint32_t n = cnt.get();
-  const uint32_t nb = (n + kTile - 1) / kTile;
+  const uint32_t nb = (n + kRTile - 1) / kRTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int nd = (int)mask + 1;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint32_t base = b * kTile;
-    uint32_t k[kIPT], v[kIPT], rank[kIPT];
+    const uint32_t base = b * kRTile;
+    uint32_t k[kRIPT], v[kRIPT], rank[kRIPT];
 #pragma unroll
-    for (int i = 0; i < kIPT; ++i) {
-      uint32_t p = base + warp * (kIPT * 32) + i * 32 + lane;
+    for (int i = 0; i < kRIPT; ++i) {
+      uint32_t p = base + warp * (kRIPT * 32) + i * 32 + lane;
       bool valid = p < n;
       k[i] = valid ? keys_in[p] : 0xffffffffu;
       v[i] = valid ? vals_in[p] : 0u;
@@ -231,17 +259,13 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
     __syncwarp();
     // stable rank of every key among the same-digit keys of this warp's segment
 #pragma unroll
-    for (int i = 0; i < kIPT; ++i) {
-      uint32_t d = (k[i] >> shift) & mask;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      int leader = __ffs(peers) - 1;
-      uint32_t before = 0;
-      if (lane == leader) {
-        before = s_whist[warp][d];
-        s_whist[warp][d] = before + (uint32_t)__popc(peers);
-      }
-      before = __shfl_sync(0xffffffffu, before, leader);
+    for (int i = 0; i < kRIPT; ++i) {
+      const uint32_t d = (k[i] >> shift) & mask;
+      const uint32_t peers = digit_peers(d);
+      const uint32_t before = s_whist[warp][d];
       rank[i] = before + (uint32_t)__popc(peers & lt_mask);
+      __syncwarp();
+      if (lane == __ffs(peers) - 1) s_whist[warp][d] = before + (uint32_t)__popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -261,14 +285,14 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
     if (threadIdx.x < nd) s_dstart[threadIdx.x] = (uint32_t)ex;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kIPT; ++i) {
+    for (int i = 0; i < kRIPT; ++i) {
       uint32_t d = (k[i] >> shift) & mask;
       uint32_t pos = s_dstart[d] + s_whist[warp][d] + rank[i];
       s_k[pos] = k[i];
       s_v[pos] = v[i];
     }
     __syncthreads();
-    const uint32_t nvalid = min((uint32_t)kTile, n - base);
+    const uint32_t nvalid = min((uint32_t)kRTile, n - base);
     for (uint32_t j = threadIdx.x; j < nvalid; j += kThreads) {
       uint32_t kk = s_k[j];
       uint32_t d = (kk >> shift) & mask;
@@ -297,9 +321,8 @@ __global__ void k_gather_counts(int n, const uint32_t *__restrict__ order, const
 
 __global__ void k_write_kout(const u64 *__restrict__ total, int64_t *__restrict__ k_out) { *k_out = (int64_t)*total; }
 
-// One block per 256 consecutive particles of the depth order: the block's output span
-// [offs[first], offs[last+1]) is filled by consecutive threads (coalesced), each finding its
-// particle by binary search over the block's 257 offsets.
+// One warp per particle of the depth order: the warp fills the particle's contiguous run of
+// entries [offs[j], offs[j+1]) with consecutive lanes (coalesced), tiles in row-major order.
 // Entries of a batch: `order` holds flattened (view, particle) indices; the emitted key is
 // the global tile id (view's tile offset + row-major tile in the view) and the value is the
 // particle index within its scene.
@@ -308,57 +331,84 @@ __global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ Batch
                                                    const uint32_t *__restrict__ offs, const short4 *__restrict__ rect,
                                                    const u64 *__restrict__ total, u64 cap, int tile_w, int tile_h,
                                                    uint32_t *__restrict__ tkeys, uint32_t *__restrict__ vals) {
-  __shared__ uint32_t s_off[kThreads + 1];
-  __shared__ uint32_t s_idx[kThreads];
-  __shared__ int s_tx0[kThreads], s_ty0[kThreads], s_tw[kThreads], s_tx[kThreads];
   const u64 K = *total;
   if (K > cap) return;
-  const int first = blockIdx.x * kThreads;
-  if (first >= n) return;
-  const int cnt = min(kThreads, n - first);
-  const int t = threadIdx.x;
-  if (t < cnt) {
-    uint32_t g = order[first + t];
-    short4 r = rect[g];
-    const int v = view_of_particle(bd, (int)g);
-    s_off[t] = offs[first + t];
-    s_idx[t] = g - (uint32_t)bd.v[v].part_off;
-    int tx0 = r.x / tile_w, tx1 = r.z / tile_w, ty0 = r.y / tile_h;
-    // fold the view's tile offset into the start tile: tile = base + ty * tiles_x + tx
-    s_tx0[t] = bd.v[v].tile_off + tx0;
-    s_ty0[t] = ty0;
-    s_tx[t] = bd.v[v].tiles_x;
-    s_tw[t] = max(tx1 - tx0 + 1, 1);
-  }
-  if (t == 0) s_off[cnt] = (first + cnt < n) ? offs[first + cnt] : (uint32_t)K;
-  __syncthreads();
-  const uint32_t start = s_off[0], end = s_off[cnt];
-  for (uint32_t p = start + t; p < end; p += kThreads) {
-    int lo = 0, hi = cnt;  // largest q with s_off[q] <= p
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (s_off[mid] <= p) lo = mid; else hi = mid;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int j0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < n; j0 += nw * 32) {
+    // every lane fetches one of the 32 particles (independent loads in flight together)
+    const int j = j0 + lane;
+    uint32_t start = 0, cnt = 0, local = 0;
+    int base = 0, w = 1, tiles_x = 0;
+    if (j < n) {
+      start = offs[j];
+      const uint32_t end = (j + 1 < n) ? offs[j + 1] : (uint32_t)K;
+      cnt = end - start;
+      if (cnt) {
+        const uint32_t g = order[j];
+        const short4 r = rect[g];
+        const DevView &view = bd.v[view_of_particle(bd, (int)g)];
+        local = g - (uint32_t)view.part_off;
+        const int tx0 = r.x / tile_w, tx1 = r.z / tile_w, ty0 = r.y / tile_h;
+        w = tx1 - tx0 + 1;
+        tiles_x = view.tiles_x;
+        base = view.tile_off + ty0 * tiles_x + tx0;
+      }
     }
-    uint32_t local = p - s_off[lo];
-    int w = s_tw[lo];
-    int ty = (int)(local / (uint32_t)w);
-    int tx = (int)(local - (uint32_t)(ty * w));
-    tkeys[p] = (uint32_t)((s_ty0[lo] + ty) * s_tx[lo] + s_tx0[lo] + tx);
-    vals[p] = s_idx[lo];
+    // then the warp writes the particles' runs one after the other, lanes over the run
+    uint32_t todo = __ballot_sync(0xffffffffu, cnt > 0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t s0 = __shfl_sync(0xffffffffu, start, src);
+      const uint32_t c0 = __shfl_sync(0xffffffffu, cnt, src);
+      const uint32_t l0 = __shfl_sync(0xffffffffu, local, src);
+      const int b0 = __shfl_sync(0xffffffffu, base, src);
+      const int w0 = __shfl_sync(0xffffffffu, w, src);
+      const int tx_0 = __shfl_sync(0xffffffffu, tiles_x, src);
+      const float inv_w = 1.f / (float)w0;
+      for (uint32_t q = lane; q < c0; q += 32) {
+        // row / column of the q-th tile of the rect: a float estimate, corrected to the exact quotient
+        int ty = (int)(((float)q + 0.5f) * inv_w);
+        if (ty * w0 > (int)q) --ty;
+        else if ((ty + 1) * w0 <= (int)q) ++ty;
+        const int tx = (int)q - ty * w0;
+        tkeys[s0 + q] = (uint32_t)(b0 + ty * tx_0 + tx);
+        vals[s0 + q] = l0;
+      }
+    }
   }
 }
 
+// Tile ranges from the sorted tile keys: four keys per thread (uint4) and their neighbours.
 __global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *__restrict__ tkeys,
                          const uint32_t *__restrict__ vals, Count cnt, const float *__restrict__ depth,
                          uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys) {
   const uint32_t K = cnt.get();
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < K; p += gridDim.x * blockDim.x) {
-    uint32_t t = tkeys[p];
-    if (p == 0 || tkeys[p - 1] != t) ranges[2 * t] = p;
-    if (p == K - 1 || tkeys[p + 1] != t) ranges[2 * t + 1] = p + 1;
-    if (keys) {
-      const int v = view_of_tile(bd, (int)t);
-      keys[p] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(depth[bd.v[v].part_off + vals[p]]);
+  const uint32_t nq = (K + 3) / 4;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint32_t p0 = 4 * q;
+    uint32_t t[6];  // t[0] = key before p0, t[1..4] = keys p0..p0+3, t[5] = key after
+    if (p0 + 4 <= K) {
+      const uint4 v = reinterpret_cast<const uint4 *>(tkeys)[q];
+      t[1] = v.x; t[2] = v.y; t[3] = v.z; t[4] = v.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[1 + i] = p0 + i < K ? tkeys[p0 + i] : 0xffffffffu;
+    }
+    t[0] = p0 > 0 ? tkeys[p0 - 1] : 0xffffffffu;
+    t[5] = p0 + 4 < K ? tkeys[p0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t p = p0 + i;
+      if (p >= K) break;
+      const uint32_t cur = t[1 + i];
+      if (t[i] != cur) ranges[2 * cur] = p;
+      if (t[2 + i] != cur) ranges[2 * cur + 1] = p + 1;
+      if (keys) {
+        const int v = view_of_tile(bd, (int)cur);
+        keys[p] = ((uint64_t)cur << 32) | (uint64_t)__float_as_uint(depth[bd.v[v].part_off + vals[p]]);
+      }
     }
   }
 }
@@ -395,7 +445,7 @@ Buffers carve(void *ws, int n, int64_t cap) {
   for (int i = 0; i < 2; ++i) b.tk[i] = a.take<uint32_t>(cc);
   b.valt = a.take<uint32_t>(cc);
   size_t maxc = nn > cc ? nn : cc;
-  size_t spine = 256 * (size_t)ceil_div(maxc, kTile);
+  size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
   b.spine = a.take<uint32_t>(spine);
   size_t maxlen = spine > maxc ? spine : maxc;
   b.chunk = a.take<u64>(ceil_div(maxlen, kTile) + 1);
@@ -411,7 +461,7 @@ size_t carve_bytes(int n, int64_t cap) {
   a.take<uint32_t>(nn); a.take<uint32_t>(nn);
   a.take<uint32_t>(cc); a.take<uint32_t>(cc); a.take<uint32_t>(cc);
   size_t maxc = nn > cc ? nn : cc;
-  size_t spine = 256 * (size_t)ceil_div(maxc, kTile);
+  size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
   a.take<uint32_t>(spine);
   size_t maxlen = spine > maxc ? spine : maxc;
   a.take<u64>(ceil_div(maxlen, kTile) + 1);
@@ -439,13 +489,13 @@ void scan(const uint32_t *in, uint32_t *out, L len, u64 max_len, u64 *chunk, u64
 int radix_sort(uint32_t *keys[2], uint32_t *vals[2], Count cnt, u64 max_count, int bits, uint32_t *spine, u64 *chunk,
                cudaStream_t s) {
   int cur = 0;
-  int g = grid_for(max_count, kTile);
+  int g = grid_for(max_count, kRTile);
   for (int shift = 0; shift < bits; shift += kRadixBits) {
     int db = bits - shift < kRadixBits ? bits - shift : kRadixBits;
     uint32_t mask = (1u << db) - 1u;
     k_radix_upsweep<<<g, kThreads, 0, s>>>(keys[cur], cnt, shift, mask, spine);
     SpineLen sl{cnt, (int)mask + 1};
-    scan(spine, spine, sl, (u64)(mask + 1) * ceil_div(max_count, kTile), chunk, nullptr, s);
+    scan(spine, spine, sl, (u64)(mask + 1) * ceil_div(max_count, kRTile), chunk, nullptr, s);
     k_radix_downsweep<<<g, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], cnt, shift, mask,
                                             spine);
     count_launches(2);
@@ -487,7 +537,8 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     uint32_t *tv[2];
     tv[passes & 1] = vals;
     tv[(passes & 1) ^ 1] = b.valt;
-    k_emit<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs,
+    const int eg = (int)std::min<u64>((u64)(n + kThreads - 1) / kThreads, (u64)device_sm_count() * 16);
+    k_emit<<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs,
                                                               reinterpret_cast<const short4 *>(rect), b.total,
                                                               (u64)cap, op.tile_w, op.tile_h, b.tk[0], tv[0]);
     count_launches(1);
