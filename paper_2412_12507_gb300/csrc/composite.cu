@@ -19,6 +19,8 @@
 //
 // Template RS selects the general ray-origin path (per-pixel origin, needed when any view
 // has a rolling shutter); without it the origin is the camera centre of the view.
+#include <cuda_bf16.h>
+
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -240,10 +242,11 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   }
 }
 
-// Sum over the 32 lanes of 32 per-lane values; afterwards lane l holds the total of value l.
-__device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32], int lane) {
+// Reduce-scatter of 16 per-lane values over the 32 lanes: afterwards lanes 2i and 2i+1 hold
+// the warp total of value i.
+__device__ __forceinline__ void warp_reduce_scatter16(float (&v)[16], int lane) {
 #pragma unroll
-  for (int o = 16, L = 16; o >= 1; o >>= 1, L >>= 1) {
+  for (int o = 16, L = 8; L >= 1; o >>= 1, L >>= 1) {
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
@@ -252,40 +255,73 @@ __device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32], int lane) 
       v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// Gradient partial number j of one (pixel, particle) pair:
-//   0..2   v = 2 dL/domega^2 (o_g + tau d_g)             (-> dL/dmu = -M^T sum v)
-//   3..11  v_r x_c with x = o - mu + tau d              (dL/dM, row-major)
-//   12     dL/dsigma
-//   16 + 3k + ch   dL/dc_ch alpha T Y_k                 (dL/dbeta_k,ch)
-template <int NSH>
-__device__ __forceinline__ float grad_value(int j, const float *vv, const float *xx, float dsig, const float *wc,
-                                            const float *Y) {
-  if (j < 3) return vv[j];
-  if (j < 12) return vv[(j - 3) / 3] * xx[(j - 3) % 3];
-  if (j == 12) return dsig;
-  if (j < 16) return 0.f;
-  if (j < 16 + 3 * NSH) return wc[(j - 16) % 3] * Y[(j - 16) / 3];
-  return 0.f;
+// Two floats as bf16 pairs hi + lo (x = hi + lo to about 2^-17): the three-term products
+// hi*hi + hi*lo + lo*hi keep FP32-level accuracy on the BF16 tensor-core path.
+__device__ __forceinline__ void split_bf16x2(float x, float y, uint32_t &hi, uint32_t &lo) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  float2 hf = __bfloat1622float2(h);
+  __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+  hi = *reinterpret_cast<uint32_t *>(&h);
+  lo = *reinterpret_cast<uint32_t *>(&l);
 }
 
+// D += A B for one m16n8k16 BF16 tile (FP32 accumulate).
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kSub = 16;     // particles per tensor-core sub-batch
+constexpr int kAStride = 40; // floats per row of a warp's A tile (bank-conflict-free fragment loads)
+
+// Shared-memory layout of the backward kernel (dynamic; bytes for a block of `warps` warps).
+template <int DEG>
+struct BwdSmem {
+  static constexpr int NSH = (DEG + 1) * (DEG + 1);
+  static constexpr int NC = NSH * 3;
+  static constexpr int ACC = ((16 + NC) + 3) / 4 * 4;  // accumulators per particle
+  static __host__ __device__ size_t geo() { return 0; }
+  static __host__ __device__ size_t aux() { return geo() + sizeof(float4) * 4 * kBatch; }
+  static __host__ __device__ size_t sh() { return aux() + sizeof(float4) * kBatch; }
+  static __host__ __device__ size_t acc() { return sh() + sizeof(float) * ((kBatch * NC + 3) / 4 * 4); }
+  static __host__ __device__ size_t amat() { return acc() + sizeof(float) * kBatch * ACC; }
+  static __host__ __device__ size_t idx(int warps) { return amat() + sizeof(float) * warps * 3 * kSub * kAStride; }
+  static __host__ __device__ size_t any(int warps) { return idx(warps) + sizeof(uint32_t) * kBatch; }
+  static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch + 16; }
+};
+
+// Backward of k_composite_fwd for one tile.  Per (pixel, particle) pair the partials are
+// dL/dbeta_k,c = w_c Y_k (w_c = dL/dc_c alpha T where the colour is not clamped), the 9
+// products v x^T for dL/dM, v for dL/dmu and dL/dsigma.  The SH part is a dense contraction
+// over the warp's 32 pixels, sum_p w_c(p) Y_k(p), done per 16-particle sub-batch on the tensor
+// cores (BF16 hi/lo split, FP32 accumulate): each lane writes its w_c into the warp's A tile
+// (rows = channel x particle, columns = pixels), the B operand holds the pixels' Y.  The 13
+// geometry partials are summed with a 16-value reduce-scatter.  Both land in per-particle
+// shared accumulators that are added to global memory once per (tile, particle).
 template <int DEG, bool RS>
 __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
                                                        const uint2 *__restrict__ ranges) {
-  constexpr int NSH = (DEG + 1) * (DEG + 1);
-  constexpr int NC = NSH * 3;
-  constexpr int NV = 16 + NC;                 // used partials
-  constexpr int NCHUNK = (NV + 31) / 32;      // 32-value reduce chunks
-  __shared__ float4 s_geo[kBatch][4];
-  __shared__ float4 s_aux[kBatch];
-  __shared__ __align__(16) float s_sh[kBatch * NC];
-  __shared__ float s_acc[kBatch][NCHUNK * 32];
-  __shared__ uint32_t s_idx[kBatch];
-  __shared__ int s_any[kBatch];
-  __shared__ uint32_t s_end;
+  using L = BwdSmem<DEG>;
+  constexpr int NSH = L::NSH;
+  constexpr int NC = L::NC;
+  constexpr int ACC = L::ACC;
+  constexpr int NT = (NSH + 7) / 8;  // 8-wide basis tiles of the B operand
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warps = blockDim.x >> 5;
+  float4(*s_geo)[4] = reinterpret_cast<float4(*)[4]>(smem + L::geo());
+  float4 *s_aux = reinterpret_cast<float4 *>(smem + L::aux());
+  float *s_sh = reinterpret_cast<float *>(smem + L::sh());
+  float *s_acc = reinterpret_cast<float *>(smem + L::acc());
+  uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem + L::idx(warps));
+  int *s_any = reinterpret_cast<int *>(smem + L::any(warps));
+  uint32_t *s_end = reinterpret_cast<uint32_t *>(smem + L::any(warps) + sizeof(int) * kBatch);
 
   const int tile = blockIdx.x;
   const DevView &view = bd.v[view_of_tile(bd, tile)];
@@ -295,12 +331,29 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
   const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
   const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  float *s_A = reinterpret_cast<float *>(smem + L::amat()) + (size_t)warp * 3 * kSub * kAStride;
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
   float Y[NSH];
   bool valid;
   pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+
+  // B operand (pixels x basis), fixed for the whole tile: the warp's Y through its A tile
+  uint32_t bhi[2][NT][2], blo[2][NT][2];
+#pragma unroll
+  for (int k = 0; k < 8 * NT; ++k) s_A[k * kAStride + lane] = k < NSH ? Y[k < NSH ? k : 0] : 0.f;
+  __syncwarp();
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const float *row = s_A + (8 * n + g8) * kAStride + 16 * ks + 2 * t4;
+      split_bf16x2(row[0], row[1], bhi[ks][n][0], blo[ks][n][0]);
+      split_bf16x2(row[8], row[9], bhi[ks][n][1], blo[ks][n][1]);
+    }
+  __syncwarp();
 
   const uint2 rg = ranges[tile];
   uint32_t my_end = 0;
@@ -314,18 +367,18 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
     Cf0 = view.rgb[pix]; Cf1 = view.rgb[plane + pix]; Cf2 = view.rgb[2 * plane + pix];
     Tf = view.tfinal[pix];
   }
-  if (threadIdx.x == 0) s_end = 0;
+  if (threadIdx.x == 0) *s_end = 0;
   __syncthreads();
-  if (my_end > rg.x) atomicMax(&s_end, my_end);
+  if (my_end > rg.x) atomicMax(s_end, my_end);
   __syncthreads();
-  const uint32_t block_end = min(s_end, rg.y);
+  const uint32_t block_end = min(*s_end, rg.y);
 
   float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;  // running prefix of the composited colour
   for (uint32_t start = rg.x; start < block_end; start += kBatch) {
     const int nb = min((uint32_t)kBatch, block_end - start);
     __syncthreads();
     if (threadIdx.x < nb) s_idx[threadIdx.x] = vals[start + threadIdx.x];
-    for (int f = threadIdx.x; f < kBatch * NCHUNK * 32; f += blockDim.x) (&s_acc[0][0])[f] = 0.f;
+    for (int f = threadIdx.x; f < kBatch * ACC; f += blockDim.x) s_acc[f] = 0.f;
     if (threadIdx.x < kBatch) s_any[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x < nb) {
@@ -334,68 +387,109 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
     }
     stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-      bool contrib = false;
-      float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
-      float3 og, dg;
-      float dd, a;
-      if (start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
-        contrib = true;
-        float al = fminf(a, op.alpha_max);
-        float r0, r1, r2;
-        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
-        float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
-        float w = al * T;
-        A0 = fmaf(c0, w, A0);
-        A1 = fmaf(c1, w, A1);
-        A2 = fmaf(c2, w, A2);
-        float inv = 1.f / (1.f - al);
-        // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
-        float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
-                    g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
-        wc[0] = r0 > 0.f ? g0 * w : 0.f;
-        wc[1] = r1 > 0.f ? g1 * w : 0.f;
-        wc[2] = r2 > 0.f ? g2 * w : 0.f;
-        T = T * (1.f - al);
-        float da = a > op.alpha_max ? 0.f : dal;
-        float sigma = s_geo[b][3].x;
-        dsig = da * a / sigma;
-        float dw2 = -0.5f * a * da;
-        float tau = -dot3(og, dg) / dd;
-        float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
-        vv[0] = 2.f * dw2 * pp.x;
-        vv[1] = 2.f * dw2 * pp.y;
-        vv[2] = 2.f * dw2 * pp.z;
-        float4 ax = s_aux[b];
-        if (RS) {
-          xx[0] = fmaf(tau, d.x, o.x - ax.x);
-          xx[1] = fmaf(tau, d.y, o.y - ax.y);
-          xx[2] = fmaf(tau, d.z, o.z - ax.z);
-        } else {
-          xx[0] = fmaf(tau, d.x, ax.x);
-          xx[1] = fmaf(tau, d.y, ax.y);
-          xx[2] = fmaf(tau, d.z, ax.z);
+    for (int sb = 0; sb < nb; sb += kSub) {
+      for (int j = 0; j < kSub; ++j) {
+        const int b = sb + j;
+        bool contrib = false;
+        float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
+        float3 og, dg;
+        float dd, a;
+        if (b < nb && start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
+          contrib = true;
+          float al = fminf(a, op.alpha_max);
+          float r0, r1, r2;
+          sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+          float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
+          float w = al * T;
+          A0 = fmaf(c0, w, A0);
+          A1 = fmaf(c1, w, A1);
+          A2 = fmaf(c2, w, A2);
+          float inv = 1.f / (1.f - al);
+          // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
+          float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
+                      g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
+          wc[0] = r0 > 0.f ? g0 * w : 0.f;
+          wc[1] = r1 > 0.f ? g1 * w : 0.f;
+          wc[2] = r2 > 0.f ? g2 * w : 0.f;
+          T = T * (1.f - al);
+          float da = a > op.alpha_max ? 0.f : dal;
+          float sigma = s_geo[b][3].x;
+          dsig = da * a / sigma;
+          float dw2 = -0.5f * a * da;
+          float tau = -dot3(og, dg) / dd;
+          float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
+          vv[0] = 2.f * dw2 * pp.x;
+          vv[1] = 2.f * dw2 * pp.y;
+          vv[2] = 2.f * dw2 * pp.z;
+          float4 ax = s_aux[b];
+          if (RS) {
+            xx[0] = fmaf(tau, d.x, o.x - ax.x);
+            xx[1] = fmaf(tau, d.y, o.y - ax.y);
+            xx[2] = fmaf(tau, d.z, o.z - ax.z);
+          } else {
+            xx[0] = fmaf(tau, d.x, ax.x);
+            xx[1] = fmaf(tau, d.y, ax.y);
+            xx[2] = fmaf(tau, d.z, ax.z);
+          }
         }
-      }
-      if (!__any_sync(0xffffffffu, contrib)) continue;
+        // SH weights into the A tile (row = channel x particle, column = pixel)
 #pragma unroll
-      for (int ch = 0; ch < NCHUNK; ++ch) {
-        float v[32];
+        for (int c = 0; c < 3; ++c) s_A[(c * kSub + j) * kAStride + lane] = wc[c];
+        if (!__any_sync(0xffffffffu, contrib)) continue;
+        float v[16];
+        v[0] = vv[0]; v[1] = vv[1]; v[2] = vv[2];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = grad_value<NSH>(ch * 32 + j, vv, xx, dsig, wc, Y);
-        warp_reduce_scatter32(v, lane);
-        atomicAdd(&s_acc[b][ch * 32 + lane], v[0]);
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = vv[r] * xx[c];
+        v[12] = dsig; v[13] = 0.f; v[14] = 0.f; v[15] = 0.f;
+        warp_reduce_scatter16(v, lane);
+        const int vi = (lane >> 1) & 15;
+        if (!(lane & 1) && vi < 13) atomicAdd(&s_acc[b * ACC + vi], v[0]);
+        if (lane == 0) s_any[b] = 1;
       }
-      if (lane == 0) s_any[b] = 1;
+      __syncwarp();
+      // SH gradients of the sub-batch: sum over the warp's pixels of w_c(p) Y_k(p)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const float *r0 = s_A + (c * kSub + g8) * kAStride + 16 * ks + 2 * t4;
+          const float *r1 = r0 + 8 * kAStride;
+          uint32_t ahi[4], alo[4];
+          split_bf16x2(r0[0], r0[1], ahi[0], alo[0]);
+          split_bf16x2(r1[0], r1[1], ahi[1], alo[1]);
+          split_bf16x2(r0[8], r0[9], ahi[2], alo[2]);
+          split_bf16x2(r1[8], r1[9], ahi[3], alo[3]);
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            mma_bf16(acc[n], ahi, bhi[ks][n][0], bhi[ks][n][1]);
+            mma_bf16(acc[n], ahi, blo[ks][n][0], blo[ks][n][1]);
+            mma_bf16(acc[n], alo, bhi[ks][n][0], bhi[ks][n][1]);
+          }
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int j = g8 + (r >= 2 ? 8 : 0), k = 8 * n + 2 * t4 + (r & 1);
+            const float val = acc[n][r];
+            if (k < NSH && sb + j < nb && val != 0.f) atomicAdd(&s_acc[(sb + j) * ACC + 16 + 3 * k + c], val);
+          }
+      }
+      __syncwarp();
     }
     __syncthreads();
-    for (int f = threadIdx.x; f < nb * NCHUNK * 32; f += blockDim.x) {
-      int b = f / (NCHUNK * 32), j = f - b * (NCHUNK * 32);
+    for (int f = threadIdx.x; f < nb * ACC; f += blockDim.x) {
+      int b = f / ACC, j = f - b * ACC;
       if (!s_any[b]) continue;
       uint32_t idx = s_idx[b];
-      float v = s_acc[b][j];
+      float v = s_acc[f];
       if (j < 13) atomicAdd(&sc.gacc[(size_t)idx * 16 + j], v);
-      else if (j >= 16 && j < NV) atomicAdd(&sc.d_sh[(size_t)idx * NC + (j - 16)], v);
+      else if (j >= 16 && j < 16 + NC) atomicAdd(&sc.d_sh[(size_t)idx * NC + (j - 16)], v);
     }
   }
 }
@@ -464,8 +558,10 @@ template <int DEG, bool RS>
 void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, cudaStream_t s) {
   const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
-  k_composite_bwd<DEG, RS><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                      reinterpret_cast<const uint2 *>(ranges));
+  const size_t smem = BwdSmem<DEG>::bytes(threads / 32);
+  cudaFuncSetAttribute(k_composite_bwd<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_composite_bwd<DEG, RS><<<blocks, threads, smem, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
+                                                         reinterpret_cast<const uint2 *>(ranges));
 }
 
 bool any_rs(const BatchDesc &bd) {
