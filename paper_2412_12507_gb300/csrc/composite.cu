@@ -11,11 +11,12 @@
 //
 // The backward replays the forward IN FORWARD ORDER: the stored rgb and T_final give the
 // suffix sums S_i = C - sum_{j<=i} c_j alpha_j T_j without dividing transmittances,
-// and n_used tells each pixel where the forward stopped.  Per (particle, warp) the 61
-// gradient partials are reduced with a transposing reduce-scatter (31 shuffles per 32
-// values), accumulated across warps in shared memory, and pushed to global memory with
-// one atomic per value per (tile, particle).  A final per-particle kernel maps the
-// accumulated dL/dM, dL/dmu, dL/dsigma onto log-scales, quaternions and logits.
+// and n_used tells each pixel where the forward stopped.  Per (particle, warp) the 13
+// geometry partials are reduced with a transposing reduce-scatter and the 3 x (deg+1)^2 SH
+// partials with a tensor-core contraction over the warp's pixels; both are accumulated
+// across warps in shared memory and pushed to global memory with one atomic per value per
+// (tile, particle).  A final per-particle kernel maps the accumulated dL/dM, dL/dmu,
+// dL/dsigma onto log-scales, quaternions and logits.
 //
 // Template RS selects the general ray-origin path (per-pixel origin, needed when any view
 // has a rolling shutter); without it the origin is the camera centre of the view.
@@ -276,33 +277,39 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-constexpr int kSub = 16;     // particles per tensor-core sub-batch
-constexpr int kAStride = 40; // floats per row of a warp's A tile (bank-conflict-free fragment loads)
+constexpr int kSlots = 8;     // particle columns of one tensor-core flush (the MMA's N)
+constexpr int kWStride = 40;  // floats per row of a warp's W tile (bank-conflict-free fragment loads)
 
 // Shared-memory layout of the backward kernel (dynamic; bytes for a block of `warps` warps).
 template <int DEG>
 struct BwdSmem {
   static constexpr int NSH = (DEG + 1) * (DEG + 1);
   static constexpr int NC = NSH * 3;
-  static constexpr int ACC = ((16 + NC) + 3) / 4 * 4;  // accumulators per particle
+  static constexpr int ACC = (16 + NC) | 1;  // accumulators per particle (odd: rows spread over banks)
   static __host__ __device__ size_t geo() { return 0; }
   static __host__ __device__ size_t aux() { return geo() + sizeof(float4) * 4 * kBatch; }
   static __host__ __device__ size_t sh() { return aux() + sizeof(float4) * kBatch; }
   static __host__ __device__ size_t acc() { return sh() + sizeof(float) * ((kBatch * NC + 3) / 4 * 4); }
-  static __host__ __device__ size_t amat() { return acc() + sizeof(float) * kBatch * ACC; }
-  static __host__ __device__ size_t idx(int warps) { return amat() + sizeof(float) * warps * 3 * kSub * kAStride; }
+  static __host__ __device__ size_t wmat() { return acc() + sizeof(float) * kBatch * ACC; }
+  // per warp: 3 channels x kSlots rows of W; the first 16 rows double as the staging area of Y
+  static constexpr int kWarpFloats = (3 * kSlots > 16 ? 3 * kSlots : 16) * kWStride;
+  static __host__ __device__ size_t idx(int warps) { return wmat() + sizeof(float) * warps * kWarpFloats; }
   static __host__ __device__ size_t any(int warps) { return idx(warps) + sizeof(uint32_t) * kBatch; }
   static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch + 16; }
 };
 
 // Backward of k_composite_fwd for one tile.  Per (pixel, particle) pair the partials are
 // dL/dbeta_k,c = w_c Y_k (w_c = dL/dc_c alpha T where the colour is not clamped), the 9
-// products v x^T for dL/dM, v for dL/dmu and dL/dsigma.  The SH part is a dense contraction
-// over the warp's 32 pixels, sum_p w_c(p) Y_k(p), done per 16-particle sub-batch on the tensor
-// cores (BF16 hi/lo split, FP32 accumulate): each lane writes its w_c into the warp's A tile
-// (rows = channel x particle, columns = pixels), the B operand holds the pixels' Y.  The 13
-// geometry partials are summed with a 16-value reduce-scatter.  Both land in per-particle
-// shared accumulators that are added to global memory once per (tile, particle).
+// products v x^T for dL/dM, v for dL/dmu and dL/dsigma.
+//
+// The SH part is a dense contraction over the warp's 32 pixels, D[k][j] = sum_p Y_k(p) W_c(p, j),
+// run on the tensor cores (m16n8k16, BF16 hi/lo split with the three cross terms, FP32
+// accumulate): A = Y^T (basis x pixels) is fixed for the tile and lives in registers; B = W
+// (pixels x particles) collects, column by column, only particles that reach at least one
+// pixel of the warp, and is contracted once kSlots columns are full (and at the end of each
+// staged batch).  The 13 geometry partials are summed with a 16-value reduce-scatter.  Both
+// land in per-particle shared accumulators that are added to global memory once per
+// (tile, particle).
 template <int DEG, bool RS>
 __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
@@ -312,7 +319,6 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   constexpr int NSH = L::NSH;
   constexpr int NC = L::NC;
   constexpr int ACC = L::ACC;
-  constexpr int NT = (NSH + 7) / 8;  // 8-wide basis tiles of the B operand
   extern __shared__ __align__(16) unsigned char smem[];
   const int warps = blockDim.x >> 5;
   float4(*s_geo)[4] = reinterpret_cast<float4(*)[4]>(smem + L::geo());
@@ -333,27 +339,32 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;
-  float *s_A = reinterpret_cast<float *>(smem + L::amat()) + (size_t)warp * 3 * kSub * kAStride;
+  float *s_W = reinterpret_cast<float *>(smem + L::wmat()) + (size_t)warp * L::kWarpFloats;
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
   float Y[NSH];
   bool valid;
   pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
 
-  // B operand (pixels x basis), fixed for the whole tile: the warp's Y through its A tile
-  uint32_t bhi[2][NT][2], blo[2][NT][2];
+  // A operand (basis x pixels), fixed for the whole tile: the warp's Y transposed through
+  // its W tile (row k = basis function k, column = lane), then split into hi + lo fragments
+  uint32_t ahi[2][4], alo[2][4];
 #pragma unroll
-  for (int k = 0; k < 8 * NT; ++k) s_A[k * kAStride + lane] = k < NSH ? Y[k < NSH ? k : 0] : 0.f;
+  for (int k = 0; k < 16; ++k) s_W[k * kWStride + lane] = k < NSH ? Y[k < NSH ? k : 0] : 0.f;
   __syncwarp();
 #pragma unroll
-  for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      const float *row = s_A + (8 * n + g8) * kAStride + 16 * ks + 2 * t4;
-      split_bf16x2(row[0], row[1], bhi[ks][n][0], blo[ks][n][0]);
-      split_bf16x2(row[8], row[9], bhi[ks][n][1], blo[ks][n][1]);
-    }
+  for (int ks = 0; ks < 2; ++ks) {
+    const float *r0 = s_W + g8 * kWStride + 16 * ks + 2 * t4;
+    const float *r1 = r0 + 8 * kWStride;
+    split_bf16x2(r0[0], r0[1], ahi[ks][0], alo[ks][0]);
+    split_bf16x2(r1[0], r1[1], ahi[ks][1], alo[ks][1]);
+    split_bf16x2(r0[8], r0[9], ahi[ks][2], alo[ks][2]);
+    split_bf16x2(r1[8], r1[9], ahi[ks][3], alo[ks][3]);
+  }
   __syncwarp();
+  // W starts finite: unused columns of a partial flush only feed their own (discarded) outputs
+#pragma unroll
+  for (int r = 0; r < 3 * kSlots; ++r) s_W[r * kWStride + lane] = 0.f;
 
   const uint2 rg = ranges[tile];
   uint32_t my_end = 0;
@@ -372,6 +383,45 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   if (my_end > rg.x) atomicMax(s_end, my_end);
   __syncthreads();
   const uint32_t block_end = min(*s_end, rg.y);
+  uint32_t warp_end = my_end;  // no pixel of this warp blends a particle at or after warp_end
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) warp_end = max(warp_end, __shfl_xor_sync(0xffffffffu, warp_end, o));
+
+  // Contracts the first `cols` columns of W with Y and adds them to the particles' SH
+  // accumulators; lane s < kSlots holds in slot_b the batch index of column s.
+  int slot_b = 0;
+  auto flush = [&](int cols) {
+    __syncwarp();
+    float acc[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float *r = s_W + (c * kSlots + g8) * kWStride + 16 * ks + 2 * t4;
+        const float2 x0 = *reinterpret_cast<const float2 *>(r), x1 = *reinterpret_cast<const float2 *>(r + 8);
+        uint32_t bhi0, blo0, bhi1, blo1;
+        split_bf16x2(x0.x, x0.y, bhi0, blo0);
+        split_bf16x2(x1.x, x1.y, bhi1, blo1);
+        mma_bf16(acc[c], ahi[ks], bhi0, bhi1);
+        mma_bf16(acc[c], ahi[ks], blo0, blo1);
+        mma_bf16(acc[c], alo[ks], bhi0, bhi1);
+      }
+    // acc[c][r]: basis g8 (+8 for r >= 2), column 2 t4 (+1 for odd r)
+    const int bA = __shfl_sync(0xffffffffu, slot_b, 2 * t4), bB = __shfl_sync(0xffffffffu, slot_b, 2 * t4 + 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int k = g8 + (r >= 2 ? 8 : 0), col = 2 * t4 + (r & 1);
+      if (k < NSH && col < cols) {
+        float *dst = s_acc + (r & 1 ? bB : bA) * ACC + 16 + 3 * k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (acc[c][r] != 0.f) atomicAdd(dst + c, acc[c][r]);
+      }
+    }
+    __syncwarp();
+  };
 
   float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;  // running prefix of the composited colour
   for (uint32_t start = rg.x; start < block_end; start += kBatch) {
@@ -387,101 +437,74 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
     }
     stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
-    for (int sb = 0; sb < nb; sb += kSub) {
-      for (int j = 0; j < kSub; ++j) {
-        const int b = sb + j;
-        bool contrib = false;
-        float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
-        float3 og, dg;
-        float dd, a;
-        if (b < nb && start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
-          contrib = true;
-          float al = fminf(a, op.alpha_max);
-          float r0, r1, r2;
-          sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
-          float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
-          float w = al * T;
-          A0 = fmaf(c0, w, A0);
-          A1 = fmaf(c1, w, A1);
-          A2 = fmaf(c2, w, A2);
-          float inv = 1.f / (1.f - al);
-          // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
-          float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
-                      g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
-          wc[0] = r0 > 0.f ? g0 * w : 0.f;
-          wc[1] = r1 > 0.f ? g1 * w : 0.f;
-          wc[2] = r2 > 0.f ? g2 * w : 0.f;
-          T = T * (1.f - al);
-          float da = a > op.alpha_max ? 0.f : dal;
-          float sigma = s_geo[b][3].x;
-          dsig = da * a / sigma;
-          float dw2 = -0.5f * a * da;
-          float tau = -dot3(og, dg) / dd;
-          float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
-          vv[0] = 2.f * dw2 * pp.x;
-          vv[1] = 2.f * dw2 * pp.y;
-          vv[2] = 2.f * dw2 * pp.z;
-          float4 ax = s_aux[b];
-          if (RS) {
-            xx[0] = fmaf(tau, d.x, o.x - ax.x);
-            xx[1] = fmaf(tau, d.y, o.y - ax.y);
-            xx[2] = fmaf(tau, d.z, o.z - ax.z);
-          } else {
-            xx[0] = fmaf(tau, d.x, ax.x);
-            xx[1] = fmaf(tau, d.y, ax.y);
-            xx[2] = fmaf(tau, d.z, ax.z);
-          }
+    // particles of this batch any pixel of the warp can still blend (warp-uniform)
+    const int nw = (int)min((uint32_t)nb, warp_end > start ? warp_end - start : 0u);
+    int cols = 0;
+    for (int b = 0; b < nw; ++b) {
+      bool contrib = false;
+      float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
+      float3 og, dg;
+      float dd, a;
+      if (start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
+        contrib = true;
+        float al = fminf(a, op.alpha_max);
+        float r0, r1, r2;
+        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+        float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
+        float w = al * T;
+        A0 = fmaf(c0, w, A0);
+        A1 = fmaf(c1, w, A1);
+        A2 = fmaf(c2, w, A2);
+        float inv = 1.f / (1.f - al);
+        // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
+        float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
+                    g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
+        wc[0] = r0 > 0.f ? g0 * w : 0.f;
+        wc[1] = r1 > 0.f ? g1 * w : 0.f;
+        wc[2] = r2 > 0.f ? g2 * w : 0.f;
+        T = T * (1.f - al);
+        float da = a > op.alpha_max ? 0.f : dal;
+        float sigma = s_geo[b][3].x;
+        dsig = da * a / sigma;
+        float dw2 = -0.5f * a * da;
+        float tau = -dot3(og, dg) / dd;
+        float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
+        vv[0] = 2.f * dw2 * pp.x;
+        vv[1] = 2.f * dw2 * pp.y;
+        vv[2] = 2.f * dw2 * pp.z;
+        float4 ax = s_aux[b];
+        if (RS) {
+          xx[0] = fmaf(tau, d.x, o.x - ax.x);
+          xx[1] = fmaf(tau, d.y, o.y - ax.y);
+          xx[2] = fmaf(tau, d.z, o.z - ax.z);
+        } else {
+          xx[0] = fmaf(tau, d.x, ax.x);
+          xx[1] = fmaf(tau, d.y, ax.y);
+          xx[2] = fmaf(tau, d.z, ax.z);
         }
-        // SH weights into the A tile (row = channel x particle, column = pixel)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s_A[(c * kSub + j) * kAStride + lane] = wc[c];
-        if (!__any_sync(0xffffffffu, contrib)) continue;
-        float v[16];
-        v[0] = vv[0]; v[1] = vv[1]; v[2] = vv[2];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = vv[r] * xx[c];
-        v[12] = dsig; v[13] = 0.f; v[14] = 0.f; v[15] = 0.f;
-        warp_reduce_scatter16(v, lane);
-        const int vi = (lane >> 1) & 15;
-        if (!(lane & 1) && vi < 13) atomicAdd(&s_acc[b * ACC + vi], v[0]);
-        if (lane == 0) s_any[b] = 1;
       }
-      __syncwarp();
-      // SH gradients of the sub-batch: sum over the warp's pixels of w_c(p) Y_k(p)
+      if (!__any_sync(0xffffffffu, contrib)) continue;
+      // SH weights into the next free column of W (row = channel x column, entry = pixel)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float acc[NT][4];
+      for (int c = 0; c < 3; ++c) s_W[(c * kSlots + cols) * kWStride + lane] = wc[c];
+      if (lane == cols) slot_b = b;
+      float v[16];
+      v[0] = vv[0]; v[1] = vv[1]; v[2] = vv[2];
 #pragma unroll
-        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const float *r0 = s_A + (c * kSub + g8) * kAStride + 16 * ks + 2 * t4;
-          const float *r1 = r0 + 8 * kAStride;
-          uint32_t ahi[4], alo[4];
-          split_bf16x2(r0[0], r0[1], ahi[0], alo[0]);
-          split_bf16x2(r1[0], r1[1], ahi[1], alo[1]);
-          split_bf16x2(r0[8], r0[9], ahi[2], alo[2]);
-          split_bf16x2(r1[8], r1[9], ahi[3], alo[3]);
-#pragma unroll
-          for (int n = 0; n < NT; ++n) {
-            mma_bf16(acc[n], ahi, bhi[ks][n][0], bhi[ks][n][1]);
-            mma_bf16(acc[n], ahi, blo[ks][n][0], blo[ks][n][1]);
-            mma_bf16(acc[n], alo, bhi[ks][n][0], bhi[ks][n][1]);
-          }
-        }
-#pragma unroll
-        for (int n = 0; n < NT; ++n)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int j = g8 + (r >= 2 ? 8 : 0), k = 8 * n + 2 * t4 + (r & 1);
-            const float val = acc[n][r];
-            if (k < NSH && sb + j < nb && val != 0.f) atomicAdd(&s_acc[(sb + j) * ACC + 16 + 3 * k + c], val);
-          }
+        for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = vv[r] * xx[c];
+      v[12] = dsig; v[13] = 0.f; v[14] = 0.f; v[15] = 0.f;
+      warp_reduce_scatter16(v, lane);
+      const int vi = (lane >> 1) & 15;
+      if (!(lane & 1) && vi < 13) atomicAdd(&s_acc[b * ACC + vi], v[0]);
+      if (lane == 0) s_any[b] = 1;
+      if (++cols == kSlots) {
+        flush(kSlots);
+        cols = 0;
       }
-      __syncwarp();
     }
+    if (cols > 0) flush(cols);
     __syncthreads();
     for (int f = threadIdx.x; f < nb * ACC; f += blockDim.x) {
       int b = f / ACC, j = f - b * ACC;
