@@ -199,8 +199,10 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
                             float *alpha, float *t_final, uint32_t *n_used, unsigned long long *stats,
                             ut_stream stream);
 
-/* Bytes of scratch memory composite_backward needs for n particles. */
-size_t ut_backward_workspace_size(int32_t n);
+/* Bytes of scratch memory composite_backward needs for n particles rendered with this camera
+ * and these options (per-particle accumulators and a per-tile schedule); 0 for invalid
+ * arguments. */
+size_t ut_backward_workspace_size(int32_t n, const ut_camera *cam, const ut_options *opt);
 
 /* Gradient of a scalar loss L through composite_forward (supplementary Sec. B):
  *   given dL/drgb[3][H][W] and dL/dalpha[H][W], writes dL/d(parameter) for every
@@ -208,7 +210,7 @@ size_t ut_backward_workspace_size(int32_t n);
  *   d_sh[n][(deg+1)^2][3] (overwritten, not accumulated).  The projection contributes no
  *   gradient: rect, depth order and tile membership are piecewise constant (Sec. 4.1).
  * Inputs: everything composite_forward was given plus its outputs rgb, t_final, n_used.
- * Workspace: >= ut_backward_workspace_size(n) bytes, 256-byte aligned. */
+ * Workspace: >= ut_backward_workspace_size(n, cam, opt) bytes, 256-byte aligned. */
 ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
                              const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges,
                              const float *rgb, const float *t_final, const uint32_t *n_used, const float *d_rgb,
@@ -259,8 +261,10 @@ typedef struct {
   float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_sh;
 } ut_scene_grads;
 
-/* Bytes of accumulator scratch render_batch_backward needs for these scenes. */
-size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes);
+/* Bytes of scratch render_batch_backward needs for these scenes and views (per-particle
+ * accumulators of every scene and a per-tile schedule over all views); 0 for invalid arguments. */
+size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views,
+                                        int32_t n_views, const ut_options *opt);
 
 /* Gradient of a loss through render_batch (supplementary Sec. B): every view's d_rgb / d_alpha
  * is propagated into its scene's parameters; gradients of views sharing a scene add up.

@@ -83,11 +83,11 @@ SIGNATURES = {
                                       _P, _P, _P, _P, _P]),
     "composite_forward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,
                                     _P, _P, _P, _P, _P]),
-    "ut_backward_workspace_size": (C.c_size_t, [C.c_int32]),
+    "ut_backward_workspace_size": (C.c_size_t, [C.c_int32, C.POINTER(UtCamera), C.POINTER(UtOptions)]),
     "ut_batch_workspace_size": (C.c_size_t, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtOptions), C.c_int64]),
     "render_batch": (C.c_int, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtParams), C.POINTER(UtOptions), _P,
                                C.c_size_t, C.c_int64, _P, _P]),
-    "ut_batch_backward_workspace_size": (C.c_size_t, [_SC, C.c_int32]),
+    "ut_batch_backward_workspace_size": (C.c_size_t, [_SC, C.c_int32, _VW, C.c_int32, C.POINTER(UtOptions)]),
     "ut_server_create": (C.c_int, [C.POINTER(UtServerConfig), _SC, C.c_int32, _P, C.c_size_t,
                                    C.POINTER(C.c_void_p)]),
     "ut_server_submit": (C.c_int, [_P, C.c_int32, C.POINTER(UtCamera), C.POINTER(C.c_uint64)]),

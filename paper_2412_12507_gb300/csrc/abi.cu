@@ -389,7 +389,11 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
   return launch_composite_fwd(bd, dop, rect, vals, tile_ranges, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
-size_t ut_backward_workspace_size(int32_t n) { return n < 0 ? 0 : backward_workspace_bytes(n); }
+size_t ut_backward_workspace_size(int32_t n, const ut_camera *cam, const ut_options *opt) {
+  if (n < 0 || !cam || !opt || opt->tile_w < 1 || opt->tile_h < 1 || cam->width < 1 || cam->height < 1) return 0;
+  int tiles = ((cam->width + opt->tile_w - 1) / opt->tile_w) * ((cam->height + opt->tile_h - 1) / opt->tile_h);
+  return backward_workspace_bytes(n) + tile_sched_bytes(tiles);
+}
 
 ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
                              const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges,
@@ -408,7 +412,8 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
   if (scene->n > 0 && (!rect || !aligned8(rect) || !d_means || !d_log_scales || !d_quats || !d_opacity_logits ||
                        !d_sh))
     return UT_ERR_INVALID_ARG;
-  if (!workspace || workspace_bytes < backward_workspace_bytes(scene->n) ||
+  const size_t acc_bytes = backward_workspace_bytes(scene->n);
+  if (!workspace || workspace_bytes < acc_bytes + tile_sched_bytes(dop.tiles_x * dop.tiles_y) ||
       (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
   BatchDesc bd;
@@ -427,7 +432,8 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
   s.d_logits = d_opacity_logits;
   s.d_sh = d_sh;
   s.grad_off = 0;
-  return launch_composite_bwd(bd, dop, rect, vals, tile_ranges, reinterpret_cast<cudaStream_t>(stream));
+  return launch_composite_bwd(bd, dop, rect, vals, tile_ranges, static_cast<char *>(workspace) + acc_bytes,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t ut_batch_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
@@ -467,11 +473,14 @@ ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *
   return launch_composite_fwd(bd, dop, rect, vals, ranges, nullptr, s);
 }
 
-size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes) {
-  if (!scenes || n_scenes < 1 || n_scenes > kMaxScenes) return 0;
+size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views,
+                                        int32_t n_views, const ut_options *opt) {
+  BatchDesc bd;
+  DevOpts dop;
+  if (make_batch(scenes, n_scenes, views, n_views, opt, bd, dop) != UT_OK) return 0;
   size_t total = 0;
   for (int k = 0; k < n_scenes; ++k) total += backward_workspace_bytes(scenes[k].n);
-  return total;
+  return total + tile_sched_bytes(bd.total_tiles);
 }
 
 ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
@@ -488,7 +497,7 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
   BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, key_capacity);
   if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
-  if (!grad_workspace || grad_workspace_bytes < ut_batch_backward_workspace_size(scenes, n_scenes) ||
+  if (!grad_workspace || grad_workspace_bytes < ut_batch_backward_workspace_size(scenes, n_scenes, views, n_views, opt) ||
       (reinterpret_cast<uintptr_t>(grad_workspace) & 255))
     return UT_ERR_INVALID_ARG;
   char *gw = static_cast<char *>(grad_workspace);
@@ -511,7 +520,7 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
   const char *ws = static_cast<const char *>(workspace);
   return launch_composite_bwd(bd, dop, reinterpret_cast<const int16_t *>(ws + L.rect),
                               reinterpret_cast<const uint32_t *>(ws + L.vals),
-                              reinterpret_cast<const uint32_t *>(ws + L.ranges),
+                              reinterpret_cast<const uint32_t *>(ws + L.ranges), gw,
                               reinterpret_cast<cudaStream_t>(stream));
 }
 

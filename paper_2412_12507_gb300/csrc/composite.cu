@@ -29,6 +29,25 @@ namespace ut3d {
 namespace {
 
 constexpr int kBatch = 64;
+constexpr int kOrderBuckets = 1024;  // log buckets of the backward's tile schedule
+
+// Tile schedule of the backward (device scratch): per-tile replay length, the tiles with work
+// ordered by decreasing length, the bucket histogram and scatter cursors, and the count.
+struct TileSched {
+  uint32_t *work, *order, *hist, *cursor, *n_work;
+};
+
+TileSched carve_tile_sched(void *p, int tiles) {
+  const size_t t = (size_t)(tiles > 0 ? tiles : 1);
+  char *c = static_cast<char *>(p);
+  TileSched ts;
+  ts.work = reinterpret_cast<uint32_t *>(c);
+  ts.order = reinterpret_cast<uint32_t *>(c + align256(sizeof(uint32_t) * t));
+  ts.hist = reinterpret_cast<uint32_t *>(c + 2 * align256(sizeof(uint32_t) * t));
+  ts.cursor = ts.hist + kOrderBuckets;
+  ts.n_work = ts.cursor + kOrderBuckets;
+  return ts;
+}
 
 // Staged particle record (4 x float4):
 //   g0 = M00 M01 M02 M10   g1 = M11 M12 M20 M21   g2 = M22 a.x a.y a.z
@@ -295,7 +314,7 @@ struct BwdSmem {
   static constexpr int kWarpFloats = (3 * kSlots > 16 ? 3 * kSlots : 16) * kWStride;
   static __host__ __device__ size_t idx(int warps) { return wmat() + sizeof(float) * warps * kWarpFloats; }
   static __host__ __device__ size_t any(int warps) { return idx(warps) + sizeof(uint32_t) * kBatch; }
-  static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch + 16; }
+  static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch; }
 };
 
 // Backward of k_composite_fwd for one tile.  Per (pixel, particle) pair the partials are
@@ -314,7 +333,7 @@ template <int DEG, bool RS>
 __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
-                                                       const uint2 *__restrict__ ranges) {
+                                                       const uint2 *__restrict__ ranges, TileSched ts) {
   using L = BwdSmem<DEG>;
   constexpr int NSH = L::NSH;
   constexpr int NC = L::NC;
@@ -327,9 +346,10 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   float *s_acc = reinterpret_cast<float *>(smem + L::acc());
   uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem + L::idx(warps));
   int *s_any = reinterpret_cast<int *>(smem + L::any(warps));
-  uint32_t *s_end = reinterpret_cast<uint32_t *>(smem + L::any(warps) + sizeof(int) * kBatch);
 
-  const int tile = blockIdx.x;
+  // tiles in the order k_tile_order gave them (most list entries to replay first)
+  if (blockIdx.x >= *ts.n_work) return;
+  const int tile = (int)ts.order[blockIdx.x];
   const DevView &view = bd.v[view_of_tile(bd, tile)];
   const DevScene &sc = bd.s[view.scene];
   const DevCam &cam = view.cam;
@@ -378,11 +398,7 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
     Cf0 = view.rgb[pix]; Cf1 = view.rgb[plane + pix]; Cf2 = view.rgb[2 * plane + pix];
     Tf = view.tfinal[pix];
   }
-  if (threadIdx.x == 0) *s_end = 0;
-  __syncthreads();
-  if (my_end > rg.x) atomicMax(s_end, my_end);
-  __syncthreads();
-  const uint32_t block_end = min(*s_end, rg.y);
+  const uint32_t block_end = rg.x + ts.work[tile];
   uint32_t warp_end = my_end;  // no pixel of this warp blends a particle at or after warp_end
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) warp_end = max(warp_end, __shfl_xor_sync(0xffffffffu, warp_end, o));
@@ -517,6 +533,74 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   }
 }
 
+// Log-spaced bucket (about 1.5 % wide) of a tile's replay length.
+__device__ __forceinline__ int work_bucket(uint32_t w) {
+  return min((int)(48.f * __log2f(1.f + (float)w)), kOrderBuckets - 1);
+}
+
+// One warp per tile: work = list entries the backward replays (up to one past the last
+// particle any of the tile's pixels blended, from n_used), and a histogram of the buckets.
+__global__ void k_tile_work(const __grid_constant__ BatchDesc bd, DevOpts op, const uint2 *__restrict__ ranges,
+                            TileSched ts) {
+  const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (tile >= bd.total_tiles) return;
+  const DevView &view = bd.v[view_of_tile(bd, tile)];
+  const int lt = tile - view.tile_off;
+  const int x0 = (lt % view.tiles_x) * op.tile_w, y0 = (lt / view.tiles_x) * op.tile_h;
+  const int W = view.cam.W, H = view.cam.H;
+  uint32_t m = 0;
+  for (int i = lane; i < op.tile_w * op.tile_h; i += 32) {
+    const int px = x0 + i % op.tile_w, py = y0 + i / op.tile_w;
+    if (px < W && py < H) m = max(m, view.n_used[(size_t)py * W + px]);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    const uint2 rg = ranges[tile];
+    const uint32_t w = m > rg.x ? min(m, rg.y) - rg.x : 0u;
+    ts.work[tile] = w;
+    if (w) atomicAdd(&ts.hist[work_bucket(w)], 1u);
+  }
+}
+
+// Counting sort of the tiles with work by descending bucket (heaviest first, so the longest
+// replays start in the first wave instead of trailing at the end).  1024 threads per block;
+// every block scans the histogram itself and scatters its share of the tiles.
+__global__ void __launch_bounds__(kOrderBuckets) k_tile_order(int total_tiles, TileSched ts) {
+  __shared__ uint32_t s_off[kOrderBuckets];
+  __shared__ uint32_t s_warp[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const uint32_t h = ts.hist[kOrderBuckets - 1 - t];  // rank t in descending bucket order
+  uint32_t incl = h;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = s_warp[lane], x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_warp[lane] = x - v;
+  }
+  __syncthreads();
+  incl += s_warp[warp];
+  s_off[kOrderBuckets - 1 - t] = incl - h;
+  if (blockIdx.x == 0 && t == kOrderBuckets - 1) *ts.n_work = incl;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + t; i < total_tiles; i += gridDim.x * blockDim.x) {
+    const uint32_t w = ts.work[i];
+    if (!w) continue;
+    const int b = work_bucket(w);
+    ts.order[s_off[b] + atomicAdd(&ts.cursor[b], 1u)] = (uint32_t)i;
+  }
+}
+
 // d(rotation matrix)/d(unit quaternion) contracted with G = dL/dR (row-major).
 __device__ __forceinline__ void rot_grad(const float *q, const float *G, float *gq) {
   float w = q[0], x = q[1], y = q[2], z = q[3];
@@ -579,12 +663,12 @@ void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
 
 template <int DEG, bool RS>
 void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                const uint32_t *ranges, cudaStream_t s) {
+                const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
   const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
   const size_t smem = BwdSmem<DEG>::bytes(threads / 32);
   cudaFuncSetAttribute(k_composite_bwd<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_composite_bwd<DEG, RS><<<blocks, threads, smem, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                         reinterpret_cast<const uint2 *>(ranges));
+                                                         reinterpret_cast<const uint2 *>(ranges), ts);
 }
 
 bool any_rs(const BatchDesc &bd) {
@@ -615,9 +699,16 @@ ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int
 
 size_t backward_workspace_bytes(int n) { return align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1)); }
 
-// Clears the scenes' accumulators and d_sh, runs the backward over every tile, then finalize.
+size_t tile_sched_bytes(int tiles) {
+  const size_t t = (size_t)(tiles > 0 ? tiles : 1);
+  return 2 * align256(sizeof(uint32_t) * t) + align256(sizeof(uint32_t) * (2 * kOrderBuckets + 1));
+}
+
+
+// Clears the scenes' accumulators and d_sh, orders the tiles by replay length, runs the
+// backward over every tile with work, then finalize.
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                               const uint32_t *ranges, cudaStream_t s) {
+                               const uint32_t *ranges, void *sched, cudaStream_t s) {
   int total = 0;
   for (int k = 0; k < bd.ns; ++k) {
     const DevScene &sc = bd.s[k];
@@ -628,9 +719,17 @@ ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int
     total = sc.grad_off + sc.n > total ? sc.grad_off + sc.n : total;
   }
   if (bd.total_tiles > 0) {
+    const TileSched ts = carve_tile_sched(sched, bd.total_tiles);
+    if (cudaMemsetAsync(ts.hist, 0, sizeof(uint32_t) * (2 * kOrderBuckets + 1), s) != cudaSuccess) return UT_ERR_CUDA;
+    const auto *rg = reinterpret_cast<const uint2 *>(ranges);
+    k_tile_work<<<(bd.total_tiles + 7) / 8, 256, 0, s>>>(bd, op, rg, ts);
+    const int ob = (bd.total_tiles + kOrderBuckets - 1) / kOrderBuckets, cap = device_sm_count();
+    k_tile_order<<<ob < cap ? ob : cap, kOrderBuckets, 0, s>>>(bd.total_tiles, ts);
+    count_launches(2);
     const bool rs = any_rs(bd);
-#define UT3D_BWD(D) \
-  (rs ? bwd_launch<D, true>(bd, op, rect, vals, ranges, s) : bwd_launch<D, false>(bd, op, rect, vals, ranges, s))
+#define UT3D_BWD(D)                                                  \
+  (rs ? bwd_launch<D, true>(bd, op, rect, vals, ranges, ts, s) \
+      : bwd_launch<D, false>(bd, op, rect, vals, ranges, ts, s))
     switch (bd.s[0].deg) {
       case 0: UT3D_BWD(0); break;
       case 1: UT3D_BWD(1); break;

@@ -45,7 +45,9 @@ ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int
 
 // Backward of the batch into the scenes' gradient outputs (accumulators cleared here).
 size_t backward_workspace_bytes(int n);
+// Scratch of the backward's tile schedule for `tiles` tiles (one per backward call).
+size_t tile_sched_bytes(int tiles);
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                               const uint32_t *ranges, cudaStream_t stream);
+                               const uint32_t *ranges, void *sched, cudaStream_t stream);
 
 }  // namespace ut3d

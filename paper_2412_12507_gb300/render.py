@@ -166,8 +166,8 @@ def composite_backward(scene: Scene, cam: dict, opts: dict | None, proj: Project
                  quats=torch.empty_like(scene.quats), opacity_logits=torch.empty_like(scene.opacity_logits),
                  sh=torch.empty_like(scene.sh))
     ws = ws or Workspace()
-    w = ws.get(abi.lib().ut_backward_workspace_size(n), dev)
     c, o, s = abi.make_camera(cam), abi.make_options(opts), scene.struct()
+    w = ws.get(abi.lib().ut_backward_workspace_size(n, C.byref(c), C.byref(o)), dev)
     d_rgb = d_rgb.contiguous()
     d_alpha = d_alpha.contiguous()
     st = abi.lib().composite_backward(C.byref(s), C.byref(c), C.byref(o), _ptr(proj.rect), _ptr(binning.vals),
@@ -319,8 +319,8 @@ class BatchRenderer:
                              _ptr(g["sh"])) for g in grads])
         sc, vw = self._structs(views, frames, d_rgb, d_alpha)
         L = abi.lib()
-        gw = self.gws.get(L.ut_batch_backward_workspace_size(sc, len(self.scenes)), dev)
         o = abi.make_options(self.opts)
+        gw = self.gws.get(L.ut_batch_backward_workspace_size(sc, len(self.scenes), vw, len(views), C.byref(o)), dev)
         st = L.render_batch_backward(sc, len(self.scenes), vw, len(views), C.byref(o), _ptr(w), w.numel(), cap,
                                      _ptr(gw), gw.numel(), gs, _stream())
         abi.check("render_batch_backward", st)

@@ -48,8 +48,11 @@ def test_workspace_sizes(L):
     b = L.ut_bin_workspace_size(1000, 20000, C.byref(cam), C.byref(o))
     assert 0 < a < b
     assert L.ut_bin_workspace_size(-1, 10, C.byref(cam), C.byref(o)) == 0
-    assert L.ut_backward_workspace_size(1000) >= 1000 * 16 * 4
-    assert L.ut_backward_workspace_size(1000) % 256 == 0
+    w = L.ut_backward_workspace_size(1000, C.byref(cam), C.byref(o))
+    tiles = 120 * 68  # 1920x1080 in 16x16 tiles
+    assert w >= 1000 * 16 * 4 + 2 * 4 * tiles and w % 256 == 0
+    assert L.ut_backward_workspace_size(-1, C.byref(cam), C.byref(o)) == 0
+    assert L.ut_backward_workspace_size(1000, None, C.byref(o)) == 0
 
 
 def _project(L, cam, opts=None, n=0, params=None):
