@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests / s")
     ap.add_argument("--serve-arena-gb", type=float, default=64.0)
+    ap.add_argument("--multiview-steps", type=int, default=5,
+                    help="timed steps of the 8-view 3M-particle fwd+bwd batch (0: skip)")
     return ap.parse_args()
 
 
@@ -296,6 +298,50 @@ def run_plain(scenes, opts, reqs, n_warm):
 
 # ---------------------------------------------------------------- our arm
 
+def run_multiview(dev, steps, warmup, timed):
+    """Eight views of one 3M-particle scene rendered and differentiated as one batch
+    (render_batch + render_batch_backward): 4 pinhole 1920x1080, 2 fisheye 1600x1600,
+    2 rolling-shutter fisheye 2048x1536 on a radius-4 orbit.  The tile shape is picked by the
+    library's autotuner over 8x8, 16x16, 32x8, 16x32; the chosen shape is then timed over
+    `steps` batch steps (forward alone, and forward + backward)."""
+    import torch
+    from paper_2412_12507_gb300 import render, synth
+    case = synth.multiview()
+    scene = render.Scene.from_arrays(case["scene"], dev)
+    cams = case["cameras"]
+    views = [(0, c) for c in cams]
+    pix = sum(c["width"] * c["height"] for c in cams)
+    rng = np.random.default_rng(78)
+    d_rgb = [torch.as_tensor(rng.standard_normal((3, c["height"], c["width"])).astype(np.float32) / pix).to(dev)
+             for c in cams]
+    d_a = [torch.as_tensor(rng.standard_normal((c["height"], c["width"])).astype(np.float32) / pix).to(dev)
+           for c in cams]
+    best, tuned = render.autotune_tiles([scene], views, case["options"], d_rgb, d_a)
+    br = render.BatchRenderer([scene], best, capacity=1 << 20)
+    frames = br.forward(views, grad=True)
+    K = int(br.k_dev.item())
+
+    def fwd():
+        br.forward(views, frames=frames, grad=True, sync_check=False)
+
+    def fwd_bwd():
+        fwd()
+        br.backward(d_rgb, d_a)
+
+    f_ms = timed(fwd, steps, warmup)
+    fb_ms = timed(fwd_bwd, steps, warmup)
+    if int(br.k_dev.item()) != K:
+        raise SystemExit("multiview key count changed during the timed region")
+    nv = len(views)
+    out = {"workload": case["name"], "particles": scene.n, "views": nv, "pixels": pix, "keys": K,
+           "tile": f"{best['tile_w']}x{best['tile_h']}", "autotune_ms_per_batch": tuned,
+           "fwd_ms_per_view": f_ms / nv, "fwd_bwd_ms_per_view": fb_ms / nv,
+           "fwd_mpix_s": pix / (f_ms / 1e3) / 1e6, "fwd_bwd_mpix_s": pix / (fb_ms / 1e3) / 1e6, "steps": steps}
+    del br, frames, scene
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -444,6 +490,10 @@ def run_ours(args):
     e2e_ms = timed(e2e_step, max(3, args.steps // 2), 3)
     clk = clocks.stop()
 
+    multiview = None
+    if args.multiview_steps > 0:
+        multiview = run_multiview(dev, args.multiview_steps, max(3, args.warmup), timed)
+
     serve = None
     if args.serve_requests > 0:
         sc_list = serving_scenes(dev)
@@ -481,6 +531,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
             "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
+            "multiview": multiview,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

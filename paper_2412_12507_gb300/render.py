@@ -359,6 +359,50 @@ def render_views(means, log_scales, quats, opacity_logits, sh, sh_degree: int, c
     return [(out[2 * j], out[2 * j + 1]) for j in range(len(cams))]
 
 
+
+TILE_CANDIDATES = ((8, 8), (16, 16), (32, 8), (16, 32))
+
+
+def autotune_tiles(scenes: list, views, opts: dict | None = None, d_rgb=None, d_alpha=None,
+                   candidates=TILE_CANDIDATES, steps: int = 3, warmup: int = 2):
+    """Picks the tile shape for a batch of views by timing it: for every candidate
+    (tile_w, tile_h) a BatchRenderer renders the batch (and, when d_rgb / d_alpha are given,
+    runs its backward) `steps` times after `warmup` untimed runs, with CUDA events on the
+    current stream.  Images do not depend on the tile shape (a pixel considers a particle iff
+    its centre lies in the particle's rect), so only the speed differs.  Returns
+    (best options dict, {"WxH": {"ms": per batch, "keys": K}})."""
+    import copy
+    base = dict(opts or {})
+    results, best, best_ms = {}, None, float("inf")
+    for tw, th in candidates:
+        op = copy.deepcopy(base)
+        op["tile_w"], op["tile_h"] = int(tw), int(th)
+        br = BatchRenderer(scenes, op, capacity=1 << 20)
+        grad = d_rgb is not None
+        frames = br.forward(views, grad=grad)  # sizes the key capacity (synchronises)
+        K = int(br.k_dev.item())
+
+        def run():
+            br.forward(views, frames=frames, grad=grad, sync_check=False)
+            if grad:
+                br.backward(d_rgb, d_alpha)
+
+        for _ in range(warmup):
+            run()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            run()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        results[f"{tw}x{th}"] = {"ms": ms, "keys": K}
+        if ms < best_ms:
+            best, best_ms = op, ms
+        del br, frames
+    return best, results
+
 # ---------------------------------------------------------------- serving
 
 class Server:

@@ -169,3 +169,32 @@ def test_multiview_autograd_matches_batch_backward():
     for a, b in zip(leaves, tot):
         e = (torch.linalg.norm(a.grad - b) / torch.linalg.norm(b)).item()
         assert e < 1e-4, e
+
+
+def test_batch_images_do_not_depend_on_tile_shape():
+    """The pixel predicate (pixel centre inside the particle's rect) makes every image of a
+    batch bit-identical for every tile shape the autotuner may pick."""
+    scenes_np = _scenes()
+    scenes = [render.Scene.from_arrays(s) for s in scenes_np]
+    views = _cams()
+    ref = None
+    for tw, th in render.TILE_CANDIDATES:
+        br = render.BatchRenderer(scenes, synth.options(tile_w=tw, tile_h=th), capacity=1 << 12)
+        frames = br.forward(views)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = frames
+            continue
+        for f, g in zip(frames, ref):
+            assert torch.equal(f.rgb, g.rgb) and torch.equal(f.alpha, g.alpha), (tw, th)
+
+
+def test_autotune_tiles_returns_a_candidate_and_timings():
+    scenes = [render.Scene.from_arrays(s) for s in _scenes()]
+    views = _cams()[:3]
+    d_rgb = [torch.ones((3, c["height"], c["width"]), device="cuda") for _, c in views]
+    d_a = [torch.ones((c["height"], c["width"]), device="cuda") for _, c in views]
+    best, res = render.autotune_tiles(scenes, views, synth.options(), d_rgb, d_a, steps=1, warmup=1)
+    assert (best["tile_w"], best["tile_h"]) in render.TILE_CANDIDATES
+    assert set(res) == {f"{w}x{h}" for w, h in render.TILE_CANDIDATES}
+    assert all(r["ms"] > 0 and r["keys"] > 0 for r in res.values())
