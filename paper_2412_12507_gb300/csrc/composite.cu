@@ -297,7 +297,11 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 constexpr int kSlots = 8;     // particle columns of one tensor-core flush (the MMA's N)
-constexpr int kWStride = 40;  // floats per row of a warp's W tile (bank-conflict-free fragment loads)
+
+// Float index of (row, col) in a warp's 32-column W tile: columns are XOR-swizzled by the row so
+// that the fragment loads of four rows (8-byte pairs, 16 lanes per phase) hit distinct banks
+// without padding.
+__device__ __forceinline__ int wtile(int row, int col) { return row * 32 + (col ^ ((row & 3) << 3)); }
 
 // Shared-memory layout of the backward kernel (dynamic; bytes for a block of `warps` warps).
 template <int DEG>
@@ -310,8 +314,10 @@ struct BwdSmem {
   static __host__ __device__ size_t sh() { return aux() + sizeof(float4) * kBatch; }
   static __host__ __device__ size_t acc() { return sh() + sizeof(float) * ((kBatch * NC + 3) / 4 * 4); }
   static __host__ __device__ size_t wmat() { return acc() + sizeof(float) * kBatch * ACC; }
-  // per warp: 3 channels x kSlots rows of W; the first 16 rows double as the staging area of Y
-  static constexpr int kWarpFloats = (3 * kSlots > 16 ? 3 * kSlots : 16) * kWStride;
+  // per warp: 3 channels x kSlots rows of W (the first 16 rows double as the staging area of
+  // Y), then the A fragments (uint4 [4][32]: hi/lo of both k-steps, lane-minor)
+  static constexpr int kWRows = 3 * kSlots > 16 ? 3 * kSlots : 16;
+  static constexpr int kWarpFloats = kWRows * 32 + 4 * 4 * 32;
   static __host__ __device__ size_t idx(int warps) { return wmat() + sizeof(float) * warps * kWarpFloats; }
   static __host__ __device__ size_t any(int warps) { return idx(warps) + sizeof(uint32_t) * kBatch; }
   static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch; }
@@ -329,8 +335,10 @@ struct BwdSmem {
 // staged batch).  The 13 geometry partials are summed with a 16-value reduce-scatter.  Both
 // land in per-particle shared accumulators that are added to global memory once per
 // (tile, particle).
-template <int DEG, bool RS>
-__global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
+// SMALL: tiles of at most 256 pixels, compiled for three resident blocks per SM (80 registers).
+template <int DEG, bool RS, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
+    k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
                                                        const uint2 *__restrict__ ranges, TileSched ts) {
@@ -360,6 +368,7 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;
   float *s_W = reinterpret_cast<float *>(smem + L::wmat()) + (size_t)warp * L::kWarpFloats;
+  uint4 *s_Af = reinterpret_cast<uint4 *>(s_W + L::kWRows * 32);
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
   float Y[NSH];
@@ -367,36 +376,37 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
   pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
 
   // A operand (basis x pixels), fixed for the whole tile: the warp's Y transposed through
-  // its W tile (row k = basis function k, column = lane), then split into hi + lo fragments
-  uint32_t ahi[2][4], alo[2][4];
+  // its W tile (row k = basis function k, column = lane), split into hi + lo fragments and
+  // parked in shared memory (s_Af[2 ks + 0] = hi, s_Af[2 ks + 1] = lo)
 #pragma unroll
-  for (int k = 0; k < 16; ++k) s_W[k * kWStride + lane] = k < NSH ? Y[k < NSH ? k : 0] : 0.f;
+  for (int k = 0; k < 16; ++k) s_W[wtile(k, lane)] = k < NSH ? Y[k < NSH ? k : 0] : 0.f;
   __syncwarp();
 #pragma unroll
   for (int ks = 0; ks < 2; ++ks) {
-    const float *r0 = s_W + g8 * kWStride + 16 * ks + 2 * t4;
-    const float *r1 = r0 + 8 * kWStride;
-    split_bf16x2(r0[0], r0[1], ahi[ks][0], alo[ks][0]);
-    split_bf16x2(r1[0], r1[1], ahi[ks][1], alo[ks][1]);
-    split_bf16x2(r0[8], r0[9], ahi[ks][2], alo[ks][2]);
-    split_bf16x2(r1[8], r1[9], ahi[ks][3], alo[ks][3]);
+    const int c0 = 16 * ks + 2 * t4;
+    uint4 hi, lo;
+    split_bf16x2(s_W[wtile(g8, c0)], s_W[wtile(g8, c0 + 1)], hi.x, lo.x);
+    split_bf16x2(s_W[wtile(g8 + 8, c0)], s_W[wtile(g8 + 8, c0 + 1)], hi.y, lo.y);
+    split_bf16x2(s_W[wtile(g8, c0 + 8)], s_W[wtile(g8, c0 + 9)], hi.z, lo.z);
+    split_bf16x2(s_W[wtile(g8 + 8, c0 + 8)], s_W[wtile(g8 + 8, c0 + 9)], hi.w, lo.w);
+    s_Af[(2 * ks) * 32 + lane] = hi;
+    s_Af[(2 * ks + 1) * 32 + lane] = lo;
   }
   __syncwarp();
   // W starts finite: unused columns of a partial flush only feed their own (discarded) outputs
 #pragma unroll
-  for (int r = 0; r < 3 * kSlots; ++r) s_W[r * kWStride + lane] = 0.f;
+  for (int r = 0; r < 3 * kSlots; ++r) s_W[wtile(r, lane)] = 0.f;
 
   const uint2 rg = ranges[tile];
   uint32_t my_end = 0;
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gA = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f;
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, gAT = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f;  // gAT = dL/dalpha T_final
   if (valid) {
     size_t pix = (size_t)py * cam.W + px;
     size_t plane = (size_t)cam.W * cam.H;
     my_end = view.n_used[pix];
     g0 = view.d_rgb[pix]; g1 = view.d_rgb[plane + pix]; g2 = view.d_rgb[2 * plane + pix];
-    gA = view.d_alpha[pix];
+    gAT = view.d_alpha[pix] * view.tfinal[pix];
     Cf0 = view.rgb[pix]; Cf1 = view.rgb[plane + pix]; Cf2 = view.rgb[2 * plane + pix];
-    Tf = view.tfinal[pix];
   }
   const uint32_t block_end = rg.x + ts.work[tile];
   uint32_t warp_end = my_end;  // no pixel of this warp blends a particle at or after warp_end
@@ -412,18 +422,22 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks)
+    for (int ks = 0; ks < 2; ++ks) {
+      const uint4 h4 = s_Af[(2 * ks) * 32 + lane], l4 = s_Af[(2 * ks + 1) * 32 + lane];
+      const uint32_t ahi[4] = {h4.x, h4.y, h4.z, h4.w}, alo[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float *r = s_W + (c * kSlots + g8) * kWStride + 16 * ks + 2 * t4;
-        const float2 x0 = *reinterpret_cast<const float2 *>(r), x1 = *reinterpret_cast<const float2 *>(r + 8);
+        const int row = c * kSlots + g8, c0 = 16 * ks + 2 * t4;
+        const float2 x0 = *reinterpret_cast<const float2 *>(s_W + wtile(row, c0));
+        const float2 x1 = *reinterpret_cast<const float2 *>(s_W + wtile(row, c0 + 8));
         uint32_t bhi0, blo0, bhi1, blo1;
         split_bf16x2(x0.x, x0.y, bhi0, blo0);
         split_bf16x2(x1.x, x1.y, bhi1, blo1);
-        mma_bf16(acc[c], ahi[ks], bhi0, bhi1);
-        mma_bf16(acc[c], ahi[ks], blo0, blo1);
-        mma_bf16(acc[c], alo[ks], bhi0, bhi1);
+        mma_bf16(acc[c], ahi, bhi0, bhi1);
+        mma_bf16(acc[c], ahi, blo0, blo1);
+        mma_bf16(acc[c], alo, bhi0, bhi1);
       }
+    }
     // acc[c][r]: basis g8 (+8 for r >= 2), column 2 t4 (+1 for odd r)
     const int bA = __shfl_sync(0xffffffffu, slot_b, 2 * t4), bB = __shfl_sync(0xffffffffu, slot_b, 2 * t4 + 1);
 #pragma unroll
@@ -474,7 +488,7 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
         float inv = 1.f / (1.f - al);
         // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
         float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
-                    g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gA * Tf * inv;
+                    g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
         wc[0] = r0 > 0.f ? g0 * w : 0.f;
         wc[1] = r1 > 0.f ? g1 * w : 0.f;
         wc[2] = r2 > 0.f ? g2 * w : 0.f;
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(512) k_composite_bwd(const __grid_constant__ B
       if (!__any_sync(0xffffffffu, contrib)) continue;
       // SH weights into the next free column of W (row = channel x column, entry = pixel)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) s_W[(c * kSlots + cols) * kWStride + lane] = wc[c];
+      for (int c = 0; c < 3; ++c) s_W[wtile(c * kSlots + cols, lane)] = wc[c];
       if (lane == cols) slot_b = b;
       float v[16];
       v[0] = vv[0]; v[1] = vv[1]; v[2] = vv[2];
@@ -661,14 +675,21 @@ void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
                                                                reinterpret_cast<const uint2 *>(ranges), nullptr);
 }
 
+template <int DEG, bool RS, bool SMALL>
+void bwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                  const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
+  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
+  const size_t smem = BwdSmem<DEG>::bytes(threads / 32);
+  cudaFuncSetAttribute(k_composite_bwd<DEG, RS, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_composite_bwd<DEG, RS, SMALL><<<blocks, threads, smem, s>>>(
+      bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
+}
+
 template <int DEG, bool RS>
 void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
-  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
-  const size_t smem = BwdSmem<DEG>::bytes(threads / 32);
-  cudaFuncSetAttribute(k_composite_bwd<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_composite_bwd<DEG, RS><<<blocks, threads, smem, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                         reinterpret_cast<const uint2 *>(ranges), ts);
+  if (op.tile_w * op.tile_h <= 256) bwd_launch_k<DEG, RS, true>(bd, op, rect, vals, ranges, ts, s);
+  else bwd_launch_k<DEG, RS, false>(bd, op, rect, vals, ranges, ts, s);
 }
 
 bool any_rs(const BatchDesc &bd) {
