@@ -431,7 +431,7 @@ def run_ours(args):
         ev[1].record(stream)
         render.bin_and_sort(r.proj, cam, op, r.capacity, ws=r.ws, out=r.binning)
         ev[2].record(stream)
-        render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame)
+        render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, ws=r.fws)
         ev[3].record(stream)
         r.backward(scene, d_rgb, d_alpha)
         ev[4].record(stream)
@@ -442,7 +442,7 @@ def run_ours(args):
 
     # algorithmic work: evaluations / blends counted by the forward kernel itself
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
-    render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, stats=stats)
+    render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, stats=stats, ws=r.fws)
     torch.cuda.synchronize()
     n_eval, n_blend = (int(v) for v in stats.cpu())
     n = scene.n

@@ -178,6 +178,10 @@ ut_status bin_and_sort_static(int32_t n, const float *depth, const int16_t *rect
                               const ut_camera *cam, const ut_options *opt, int64_t key_capacity, uint64_t *keys,
                               uint32_t *vals, uint32_t *tile_ranges, int64_t *k_out, ut_stream stream);
 
+/* Bytes of scratch memory composite_forward needs for this camera and these options; 0 for
+ * invalid arguments. */
+size_t ut_forward_workspace_size(const ut_camera *cam, const ut_options *opt);
+
 /* Front-to-back compositing (eq. QuadratureVolumeRendering) with the particle response
  * evaluated in 3D at its maximum along the pixel ray (eq. GaussianMaxResponse):
  *   o_g = S^-1 R^T (o - mu), d_g = S^-1 R^T d, omega^2 = |o_g x d_g|^2 / |d_g|^2,
@@ -191,13 +195,15 @@ ut_status bin_and_sort_static(int32_t n, const float *depth, const int16_t *rect
  * Outputs (device): rgb[3][H][W] (planar), alpha[H][W] = 1 - T_final,
  *   t_final[H][W] = T_final, n_used[H][W] = one past the position in vals of the last
  *   blended particle (0 if none; consumed by composite_backward).
+ * Workspace: >= ut_forward_workspace_size(cam, opt) bytes, 256-byte aligned (the tile
+ *   schedule: tiles are composited longest predicted walk first; the order changes no result).
  * stats (device, nullable): if given, stats[0] += number of (pixel, particle) response
  *   evaluations (pixel inside the rect, before the pixel stopped) and stats[1] += number
  *   of blended particles; a measurement aid, NULL in normal use. */
 ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
                             const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges, float *rgb,
-                            float *alpha, float *t_final, uint32_t *n_used, unsigned long long *stats,
-                            ut_stream stream);
+                            float *alpha, float *t_final, uint32_t *n_used, void *workspace,
+                            size_t workspace_bytes, unsigned long long *stats, ut_stream stream);
 
 /* Bytes of scratch memory composite_backward needs for n particles rendered with this camera
  * and these options (per-particle accumulators and a per-tile schedule); 0 for invalid

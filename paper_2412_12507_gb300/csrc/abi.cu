@@ -271,7 +271,7 @@ ut_status make_batch(const ut_scene *scenes, int ns, const ut_view *views, int n
 // Layout of the render_batch workspace: projection of every flattened entry, ranges of every
 // global tile, the sorted values, then bin_and_sort's own scratch.
 struct BatchLayout {
-  size_t mean2d, cov2d, depth, rect, ntiles, ranges, vals, bin, total;
+  size_t mean2d, cov2d, depth, rect, ntiles, ranges, vals, sched, bin, total;
 };
 
 BatchLayout batch_layout(long long part, long long tiles, long long cap) {
@@ -285,6 +285,7 @@ BatchLayout batch_layout(long long part, long long tiles, long long cap) {
   L.ntiles = off; off += align256(p * 4);
   L.ranges = off; off += align256(t * 8);
   L.vals = off; off += align256(c * 4);
+  L.sched = off; off += tile_sched_bytes((int)t);
   L.bin = off; off += bin_workspace_bytes((int)p, (int64_t)c, (int)t);
   L.total = off;
   return L;
@@ -368,10 +369,16 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
+size_t ut_forward_workspace_size(const ut_camera *cam, const ut_options *opt) {
+  if (!cam || !opt || opt->tile_w < 1 || opt->tile_h < 1 || cam->width < 1 || cam->height < 1) return 0;
+  int tiles = ((cam->width + opt->tile_w - 1) / opt->tile_w) * ((cam->height + opt->tile_h - 1) / opt->tile_h);
+  return tile_sched_bytes(tiles);
+}
+
 ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
                             const int16_t *rect, const uint32_t *vals, const uint32_t *tile_ranges, float *rgb,
-                            float *alpha, float *t_final, uint32_t *n_used, unsigned long long *stats,
-                            ut_stream stream) {
+                            float *alpha, float *t_final, uint32_t *n_used, void *workspace,
+                            size_t workspace_bytes, unsigned long long *stats, ut_stream stream) {
   ut_status st = check_scene(scene, true);
   if (st != UT_OK) return st;
   DevCam dc;
@@ -380,13 +387,17 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
   if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
   if (!tile_ranges || !rgb || !alpha || !t_final || !n_used || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
   if (scene->n > 0 && (!rect || !aligned8(rect))) return UT_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < tile_sched_bytes(dop.tiles_x * dop.tiles_y) ||
+      (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return UT_ERR_INVALID_ARG;
   BatchDesc bd;
   single_view(bd, dc, dop, scene, scene->n);
   bd.v[0].rgb = rgb;
   bd.v[0].alpha = alpha;
   bd.v[0].tfinal = t_final;
   bd.v[0].n_used = n_used;
-  return launch_composite_fwd(bd, dop, rect, vals, tile_ranges, stats, reinterpret_cast<cudaStream_t>(stream));
+  return launch_composite_fwd(bd, dop, rect, vals, tile_ranges, stats, workspace,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t ut_backward_workspace_size(int32_t n, const ut_camera *cam, const ut_options *opt) {
@@ -470,7 +481,7 @@ ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *
   if ((st = launch_bin(bd, depth, rect, ntiles, dop, ws + L.bin, key_capacity, nullptr, vals, ranges, k_out, s)) !=
       UT_OK)
     return st;
-  return launch_composite_fwd(bd, dop, rect, vals, ranges, nullptr, s);
+  return launch_composite_fwd(bd, dop, rect, vals, ranges, nullptr, ws + L.sched, s);
 }
 
 size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views,

@@ -177,14 +177,17 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
                                                        const uint2 *__restrict__ ranges,
-                                                       unsigned long long *__restrict__ stats) {
+                                                       unsigned long long *__restrict__ stats, TileSched ts) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
   __shared__ float4 s_geo[kBatch][4];
   __shared__ __align__(16) float s_sh[kBatch * NC];
   __shared__ uint32_t s_idx[kBatch];
 
-  const int tile = blockIdx.x;
+  // tiles in the order k_tile_order gave them (longest predicted walk first); every tile is
+  // in the order, so every pixel is written
+  if (blockIdx.x >= *ts.n_work) return;
+  const int tile = (int)ts.order[blockIdx.x];
   const DevView &view = bd.v[view_of_tile(bd, tile)];
   const DevScene &sc = bd.s[view.scene];
   const DevCam &cam = view.cam;
@@ -552,6 +555,67 @@ __device__ __forceinline__ int work_bucket(uint32_t w) {
   return min((int)(48.f * __log2f(1.f + (float)w)), kOrderBuckets - 1);
 }
 
+// Forward schedule estimate, one warp per tile.  A heuristic that only orders the tiles (no
+// result depends on it): a tile's pixels saturate after roughly a fixed optical depth of
+// particles that cover the whole tile, so the estimate is the list position where
+// sum -ln(1 - 0.3 sigma) over particles whose rect contains the tile's pixels reaches
+// kFwdDepth, or the end of the first kFwdCap entries.  Every tile gets work >= 1 so that
+// every tile, even an empty one, is scheduled (its pixels must still be written).
+constexpr int kFwdCap = 512;
+constexpr float kFwdDepth = 40.f;
+
+__global__ void k_fwd_predict(const __grid_constant__ BatchDesc bd, DevOpts op, const short4 *__restrict__ rect,
+                              const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, TileSched ts) {
+  const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (tile >= bd.total_tiles) return;
+  const DevView &view = bd.v[view_of_tile(bd, tile)];
+  const float *logits = bd.s[view.scene].logits;
+  const int lt = tile - view.tile_off;
+  const int x0 = (lt % view.tiles_x) * op.tile_w, y0 = (lt / view.tiles_x) * op.tile_h;
+  const int x1 = min(x0 + op.tile_w, view.cam.W) - 1, y1 = min(y0 + op.tile_h, view.cam.H) - 1;
+  const uint2 rg = ranges[tile];
+  const uint32_t end = min(rg.y, rg.x + (uint32_t)kFwdCap);
+  uint32_t pred = end - rg.x;
+  float tau = 0.f;
+  bool found = false;
+  for (uint32_t base = rg.x; base < end && !found; base += 128) {
+    float c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // four chunks of 32 entries in flight per step
+      const uint32_t k = base + 32 * j + lane;
+      c[j] = 0.f;
+      if (k < end) {
+        const uint32_t idx = vals[k];
+        const short4 r = rect[view.part_off + idx];
+        if (r.x <= x0 && r.y <= y0 && r.z >= x1 && r.w >= y1) {
+          const float sg = 1.f / (1.f + __expf(-logits[idx]));
+          c[j] = -__logf(1.f - fminf(0.3f * sg, 0.99f));
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float incl = c[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, !found && tau + incl >= kFwdDepth);
+      if (hit) {
+        pred = base + 32 * j + (__ffs(hit) - 1) + 1 - rg.x;
+        found = true;
+      }
+      tau += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (lane == 0) {
+    const uint32_t w = (rg.y > rg.x ? pred : 0u) + 1u;
+    ts.work[tile] = w;
+    atomicAdd(&ts.hist[work_bucket(w)], 1u);
+  }
+}
+
 // One warp per tile: work = list entries the backward replays (up to one past the last
 // particle any of the tile's pixels blended, from n_used), and a histogram of the buckets.
 __global__ void k_tile_work(const __grid_constant__ BatchDesc bd, DevOpts op, const uint2 *__restrict__ ranges,
@@ -665,14 +729,14 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
 
 template <int DEG, bool RS>
 void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                const uint32_t *ranges, unsigned long long *stats, cudaStream_t s) {
+                const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
   const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
   if (stats)
     k_composite_fwd<DEG, RS, true><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                              reinterpret_cast<const uint2 *>(ranges), stats);
+                                                              reinterpret_cast<const uint2 *>(ranges), stats, ts);
   else
     k_composite_fwd<DEG, RS, false><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                               reinterpret_cast<const uint2 *>(ranges), nullptr);
+                                                               reinterpret_cast<const uint2 *>(ranges), nullptr, ts);
 }
 
 template <int DEG, bool RS, bool SMALL>
@@ -700,13 +764,21 @@ bool any_rs(const BatchDesc &bd) {
 
 }  // namespace
 
+// Predicts each tile's walk, orders the tiles longest first, then composites them in that order.
 ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                               const uint32_t *ranges, unsigned long long *stats, cudaStream_t s) {
+                               const uint32_t *ranges, unsigned long long *stats, void *sched, cudaStream_t s) {
   if (bd.total_tiles == 0) return UT_OK;
+  const TileSched ts = carve_tile_sched(sched, bd.total_tiles);
+  if (cudaMemsetAsync(ts.hist, 0, sizeof(uint32_t) * (2 * kOrderBuckets + 1), s) != cudaSuccess) return UT_ERR_CUDA;
+  k_fwd_predict<<<(bd.total_tiles + 7) / 8, 256, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
+                                                         reinterpret_cast<const uint2 *>(ranges), ts);
+  const int ob = (bd.total_tiles + kOrderBuckets - 1) / kOrderBuckets, cap = device_sm_count();
+  k_tile_order<<<ob < cap ? ob : cap, kOrderBuckets, 0, s>>>(bd.total_tiles, ts);
+  count_launches(2);
   const bool rs = any_rs(bd);
-#define UT3D_FWD(D)                                                 \
-  (rs ? fwd_launch<D, true>(bd, op, rect, vals, ranges, stats, s) \
-      : fwd_launch<D, false>(bd, op, rect, vals, ranges, stats, s))
+#define UT3D_FWD(D)                                                     \
+  (rs ? fwd_launch<D, true>(bd, op, rect, vals, ranges, stats, ts, s) \
+      : fwd_launch<D, false>(bd, op, rect, vals, ranges, stats, ts, s))
   switch (bd.s[0].deg) {
     case 0: UT3D_FWD(0); break;
     case 1: UT3D_FWD(1); break;

@@ -39,13 +39,14 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                      int64_t *k_out, cudaStream_t stream);
 
-// Compositing of every global tile of the batch into the views' outputs.
+// Compositing of every global tile of the batch into the views' outputs; sched: scratch of
+// tile_sched_bytes(total tiles) for the tile order.
 ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                               const uint32_t *ranges, unsigned long long *stats, cudaStream_t stream);
+                               const uint32_t *ranges, unsigned long long *stats, void *sched, cudaStream_t stream);
 
 // Backward of the batch into the scenes' gradient outputs (accumulators cleared here).
 size_t backward_workspace_bytes(int n);
-// Scratch of the backward's tile schedule for `tiles` tiles (one per backward call).
+// Scratch of a tile schedule (forward or backward) for `tiles` tiles.
 size_t tile_sched_bytes(int tiles);
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                                const uint32_t *ranges, void *sched, cudaStream_t stream);

@@ -140,7 +140,8 @@ class Frame:
 
 
 def composite_forward(scene: Scene, cam: dict, opts: dict | None, proj: Projection, binning: Binning,
-                      out: Frame | None = None, stats: torch.Tensor | None = None) -> Frame:
+                      out: Frame | None = None, stats: torch.Tensor | None = None,
+                      ws: Workspace | None = None) -> Frame:
     """composite_forward: front-to-back compositing with 3D max-response evaluation."""
     W, H = int(cam["width"]), int(cam["height"])
     dev = scene.means.device
@@ -150,9 +151,11 @@ def composite_forward(scene: Scene, cam: dict, opts: dict | None, proj: Projecti
                     torch.empty((H, W), dtype=torch.float32, device=dev),
                     torch.empty((H, W), dtype=torch.int32, device=dev))
     c, o, s = abi.make_camera(cam), abi.make_options(opts), scene.struct()
+    ws = ws or Workspace()
+    w = ws.get(abi.lib().ut_forward_workspace_size(C.byref(c), C.byref(o)), dev)
     st = abi.lib().composite_forward(C.byref(s), C.byref(c), C.byref(o), _ptr(proj.rect), _ptr(binning.vals),
                                      _ptr(binning.ranges), _ptr(out.rgb), _ptr(out.alpha), _ptr(out.t_final),
-                                     _ptr(out.n_used), _ptr(stats), _stream())
+                                     _ptr(out.n_used), _ptr(w), w.numel(), _ptr(stats), _stream())
     abi.check("composite_forward", st)
     return out
 
@@ -187,6 +190,7 @@ class Renderer:
     capacity: int = 1 << 20
     growth: float = 1.25
     ws: Workspace = field(default_factory=Workspace)
+    fws: Workspace = field(default_factory=Workspace)
     bws: Workspace = field(default_factory=Workspace)
     binning: Binning | None = None
     proj: Projection | None = None
@@ -204,7 +208,7 @@ class Renderer:
             if K <= self.binning.capacity:
                 break
             self.capacity = int(K * self.growth) + 1
-        self.frame = composite_forward(scene, self.cam, self.opts, self.proj, self.binning, self.frame)
+        self.frame = composite_forward(scene, self.cam, self.opts, self.proj, self.binning, self.frame, ws=self.fws)
         return self.frame
 
     def backward(self, scene: Scene, d_rgb: torch.Tensor, d_alpha: torch.Tensor):

@@ -53,6 +53,9 @@ def test_workspace_sizes(L):
     assert w >= 1000 * 16 * 4 + 2 * 4 * tiles and w % 256 == 0
     assert L.ut_backward_workspace_size(-1, C.byref(cam), C.byref(o)) == 0
     assert L.ut_backward_workspace_size(1000, None, C.byref(o)) == 0
+    f = L.ut_forward_workspace_size(C.byref(cam), C.byref(o))
+    assert f >= 2 * 4 * tiles and f % 256 == 0
+    assert L.ut_forward_workspace_size(None, C.byref(o)) == 0
 
 
 def _project(L, cam, opts=None, n=0, params=None):
