@@ -194,6 +194,13 @@ DevScene scene_desc(const ut_scene &s) {
   return d;
 }
 
+// Bits needed to hold the indices 0 .. count - 1.
+int bits_for_count(long long count) {
+  int b = 0;
+  while ((1ll << b) < count) ++b;
+  return b;
+}
+
 // A batch of one view of one scene (the single-view entry points).
 void single_view(BatchDesc &bd, const DevCam &cam, const DevOpts &op, const ut_scene *scene, int n) {
   std::memset(&bd, 0, sizeof(bd));
@@ -205,6 +212,9 @@ void single_view(BatchDesc &bd, const DevCam &cam, const DevOpts &op, const ut_s
   bd.v[0].n = n;
   bd.v[0].tiles_x = op.tiles_x;
   bd.v[0].tiles_y = op.tiles_y;
+  bd.total_cols = op.tiles_x;
+  bd.total_rows = op.tiles_y;
+  bd.col_bits = bits_for_count(op.tiles_x);
   if (scene) bd.s[0] = scene_desc(*scene);
   bd.s[0].n = n;
 }
@@ -237,7 +247,7 @@ ut_status make_batch(const ut_scene *scenes, int ns, const ut_view *views, int n
   }
   bd.ns = ns;
   bd.nv = nv;
-  long long part = 0, tiles = 0;
+  long long part = 0, tiles = 0, cols = 0, rows = 0, max_tx = 1;
   for (int v = 0; v < nv; ++v) {
     const ut_view &vw = views[v];
     if (vw.scene < 0 || vw.scene >= ns || !vw.rgb || !vw.alpha) return UT_ERR_INVALID_ARG;
@@ -253,6 +263,8 @@ ut_status make_batch(const ut_scene *scenes, int ns, const ut_view *views, int n
     d.tile_off = (int)tiles;
     d.tiles_x = o.tiles_x;
     d.tiles_y = o.tiles_y;
+    d.col_off = (int)cols;
+    d.row_off = (int)rows;
     d.rgb = vw.rgb;
     d.alpha = vw.alpha;
     d.tfinal = vw.t_final;
@@ -261,10 +273,18 @@ ut_status make_batch(const ut_scene *scenes, int ns, const ut_view *views, int n
     d.d_alpha = vw.d_alpha;
     part += d.n;
     tiles += (long long)o.tiles_x * o.tiles_y;
+    cols += o.tiles_x;
+    rows += o.tiles_y;
+    max_tx = o.tiles_x > max_tx ? o.tiles_x : max_tx;
   }
   if (part >= (1ll << 31) || tiles >= (1ll << 31)) return UT_ERR_INVALID_ARG;
   bd.total_particles = (int)part;
   bd.total_tiles = (int)tiles;
+  bd.total_cols = (int)cols;
+  bd.total_rows = (int)rows;
+  bd.col_bits = bits_for_count(max_tx);
+  // binning packs a global tile column and a particle's tile-row count into 16 bits each
+  if (cols > 0xffff || rows > 0xffff || bd.col_bits + bits_for_count(rows) > 32) return UT_ERR_INVALID_ARG;
   return UT_OK;
 }
 

@@ -2,14 +2,18 @@
 // (Sec. 4.3; the Duplicate and Sort phases of Table 2).
 //
 // The result equals a stable sort of key = (tile << 32) | bits(depth) over the entries
-// emitted per particle in index order and per tile in row-major order, but it is
-// computed in two cheaper steps:
+// emitted per particle in index order and per tile in row-major order, but it is computed
+// in cheaper steps:
 //   1. a stable LSD radix sort of the N particle depths (bits(depth), index);
-//   2. emission of the K (tile, particle) entries in that depth order, then a stable
-//      LSD radix sort on the tile id alone (ceil(log2 T) bits instead of 32 + log2 T).
-// Both orders are (tile, bits(depth), particle index), so the outputs are identical,
-// while step 2 moves 8 bytes per entry per pass over ceil(log2 T / 8) passes instead of
-// 12 bytes over ceil((32 + log2 T) / 8) passes.
+//   2. emission, in that depth order, of one entry per (particle, tile column) it covers,
+//      and a stable radix sort of those entries by global tile column;
+//   3. emission, in that (column, depth) order, of one entry per (particle, tile) — the
+//      rows of each column entry — and a stable radix sort by global tile row.
+// A stable sort by row of a sequence ordered by (column, depth) is ordered by
+// (row, column, depth) = (tile, depth), so the outputs are identical, while the K entries
+// pass through one 8-bit radix pass per ceil(log2 rows / 8) (one pass for a 1080p view)
+// instead of ceil(log2 tiles / 8) passes, and only the shorter column list (one entry per
+// covered column, not per tile) pays for the column order.
 //
 // The radix sort is the project's own: per 8-bit digit pass an upsweep (per-warp shared
 // histograms fed by uint4 key loads), a digit-major exclusive scan, and a downsweep that
@@ -32,14 +36,17 @@ constexpr int kRadixBits = 8;
 
 typedef unsigned long long u64;
 
-// Element count of a pass: a host constant, or a device total that is honoured only if
-// it fits the caller's capacity (0 otherwise, so an overflowing call writes nothing).
+// Element count of a pass: a host constant, or a device total that is honoured only if it
+// and the optional guard total (the call's K) fit the caller's capacity (0 otherwise, so an
+// overflowing call writes nothing).
 struct Count {
   const u64 *dev;
   u64 cap;
   uint32_t host;
+  const u64 *guard = nullptr;
   __device__ __forceinline__ uint32_t get() const {
     if (!dev) return host;
+    if (guard && *guard > cap) return 0u;
     u64 v = *dev;
     return v <= cap ? (uint32_t)v : 0u;
   }
@@ -85,7 +92,16 @@ __device__ __forceinline__ u64 block_excl_scan_u64(u64 x, u64 *s_warp, u64 &excl
 
 // ---------------------------------------------------------------- exclusive scan (u32 -> u32, u64 total)
 
-template <class L>
+// Input transforms of the scans: the value itself, or the upper 16 bits (the tile height a
+// column key carries).
+struct Ident {
+  __device__ __forceinline__ uint32_t operator()(uint32_t v) const { return v; }
+};
+struct High16 {
+  __device__ __forceinline__ uint32_t operator()(uint32_t v) const { return v >> 16; }
+};
+
+template <class L, class X = Ident>
 __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *__restrict__ in, L len,
                                                           u64 *__restrict__ chunk) {
   __shared__ u64 s_warp[kWarps + 1];
@@ -97,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *__rest
 #pragma unroll 4
     for (int i = 0; i < kIPT; ++i) {
       uint32_t p = base + i * kThreads + threadIdx.x;
-      if (p < n) s += in[p];
+      if (p < n) s += X()(in[p]);
     }
     u64 ex;
     u64 tot = block_excl_scan_u64(s, s_warp, ex);
@@ -135,7 +151,7 @@ __global__ void __launch_bounds__(1024) k_scan_spine(u64 *__restrict__ chunk, L 
 // skewed shared-memory index: conflict-free for both coalesced loads and per-thread runs
 __device__ __forceinline__ int skew(int p) { return p + (p >> 5); }
 
-template <class L>
+template <class L, class X = Ident>
 __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint32_t *out, L len,
                                                         const u64 *__restrict__ chunk) {
   __shared__ uint32_t s_v[kTile + kTile / 32];
@@ -148,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint
     for (int i = 0; i < kIPT; ++i) {
       int q = i * kThreads + threadIdx.x;
       uint32_t p = base + q;
-      s_v[skew(q)] = p < n ? in[p] : 0u;
+      s_v[skew(q)] = p < n ? X()(in[p]) : 0u;
     }
     __syncthreads();
     uint32_t v[kIPT];
@@ -193,7 +209,8 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 }
 
 // Per radix tile, the count of each digit (digit-major layout counts[d * nb + b]).  Keys are
-// read as uint4; every warp counts into its own shared histogram.
+// read as uint4 (the next tile's while the current one is counted into the warps' shared
+// histograms and totalled).
 __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t *__restrict__ keys, Count cnt, int shift,
                                                             uint32_t mask, uint32_t *__restrict__ counts) {
   __shared__ uint32_t s_wh[kWarps][256];
@@ -201,23 +218,41 @@ __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t *__re
   const uint32_t nb = (n + kRTile - 1) / kRTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *wh = s_wh[warp];
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    for (int d = lane; d < 256; d += 32) wh[d] = 0;
-    __syncwarp();
-    const uint32_t base = b * kRTile;
+  constexpr int kQ = kRIPT / 4;
+  uint32_t b = blockIdx.x;
+  if (b >= nb) return;
+  uint4 q[kQ];
+  auto load = [&](uint32_t t) {
+    const uint32_t base = t * kRTile;
     if (base + kRTile <= n) {
       const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + base);
 #pragma unroll
-      for (int i = 0; i < kRIPT / 4; ++i) {
-        uint4 q = k4[i * kThreads + threadIdx.x];
-        atomicAdd(&wh[(q.x >> shift) & mask], 1u);
-        atomicAdd(&wh[(q.y >> shift) & mask], 1u);
-        atomicAdd(&wh[(q.z >> shift) & mask], 1u);
-        atomicAdd(&wh[(q.w >> shift) & mask], 1u);
+      for (int i = 0; i < kQ; ++i) q[i] = k4[i * kThreads + threadIdx.x];
+    } else {  // ragged last tile: element loads, 0xffffffff marks "no key"
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const uint32_t p = base + 4 * (i * kThreads + threadIdx.x);
+        q[i].x = p < n ? keys[p] : 0xffffffffu;
+        q[i].y = p + 1 < n ? keys[p + 1] : 0xffffffffu;
+        q[i].z = p + 2 < n ? keys[p + 2] : 0xffffffffu;
+        q[i].w = p + 3 < n ? keys[p + 3] : 0xffffffffu;
       }
-    } else {
-      for (uint32_t p = base + threadIdx.x; p < n; p += kThreads) atomicAdd(&wh[(keys[p] >> shift) & mask], 1u);
     }
+  };
+  load(b);
+  for (; b < nb; b += gridDim.x) {
+    for (int d = lane; d < 256; d += 32) wh[d] = 0;
+    __syncwarp();
+    const uint32_t base = b * kRTile;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const uint32_t p = base + 4 * (i * kThreads + threadIdx.x);
+      if (p < n) atomicAdd(&wh[(q[i].x >> shift) & mask], 1u);
+      if (p + 1 < n) atomicAdd(&wh[(q[i].y >> shift) & mask], 1u);
+      if (p + 2 < n) atomicAdd(&wh[(q[i].z >> shift) & mask], 1u);
+      if (p + 3 < n) atomicAdd(&wh[(q[i].w >> shift) & mask], 1u);
+    }
+    if (b + gridDim.x < nb) load(b + gridDim.x);
     __syncthreads();
     if (threadIdx.x <= mask) {
       uint32_t s = 0;
@@ -229,6 +264,27 @@ __global__ void __launch_bounds__(kThreads) k_radix_upsweep(const uint32_t *__re
   }
 }
 
+// Keys and values of radix tile b (kRIPT per thread, warp-contiguous segments; past n: keys
+// 0xffffffff, which sort last and are never written out).
+__device__ __forceinline__ void load_radix_tile(const uint32_t *__restrict__ keys_in,
+                                                const uint32_t *__restrict__ vals_in, uint32_t n, uint32_t b,
+                                                uint32_t (&k)[kRIPT], uint32_t (&v)[kRIPT]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t base = b * kRTile + warp * (kRIPT * 32) + lane;
+#pragma unroll
+  for (int i = 0; i < kRIPT; ++i) {
+    const uint32_t p = base + i * 32;
+    const bool valid = p < n;
+    k[i] = valid ? keys_in[p] : 0xffffffffu;
+    v[i] = valid ? vals_in[p] : 0u;
+  }
+}
+
+// Stable scatter of one digit pass.  Per radix tile: every key's rank among the same-digit
+// keys of its warp segment (leader lane bumps the warp's digit counter, the old value is
+// broadcast), digit starts from the per-warp counts and a block scan, a scatter into shared
+// memory in digit order, and a write-out grouped by digit (coalesced runs).  The next tile's
+// keys, values and global digit offsets are loaded while the current tile is written out.
 __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
                                                               const uint32_t *__restrict__ vals_in,
                                                               uint32_t *__restrict__ keys_out,
@@ -245,28 +301,25 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int nd = (int)mask + 1;
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint32_t base = b * kRTile;
-    uint32_t k[kRIPT], v[kRIPT], rank[kRIPT];
-#pragma unroll
-    for (int i = 0; i < kRIPT; ++i) {
-      uint32_t p = base + warp * (kRIPT * 32) + i * 32 + lane;
-      bool valid = p < n;
-      k[i] = valid ? keys_in[p] : 0xffffffffu;
-      v[i] = valid ? vals_in[p] : 0u;
-    }
+  uint32_t b = blockIdx.x;
+  if (b >= nb) return;
+  uint32_t k[kRIPT], v[kRIPT];
+  load_radix_tile(keys_in, vals_in, n, b, k, v);
+  uint32_t goff = threadIdx.x < nd ? offsets[(size_t)threadIdx.x * nb + b] : 0u;
+  for (; b < nb; b += gridDim.x) {
     for (int d = lane; d < nd; d += 32) s_whist[warp][d] = 0;
     __syncwarp();
     // stable rank of every key among the same-digit keys of this warp's segment
+    uint32_t rank[kRIPT];
 #pragma unroll
     for (int i = 0; i < kRIPT; ++i) {
       const uint32_t d = (k[i] >> shift) & mask;
       const uint32_t peers = digit_peers(d);
-      const uint32_t before = s_whist[warp][d];
+      const int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (lane == leader) before = atomicAdd(&s_whist[warp][d], (uint32_t)__popc(peers));
+      before = __shfl_sync(0xffffffffu, before, leader);
       rank[i] = before + (uint32_t)__popc(peers & lt_mask);
-      __syncwarp();
-      if (lane == __ffs(peers) - 1) s_whist[warp][d] = before + (uint32_t)__popc(peers);
-      __syncwarp();
     }
     __syncthreads();
     // per digit: offsets of each warp's run, block totals, and the digit starts in the tile
@@ -278,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
         s_whist[w][threadIdx.x] = tot;
         tot += c;
       }
-      s_goff[threadIdx.x] = offsets[(size_t)threadIdx.x * nb + b];
+      s_goff[threadIdx.x] = goff;
     }
     u64 ex;
     block_excl_scan_u64(tot, s_warp, ex);
@@ -291,8 +344,13 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
       s_k[pos] = k[i];
       s_v[pos] = v[i];
     }
+    const uint32_t bn = b + gridDim.x;
+    if (bn < nb) {  // prefetch the next tile into the now free registers
+      load_radix_tile(keys_in, vals_in, n, bn, k, v);
+      goff = threadIdx.x < nd ? offsets[(size_t)threadIdx.x * nb + bn] : 0u;
+    }
     __syncthreads();
-    const uint32_t nvalid = min((uint32_t)kRTile, n - base);
+    const uint32_t nvalid = min((uint32_t)kRTile, n - b * kRTile);
     for (uint32_t j = threadIdx.x; j < nvalid; j += kThreads) {
       uint32_t kk = s_k[j];
       uint32_t d = (kk >> shift) & mask;
@@ -300,7 +358,8 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
       keys_out[g] = kk;
       vals_out[g] = s_v[j];
     }
-    __syncthreads();
+    // the next tile's first write to shared memory that the write-out reads (s_goff, s_dstart,
+    // s_k, s_v) comes after its first __syncthreads, so no barrier is needed here
   }
 }
 
@@ -314,73 +373,131 @@ __global__ void k_depth_init(int n, const float *__restrict__ depth, const uint3
   }
 }
 
-__global__ void k_gather_counts(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ ntiles,
-                                uint32_t *__restrict__ cnt) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) cnt[j] = ntiles[order[j]];
+// Depth order -> number of tile columns each particle covers (0 if culled).
+__global__ void k_gather_widths(int n, const uint32_t *__restrict__ order, const uint32_t *__restrict__ ntiles,
+                                const short4 *__restrict__ rect, int tile_w, uint32_t *__restrict__ cnt) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t g = order[j];
+    uint32_t w = 0;
+    if (ntiles[g]) {
+      const short4 r = rect[g];
+      w = (uint32_t)(r.z / tile_w - r.x / tile_w + 1);
+    }
+    cnt[j] = w;
+  }
 }
 
 __global__ void k_write_kout(const u64 *__restrict__ total, int64_t *__restrict__ k_out) { *k_out = (int64_t)*total; }
 
-// One warp per particle of the depth order: the warp fills the particle's contiguous run of
-// entries [offs[j], offs[j+1]) with consecutive lanes (coalesced), tiles in row-major order.
-// Entries of a batch: `order` holds flattened (view, particle) indices; the emitted key is
-// the global tile id (view's tile offset + row-major tile in the view) and the value is the
-// particle index within its scene.
-__global__ void __launch_bounds__(kThreads) k_emit(const __grid_constant__ BatchDesc bd, int n,
-                                                   const uint32_t *__restrict__ order,
-                                                   const uint32_t *__restrict__ offs, const short4 *__restrict__ rect,
-                                                   const u64 *__restrict__ total, u64 cap, int tile_w, int tile_h,
-                                                   uint32_t *__restrict__ tkeys, uint32_t *__restrict__ vals) {
-  const u64 K = *total;
-  if (K > cap) return;
+// Lane owning output position p among the warp's 32 consecutive runs (run l starts at
+// start_l; starts are non-decreasing, lanes past the items hold 0xffffffff): the last lane
+// whose run starts at or before p.  Every lane of the warp must call it.
+__device__ __forceinline__ int run_owner(uint32_t start, uint32_t p) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const uint32_t s = __shfl_sync(0xffffffffu, start, (lo + step) & 31);
+    if (lo + step < 32 && s <= p) lo += step;
+  }
+  return lo;
+}
+
+// Column entries, one warp per 32 particles of the depth order.  The particles' runs are
+// consecutive in the output, so the warp writes their union [start_0, end_31) with all lanes,
+// each lane finding the run of its position.  Key = (tile rows covered << 16) | global tile
+// column (the sort uses the low bits only; the height rides along for the row stage),
+// value = flattened particle index.
+__global__ void __launch_bounds__(kThreads) k_emit_cols(const __grid_constant__ BatchDesc bd, int n,
+                                                        const uint32_t *__restrict__ order,
+                                                        const uint32_t *__restrict__ offs,
+                                                        const uint32_t *__restrict__ widths,
+                                                        const short4 *__restrict__ rect, Count total, int tile_w,
+                                                        int tile_h, uint32_t *__restrict__ ckeys,
+                                                        uint32_t *__restrict__ cvals) {
+  if (total.get() == 0) return;  // nothing to emit, or more than the capacity
   const int lane = threadIdx.x & 31;
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   for (int j0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; j0 < n; j0 += nw * 32) {
-    // every lane fetches one of the 32 particles (independent loads in flight together)
     const int j = j0 + lane;
-    uint32_t start = 0, cnt = 0, local = 0;
-    int base = 0, w = 1, tiles_x = 0;
+    uint32_t start = 0xffffffffu, end = 0, g = 0, key0 = 0;
     if (j < n) {
       start = offs[j];
-      const uint32_t end = (j + 1 < n) ? offs[j + 1] : (uint32_t)K;
-      cnt = end - start;
-      if (cnt) {
-        const uint32_t g = order[j];
+      const uint32_t w = widths[j];
+      end = start + w;
+      if (w) {
+        g = order[j];
         const short4 r = rect[g];
-        const DevView &view = bd.v[view_of_particle(bd, (int)g)];
-        local = g - (uint32_t)view.part_off;
-        const int tx0 = r.x / tile_w, tx1 = r.z / tile_w, ty0 = r.y / tile_h;
-        w = tx1 - tx0 + 1;
-        tiles_x = view.tiles_x;
-        base = view.tile_off + ty0 * tiles_x + tx0;
+        const uint32_t h = (uint32_t)(r.w / tile_h - r.y / tile_h + 1);
+        key0 = (h << 16) | (uint32_t)(bd.v[view_of_particle(bd, (int)g)].col_off + r.x / tile_w);
       }
     }
-    // then the warp writes the particles' runs one after the other, lanes over the run
-    uint32_t todo = __ballot_sync(0xffffffffu, cnt > 0);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t s0 = __shfl_sync(0xffffffffu, start, src);
-      const uint32_t c0 = __shfl_sync(0xffffffffu, cnt, src);
-      const uint32_t l0 = __shfl_sync(0xffffffffu, local, src);
-      const int b0 = __shfl_sync(0xffffffffu, base, src);
-      const int w0 = __shfl_sync(0xffffffffu, w, src);
-      const int tx_0 = __shfl_sync(0xffffffffu, tiles_x, src);
-      const float inv_w = 1.f / (float)w0;
-      for (uint32_t q = lane; q < c0; q += 32) {
-        // row / column of the q-th tile of the rect: a float estimate, corrected to the exact quotient
-        int ty = (int)(((float)q + 0.5f) * inv_w);
-        if (ty * w0 > (int)q) --ty;
-        else if ((ty + 1) * w0 <= (int)q) ++ty;
-        const int tx = (int)q - ty * w0;
-        tkeys[s0 + q] = (uint32_t)(b0 + ty * tx_0 + tx);
-        vals[s0 + q] = l0;
+    const uint32_t S = __shfl_sync(0xffffffffu, start, 0);
+    const uint32_t E = __shfl_sync(0xffffffffu, end, min(31, n - 1 - j0));
+    for (uint32_t b = S; b < E; b += 32) {
+      const uint32_t p = b + lane;
+      const int l = run_owner(start, p);
+      const uint32_t s0 = __shfl_sync(0xffffffffu, start, l);
+      const uint32_t k0 = __shfl_sync(0xffffffffu, key0, l);
+      const uint32_t g0 = __shfl_sync(0xffffffffu, g, l);
+      if (p < E) {
+        ckeys[p] = k0 + (p - s0);
+        cvals[p] = g0;
       }
     }
   }
 }
 
-// Tile ranges from the sorted tile keys: four keys per thread (uint4) and their neighbours.
+// Row entries, one warp per 32 column entries (in column order), written like k_emit_cols:
+// each column entry expands into its particle's tile rows, ascending.  Key = (global tile
+// row << col_bits) | column within the view, value = particle index within its scene.
+__global__ void __launch_bounds__(kThreads) k_emit_rows(const __grid_constant__ BatchDesc bd, Count ccount,
+                                                        const uint32_t *__restrict__ ckeys,
+                                                        const uint32_t *__restrict__ cvals,
+                                                        const uint32_t *__restrict__ offs,
+                                                        const short4 *__restrict__ rect, Count total, int tile_h,
+                                                        uint32_t *__restrict__ rkeys, uint32_t *__restrict__ rvals) {
+  if (total.get() == 0) return;
+  const uint32_t m = ccount.get();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t i0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; i0 < m; i0 += nw * 32) {
+    const uint32_t i = i0 + lane;
+    uint32_t start = 0xffffffffu, end = 0, local = 0, key0 = 0;
+    if (i < m) {
+      const uint32_t ck = ckeys[i];
+      start = offs[i];
+      end = start + (ck >> 16);
+      const uint32_t g = cvals[i];
+      const DevView &view = bd.v[view_of_particle(bd, (int)g)];
+      local = g - (uint32_t)view.part_off;
+      const uint32_t tx = (ck & 0xffffu) - (uint32_t)view.col_off;
+      key0 = ((uint32_t)(view.row_off + rect[g].y / tile_h) << bd.col_bits) | tx;
+    }
+    const uint32_t S = __shfl_sync(0xffffffffu, start, 0);
+    const uint32_t E = __shfl_sync(0xffffffffu, end, (int)min(31u, m - 1 - i0));
+    for (uint32_t b = S; b < E; b += 32) {
+      const uint32_t p = b + lane;
+      const int l = run_owner(start, p);
+      const uint32_t s0 = __shfl_sync(0xffffffffu, start, l);
+      const uint32_t k0 = __shfl_sync(0xffffffffu, key0, l);
+      const uint32_t l0 = __shfl_sync(0xffffffffu, local, l);
+      if (p < E) {
+        rkeys[p] = k0 + ((p - s0) << bd.col_bits);
+        rvals[p] = l0;
+      }
+    }
+  }
+}
+
+// Global tile id of a sorted (row << col_bits | column) key.
+__device__ __forceinline__ uint32_t tile_of_key(const BatchDesc &bd, uint32_t key) {
+  const int row = (int)(key >> bd.col_bits);
+  const DevView &v = bd.v[view_of_row(bd, row)];
+  return (uint32_t)(v.tile_off + (row - v.row_off) * v.tiles_x) + (key & ((1u << bd.col_bits) - 1u));
+}
+
+// Tile ranges from the sorted keys: four keys per thread (uint4) and their neighbours (equal
+// keys <=> equal tiles).
 __global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *__restrict__ tkeys,
                          const uint32_t *__restrict__ vals, Count cnt, const float *__restrict__ depth,
                          uint32_t *__restrict__ ranges, uint64_t *__restrict__ keys) {
@@ -403,11 +520,14 @@ __global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *_
       const uint32_t p = p0 + i;
       if (p >= K) break;
       const uint32_t cur = t[1 + i];
-      if (t[i] != cur) ranges[2 * cur] = p;
-      if (t[2 + i] != cur) ranges[2 * cur + 1] = p + 1;
+      const bool first = t[i] != cur, last = t[2 + i] != cur;
+      if (!(first || last || keys)) continue;
+      const uint32_t tile = tile_of_key(bd, cur);
+      if (first) ranges[2 * tile] = p;
+      if (last) ranges[2 * tile + 1] = p + 1;
       if (keys) {
-        const int v = view_of_tile(bd, (int)cur);
-        keys[p] = ((uint64_t)cur << 32) | (uint64_t)__float_as_uint(depth[bd.v[v].part_off + vals[p]]);
+        const int v = view_of_tile(bd, (int)tile);
+        keys[p] = ((uint64_t)tile << 32) | (uint64_t)__float_as_uint(depth[bd.v[v].part_off + vals[p]]);
       }
     }
   }
@@ -429,44 +549,35 @@ struct Arena {
 inline uint32_t ceil_div(u64 a, u64 b) { return (uint32_t)((a + b - 1) / b); }
 
 struct Buffers {
-  uint32_t *dk[2], *dv[2], *cnt, *offs, *tk[2], *valt, *spine;
-  u64 *chunk, *total;
+  uint32_t *dk[2], *dv[2], *cnt, *offs, *x[3], *spine;
+  u64 *chunk, *total;  // total[0] = column entries, total[1] = K
 };
 
-Buffers carve(void *ws, int n, int64_t cap) {
+// Workspace layout; with ws == nullptr only the size is accumulated.
+Buffers carve(void *ws, int n, int64_t cap, size_t *bytes = nullptr) {
   Arena a{static_cast<char *>(ws), 0};
   Buffers b;
   size_t nn = (size_t)(n > 0 ? n : 1);
   size_t cc = (size_t)(cap > 0 ? cap : 1);
+  size_t maxc = nn > cc ? nn : cc;
   for (int i = 0; i < 2; ++i) b.dk[i] = a.take<uint32_t>(nn);
   for (int i = 0; i < 2; ++i) b.dv[i] = a.take<uint32_t>(nn);
-  b.cnt = a.take<uint32_t>(nn);
-  b.offs = a.take<uint32_t>(nn);
-  for (int i = 0; i < 2; ++i) b.tk[i] = a.take<uint32_t>(cc);
-  b.valt = a.take<uint32_t>(cc);
-  size_t maxc = nn > cc ? nn : cc;
+  b.cnt = a.take<uint32_t>(maxc);   // widths per particle, then heights per column entry
+  b.offs = a.take<uint32_t>(maxc);  // their exclusive scans
+  for (int i = 0; i < 3; ++i) b.x[i] = a.take<uint32_t>(cc);
   size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
   b.spine = a.take<uint32_t>(spine);
   size_t maxlen = spine > maxc ? spine : maxc;
   b.chunk = a.take<u64>(ceil_div(maxlen, kTile) + 1);
   b.total = a.take<u64>(2);
+  if (bytes) *bytes = a.off;
   return b;
 }
 
 size_t carve_bytes(int n, int64_t cap) {
-  Arena a{nullptr, 0};
-  size_t nn = (size_t)(n > 0 ? n : 1);
-  size_t cc = (size_t)(cap > 0 ? cap : 1);
-  a.take<uint32_t>(nn); a.take<uint32_t>(nn); a.take<uint32_t>(nn); a.take<uint32_t>(nn);
-  a.take<uint32_t>(nn); a.take<uint32_t>(nn);
-  a.take<uint32_t>(cc); a.take<uint32_t>(cc); a.take<uint32_t>(cc);
-  size_t maxc = nn > cc ? nn : cc;
-  size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
-  a.take<uint32_t>(spine);
-  size_t maxlen = spine > maxc ? spine : maxc;
-  a.take<u64>(ceil_div(maxlen, kTile) + 1);
-  a.take<u64>(2);
-  return a.off;
+  size_t bytes = 0;
+  carve(nullptr, n, cap, &bytes);
+  return bytes;
 }
 
 int grid_for(u64 items, int per_block) {
@@ -476,22 +587,23 @@ int grid_for(u64 items, int per_block) {
   return (int)(need < cap ? need : cap);
 }
 
-template <class L>
+template <class L, class X = Ident>
 void scan(const uint32_t *in, uint32_t *out, L len, u64 max_len, u64 *chunk, u64 *total, cudaStream_t s) {
   int g = grid_for(max_len, kTile);
-  k_scan_reduce<L><<<g, kThreads, 0, s>>>(in, len, chunk);
+  k_scan_reduce<L, X><<<g, kThreads, 0, s>>>(in, len, chunk);
   k_scan_spine<L><<<1, 1024, 0, s>>>(chunk, len, total);
-  k_scan_down<L><<<g, kThreads, 0, s>>>(in, out, len, chunk);
+  k_scan_down<L, X><<<g, kThreads, 0, s>>>(in, out, len, chunk);
   count_launches(3);
 }
 
 // Sorts (keys, vals) in place across the two buffers; returns the buffer index holding the result.
-int radix_sort(uint32_t *keys[2], uint32_t *vals[2], Count cnt, u64 max_count, int bits, uint32_t *spine, u64 *chunk,
-               cudaStream_t s) {
+// Bits [shift0, shift0 + bits) of the keys are sorted.
+int radix_sort(uint32_t *keys[2], uint32_t *vals[2], Count cnt, u64 max_count, int shift0, int bits,
+               uint32_t *spine, u64 *chunk, cudaStream_t s) {
   int cur = 0;
   int g = grid_for(max_count, kRTile);
-  for (int shift = 0; shift < bits; shift += kRadixBits) {
-    int db = bits - shift < kRadixBits ? bits - shift : kRadixBits;
+  for (int shift = shift0; shift < shift0 + bits; shift += kRadixBits) {
+    int db = shift0 + bits - shift < kRadixBits ? shift0 + bits - shift : kRadixBits;
     uint32_t mask = (1u << db) - 1u;
     k_radix_upsweep<<<g, kThreads, 0, s>>>(keys[cur], cnt, shift, mask, spine);
     SpineLen sl{cnt, (int)mask + 1};
@@ -519,35 +631,50 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
                      int64_t *k_out, cudaStream_t s) {
   const int n = bd.total_particles;
   const int tiles = bd.total_tiles;
+  const short4 *r4 = reinterpret_cast<const short4 *>(rect);
   Buffers b = carve(ws, n, cap);
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, s) != cudaSuccess) return UT_ERR_CUDA;
-  if (cudaMemsetAsync(b.total, 0, sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
+  if (cudaMemsetAsync(b.total, 0, 2 * sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
   if (n > 0) {
-    int g = grid_for(n, kThreads);
+    const int g = grid_for(n, kThreads);
+    const Count cn{nullptr, 0, (uint32_t)n};
+    // K = sum of ntiles (reported even when it exceeds the capacity)
+    k_scan_reduce<Count><<<grid_for(n, kTile), kThreads, 0, s>>>(ntiles, cn, b.chunk);
+    k_scan_spine<Count><<<1, 1024, 0, s>>>(b.chunk, cn, b.total + 1);
     k_depth_init<<<g, kThreads, 0, s>>>(n, depth, ntiles, b.dk[0], b.dv[0]);
-    count_launches(1);
-    Count cn{nullptr, 0, (uint32_t)n};
-    int r = radix_sort(b.dk, b.dv, cn, (u64)n, 32, b.spine, b.chunk, s);
-    k_gather_counts<<<g, kThreads, 0, s>>>(n, b.dv[r], ntiles, b.cnt);
+    count_launches(3);
+    const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s);
+    // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
+    // and the caller's vals, arranged so that the last row pass lands in vals
+    const int cbits = bits_for(bd.total_cols), rbits = bits_for(bd.total_rows);
+    const int cp = (cbits + kRadixBits - 1) / kRadixBits, rp = (rbits + kRadixBits - 1) / kRadixBits;
+    uint32_t *r0 = (rp & 1) ? b.x[2] : vals;           // row values start here ...
+    uint32_t *r1 = r0 == vals ? b.x[2] : vals;         // ... and end in vals
+    uint32_t *cv[2], *ck[2] = {b.x[0], b.x[1]};
+    cv[0] = (cp & 1) ? r0 : r1;                        // column values end in r1
+    cv[1] = cv[0] == r0 ? r1 : r0;
+    // 2. column entries in depth order, sorted by global tile column
+    k_gather_widths<<<g, kThreads, 0, s>>>(n, b.dv[r], ntiles, r4, op.tile_w, b.cnt);
     count_launches(1);
     scan(b.cnt, b.offs, cn, (u64)n, b.chunk, b.total, s);
-    // tile sort: the final pass must land in the caller's vals buffer
-    int tb = bits_for(tiles);
-    int passes = (tb + kRadixBits - 1) / kRadixBits;
-    uint32_t *tv[2];
-    tv[passes & 1] = vals;
-    tv[(passes & 1) ^ 1] = b.valt;
+    const Count cc{b.total, (u64)cap, 0, b.total + 1};  // nothing is written unless K fits
     const int eg = (int)std::min<u64>((u64)(n + kThreads - 1) / kThreads, (u64)device_sm_count() * 16);
-    k_emit<<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs,
-                                                              reinterpret_cast<const short4 *>(rect), b.total,
-                                                              (u64)cap, op.tile_w, op.tile_h, b.tk[0], tv[0]);
+    k_emit_cols<<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs, b.cnt, r4, cc, op.tile_w, op.tile_h, ck[0], cv[0]);
     count_launches(1);
-    Count ck{b.total, (u64)cap, 0};
-    int rr = radix_sort(b.tk, tv, ck, (u64)cap, tb, b.spine, b.chunk, s);
-    k_ranges<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(bd, b.tk[rr], tv[rr], ck, depth, ranges, keys);
+    const int rc = radix_sort(ck, cv, cc, (u64)cap, 0, cbits, b.spine, b.chunk, s);
+    // 3. row entries in (column, depth) order, sorted by global tile row; the run lengths are
+    //    the heights carried in the column keys
+    scan<Count, High16>(ck[rc], b.offs, cc, (u64)cap, b.chunk, nullptr, s);
+    const Count ck2{b.total + 1, (u64)cap, 0};
+    uint32_t *rk[2] = {ck[rc ^ 1], ck[rc]}, *rv[2] = {r0, r1};
+    const int rg = (int)std::min<u64>(((u64)cap + kThreads - 1) / kThreads, (u64)device_sm_count() * 16);
+    k_emit_rows<<<rg, kThreads, 0, s>>>(bd, cc, ck[rc], cv[rc], b.offs, r4, ck2, op.tile_h, rk[0], rv[0]);
+    count_launches(1);
+    const int rr = radix_sort(rk, rv, ck2, (u64)cap, bd.col_bits, rbits, b.spine, b.chunk, s);
+    k_ranges<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(bd, rk[rr], rv[rr], ck2, depth, ranges, keys);
     count_launches(1);
   }
-  k_write_kout<<<1, 1, 0, s>>>(b.total, k_out);
+  k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }

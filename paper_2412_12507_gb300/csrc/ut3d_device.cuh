@@ -51,6 +51,7 @@ struct DevView {
   int scene;
   int part_off, n;             // flattened particle range of this view
   int tile_off, tiles_x, tiles_y;
+  int col_off, row_off;         // global tile-column / tile-row offsets of this view (binning)
   float *rgb, *alpha, *tfinal;  // outputs ([3][H][W], [H][W], [H][W]); tfinal may be null
   uint32_t *n_used;             // [H][W], may be null
   const float *d_rgb, *d_alpha; // backward inputs
@@ -70,9 +71,21 @@ struct DevScene {
 struct BatchDesc {
   int nv, ns;
   int total_particles, total_tiles;
+  int total_cols, total_rows;   // tile columns / rows summed over the views
+  int col_bits;                 // bits of the largest per-view tile-column index
   DevView v[kMaxViews];
   DevScene s[kMaxScenes];
 };
+
+// View owning global tile row r (views are sorted by row_off).
+__device__ __forceinline__ int view_of_row(const BatchDesc &b, int r) {
+  int lo = 0, hi = b.nv - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.v[mid].row_off <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 // View owning flattened particle g (views are sorted by part_off).
 __device__ __forceinline__ int view_of_particle(const BatchDesc &b, int g) {
