@@ -3,10 +3,11 @@
 // hand-written backward (supplementary Sec. B), for a batch of views.
 //
 // One thread block per image tile (global tile ids over all views of the batch), one thread
-// per pixel.  The tile's depth-sorted particle list is consumed in batches of kBatch
-// particles: the block gathers each batch's parameters once, activates them (M = S^-1 R^T,
-// sigma, the alpha_min test threshold, packed rect) into shared memory together with their
-// SH coefficients, and every pixel then walks the batch from shared memory.  The block
+// per pixel.  The tile's depth-sorted particle list is consumed in batches of kBatchF
+// (forward) or kBatch (backward) particles: the block gathers each batch's parameters once,
+// activates them (M = S^-1 R^T, sigma, the alpha_min test threshold, packed rect) into
+// shared memory together with their SH coefficients, and every pixel then walks the batch
+// from shared memory.  The block
 // leaves the list as soon as every pixel's transmittance has dropped below t_min.
 //
 // The backward replays the forward IN FORWARD ORDER: the stored rgb and T_final give the
@@ -28,7 +29,8 @@
 namespace ut3d {
 namespace {
 
-constexpr int kBatch = 64;
+constexpr int kBatch = 64;    // particles staged per block step (backward)
+constexpr int kBatchF = 128;  // particles staged per block step (forward)
 constexpr int kOrderBuckets = 1024;  // log buckets of the backward's tile schedule
 
 // Tile schedule of the backward (device scratch): per-tile replay length, the tiles with work
@@ -180,9 +182,9 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
                                                        unsigned long long *__restrict__ stats, TileSched ts) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
-  __shared__ float4 s_geo[kBatch][4];
-  __shared__ __align__(16) float s_sh[kBatch * NC];
-  __shared__ uint32_t s_idx[kBatch];
+  __shared__ float4 s_geo[kBatchF][4];
+  __shared__ __align__(16) float s_sh[kBatchF * NC];
+  __shared__ uint32_t s_idx[kBatchF];
 
   // tiles in the order k_tile_order gave them (longest predicted walk first); every tile is
   // in the order, so every pixel is written
@@ -206,14 +208,14 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   unsigned long long n_eval = 0, n_blend = 0;
   bool done = !valid;
   const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+  for (uint32_t start = rg.x; start < rg.y; start += kBatchF) {
     if (__syncthreads_count(!done) == 0) break;
-    const int nb = min((uint32_t)kBatch, rg.y - start);
-    if (threadIdx.x < nb) s_idx[threadIdx.x] = vals[start + threadIdx.x];
+    const int nb = min((uint32_t)kBatchF, rg.y - start);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
     __syncthreads();
-    if (threadIdx.x < nb) {
-      uint32_t idx = s_idx[threadIdx.x];
-      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[threadIdx.x], nullptr);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      uint32_t idx = s_idx[t];
+      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], nullptr);
     }
     stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
