@@ -62,6 +62,29 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def dist_env():
+    """(world size, rank, local rank) of this process; 1, 0, 0 without a launcher."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The maximum of a per-rank number over all ranks (a job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_s(pixels_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank renders its own replica, so the job's pixels are
+    world x pixels_per_rank in the slowest rank's time."""
+    return world * pixels_per_rank / (ms / 1e3) / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -174,8 +197,8 @@ def oracle_frame_time(case, budget_s, seed=0):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = dist_env()
+    if rank != 0:  # under torchrun only rank 0 times the oracle; the others exit without work
         return
     case = workload(args.workload)
     W, H = case["camera"]["width"], case["camera"]["height"]
@@ -348,9 +371,7 @@ def run_ours(args):
 
     from paper_2412_12507_gb300 import abi, build, render
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -398,12 +419,7 @@ def run_ours(args):
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms / steps
+        return max_over_ranks(e0.elapsed_time(e1), world, dev) / steps
 
     # launches per step (host-side counter of the library)
     c0 = L.ut_kernel_launch_count()
@@ -517,17 +533,17 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * P / (fwd_ms / 1e3) / 1e6, "unit": "Mpix/s", "n_gpus": world,
+            "metric": METRIC, "value": job_mpix_s(P, world, fwd_ms), "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": fwd_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": case["name"], "particles": n, "width": W, "height": H,
                        "camera": "fisheye+rolling_shutter", "sh_degree": int(sc_np["sh_degree"]),
                        "tile": f"{op['tile_w']}x{op['tile_h']}", "keys": K, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (236 MB scene + 2 x keys), no flush"},
-            "fwd_ms": fwd_ms, "fwd_bwd_ms_per_view": fb_ms, "fwd_bwd_mpix_s": world * P / (fb_ms / 1e3) / 1e6,
+            "fwd_ms": fwd_ms, "fwd_bwd_ms_per_view": fb_ms, "fwd_bwd_mpix_s": job_mpix_s(P, world, fb_ms),
             "kernels": kernels, "evaluations": n_eval, "blended": n_blend,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "e2e": {"value": world * P / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_mpix_s(P, world, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
             "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
