@@ -56,7 +56,7 @@ class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("t_min", C.c_double),
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("rs_iters", C.c_int32),
                 ("ut_alpha", C.c_double), ("ut_beta", C.c_double), ("ut_kappa", C.c_double),
-                ("extent_sigma", C.c_double)]
+                ("extent_sigma", C.c_double), ("projection", C.c_int32), ("colour_mode", C.c_int32)]
 
 
 class Tol(C.Structure):
@@ -80,6 +80,8 @@ def lib():
         L.orc_ut_estimate.restype = C.c_int
         L.orc_ut_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, C.c_double, C.c_double,
                                       C.c_double, P, P, P, P, P, P, P]
+        L.orc_ewa_estimate.restype = C.c_int
+        L.orc_ewa_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, P, P, P, P, P, P, P]
         L.orc_project.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), C.POINTER(Tol),
                                   P, P, P, P, P, P, P, P]
         L.orc_count_keys.restype = C.c_int64
@@ -144,6 +146,8 @@ def make_options(opts: dict | None = None) -> Options:
     r.ut_alpha, r.ut_beta, r.ut_kappa = (float(o.get(k, d)) for k, d in
                                          (("ut_alpha", 1.0), ("ut_beta", 2.0), ("ut_kappa", 0.0)))
     r.extent_sigma = float(o.get("extent_sigma", 3.0))
+    r.projection = int(o.get("projection", 0))    # 0 UT, 1 EWA
+    r.colour_mode = int(o.get("colour_mode", 0))  # 0 per pixel, 1 per particle
     return r
 
 
@@ -217,8 +221,18 @@ def ut_estimate(cam: dict, mu, R, s, ut=(1.0, 2.0, 0.0), rs_iters: int = 3):
     return bool(v), vmu, cov
 
 
+def ewa_estimate(cam: dict, mu, R, s, rs_iters: int = 3):
+    """First-order (EWA) 2D mean and covariance (xx, xy, yy) of one Gaussian (eq. ewa_splatting)."""
+    c = make_camera(cam)
+    tm = theta_max(c.k) if c.model == 1 else np.pi / 2
+    vmu, cov, t, m = np.zeros(2), np.zeros(3), np.zeros(1), np.zeros(1)
+    v = lib().orc_ewa_estimate(C.byref(c), tm, rs_iters, _p(_f64(mu)), _p(_f64(np.asarray(R).reshape(9))),
+                               _p(_f64(s)), _p(vmu), _p(cov), _p(t), _p(m))
+    return bool(v), vmu, cov
+
+
 def project(scene: dict, cam: dict, opts: dict | None = None, tol: dict | None = None) -> dict:
-    """Per-particle UT projection (Algorithm 1) for the whole scene."""
+    """Per-particle projection (Algorithm 1; UT, or EWA when opts["projection"] == 1) of the scene."""
     S = _SceneArrays(scene)
     n = S.n
     out = dict(mean2d=np.zeros((n, 2)), cov2d=np.zeros((n, 3)), depth=np.zeros(n),

@@ -16,6 +16,8 @@
  *     shutter ("a different extrinsic matrix" per sigma point, Sec. 1).
  *   - Duplicate keys (tile | depth) and their global stable sort per tile
  *     (Sec. 4.3, Table 2 phases Duplicate and Sort).
+ *   - The first-order (EWA) projection Sigma' = J W Sigma W^T J^T of 3DGS (eq. ewa_splatting),
+ *     with J the Jacobian of the camera map at the mean, as the A/B baseline of the UT.
  *   - Front-to-back volumetric compositing (eq. QuadratureVolumeRendering) with
  *     each particle evaluated in 3D at its maximum response along the pixel ray
  *     (Sec. 4.2, eq. GaussianMaxResponse), brute force over ALL particles in
@@ -67,6 +69,9 @@ typedef struct {
   int32_t rs_iters;
   double ut_alpha, ut_beta, ut_kappa;
   double extent_sigma;
+  int32_t projection;  /* 0: Unscented Transform (Sec. 4.1); 1: first-order EWA (eq. ewa_splatting) */
+  int32_t colour_mode; /* 0: SH at each pixel's ray direction; 1: SH once per particle at the
+                          direction from the camera centre (at the mean's shutter time) to the mean */
 } orc_options;
 
 /* near-tie tolerances used only to flag pixels whose FP32 result may legitimately differ */
@@ -400,7 +405,76 @@ int orc_ut_estimate(const orc_camera *c, double theta_max, int rs_iters, double 
   return 1;
 }
 
-/* Per-particle projection (Algorithm 1): UT estimate, opacity-tightened extent,
+/* Jacobian d g / d x_c (2x3, row-major) of the camera map at a camera-space point.
+ * Pinhole: u = fx X/Z + cx.  Fisheye: u = fx s X + cx with s = theta_d(theta)/rho,
+ * theta = atan2(rho, Z), so d s = (theta_d' d theta - s d rho) / rho with
+ * d theta = (X Z, Y Z, -rho^2) / (rho r^2) and d rho = (X, Y, 0) / rho; on the axis (rho = 0)
+ * theta_d ~ rho / Z and the map is the pinhole one.  Orthographic: u = fx X + cx. */
+static void orc_cam_jacobian(const orc_camera *c, const double xc[3], double J[6]) {
+  double X = xc[0], Y = xc[1], Z = xc[2];
+  if (c->model == 0) {
+    J[0] = c->fx / Z; J[1] = 0.0; J[2] = -c->fx * X / (Z * Z);
+    J[3] = 0.0; J[4] = c->fy / Z; J[5] = -c->fy * Y / (Z * Z);
+  } else if (c->model == 1) {
+    double rho2 = X * X + Y * Y, rho = sqrt(rho2), r2 = rho2 + Z * Z;
+    if (rho > 0.0) {
+      double th = atan2(rho, Z);
+      double s = orc_theta_d(c->k, th) / rho, tdp = orc_theta_d_prime(c->k, th);
+      double dth[3] = {X * Z / (rho * r2), Y * Z / (rho * r2), -rho / r2};
+      double drho[3] = {X / rho, Y / rho, 0.0};
+      double ds[3];
+      for (int j = 0; j < 3; ++j) ds[j] = (tdp * dth[j] - s * drho[j]) / rho;
+      J[0] = c->fx * (s + X * ds[0]); J[1] = c->fx * X * ds[1]; J[2] = c->fx * X * ds[2];
+      J[3] = c->fy * Y * ds[0]; J[4] = c->fy * (s + Y * ds[1]); J[5] = c->fy * Y * ds[2];
+    } else {
+      J[0] = c->fx / Z; J[1] = 0.0; J[2] = 0.0;
+      J[3] = 0.0; J[4] = c->fy / Z; J[5] = 0.0;
+    }
+  } else {
+    J[0] = c->fx; J[1] = 0.0; J[2] = 0.0;
+    J[3] = 0.0; J[4] = c->fy; J[5] = 0.0;
+  }
+}
+
+/* First-order (EWA) estimate of the 2D mean and covariance (eq. ewa_splatting, the 3DGS
+ * baseline the UT replaces): v_mu = g(W mu) and Sigma' = J W Sigma W^T J^T, J the Jacobian of g
+ * at the camera-space mean.  Under a rolling shutter W is the pose at the mean's own shutter
+ * time (the fixed point of orc_project_world); the dependence of the pose on the projected row
+ * is not linearised.  Only the mean must project validly. */
+int orc_ewa_estimate(const orc_camera *c, double theta_max, int rs_iters, const double mu[3], const double R[9],
+                     const double s[3], double vmu[2], double cov[3], double *t_mean, double *margin) {
+  double t = 0.0, m = INFINITY;
+  int valid = orc_project_world(c, theta_max, rs_iters, mu, vmu, &t, &m);
+  if (t_mean) *t_mean = t;
+  if (margin) *margin = m;
+  if (!valid) return 0;
+  double Rc[9], Tc[3], xc[3], J[6], A[6];
+  orc_pose_at(c, t, Rc, Tc);
+  for (int r = 0; r < 3; ++r) xc[r] = Rc[3 * r] * mu[0] + Rc[3 * r + 1] * mu[1] + Rc[3 * r + 2] * mu[2] + Tc[r];
+  orc_cam_jacobian(c, xc, J);
+  /* A = J W (R S): column k is J W (s_k R[:,k]); Sigma' = A A^T */
+  for (int k = 0; k < 3; ++k) {
+    double col[3] = {s[k] * R[k], s[k] * R[3 + k], s[k] * R[6 + k]}, w[3];
+    for (int r = 0; r < 3; ++r) w[r] = Rc[3 * r] * col[0] + Rc[3 * r + 1] * col[1] + Rc[3 * r + 2] * col[2];
+    A[k] = J[0] * w[0] + J[1] * w[1] + J[2] * w[2];
+    A[3 + k] = J[3] * w[0] + J[4] * w[1] + J[5] * w[2];
+  }
+  cov[0] = A[0] * A[0] + A[1] * A[1] + A[2] * A[2];
+  cov[1] = A[0] * A[3] + A[1] * A[4] + A[2] * A[5];
+  cov[2] = A[3] * A[3] + A[4] * A[4] + A[5] * A[5];
+  return 1;
+}
+
+/* The projection the options select: UT (Algorithm 2) or EWA. */
+static int orc_estimate(const orc_camera *c, double theta_max, const orc_options *op, const double mu[3],
+                        const double R[9], const double s[3], double vmu[2], double cov[3], double *t_mean,
+                        double *margin) {
+  if (op->projection == 1) return orc_ewa_estimate(c, theta_max, op->rs_iters, mu, R, s, vmu, cov, t_mean, margin);
+  return orc_ut_estimate(c, theta_max, op->rs_iters, op->ut_alpha, op->ut_beta, op->ut_kappa, mu, R, s, vmu, cov,
+                         t_mean, margin);
+}
+
+/* Per-particle projection (Algorithm 1): UT (or EWA) estimate, opacity-tightened extent,
  * pixel rectangle, depth, tile count.
  * Outputs (arrays of n): mean2d[2], cov2d[3], depth (FP64), depth32 (the FP64 depth rounded
  * to FP32, which enters the sort key), rect[4] = (x0,y0,x1,y1) inclusive pixel indices
@@ -428,8 +502,7 @@ void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op
     double sig_margin = (p.sigma - op->alpha_min) / op->alpha_min;
     if (fabs(sig_margin) < tol->eps_rel) tie[i] = 1;
     double vmu[2], cov[3], tmu = 0.0, vm;
-    int valid = orc_ut_estimate(c, theta_max, op->rs_iters, op->ut_alpha, op->ut_beta, op->ut_kappa, p.mu,
-                                p.R, p.s, vmu, cov, &tmu, &vm);
+    int valid = orc_estimate(c, theta_max, op, p.mu, p.R, p.s, vmu, cov, &tmu, &vm);
     if (fabs(vm) < tol->eps_rel) tie[i] = 1;
     if (!valid) {
       if (tie[i]) {
@@ -438,8 +511,7 @@ void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op
         c2.near_plane = 1e-9;
         /* the polynomial fisheye extends to the whole sphere but the pole behind the camera */
         double th2 = c->model == 1 ? ORC_PI : theta_max;
-        if (orc_ut_estimate(&c2, th2, op->rs_iters, op->ut_alpha, op->ut_beta,
-                            op->ut_kappa, p.mu, p.R, p.s, vmu, cov, NULL, NULL)) {
+        if (orc_estimate(&c2, th2, op, p.mu, p.R, p.s, vmu, cov, NULL, NULL)) {
           double k = op->extent_sigma;
           double hx = k * sqrt(cov[0]), hy = k * sqrt(cov[2]);
           edges[4 * i + 0] = vmu[0] - hx - 0.5; edges[4 * i + 1] = vmu[0] + hx - 0.5;
@@ -549,6 +621,8 @@ typedef struct {
   int norder;
   int32_t *tie_list;
   int ntie;
+  double *Yp;    /* colour_mode 1: SH basis at each particle's direction [n][16] */
+  double *dYdmu; /* colour_mode 1: its derivative with respect to the mean [n][3][16] */
 } orc_ctx;
 
 static const float *orc_depth_sort_key;
@@ -569,6 +643,7 @@ static void orc_ctx_init(orc_ctx *x, const orc_scene *sc, const int32_t *rect, c
   x->tie_list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(sc->n > 0 ? sc->n : 1));
   x->rect = rect; x->depth32 = depth32; x->edges = edges; x->tie = tie;
   x->norder = 0; x->ntie = 0;
+  x->Yp = NULL; x->dYdmu = NULL;
   for (int i = 0; i < sc->n; ++i) {
     orc_load_particle(sc, i, &x->P[i]);
     const int32_t *r = rect + 4 * i;
@@ -579,7 +654,51 @@ static void orc_ctx_init(orc_ctx *x, const orc_scene *sc, const int32_t *rect, c
   qsort(x->order, (size_t)x->norder, sizeof(int32_t), orc_order_cmp);
 }
 
-static void orc_ctx_free(orc_ctx *x) { free(x->P); free(x->order); free(x->tie_list); }
+static void orc_ctx_free(orc_ctx *x) { free(x->P); free(x->order); free(x->tie_list); free(x->Yp); free(x->dYdmu); }
+
+/* Colour direction of a particle in colour_mode 1: the unit vector from the camera centre
+ * -R(t)^T T(t), at the mean's shutter time t (the fixed point of orc_project_world), to mu. */
+static void orc_particle_dir(const orc_camera *c, double theta_max, int rs_iters, const double mu[3],
+                             double dir[3]) {
+  double uv[2], t = 0.0, m, R[9], T[3], v[3];
+  orc_project_world(c, theta_max, rs_iters, mu, uv, &t, &m);
+  orc_pose_at(c, t, R, T);
+  for (int j = 0; j < 3; ++j) v[j] = mu[j] + (R[j] * T[0] + R[3 + j] * T[1] + R[6 + j] * T[2]);
+  double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int j = 0; j < 3; ++j) dir[j] = v[j] / nv;
+}
+
+/* colour_mode 1: the SH basis at every particle's direction, and its derivative with respect
+ * to the mean by FP64 central differences (the shutter time, like the whole projection, is a
+ * discrete selection and carries no gradient: it is held fixed). */
+static void orc_ctx_colour(orc_ctx *x, const orc_camera *c, double theta_max, const orc_options *op) {
+  size_t n = (size_t)(x->n > 0 ? x->n : 1);
+  x->Yp = (double *)calloc(n * 16, sizeof(double));
+  x->dYdmu = (double *)calloc(n * 48, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int q = 0; q < x->norder; ++q) {
+    int i = x->order[q];
+    const orc_particle *p = &x->P[i];
+    double dir[3], uv[2], t = 0.0, m, R[9], T[3], C[3];
+    orc_particle_dir(c, theta_max, op->rs_iters, p->mu, dir);
+    orc_sh_basis(x->deg, dir, x->Yp + 16 * (size_t)i);
+    orc_project_world(c, theta_max, op->rs_iters, p->mu, uv, &t, &m);
+    orc_pose_at(c, t, R, T);
+    for (int j = 0; j < 3; ++j) C[j] = -(R[j] * T[0] + R[3 + j] * T[1] + R[6 + j] * T[2]);
+    double v[3] = {p->mu[0] - C[0], p->mu[1] - C[1], p->mu[2] - C[2]};
+    double h = 1e-5 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int j = 0; j < 3; ++j) {
+      double vp[3] = {v[0], v[1], v[2]}, vm[3] = {v[0], v[1], v[2]}, Yp[16], Ym[16];
+      vp[j] += h; vm[j] -= h;
+      double np = sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
+      double nm = sqrt(vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]);
+      for (int r = 0; r < 3; ++r) { vp[r] /= np; vm[r] /= nm; }
+      orc_sh_basis(x->deg, vp, Yp);
+      orc_sh_basis(x->deg, vm, Ym);
+      for (int k = 0; k < x->nsh; ++k) x->dYdmu[48 * (size_t)i + 16 * j + k] = (Yp[k] - Ym[k]) / (2.0 * h);
+    }
+  }
+}
 
 /* Maximum response of particle p along the ray o + tau d (eq. GaussianMaxResponse):
  * o_g = S^-1 R^T (o - mu), d_g = S^-1 R^T d, tau_max = -o_g.d_g / d_g.d_g, and the squared
@@ -656,10 +775,11 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     double alpha = a < op->alpha_max ? a : op->alpha_max;
     double Tn = T * (1.0 - alpha);
     const float *beta = sc->sh + (size_t)i * x->nsh * 3;
+    const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
     double raw[3], col[3], cmax = 0.0;
     for (int ch = 0; ch < 3; ++ch) {
       double s = 0.5;
-      for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Y[kk];
+      for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Yc[kk];
       raw[ch] = s;
       col[ch] = s > 0.0 ? s : 0.0;
       cmax = fmax(cmax, col[ch]);
@@ -724,6 +844,7 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, edges, tie);
   double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int q = 0; q < npix; ++q) {
     int px = pix_x[q], py = pix_y[q];
@@ -764,6 +885,7 @@ void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options
   for (int j = 0; j < nlist; ++j) x.order[j] = (int32_t)list[j];
   x.norder = nlist;
   double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
   orc_tol tol = {0, 0, 0, 0, 0};
   double o[3], d[3], Y[16];
   int valid;
@@ -799,8 +921,9 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
   int n = sc->n, nsh = x.nsh;
   double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
-  /* accumulators: dM (9), dmu (3), dsigma (1) */
-  double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 13, sizeof(double));
+  if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
+  /* accumulators: dM (9), dmu (3), dsigma (1), dL/d colour (3, colour_mode 1) */
+  double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double));
   memset(d_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
   orc_tol tol = {0, 0, 0, 0, 0};
 #pragma omp parallel
@@ -825,10 +948,16 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
         double dalpha = gA * Tf / om1;
         for (int ch = 0; ch < 3; ++ch) dalpha += g[ch] * (k->col[ch] * k->T - S[ch] / om1);
         for (int ch = 0; ch < 3; ++ch) S[ch] += k->col[ch] * k->alpha * k->T;
-        /* colour: d c / d beta = Y where the clamp is inactive */
+        /* colour: d c / d beta = Y where the clamp is inactive (colour_mode 1: the particle's
+         * basis, and the colour gradient is kept to be mapped onto beta and mu below) */
         for (int ch = 0; ch < 3; ++ch) {
           if (!(k->raw[ch] > 0.0)) continue;
           double gc = g[ch] * k->alpha * k->T;
+          if (op->colour_mode == 1) {
+#pragma omp atomic
+            acc[16 * (size_t)k->i + 13 + ch] += gc;
+            continue;
+          }
           for (int kk = 0; kk < nsh; ++kk) {
 #pragma omp atomic
             d_sh[((size_t)k->i * nsh + kk) * 3 + ch] += gc * Y[kk];
@@ -842,7 +971,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
           pv[j] = 2.0 * dw2 * (k->og[j] + k->tau * k->dg[j]); /* dL/d o_g */
           xw[j] = o[j] - p->mu[j] + k->tau * d[j];             /* o - mu + tau d */
         }
-        double *A = acc + 13 * (size_t)k->i;
+        double *A = acc + 16 * (size_t)k->i;
         for (int r = 0; r < 3; ++r)
           for (int j = 0; j < 3; ++j) {
 #pragma omp atomic
@@ -861,8 +990,21 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   }
   for (int i = 0; i < n; ++i) {
     const orc_particle *p = &x.P[i];
-    const double *A = acc + 13 * (size_t)i;
+    const double *A = acc + 16 * (size_t)i;
     for (int j = 0; j < 3; ++j) d_means[3 * i + j] = A[9 + j];
+    if (op->colour_mode == 1) {
+      /* c_ch = sum_k beta_k,ch Y_k(dir(mu)) + 1/2: dL/dbeta_k,ch = gc_ch Y_k and
+       * dL/dmu_j += sum_ch gc_ch sum_k beta_k,ch dY_k/dmu_j */
+      const float *beta = sc->sh + (size_t)i * nsh * 3;
+      for (int ch = 0; ch < 3; ++ch) {
+        double gc = A[13 + ch];
+        if (gc == 0.0) continue;
+        for (int kk = 0; kk < nsh; ++kk) {
+          d_sh[((size_t)i * nsh + kk) * 3 + ch] += gc * x.Yp[16 * (size_t)i + kk];
+          for (int j = 0; j < 3; ++j) d_means[3 * i + j] += gc * beta[3 * kk + ch] * x.dYdmu[48 * (size_t)i + 16 * j + kk];
+        }
+      }
+    }
     /* M_kj = R_jk / s_k, s_k = exp(l_k): dL/dl_k = -sum_j dM_kj M_kj; dL/dR_jk = dM_kj / s_k */
     double G[9];
     for (int k = 0; k < 3; ++k) {

@@ -489,6 +489,118 @@ def test_bin_edge_cases(orc):
     assert len(k) == 0 and not r.any()
 
 
+# ------------------------------------------------------------------ EWA projection (the A/B baseline)
+
+def test_ewa_exact_for_affine_camera(orc):
+    """For an affine camera the first-order (EWA) estimate is exact: A mu + b, A Sigma A^T."""
+    rng = np.random.default_rng(12)
+    Rc = axis_angle_rot([0.3, -1.0, 0.2], 0.7)
+    cam = synth.camera("ortho", 100, 80, fx=37.0, fy=29.0, cx=41.0, cy=33.0, q=synth._rot_to_quat(Rc),
+                       t=np.array([0.2, -0.1, 1.5]))
+    Rc, tc = rot(cam["q_start"]), np.array(cam["t_start"])
+    for _ in range(10):
+        mu = rng.uniform(-1, 1, 3)
+        R = rot(rng.standard_normal(4))
+        s = np.exp(rng.normal(-1.5, 0.5, 3))
+        ok, vmu, cov = orc.ewa_estimate(cam, mu, R, s)
+        assert ok
+        A = np.array([[37.0, 0, 0], [0, 29.0, 0]]) @ Rc
+        C2 = A @ (R @ np.diag(s**2) @ R.T) @ A.T
+        assert np.allclose(vmu, A @ mu + np.array([37.0 * tc[0] + 41.0, 29.0 * tc[1] + 33.0]), atol=1e-10)
+        assert np.allclose(cov, [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("model,k", [("pinhole", (0, 0, 0, 0)), ("fisheye", (0, 0, 0, 0)),
+                                     ("fisheye", (0.04, -0.03, 0.01, -0.005))])
+def test_ewa_jacobian_matches_finite_differences(orc, model, k):
+    """EWA covariance = J Sigma J^T with J = d g(W x) / d x at the mean, here taken by central
+    differences of the oracle's own world-to-pixel map (an independent route to J), at points
+    across the field of view including the optical axis."""
+    rng = np.random.default_rng(13)
+    q, t = synth.look_at_pose([0.3, -0.2, -3.0])
+    cam = synth.camera(model, 640, 480, k=list(k), q=q, t=t) if model == "fisheye" else \
+        synth.camera(model, 640, 480, fx=400.0, fy=380.0, q=q, t=t)
+    Rc, tc = rot(cam["q_start"]), np.array(cam["t_start"])
+    pts = [-Rc.T @ tc + Rc.T @ np.array([0.0, 0.0, 2.5])]  # on the optical axis
+    while len(pts) < 12:
+        d = Rc.T @ np.array([*rng.uniform(-0.9, 0.9, 2), 1.0])
+        pts.append(-Rc.T @ tc + rng.uniform(1.5, 4.0) * d)
+    for mu in pts:
+        R = rot(rng.standard_normal(4))
+        s = np.exp(rng.normal(-2.5, 0.4, 3))
+        ok, vmu, cov = orc.ewa_estimate(cam, mu, R, s)
+        assert ok
+        h = 1e-6
+        J = np.zeros((2, 3))
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = h
+            J[:, j] = (orc.project_point(cam, mu + e)[1] - orc.project_point(cam, mu - e)[1]) / (2 * h)
+        C2 = J @ (R @ np.diag(s**2) @ R.T) @ J.T
+        assert np.allclose(vmu, orc.project_point(cam, mu)[1], atol=1e-9)
+        assert np.allclose(cov, [C2[0, 0], C2[0, 1], C2[1, 1]], rtol=1e-6, atol=1e-6 * np.abs(C2).max())
+
+
+def test_ewa_and_ut_agree_to_first_order(orc):
+    """Both estimates match the true moments to first order in the Gaussian's size, so their
+    covariances agree as the scale shrinks: the relative gap falls like s^2 (halving s quarters it)."""
+    cam = synth.camera("fisheye", 640, 480, k=[0.03, -0.02, 0.0, 0.0])
+    mu = np.array([1.5, -0.8, 1.2])
+    R = rot([0.9, 0.1, -0.3, 0.2])
+    gaps = []
+    for sc in (0.08, 0.04, 0.02):
+        s = sc * np.array([1.0, 0.6, 0.3])
+        _, _, cu = orc.ut_estimate(cam, mu, R, s)
+        _, _, ce = orc.ewa_estimate(cam, mu, R, s)
+        gaps.append(abs(cu[0] - ce[0]) / ce[0] + abs(cu[2] - ce[2]) / ce[2])
+    assert gaps[0] > 1e-4
+    assert 3.0 < gaps[0] / gaps[1] < 5.0 and 3.0 < gaps[1] / gaps[2] < 5.0, gaps
+
+
+def test_ewa_projection_option(orc):
+    """project() with projection = 1 reports the EWA moments."""
+    sc = synth.scene_cube(50, 14, deg=0)
+    cam = synth.camera("fisheye", 320, 240, k=[0.02, 0.0, 0.0, 0.0])
+    pe = orc.project(sc, cam, synth.options(projection=1))
+    i = int(np.argmax(pe["ntiles"]))
+    ok, vmu, cov = orc.ewa_estimate(cam, sc["means"][i].astype(float), rot(sc["quats"][i].astype(float)),
+                                    np.exp(sc["log_scales"][i].astype(float)))
+    assert ok and np.allclose(pe["mean2d"][i], vmu) and np.allclose(pe["cov2d"][i], cov)
+
+
+# ------------------------------------------------------------------ per-particle colour (colour_mode 1)
+
+def test_per_particle_colour_equals_per_pixel_for_degree_zero(orc):
+    """Degree-0 SH does not depend on the direction: both colour modes render the same image."""
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    a = orc.render(sc, cam, op, proj=orc.project(sc, cam, op))
+    op1 = dict(op, colour_mode=1)
+    b = orc.render(sc, cam, op1, proj=orc.project(sc, cam, op1))
+    assert np.array_equal(a["rgb"], b["rgb"]) and np.array_equal(a["alpha"], b["alpha"])
+
+
+def test_per_particle_colour_at_the_pixel_through_the_mean(orc):
+    """A particle whose mean lies on a pixel's ray has, at that pixel, the same view direction
+    in both colour modes, so the two renders agree there (degree 3)."""
+    cam = synth.camera("pinhole", 32, 32, fx=40.0, fy=40.0)
+    px, py = 20, 11
+    _, o, d = orc.pixel_ray(cam, px + 0.5, py + 0.5)
+    rng = np.random.default_rng(15)
+    mu = np.asarray(o) + 2.5 * np.asarray(d) / np.linalg.norm(d)
+    sh = rng.normal(0, 0.3, (16, 3))
+    sc = one_scene(mu, [-2.0, -2.2, -1.8], [0.9, 0.1, 0.2, -0.3], 1.0, sh, deg=3)
+    proj = dict(rect=np.array([[0, 0, 31, 31]], np.int32), depth32=np.array([2.5], np.float32))
+    a = orc.render(sc, cam, synth.options(), proj=proj, pixels=([px], [py]))
+    b = orc.render(sc, cam, synth.options(colour_mode=1), proj=proj, pixels=([px], [py]))
+    assert a["alpha"][0] > 0.1
+    assert np.allclose(a["rgb"], b["rgb"], rtol=0, atol=1e-6)
+    # elsewhere the modes differ (the direction changes across the footprint)
+    a2 = orc.render(sc, cam, synth.options(), proj=proj, pixels=([px + 3], [py - 2]))
+    b2 = orc.render(sc, cam, synth.options(colour_mode=1), proj=proj, pixels=([px + 3], [py - 2]))
+    assert np.abs(a2["rgb"] - b2["rgb"]).max() > 1e-5
+
+
 # ------------------------------------------------------------------ gradients
 
 def _fd_scene(n=12, deg=1, seed=31):
@@ -504,12 +616,14 @@ def _loss(orc, sc, cam, op, proj, pix, g_rgb, g_a):
     return float(np.sum(o["rgb"] * g_rgb) + np.sum(o["alpha"] * g_a))
 
 
-def test_gradients_match_central_differences(orc):
+@pytest.mark.parametrize("colour_mode,deg", [(0, 1), (1, 2)])
+def test_gradients_match_central_differences(orc, colour_mode, deg):
     """FP64 analytic gradients vs Richardson-extrapolated central differences (steps 2^-9, 2^-10,
-    exact in FP32) with the culling decisions held fixed (they carry no gradient, Sec. 4.1)."""
-    sc = _fd_scene()
+    exact in FP32) with the culling decisions held fixed (they carry no gradient, Sec. 4.1).
+    colour_mode 1 includes the mean's gradient through the per-particle view direction."""
+    sc = _fd_scene(deg=deg)
     cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
-    op = synth.options(t_min=1e-4)
+    op = synth.options(t_min=1e-4, colour_mode=colour_mode)
     proj = orc.project(sc, cam, op)
     yy, xx = np.mgrid[0:20, 0:24]
     px, py = xx.reshape(-1), yy.reshape(-1)
