@@ -98,12 +98,27 @@ typedef struct {
  *   extent: half-widths k sqrt(Sigma'_xx), k sqrt(Sigma'_yy) with
  *   k = min(extent_sigma, sqrt(2 ln(sigma / alpha_min))) ("use opacity to compute a
  *   tighter 2D extent", Algorithm 1).  tile_w * tile_h must be 64..512 and a multiple of 32.
- *   newton_iters bounds the fisheye ray inversion (safeguarded Newton). */
+ *   newton_iters bounds the fisheye ray inversion (safeguarded Newton).
+ *   projection: UT_PROJECTION_UT (default; Sec. 4.1) or UT_PROJECTION_EWA, the first-order
+ *   estimate of 3DGS (eq. ewa_splatting) kept as an A/B baseline: v = g(W mu),
+ *   Sigma' = J W Sigma W^T J^T with J the Jacobian of g at the camera-space mean (under a
+ *   rolling shutter, W is the pose at the mean's own shutter time).  It changes only the 2D
+ *   extent and the culling (compositing is in 3D either way).
+ *   colour_mode: UT_COLOUR_PER_PIXEL (default; SH at each pixel's ray direction, Sec. 3) or
+ *   UT_COLOUR_PER_PARTICLE, a faster mode that evaluates the SH once per particle at the
+ *   direction from the camera centre (at the mean's shutter time) to the mean; its gradient
+ *   also reaches the mean through that direction. */
+#define UT_PROJECTION_UT 0
+#define UT_PROJECTION_EWA 1
+#define UT_COLOUR_PER_PIXEL 0
+#define UT_COLOUR_PER_PARTICLE 1
 typedef struct {
   int32_t tile_w, tile_h;
   float t_min, alpha_min, alpha_max;
   int32_t rs_iters, newton_iters;
   float extent_sigma;
+  int32_t projection;
+  int32_t colour_mode;
 } ut_options;
 
 void ut_default_options(ut_options *opt);

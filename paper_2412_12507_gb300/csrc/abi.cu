@@ -154,6 +154,9 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
       !(o->alpha_max < 1) || !(o->extent_sigma > 0))
     return UT_ERR_INVALID_ARG;
   if (o->rs_iters < 0 || o->rs_iters > 64 || o->newton_iters < 1 || o->newton_iters > 64) return UT_ERR_INVALID_ARG;
+  if ((o->projection != UT_PROJECTION_UT && o->projection != UT_PROJECTION_EWA) ||
+      (o->colour_mode != UT_COLOUR_PER_PIXEL && o->colour_mode != UT_COLOUR_PER_PARTICLE))
+    return UT_ERR_INVALID_ARG;
   d.tile_w = o->tile_w;
   d.tile_h = o->tile_h;
   d.tiles_x = (c->width + o->tile_w - 1) / o->tile_w;
@@ -164,6 +167,8 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
   d.extent_sigma = o->extent_sigma;
   d.rs_iters = o->rs_iters;
   d.newton_iters = o->newton_iters;
+  d.projection = o->projection;
+  d.colour_mode = o->colour_mode;
   return UT_OK;
 }
 
@@ -328,6 +333,8 @@ void ut_default_options(ut_options *o) {
   o->rs_iters = 3;
   o->newton_iters = 12;
   o->extent_sigma = 3.f;
+  o->projection = UT_PROJECTION_UT;
+  o->colour_mode = UT_COLOUR_PER_PIXEL;
 }
 
 uint64_t ut_kernel_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }

@@ -160,6 +160,99 @@ __device__ __forceinline__ bool eval_response(const float4 *g, int px, int py, f
   return true;
 }
 
+// Per-particle colour mode: unit view direction of a particle, from the camera centre at the
+// mean's shutter time (the rolling-shutter fixed point; t = 0 for a global shutter) to the
+// mean, and 1 / the distance.
+template <bool RS>
+__device__ __forceinline__ float3 particle_dir(const DevCam &cam, const DevOpts &op, float3 mu, float &inv_len) {
+  float3 c = make_float3(cam.cen[0], cam.cen[1], cam.cen[2]);
+  if (RS && cam.rs) {
+    float2 uv;
+    float t;
+    project_world(cam, op.rs_iters, mat3_mul(cam.R0, mu), uv, t);
+    // centre -R(t)^T T(t) with R(t) = Rot(ax, t phi) R0
+    const float3 Tt = make_float3(fmaf(t, cam.dT[0], cam.T0[0]), fmaf(t, cam.dT[1], cam.T0[1]),
+                                  fmaf(t, cam.dT[2], cam.T0[2]));
+    c = mat3_tmul(cam.R0, rotate_axis(cam.ax, make_float3(-Tt.x, -Tt.y, -Tt.z), -t * cam.phi));
+  }
+  const float3 v = make_float3(mu.x - c.x, mu.y - c.y, mu.z - c.z);
+  inv_len = rsqrtf(dot3(v, v));
+  return make_float3(v.x * inv_len, v.y * inv_len, v.z * inv_len);
+}
+
+// Per-particle colour mode: raw colour sum_k beta_k,ch Y_k(dir) + 1/2 of particle idx.
+template <int DEG, bool RS>
+__device__ __forceinline__ float4 particle_colour(const DevScene &sc, const DevCam &cam, const DevOpts &op,
+                                                  uint32_t idx) {
+  constexpr int NSH = (DEG + 1) * (DEG + 1);
+  const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
+  float il;
+  const float3 dir = particle_dir<RS>(cam, op, mu, il);
+  float Y[NSH];
+  sh_basis<DEG>(dir.x, dir.y, dir.z, Y);
+  const float *beta = sc.sh + (size_t)idx * NSH * 3;
+  float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
+#pragma unroll
+  for (int k = 0; k < NSH; ++k) {
+    r0 = fmaf(beta[3 * k], Y[k], r0);
+    r1 = fmaf(beta[3 * k + 1], Y[k], r1);
+    r2 = fmaf(beta[3 * k + 2], Y[k], r2);
+  }
+  return make_float4(r0, r1, r2, 0.f);
+}
+
+// sum_k a_k grad p_k(x, y, z) for the polynomials p_k that sh_basis evaluates on the unit sphere
+// (differentiated as polynomials in x, y, z; callers project onto the tangent plane).
+template <int DEG>
+__device__ __forceinline__ float3 sh_poly_grad(float x, float y, float z, const float *a) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  if (DEG >= 1) {
+    const float c1 = 0.4886025119029199f;
+    gy -= c1 * a[1];
+    gz += c1 * a[2];
+    gx -= c1 * a[3];
+  }
+  if (DEG >= 2) {
+    const float c4 = 1.0925484305920792f, c6 = 0.31539156525252005f, c8 = 0.5462742152960396f;
+    gx += c4 * y * a[4];
+    gy += c4 * x * a[4];
+    gy -= c4 * z * a[5];
+    gz -= c4 * y * a[5];
+    gx -= 2.f * c6 * x * a[6];
+    gy -= 2.f * c6 * y * a[6];
+    gz += 4.f * c6 * z * a[6];
+    gx -= c4 * z * a[7];
+    gz -= c4 * x * a[7];
+    gx += 2.f * c8 * x * a[8];
+    gy -= 2.f * c8 * y * a[8];
+  }
+  if (DEG >= 3) {
+    const float c9 = 0.5900435899266435f, c10 = 2.890611442640554f, c11 = 0.4570457994644658f,
+                c12 = 0.3731763325901154f, c14 = 1.445305721320277f;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    gx -= 6.f * c9 * x * y * a[9];
+    gy -= 3.f * c9 * (xx - yy) * a[9];
+    gx += c10 * y * z * a[10];
+    gy += c10 * x * z * a[10];
+    gz += c10 * x * y * a[10];
+    gx += 2.f * c11 * x * y * a[11];
+    gy -= c11 * (4.f * zz - xx - 3.f * yy) * a[11];
+    gz -= 8.f * c11 * y * z * a[11];
+    gx -= 6.f * c12 * x * z * a[12];
+    gy -= 6.f * c12 * y * z * a[12];
+    gz += c12 * (6.f * zz - 3.f * xx - 3.f * yy) * a[12];
+    gx -= c11 * (4.f * zz - 3.f * xx - yy) * a[13];
+    gy += 2.f * c11 * x * y * a[13];
+    gz -= 8.f * c11 * x * z * a[13];
+    gx += 2.f * c14 * x * z * a[14];
+    gy -= 2.f * c14 * y * z * a[14];
+    gz += c14 * (xx - yy) * a[14];
+    gx -= 3.f * c9 * (xx - yy) * a[15];
+    gy += 6.f * c9 * x * y * a[15];
+  }
+  return make_float3(gx, gy, gz);
+}
+
 template <int DEG>
 __device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op, int px, int py, bool inside,
                                             float3 &o, float3 &d, float *Y, bool &valid) {
@@ -174,7 +267,9 @@ __device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op
   }
 }
 
-template <int DEG, bool RS, bool STATS>
+// PP: per-particle colour mode (the colour of each staged particle is evaluated once, at its
+// view direction, while staging; pixels read it from shared memory).
+template <int DEG, bool RS, bool STATS, bool PP>
 __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
@@ -182,8 +277,10 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
                                                        unsigned long long *__restrict__ stats, TileSched ts) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
+  constexpr int PDEG = PP ? 0 : DEG;        // per-pixel SH basis only when colours are per pixel
+  constexpr int NST = PP ? 4 : NC;          // staged colour floats per particle
   __shared__ float4 s_geo[kBatchF][4];
-  __shared__ __align__(16) float s_sh[kBatchF * NC];
+  __shared__ __align__(16) float s_sh[kBatchF * NST];
   __shared__ uint32_t s_idx[kBatchF];
 
   // tiles in the order k_tile_order gave them (longest predicted walk first); every tile is
@@ -199,9 +296,9 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
-  float Y[NSH];
+  float Y[(PDEG + 1) * (PDEG + 1)];
   bool valid;
-  pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+  pixel_setup<PDEG>(cam, op, px, py, inside, o, d, Y, valid);
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   uint32_t last = 0;
@@ -216,8 +313,9 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
       uint32_t idx = s_idx[t];
       stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], nullptr);
+      if (PP) reinterpret_cast<float4 *>(s_sh)[t] = particle_colour<DEG, RS>(sc, cam, op, idx);
     }
-    stage_sh<NC>(sc, s_idx, nb, s_sh);
+    if (!PP) stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
     if (done) continue;
     for (int b = 0; b < nb; ++b) {
@@ -236,7 +334,12 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
       }
       if (STATS) ++n_blend;
       float r0, r1, r2;
-      sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+      if (PP) {
+        const float4 c = reinterpret_cast<const float4 *>(s_sh)[b];
+        r0 = c.x; r1 = c.y; r2 = c.z;
+      } else {
+        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+      }
       float w = al * T;
       C0 = fmaf(fmaxf(r0, 0.f), w, C0);
       C1 = fmaf(fmaxf(r1, 0.f), w, C1);
@@ -309,20 +412,22 @@ constexpr int kSlots = 8;     // particle columns of one tensor-core flush (the 
 __device__ __forceinline__ int wtile(int row, int col) { return row * 32 + (col ^ ((row & 3) << 3)); }
 
 // Shared-memory layout of the backward kernel (dynamic; bytes for a block of `warps` warps).
-template <int DEG>
+// PP: per-particle colour mode (no SH coefficients staged, no W tiles).
+template <int DEG, bool PP>
 struct BwdSmem {
   static constexpr int NSH = (DEG + 1) * (DEG + 1);
   static constexpr int NC = NSH * 3;
-  static constexpr int ACC = (16 + NC) | 1;  // accumulators per particle (odd: rows spread over banks)
+  static constexpr int NST = PP ? 4 : NC;                   // staged colour floats per particle
+  static constexpr int ACC = PP ? 17 : (16 + NC) | 1;      // accumulators per particle (odd: rows spread over banks)
   static __host__ __device__ size_t geo() { return 0; }
   static __host__ __device__ size_t aux() { return geo() + sizeof(float4) * 4 * kBatch; }
   static __host__ __device__ size_t sh() { return aux() + sizeof(float4) * kBatch; }
-  static __host__ __device__ size_t acc() { return sh() + sizeof(float) * ((kBatch * NC + 3) / 4 * 4); }
+  static __host__ __device__ size_t acc() { return sh() + sizeof(float) * ((kBatch * NST + 3) / 4 * 4); }
   static __host__ __device__ size_t wmat() { return acc() + sizeof(float) * kBatch * ACC; }
   // per warp: 3 channels x kSlots rows of W (the first 16 rows double as the staging area of
   // Y), then the A fragments (uint4 [4][32]: hi/lo of both k-steps, lane-minor)
-  static constexpr int kWRows = 3 * kSlots > 16 ? 3 * kSlots : 16;
-  static constexpr int kWarpFloats = kWRows * 32 + 4 * 4 * 32;
+  static constexpr int kWRows = PP ? 0 : (3 * kSlots > 16 ? 3 * kSlots : 16);
+  static constexpr int kWarpFloats = PP ? 0 : kWRows * 32 + 4 * 4 * 32;
   static __host__ __device__ size_t idx(int warps) { return wmat() + sizeof(float) * warps * kWarpFloats; }
   static __host__ __device__ size_t any(int warps) { return idx(warps) + sizeof(uint32_t) * kBatch; }
   static __host__ __device__ size_t bytes(int warps) { return any(warps) + sizeof(int) * kBatch; }
@@ -334,22 +439,26 @@ struct BwdSmem {
 //
 // The SH part is a dense contraction over the warp's 32 pixels, D[k][j] = sum_p Y_k(p) W_c(p, j),
 // run on the tensor cores (m16n8k16, BF16 hi/lo split with the three cross terms, FP32
-// accumulate): A = Y^T (basis x pixels) is fixed for the tile and lives in registers; B = W
-// (pixels x particles) collects, column by column, only particles that reach at least one
-// pixel of the warp, and is contracted once kSlots columns are full (and at the end of each
-// staged batch).  The 13 geometry partials are summed with a 16-value reduce-scatter.  Both
-// land in per-particle shared accumulators that are added to global memory once per
-// (tile, particle).
+// accumulate): A = Y^T (basis x pixels) is fixed for the tile and its fragments are parked in
+// shared memory; B = W (pixels x particles) collects, column by column, only particles that
+// reach at least one pixel of the warp, and is contracted once kSlots columns are full (and at
+// the end of each staged batch).  The 13 geometry partials are summed with a 16-value
+// reduce-scatter.  Both land in per-particle shared accumulators that are added to global
+// memory once per (tile, particle).
+// PP (per-particle colour mode): the colour gradient dL/dc is one 3-vector per particle, summed
+// in the three spare slots of the reduce-scatter; at the per-(tile, particle) flush it becomes
+// dL/dbeta = dL/dc Y(dir) and the mean's gradient through the view direction.
 // SMALL: tiles of at most 256 pixels, compiled for three resident blocks per SM (80 registers).
-template <int DEG, bool RS, bool SMALL>
+template <int DEG, bool RS, bool SMALL, bool PP>
 __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
     k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
                                                        const uint32_t *__restrict__ vals,
                                                        const uint2 *__restrict__ ranges, TileSched ts) {
-  using L = BwdSmem<DEG>;
+  using L = BwdSmem<DEG, PP>;
   constexpr int NSH = L::NSH;
   constexpr int NC = L::NC;
+  constexpr int PDEG = PP ? 0 : DEG;  // per-pixel SH basis only when colours are per pixel
   constexpr int ACC = L::ACC;
   extern __shared__ __align__(16) unsigned char smem[];
   const int warps = blockDim.x >> 5;
@@ -376,10 +485,11 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
   uint4 *s_Af = reinterpret_cast<uint4 *>(s_W + L::kWRows * 32);
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
-  float Y[NSH];
+  float Y[(PDEG + 1) * (PDEG + 1)];
   bool valid;
-  pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+  pixel_setup<PDEG>(cam, op, px, py, inside, o, d, Y, valid);
 
+  if constexpr (!PP) {
   // A operand (basis x pixels), fixed for the whole tile: the warp's Y transposed through
   // its W tile (row k = basis function k, column = lane), split into hi + lo fragments and
   // parked in shared memory (s_Af[2 ks + 0] = hi, s_Af[2 ks + 1] = lo)
@@ -401,6 +511,7 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
   // W starts finite: unused columns of a partial flush only feed their own (discarded) outputs
 #pragma unroll
   for (int r = 0; r < 3 * kSlots; ++r) s_W[wtile(r, lane)] = 0.f;
+  }
 
   const uint2 rg = ranges[tile];
   uint32_t my_end = 0;
@@ -469,8 +580,9 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
     if (threadIdx.x < nb) {
       uint32_t idx = s_idx[threadIdx.x];
       stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[threadIdx.x], &s_aux[threadIdx.x]);
+      if (PP) reinterpret_cast<float4 *>(s_sh)[threadIdx.x] = particle_colour<DEG, RS>(sc, cam, op, idx);
     }
-    stage_sh<NC>(sc, s_idx, nb, s_sh);
+    if (!PP) stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
     // particles of this batch any pixel of the warp can still blend (warp-uniform)
     const int nw = (int)min((uint32_t)nb, warp_end > start ? warp_end - start : 0u);
@@ -484,7 +596,12 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
         contrib = true;
         float al = fminf(a, op.alpha_max);
         float r0, r1, r2;
-        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+        if (PP) {
+          const float4 cr = reinterpret_cast<const float4 *>(s_sh)[b];
+          r0 = cr.x; r1 = cr.y; r2 = cr.z;
+        } else {
+          sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+        }
         float c0 = fmaxf(r0, 0.f), c1 = fmaxf(r1, 0.f), c2 = fmaxf(r2, 0.f);
         float w = al * T;
         A0 = fmaf(c0, w, A0);
@@ -519,27 +636,32 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
         }
       }
       if (!__any_sync(0xffffffffu, contrib)) continue;
-      // SH weights into the next free column of W (row = channel x column, entry = pixel)
+      if (!PP) {
+        // SH weights into the next free column of W (row = channel x column, entry = pixel)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) s_W[wtile(c * kSlots + cols, lane)] = wc[c];
-      if (lane == cols) slot_b = b;
+        for (int c = 0; c < 3; ++c) s_W[wtile(c * kSlots + cols, lane)] = wc[c];
+        if (lane == cols) slot_b = b;
+      }
       float v[16];
       v[0] = vv[0]; v[1] = vv[1]; v[2] = vv[2];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = vv[r] * xx[c];
-      v[12] = dsig; v[13] = 0.f; v[14] = 0.f; v[15] = 0.f;
+      v[12] = dsig;
+      v[13] = PP ? wc[0] : 0.f;
+      v[14] = PP ? wc[1] : 0.f;
+      v[15] = PP ? wc[2] : 0.f;
       warp_reduce_scatter16(v, lane);
       const int vi = (lane >> 1) & 15;
-      if (!(lane & 1) && vi < 13) atomicAdd(&s_acc[b * ACC + vi], v[0]);
+      if (!(lane & 1) && vi < (PP ? 16 : 13)) atomicAdd(&s_acc[b * ACC + vi], v[0]);
       if (lane == 0) s_any[b] = 1;
-      if (++cols == kSlots) {
+      if (!PP && ++cols == kSlots) {
         flush(kSlots);
         cols = 0;
       }
     }
-    if (cols > 0) flush(cols);
+    if (!PP && cols > 0) flush(cols);
     __syncthreads();
     for (int f = threadIdx.x; f < nb * ACC; f += blockDim.x) {
       int b = f / ACC, j = f - b * ACC;
@@ -547,7 +669,36 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
       uint32_t idx = s_idx[b];
       float v = s_acc[f];
       if (j < 13) atomicAdd(&sc.gacc[(size_t)idx * 16 + j], v);
-      else if (j >= 16 && j < 16 + NC) atomicAdd(&sc.d_sh[(size_t)idx * NC + (j - 16)], v);
+      else if (!PP && j >= 16 && j < 16 + NC) atomicAdd(&sc.d_sh[(size_t)idx * NC + (j - 16)], v);
+    }
+    if (PP) {
+      // dL/dc of this tile's pixels -> dL/dbeta_k,ch = dL/dc_ch Y_k(dir) and the mean's gradient
+      // through dir = (mu - c) / |mu - c|: (I - dir dir^T) / |mu - c| sum_ch dL/dc_ch grad c_ch
+      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        if (!s_any[b]) continue;
+        const float g0c = s_acc[b * ACC + 13], g1c = s_acc[b * ACC + 14], g2c = s_acc[b * ACC + 15];
+        if (g0c == 0.f && g1c == 0.f && g2c == 0.f) continue;
+        const uint32_t idx = s_idx[b];
+        const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
+        float il;
+        const float3 dir = particle_dir<RS>(cam, op, mu, il);
+        float Yp[NSH], a[NSH];
+        sh_basis<DEG>(dir.x, dir.y, dir.z, Yp);
+        const float *beta = sc.sh + (size_t)idx * NC;
+        float *dsh = sc.d_sh + (size_t)idx * NC;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k) {
+          a[k] = fmaf(g0c, beta[3 * k], fmaf(g1c, beta[3 * k + 1], g2c * beta[3 * k + 2]));
+          if (g0c != 0.f) atomicAdd(&dsh[3 * k], g0c * Yp[k]);
+          if (g1c != 0.f) atomicAdd(&dsh[3 * k + 1], g1c * Yp[k]);
+          if (g2c != 0.f) atomicAdd(&dsh[3 * k + 2], g2c * Yp[k]);
+        }
+        const float3 G = sh_poly_grad<DEG>(dir.x, dir.y, dir.z, a);
+        const float gd = dot3(G, dir);
+        atomicAdd(&sc.gacc[(size_t)idx * 16 + 13], (G.x - gd * dir.x) * il);
+        atomicAdd(&sc.gacc[(size_t)idx * 16 + 14], (G.y - gd * dir.y) * il);
+        atomicAdd(&sc.gacc[(size_t)idx * 16 + 15], (G.z - gd * dir.z) * il);
+      }
     }
   }
 }
@@ -703,7 +854,9 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
     float out_m[3] = {0.f, 0.f, 0.f}, out_s[3] = {0.f, 0.f, 0.f}, out_q[4] = {0.f, 0.f, 0.f, 0.f}, out_l = 0.f;
     if (ok) {
       float v0 = A[0], v1 = A[1], v2 = A[2];
-      for (int j = 0; j < 3; ++j) out_m[j] = -(p.M[j] * v0 + p.M[3 + j] * v1 + p.M[6 + j] * v2);
+      // slots 13..15: the mean's gradient through the per-particle view direction (zero in
+      // the per-pixel colour mode)
+      for (int j = 0; j < 3; ++j) out_m[j] = A[13 + j] - (p.M[j] * v0 + p.M[3 + j] * v1 + p.M[6 + j] * v2);
       float G[9];
       for (int k = 0; k < 3; ++k) {
         float acc = 0.f;
@@ -729,33 +882,59 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
   }
 }
 
+template <int DEG, bool RS, bool PP>
+void fwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                  const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
+  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
+  const short4 *r4 = reinterpret_cast<const short4 *>(rect);
+  const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
+  if (stats)
+    k_composite_fwd<DEG, RS, true, PP><<<blocks, threads, 0, s>>>(bd, op, r4, vals, rg, stats, ts);
+  else
+    k_composite_fwd<DEG, RS, false, PP><<<blocks, threads, 0, s>>>(bd, op, r4, vals, rg, nullptr, ts);
+}
+
+// Degree 0 colours do not depend on the direction: both colour modes run the per-pixel kernel.
 template <int DEG, bool RS>
 void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
-  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
-  if (stats)
-    k_composite_fwd<DEG, RS, true><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                              reinterpret_cast<const uint2 *>(ranges), stats, ts);
-  else
-    k_composite_fwd<DEG, RS, false><<<blocks, threads, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                               reinterpret_cast<const uint2 *>(ranges), nullptr, ts);
+  if constexpr (DEG > 0) {
+    if (op.colour_mode == UT_COLOUR_PER_PARTICLE) {
+      fwd_launch_k<DEG, RS, true>(bd, op, rect, vals, ranges, stats, ts, s);
+      return;
+    }
+  }
+  fwd_launch_k<DEG, RS, false>(bd, op, rect, vals, ranges, stats, ts, s);
 }
 
-template <int DEG, bool RS, bool SMALL>
+template <int DEG, bool RS, bool SMALL, bool PP>
 void bwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                   const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
   const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
-  const size_t smem = BwdSmem<DEG>::bytes(threads / 32);
-  cudaFuncSetAttribute(k_composite_bwd<DEG, RS, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_composite_bwd<DEG, RS, SMALL><<<blocks, threads, smem, s>>>(
+  const size_t smem = BwdSmem<DEG, PP>::bytes(threads / 32);
+  cudaFuncSetAttribute(k_composite_bwd<DEG, RS, SMALL, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_composite_bwd<DEG, RS, SMALL, PP><<<blocks, threads, smem, s>>>(
       bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
 }
 
+template <int DEG, bool RS, bool PP>
+void bwd_launch_pp(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
+                   const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
+  if (op.tile_w * op.tile_h <= 256) bwd_launch_k<DEG, RS, true, PP>(bd, op, rect, vals, ranges, ts, s);
+  else bwd_launch_k<DEG, RS, false, PP>(bd, op, rect, vals, ranges, ts, s);
+}
+
+// Degree 0 colours do not depend on the direction: both colour modes run the per-pixel kernel.
 template <int DEG, bool RS>
 void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
-  if (op.tile_w * op.tile_h <= 256) bwd_launch_k<DEG, RS, true>(bd, op, rect, vals, ranges, ts, s);
-  else bwd_launch_k<DEG, RS, false>(bd, op, rect, vals, ranges, ts, s);
+  if constexpr (DEG > 0) {
+    if (op.colour_mode == UT_COLOUR_PER_PARTICLE) {
+      bwd_launch_pp<DEG, RS, true>(bd, op, rect, vals, ranges, ts, s);
+      return;
+    }
+  }
+  bwd_launch_pp<DEG, RS, false>(bd, op, rect, vals, ranges, ts, s);
 }
 
 bool any_rs(const BatchDesc &bd) {

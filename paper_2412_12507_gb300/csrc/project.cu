@@ -1,4 +1,5 @@
-// project.cu — Unscented-Transform projection of every particle (Sec. 4.1; Algorithms 1-2).
+// project.cu — Unscented-Transform projection of every particle (Sec. 4.1; Algorithms 1-2),
+// or, as an A/B baseline, the first-order EWA projection of 3DGS (eq. ewa_splatting).
 //
 // One thread per (view, particle) entry of the flattened batch, one warp per 32
 // consecutive entries.  When a warp's 32 entries belong to one view, the warp loads its 32
@@ -16,6 +17,10 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// EWA: the first-order projection of 3DGS (eq. ewa_splatting) instead of the UT, as an A/B
+// baseline: the mean projects through g and the covariance through the Jacobian of g at the
+// camera-space mean (under a rolling shutter, at the pose of the mean's own shutter time).
+template <bool EWA>
 __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__ BatchDesc bd, DevOpts op, UTWeights w,
                                                          float2 *__restrict__ mean2d, float *__restrict__ cov2d,
                                                          float *__restrict__ depth, short4 *__restrict__ rect,
@@ -63,35 +68,52 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__
   bool ok = live && activate(mu, ls, q4, logit, p);
   ok = ok && (p.sigma >= op.alpha_min);
 
-  // sigma points in start-pose camera rotation: y_0 = R0 mu, y_(1+k) / y_(4+k) = y_0 +- gamma s_k R0 R[:,k]
-  float2 v[7];
+  float2 vm;
   float t_mu = 0.f;
   float3 y0 = mat3_mul(cam.R0, mu);
-  ok = ok & project_world(cam, op.rs_iters, y0, v[0], t_mu);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float gs = w.gamma * p.s[k];
-    float3 col = make_float3(gs * p.R[k], gs * p.R[3 + k], gs * p.R[6 + k]);
-    float3 dy = mat3_mul(cam.R0, col);
-    float tt;
-    ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v[1 + k], tt);
-    ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x - dy.x, y0.y - dy.y, y0.z - dy.z), v[4 + k], tt);
-  }
-  // eq. 2d_conic_1 / 2d_conic_2
-  float2 vm = make_float2(w.wm0 * v[0].x, w.wm0 * v[0].y);
-#pragma unroll
-  for (int j = 1; j < 7; ++j) {
-    vm.x = fmaf(w.wi, v[j].x, vm.x);
-    vm.y = fmaf(w.wi, v[j].y, vm.y);
-  }
   float cxx = 0.f, cxy = 0.f, cyy = 0.f;
+  if (EWA) {
+    ok = ok & project_world(cam, op.rs_iters, y0, vm, t_mu);
+    float3 ju, jv;
+    cam_jacobian(cam, cam_point_at(cam, y0, t_mu), ju, jv);
+    // Sigma' = A A^T with column k of A = J W (s_k R[:,k]), W the pose at t_mu
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    float ww = j == 0 ? w.wc0 : w.wi;
-    float dx = v[j].x - vm.x, dy = v[j].y - vm.y;
-    cxx = fmaf(ww * dx, dx, cxx);
-    cxy = fmaf(ww * dx, dy, cxy);
-    cyy = fmaf(ww * dy, dy, cyy);
+    for (int k = 0; k < 3; ++k) {
+      float3 col = mat3_mul(cam.R0, make_float3(p.s[k] * p.R[k], p.s[k] * p.R[3 + k], p.s[k] * p.R[6 + k]));
+      if (cam.rs) col = rotate_axis(cam.ax, col, t_mu * cam.phi);
+      const float au = dot3(ju, col), av = dot3(jv, col);
+      cxx = fmaf(au, au, cxx);
+      cxy = fmaf(au, av, cxy);
+      cyy = fmaf(av, av, cyy);
+    }
+  } else {
+    // sigma points in start-pose camera rotation: y_0 = R0 mu, y_(1+k) / y_(4+k) = y_0 +- gamma s_k R0 R[:,k]
+    float2 v[7];
+    ok = ok & project_world(cam, op.rs_iters, y0, v[0], t_mu);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float gs = w.gamma * p.s[k];
+      float3 col = make_float3(gs * p.R[k], gs * p.R[3 + k], gs * p.R[6 + k]);
+      float3 dy = mat3_mul(cam.R0, col);
+      float tt;
+      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v[1 + k], tt);
+      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x - dy.x, y0.y - dy.y, y0.z - dy.z), v[4 + k], tt);
+    }
+    // eq. 2d_conic_1 / 2d_conic_2
+    vm = make_float2(w.wm0 * v[0].x, w.wm0 * v[0].y);
+#pragma unroll
+    for (int j = 1; j < 7; ++j) {
+      vm.x = fmaf(w.wi, v[j].x, vm.x);
+      vm.y = fmaf(w.wi, v[j].y, vm.y);
+    }
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      float ww = j == 0 ? w.wc0 : w.wi;
+      float dx = v[j].x - vm.x, dy = v[j].y - vm.y;
+      cxx = fmaf(ww * dx, dx, cxx);
+      cxy = fmaf(ww * dx, dy, cxy);
+      cyy = fmaf(ww * dy, dy, cyy);
+    }
   }
   float3 xc = cam_point_at(cam, y0, t_mu);
   float dep = sqrtf(fmaf(xc.x, xc.x, fmaf(xc.y, xc.y, xc.z * xc.z)));
@@ -141,8 +163,12 @@ ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights
   const int n = bd.total_particles;
   if (n == 0) return UT_OK;
   int blocks = (n + kWarps * 32 - 1) / (kWarps * 32);
-  k_project<<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d, depth,
-                                                reinterpret_cast<short4 *>(rect), ntiles);
+  if (op.projection == UT_PROJECTION_EWA)
+    k_project<true><<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d, depth,
+                                                        reinterpret_cast<short4 *>(rect), ntiles);
+  else
+    k_project<false><<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d,
+                                                         depth, reinterpret_cast<short4 *>(rect), ntiles);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }

@@ -34,6 +34,8 @@ struct DevOpts {
   int tile_w, tile_h, tiles_x, tiles_y;
   float t_min, alpha_min, alpha_max, extent_sigma;
   int rs_iters, newton_iters;
+  int projection;   // UT_PROJECTION_UT / UT_PROJECTION_EWA
+  int colour_mode;  // UT_COLOUR_PER_PIXEL / UT_COLOUR_PER_PARTICLE
 };
 
 // ---------------------------------------------------------------- batches of views
@@ -177,6 +179,34 @@ __device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &u
   uv.x = fmaf(c.fx * s, p.x, c.cx);
   uv.y = fmaf(c.fy * s, p.y, c.cy);
   return (r3 > c.near_plane) && (th <= c.theta_max);
+}
+
+// Jacobian d g / d x_c (rows u, v) of the camera map at a camera-space point.  Fisheye:
+// u = fx s X + cx with s = theta_d(theta) / rho, theta = atan2(rho, Z), hence
+// d s = (theta_d'(theta) d theta - s d rho) / rho, d theta = (X Z, Y Z, -rho^2) / (rho r^2),
+// d rho = (X, Y, 0) / rho; on the optical axis the map is the pinhole one.
+__device__ __forceinline__ void cam_jacobian(const DevCam &c, float3 p, float3 &ju, float3 &jv) {
+  if (c.model == UT_CAM_PINHOLE) {
+    const float iz = 1.f / p.z;
+    ju = make_float3(c.fx * iz, 0.f, -c.fx * p.x * iz * iz);
+    jv = make_float3(0.f, c.fy * iz, -c.fy * p.y * iz * iz);
+    return;
+  }
+  const float rho2 = fmaf(p.x, p.x, p.y * p.y), rho = sqrtf(rho2);
+  if (!(rho > 0.f)) {
+    ju = make_float3(c.fx / p.z, 0.f, 0.f);
+    jv = make_float3(0.f, c.fy / p.z, 0.f);
+    return;
+  }
+  const float r2 = fmaf(p.z, p.z, rho2);
+  const float th = atan2f(rho, p.z);
+  const float irho = 1.f / rho;
+  const float s = theta_d_poly(c, th) * irho, tdp = theta_d_prime(c, th);
+  const float a = p.z / (rho * r2);
+  const float3 ds = make_float3((tdp * p.x * a - s * p.x * irho) * irho, (tdp * p.y * a - s * p.y * irho) * irho,
+                                (-tdp * rho / r2) * irho);
+  ju = make_float3(c.fx * fmaf(p.x, ds.x, s), c.fx * p.x * ds.y, c.fx * p.x * ds.z);
+  jv = make_float3(c.fy * p.y * ds.x, c.fy * fmaf(p.y, ds.y, s), c.fy * p.y * ds.z);
 }
 
 // Projection of a world point with the rolling-shutter time fixed point

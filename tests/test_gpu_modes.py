@@ -1,0 +1,147 @@
+"""Parity of the optional modes with the FP64 oracle, through the C ABI:
+
+- projection = EWA: the first-order projection of 3DGS (eq. ewa_splatting), the A/B
+  baseline of the UT — 2D moments, depth, culling and rects, then full renders;
+- colour_mode = per particle: SH evaluated once per particle at its view direction —
+  renders and gradients (including the mean's gradient through the direction).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_helpers import TOL, compare_frame, run_gpu, sample_pixels, to_np  # noqa: E402
+from paper_2412_12507_gb300 import abi, render, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2412_12507_gb300 import build
+    build.build()
+    abi.lib()
+
+
+def _cases():
+    return {
+        "fisheye_shell": synth.fisheye_shell(n=20_000, width=640, height=360),
+        "rs_fisheye": synth.rs_fisheye(n=20_000, width=480, height=270),
+        "pinhole_deg2_ragged": dict(scene=synth.scene_cube(3000, 9, deg=2, log_s=(-3.2, 0.4)),
+                                    camera=synth.camera("pinhole", 150, 97, fx=120.0, fy=110.0, cx=70.3, cy=50.1),
+                                    options=synth.options()),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ewa_projection_matches_oracle(name):
+    case = CASES[name]
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], projection=1)
+    g = run_gpu(sc, cam, op)
+    ref = oracle.project(sc, cam, op, TOL)
+    p = g["proj"]
+    rect = to_np(p.rect).astype(np.int64)
+    nt = to_np(p.ntiles)
+    valid_g, valid_o = nt > 0, ref["ntiles"] > 0
+    e = ref["edges"]
+    edge_tie = np.any(np.abs(e - np.round(e)) < TOL["eps_px"], axis=1) & np.isfinite(e).all(axis=1)
+    tie = (ref["tie"] != 0) | edge_tie
+    mism = valid_g != valid_o
+    assert not np.any(mism & ~tie), np.nonzero(mism & ~tie)[0][:10]
+    both = valid_g & valid_o
+    assert both.sum() > 0.2 * len(valid_o)
+    m2 = to_np(p.mean2d)[both]
+    assert np.max(np.abs(m2 - ref["mean2d"][both])) < 5e-3
+    c2 = to_np(p.cov2d)[both]
+    scale = ref["cov2d"][both][:, [0, 2]].sum(1)
+    cov_err = np.max(np.abs(c2 - ref["cov2d"][both]).max(1) / (scale + 1e-6))
+    assert cov_err < 2e-4, cov_err
+    dep = to_np(p.depth)[both]
+    assert np.max(np.abs(dep - ref["depth"][both]) / ref["depth"][both]) < 2e-6
+    diff = rect[both] != ref["rect"][both]
+    eb = e[both][:, [0, 2, 1, 3]]
+    assert not np.any(diff & ~(np.abs(eb - np.round(eb)) < TOL["eps_px"]))
+    # the EWA moments are not the UT ones (a fisheye bends the footprint)
+    if name != "pinhole_deg2_ragged":
+        ut = oracle.project(sc, cam, case["options"], TOL)
+        assert np.abs(ut["cov2d"][both] - ref["cov2d"][both]).max() > 1e-3 * np.abs(ref["cov2d"][both]).max()
+
+
+@pytest.mark.parametrize("name,mode", [("rs_fisheye", dict(projection=1)),
+                                       ("rs_fisheye", dict(colour_mode=1)),
+                                       ("fisheye_shell", dict(colour_mode=1)),
+                                       ("pinhole_deg2_ragged", dict(colour_mode=1, projection=1))])
+def test_mode_render_matches_oracle(name, mode):
+    case = CASES[name]
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], **mode)
+    g = run_gpu(sc, cam, op)
+    W, H = cam["width"], cam["height"]
+    pix = None if W * H <= 70_000 else sample_pixels(W, H, 20_000, 7)
+    ref = oracle.render(sc, cam, op, proj=oracle.project(sc, cam, op, TOL), pixels=pix, tol=TOL)
+    r = compare_frame(g["frame"], ref)
+    print(name, mode, r)
+    assert r["n_bad"] == 0, r
+    assert r["n_flagged"] <= 0.03 * r["n"], r
+
+
+def test_per_particle_colour_degree_zero_is_the_per_pixel_image():
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    a = run_gpu(sc, cam, op)["frame"]
+    b = run_gpu(sc, cam, dict(op, colour_mode=1))["frame"]
+    assert torch.equal(a.rgb, b.rgb) and torch.equal(a.alpha, b.alpha)
+
+
+GRAD_CASES = {
+    "rs_fisheye_crop": lambda: synth.rs_fisheye(n=2000, width=320, height=180),
+    "pinhole_deg2": lambda: dict(scene=synth.scene_cube(1500, 13, deg=2, log_s=(-2.8, 0.4)),
+                                 camera=synth.camera("pinhole", 96, 80, fx=90.0, fy=90.0),
+                                 options=synth.options()),
+}
+
+
+def _grad_compare(got, ref, name, rel=1e-3):
+    g = got.reshape(-1).astype(np.float64)
+    r = ref.reshape(-1)
+    e = np.linalg.norm(g - r) / np.linalg.norm(r)
+    assert e <= rel, (name, e)
+    bad = np.abs(g - r) > rel * np.abs(r) + 1e-4 * np.max(np.abs(r))
+    assert bad.mean() < 1e-3, (name, bad.sum())
+    return e
+
+
+@pytest.mark.parametrize("name", list(GRAD_CASES))
+def test_per_particle_colour_backward_matches_oracle(name):
+    """Gradients of all five parameter tensors in the per-particle colour mode, including the
+    means' gradient through the view direction, against the FP64 oracle's."""
+    case = GRAD_CASES[name]()
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], colour_mode=1)
+    W, H = cam["width"], cam["height"]
+    proj_ref = oracle.project(sc, cam, op, TOL)
+    ref_f = oracle.render(sc, cam, op, proj=proj_ref, tol=TOL)
+    flagged = (ref_f["flags"] & (oracle.F_FORWARD_TIES | oracle.F_ALPHA_MAX)) != 0
+    rng = np.random.default_rng(321)
+    w_rgb = rng.standard_normal((H * W, 3)) * ~flagged[:, None]
+    w_a = rng.standard_normal(H * W) * ~flagged
+    ref = oracle.backward(sc, cam, op, proj_ref, (ref_f["px"], ref_f["py"]), w_rgb, w_a)
+    g = run_gpu(sc, cam, op)
+    d_rgb = torch.as_tensor(w_rgb.T.reshape(3, H, W).astype(np.float32)).cuda()
+    d_a = torch.as_tensor(w_a.reshape(H, W).astype(np.float32)).cuda()
+    grads = render.composite_backward(g["scene"], cam, op, g["proj"], g["binning"], g["frame"], d_rgb, d_a)
+    torch.cuda.synchronize()
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        e = _grad_compare(to_np(grads[k]), ref[k], k)
+        print(name, k, f"rel err {e:.2e}")
+    # the two colour modes give different gradients (the mode is not silently ignored)
+    op0 = dict(op, colour_mode=0)
+    ref0 = oracle.backward(sc, cam, op0, oracle.project(sc, cam, op0, TOL), (ref_f["px"], ref_f["py"]), w_rgb, w_a)
+    assert np.linalg.norm(ref0["sh"] - ref["sh"]) > 1e-3 * np.linalg.norm(ref["sh"])
