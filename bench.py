@@ -365,6 +365,60 @@ def run_multiview(dev, steps, warmup, timed):
     return out
 
 
+def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
+    """A/B lines on the bench workload: the UT projection against the first-order EWA one
+    (the paper's "Preprocess" comparison with 3DGS; per call, and the whole forward with each),
+    and the per-particle SH colour mode (forward and forward + backward) against the
+    per-pixel one."""
+    import torch
+    from paper_2412_12507_gb300 import render
+    P = cam["width"] * cam["height"]
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def per_call(fn, n=max(5, steps)):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for name, mode in (("ut", {}), ("ewa", {"projection": 1})):
+        o = dict(op, **mode)
+        pr = render.project(scene, cam, o)
+        proj_ms = per_call(lambda: render.project(scene, cam, o, pr))
+        r = render.Renderer(cam, o, capacity=1 << 20)
+        r.forward(scene)
+        torch.cuda.synchronize()
+        K = r.binning.count()
+        fwd_ms = timed(lambda: r.forward(scene, sync_check=False), steps, warmup)
+        out[name] = {"project_ms": proj_ms, "fwd_ms": fwd_ms, "keys": K, "fwd_mpix_s": P / (fwd_ms / 1e3) / 1e6}
+        del r
+    out["ewa_over_ut_project"] = out["ewa"]["project_ms"] / out["ut"]["project_ms"]
+    o = dict(op, colour_mode=1)
+    r = render.Renderer(cam, o, capacity=1 << 20)
+    r.forward(scene)
+    torch.cuda.synchronize()
+    f_ms = timed(lambda: r.forward(scene, sync_check=False), steps, warmup)
+
+    def fb():
+        r.forward(scene, sync_check=False)
+        r.backward(scene, d_rgb, d_alpha)
+
+    fb_ms = timed(fb, steps, warmup)
+    out["per_particle_colour"] = {"fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "fwd_mpix_s": P / (f_ms / 1e3) / 1e6,
+                                  "fwd_bwd_mpix_s": P / (fb_ms / 1e3) / 1e6}
+    del r
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -430,7 +484,7 @@ def run_ours(args):
     launches_fb = L.ut_kernel_launch_count() - c0
     torch.cuda.synchronize()
 
-    # clocks are sampled from here through the e2e steps (every timed region; 200 ms period)
+    # clocks are sampled from here through the multi-view batch (every timed region; 200 ms period)
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     fwd_ms = timed(fwd, args.steps, max(3, args.warmup))
@@ -504,11 +558,13 @@ def run_ours(args):
         out_host[3].copy_(f.alpha, non_blocking=True)
 
     e2e_ms = timed(e2e_step, max(3, args.steps // 2), 3)
-    clk = clocks.stop()
+
+    variants = run_variants(scene, cam, op, d_rgb, d_alpha, timed, args.steps, max(3, args.warmup))
 
     multiview = None
     if args.multiview_steps > 0:
         multiview = run_multiview(dev, args.multiview_steps, max(3, args.warmup), timed)
+    clk = clocks.stop()  # sampled over every timed region above
 
     serve = None
     if args.serve_requests > 0:
@@ -547,6 +603,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
             "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
+            "variants": variants,
             "multiview": multiview,
             "serve": serve,
         }
