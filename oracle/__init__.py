@@ -56,7 +56,8 @@ class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("t_min", C.c_double),
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("rs_iters", C.c_int32),
                 ("ut_alpha", C.c_double), ("ut_beta", C.c_double), ("ut_kappa", C.c_double),
-                ("extent_sigma", C.c_double), ("projection", C.c_int32), ("colour_mode", C.c_int32)]
+                ("extent_sigma", C.c_double), ("projection", C.c_int32), ("colour_mode", C.c_int32),
+                ("kernel_degree", C.c_int32)]
 
 
 class Tol(C.Structure):
@@ -80,6 +81,8 @@ def lib():
         L.orc_ut_estimate.restype = C.c_int
         L.orc_ut_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, C.c_double, C.c_double,
                                       C.c_double, P, P, P, P, P, P, P]
+        L.orc_cam_limit.restype = C.c_double
+        L.orc_cam_limit.argtypes = [C.POINTER(Camera)]
         L.orc_ewa_estimate.restype = C.c_int
         L.orc_ewa_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, P, P, P, P, P, P, P]
         L.orc_project.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), C.POINTER(Tol),
@@ -119,7 +122,7 @@ def _i32(a):
 def make_camera(cam: dict) -> Camera:
     """cam: dict with model ('pinhole'|'fisheye'|'ortho' or 0/1/2), width, height, fx, fy, cx, cy,
     k (4), q_start (w,x,y,z), t_start, q_end, t_end, rolling_shutter, near_plane."""
-    models = {"pinhole": 0, "fisheye": 1, "ortho": 2}
+    models = {"pinhole": 0, "fisheye": 1, "ortho": 2, "pinhole_radial": 3}
     m = cam["model"]
     c = Camera()
     c.model = models[m] if isinstance(m, str) else int(m)
@@ -148,6 +151,7 @@ def make_options(opts: dict | None = None) -> Options:
     r.extent_sigma = float(o.get("extent_sigma", 3.0))
     r.projection = int(o.get("projection", 0))    # 0 UT, 1 EWA
     r.colour_mode = int(o.get("colour_mode", 0))  # 0 per pixel, 1 per particle
+    r.kernel_degree = int(o.get("kernel_degree", 2))  # generalised Gaussian degree n
     return r
 
 
@@ -193,7 +197,7 @@ def sh_basis(deg: int, d) -> np.ndarray:
 def project_point(cam: dict, x, rs_iters: int = 3):
     """g(x) for a world point (rolling-shutter fixed point included). Returns (valid, uv, t)."""
     c = make_camera(cam)
-    tm = theta_max(c.k) if c.model == 1 else np.pi / 2
+    tm = lib().orc_cam_limit(C.byref(c))
     uv = np.zeros(2)
     t = np.zeros(1)
     m = np.zeros(1)
@@ -204,7 +208,7 @@ def project_point(cam: dict, x, rs_iters: int = 3):
 def pixel_ray(cam: dict, px: float, py: float):
     """World ray (o, d) through the pixel-plane point (px, py). Returns (valid, o, d)."""
     c = make_camera(cam)
-    tm = theta_max(c.k) if c.model == 1 else np.pi / 2
+    tm = lib().orc_cam_limit(C.byref(c))
     o, d, em, dp = np.zeros(3), np.zeros(3), np.zeros(1), np.zeros(1)
     v = lib().orc_pixel_ray(C.byref(c), tm, float(px), float(py), _p(o), _p(d), _p(em), _p(dp))
     return bool(v), o, d
@@ -213,7 +217,7 @@ def pixel_ray(cam: dict, px: float, py: float):
 def ut_estimate(cam: dict, mu, R, s, ut=(1.0, 2.0, 0.0), rs_iters: int = 3):
     """Unscented-Transform 2D mean and covariance (xx, xy, yy) of one Gaussian."""
     c = make_camera(cam)
-    tm = theta_max(c.k) if c.model == 1 else np.pi / 2
+    tm = lib().orc_cam_limit(C.byref(c))
     vmu, cov, t, m = np.zeros(2), np.zeros(3), np.zeros(1), np.zeros(1)
     v = lib().orc_ut_estimate(C.byref(c), tm, rs_iters, float(ut[0]), float(ut[1]), float(ut[2]),
                               _p(_f64(mu)), _p(_f64(np.asarray(R).reshape(9))), _p(_f64(s)), _p(vmu), _p(cov),
@@ -224,7 +228,7 @@ def ut_estimate(cam: dict, mu, R, s, ut=(1.0, 2.0, 0.0), rs_iters: int = 3):
 def ewa_estimate(cam: dict, mu, R, s, rs_iters: int = 3):
     """First-order (EWA) 2D mean and covariance (xx, xy, yy) of one Gaussian (eq. ewa_splatting)."""
     c = make_camera(cam)
-    tm = theta_max(c.k) if c.model == 1 else np.pi / 2
+    tm = lib().orc_cam_limit(C.byref(c))
     vmu, cov, t, m = np.zeros(2), np.zeros(3), np.zeros(1), np.zeros(1)
     v = lib().orc_ewa_estimate(C.byref(c), tm, rs_iters, _p(_f64(mu)), _p(_f64(np.asarray(R).reshape(9))),
                                _p(_f64(s)), _p(vmu), _p(cov), _p(t), _p(m))

@@ -48,7 +48,8 @@
 #define ORC_PI 3.14159265358979323846
 
 typedef struct {
-  int32_t model;           /* 0 pinhole, 1 fisheye (polynomial), 2 orthographic (test-only affine) */
+  int32_t model;           /* 0 pinhole, 1 fisheye (polynomial), 2 orthographic (test-only affine),
+                              3 pinhole with radial distortion k1..k3 */
   int32_t width, height;
   int32_t rolling_shutter; /* 0 global shutter (start pose), 1 rows exposed top to bottom */
   double fx, fy, cx, cy;
@@ -72,6 +73,7 @@ typedef struct {
   int32_t projection;  /* 0: Unscented Transform (Sec. 4.1); 1: first-order EWA (eq. ewa_splatting) */
   int32_t colour_mode; /* 0: SH at each pixel's ray direction; 1: SH once per particle at the
                           direction from the camera centre (at the mean's shutter time) to the mean */
+  int32_t kernel_degree; /* n of the generalised Gaussian (supplementary Sec. A); 2 = Gaussian */
 } orc_options;
 
 /* near-tie tolerances used only to flag pixels whose FP32 result may legitimately differ */
@@ -188,6 +190,62 @@ static double orc_theta_inverse(const double k[4], double theta_max, double rd) 
   return th;
 }
 
+/* ------------------------------------------------------------------ radial pinhole */
+
+/* r_d(r) = r (1 + k1 r^2 + k2 r^4 + k3 r^6) on the normalised image plane, and its derivative. */
+static double orc_radial_rd(const double k[4], double r) {
+  double q = r * r;
+  return r * (1.0 + q * (k[0] + q * (k[1] + q * k[2])));
+}
+
+static double orc_radial_rd_prime(const double k[4], double r) {
+  double q = r * r;
+  return 1.0 + q * (3 * k[0] + q * (5 * k[1] + q * 7 * k[2]));
+}
+
+/* Largest normalised radius the radial model images: the first zero of d r_d / d r on
+ * (0, 10] (the distortion polynomial turns over there), else unbounded. */
+static double orc_radial_rmax(const double k[4]) {
+  const int steps = 1 << 14;
+  double lo = 0.0, prev = orc_radial_rd_prime(k, 0.0);
+  for (int i = 1; i <= steps; ++i) {
+    double r = 10.0 * (double)i / steps;
+    double v = orc_radial_rd_prime(k, r);
+    if (v <= 0.0 && prev > 0.0) {
+      double a = lo, b = r;
+      for (int it = 0; it < 200; ++it) {
+        double m = 0.5 * (a + b);
+        if (orc_radial_rd_prime(k, m) > 0.0) a = m; else b = m;
+      }
+      return a;
+    }
+    lo = r; prev = v;
+  }
+  return INFINITY;
+}
+
+/* r >= 0 with r_d(r) = rd on the increasing branch [0, rmax]: bisection on a bracket. */
+static double orc_radial_inverse(const double k[4], double rmax, double rd) {
+  double a = 0.0, b = rmax;
+  if (!isfinite(b)) {
+    b = rd > 1.0 ? rd : 1.0;
+    while (orc_radial_rd(k, b) < rd) b *= 2.0;
+  }
+  for (int it = 0; it < 300 && b - a > 1e-16 * (1.0 + b); ++it) {
+    double m = 0.5 * (a + b);
+    if (orc_radial_rd(k, m) < rd) a = m; else b = m;
+  }
+  return 0.5 * (a + b);
+}
+
+/* The model's field limit passed to the projection / ray functions: theta_max for the
+ * fisheye, the largest normalised radius for the radial pinhole, pi/2 otherwise (unused). */
+double orc_cam_limit(const orc_camera *c) {
+  if (c->model == 1) return orc_theta_max(c->k);
+  if (c->model == 3) return orc_radial_rmax(c->k);
+  return 0.5 * ORC_PI;
+}
+
 /* ------------------------------------------------------------------ camera model g(x) */
 
 /* Projects a camera-space point; returns 1 if it is imaged.  *margin receives the
@@ -217,6 +275,18 @@ static int orc_project_cam(const orc_camera *c, double theta_max, const double x
       uv[0] = c->cx;
       uv[1] = c->cy;
     }
+    return 1;
+  } else if (c->model == 3) {
+    /* theta_max carries the largest normalised radius of the radial model */
+    double m1 = (Z - c->near_plane) / c->near_plane;
+    if (!(Z > c->near_plane)) { *margin = m1; return 0; }
+    double xn = X / Z, yn = Y / Z, r = sqrt(xn * xn + yn * yn);
+    double m2 = isfinite(theta_max) ? (theta_max - r) / theta_max : INFINITY;
+    *margin = m1 < m2 ? m1 : m2;
+    if (!(r <= theta_max)) return 0;
+    double q = r * r, sd = 1.0 + q * (c->k[0] + q * (c->k[1] + q * c->k[2]));
+    uv[0] = c->fx * xn * sd + c->cx;
+    uv[1] = c->fy * yn * sd + c->cy;
     return 1;
   } else {
     *margin = INFINITY;
@@ -287,6 +357,19 @@ int orc_pixel_ray(const orc_camera *c, double theta_max, double px, double py, d
     if (rd > 0) {
       double s = sin(th) / rd;
       dc[0] = s * mx; dc[1] = s * my; dc[2] = cos(th);
+    } else {
+      dc[0] = 0; dc[1] = 0; dc[2] = 1;
+    }
+  } else if (c->model == 3) {
+    /* theta_max carries the largest normalised radius r_max of the radial model */
+    double rd = sqrt(mx * mx + my * my);
+    double rdmax = isfinite(theta_max) ? orc_radial_rd(c->k, theta_max) : INFINITY;
+    *edge_margin = isfinite(rdmax) ? (rdmax - rd) / rdmax : INFINITY;
+    if (!(rd <= rdmax)) return 0;
+    double r = orc_radial_inverse(c->k, theta_max, rd);
+    *dprime = orc_radial_rd_prime(c->k, r);
+    if (rd > 0) {
+      dc[0] = mx * r / rd; dc[1] = my * r / rd; dc[2] = 1.0;
     } else {
       dc[0] = 0; dc[1] = 0; dc[2] = 1;
     }
@@ -409,10 +492,11 @@ int orc_ut_estimate(const orc_camera *c, double theta_max, int rs_iters, double 
  * Pinhole: u = fx X/Z + cx.  Fisheye: u = fx s X + cx with s = theta_d(theta)/rho,
  * theta = atan2(rho, Z), so d s = (theta_d' d theta - s d rho) / rho with
  * d theta = (X Z, Y Z, -rho^2) / (rho r^2) and d rho = (X, Y, 0) / rho; on the axis (rho = 0)
- * theta_d ~ rho / Z and the map is the pinhole one.  Orthographic: u = fx X + cx. */
+ * theta_d ~ rho / Z and the map is the pinhole one.  Orthographic: u = fx X + cx.  Radial
+ * pinhole: the undistorted pinhole Jacobian, as 3DGS's EWA uses (it ignores the distortion). */
 static void orc_cam_jacobian(const orc_camera *c, const double xc[3], double J[6]) {
   double X = xc[0], Y = xc[1], Z = xc[2];
-  if (c->model == 0) {
+  if (c->model == 0 || c->model == 3) { /* radial pinhole: the undistorted Jacobian of 3DGS */
     J[0] = c->fx / Z; J[1] = 0.0; J[2] = -c->fx * X / (Z * Z);
     J[3] = 0.0; J[4] = c->fy / Z; J[5] = -c->fy * Y / (Z * Z);
   } else if (c->model == 1) {
@@ -484,7 +568,7 @@ static int orc_estimate(const orc_camera *c, double theta_max, const orc_options
 void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
                  double *mean2d, double *cov2d, double *depth, float *depth32, int32_t *rect,
                  int32_t *ntiles, double *edges, int32_t *tie) {
-  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  double theta_max = orc_cam_limit(c);
   int W = c->width, H = c->height;
 #pragma omp parallel for schedule(dynamic, 256)
   for (int i = 0; i < sc->n; ++i) {
@@ -531,8 +615,11 @@ void orc_project(const orc_scene *sc, const orc_camera *c, const orc_options *op
     depth[i] = dep;
     depth32[i] = (float)dep;
     if (!(p.sigma >= op->alpha_min)) continue;
-    /* opacity-tightened extent: where sigma * exp(-k^2/2) falls to alpha_min, capped */
-    double k = sqrt(2.0 * log(p.sigma / op->alpha_min));
+    /* opacity-tightened extent: the Mahalanobis distance where sigma rho falls to alpha_min
+     * (Gaussian: sqrt(2 ln(sigma / alpha_min)); degree n: (2 ln(sigma / alpha_min) 3^(n-2))^(1/n)), capped */
+    int kn = op->kernel_degree > 0 ? op->kernel_degree : 2;
+    double k = kn == 2 ? sqrt(2.0 * log(p.sigma / op->alpha_min))
+                       : pow(2.0 * log(p.sigma / op->alpha_min) * pow(3.0, kn - 2.0), 1.0 / kn);
     if (k > op->extent_sigma) k = op->extent_sigma;
     double hx = k * sqrt(cov[0]), hy = k * sqrt(cov[2]);
     double e0 = vmu[0] - hx - 0.5, e1 = vmu[0] + hx - 0.5, e2 = vmu[1] - hy - 0.5, e3 = vmu[1] + hy - 0.5;
@@ -717,9 +804,27 @@ static double orc_omega2(const orc_particle *p, const double o[3], const double 
   return (cx * cx + cy * cy + cz * cz) / dd;
 }
 
+/* Maximum response along the ray for the kernel of degree n (supplementary Sec. A): the
+ * generalised Gaussian exp(-lambda d^n) of the Mahalanobis distance d, with lambda chosen so
+ * that the response at d = r = 3 equals the Gaussian's exp(-r^2/2), i.e.
+ * rho = exp(-1/2 3^(2-n) (omega^2)^(n/2)); it peaks at the same tau_max as the Gaussian
+ * (it is decreasing in d).  n = 2 is eq. gaussian_kernel. */
+static double orc_response(const orc_options *op, double w2) {
+  int n = op->kernel_degree > 0 ? op->kernel_degree : 2;
+  if (n == 2) return exp(-0.5 * w2);
+  return exp(-0.5 * pow(3.0, 2.0 - n) * pow(w2, 0.5 * n));
+}
+
+/* d rho / d omega^2 */
+static double orc_dresponse(const orc_options *op, double w2, double rho) {
+  int n = op->kernel_degree > 0 ? op->kernel_degree : 2;
+  if (n == 2) return -0.5 * rho;
+  return -0.5 * pow(3.0, 2.0 - n) * 0.5 * n * pow(w2, 0.5 * n - 1.0) * rho;
+}
+
 typedef struct {
   int i;
-  double alpha, a, T, rho, tau, og[3], dg[3], raw[3], col[3];
+  double alpha, a, T, rho, tau, w2, og[3], dg[3], raw[3], col[3];
 } orc_contrib;
 
 /* Composites one pixel ray over the particles in `order` (eq. QuadratureVolumeRendering with
@@ -755,13 +860,13 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
         int ny = py >= e[2] - tol->eps_px && py <= e[3] + tol->eps_px;
         if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && px >= 0 && py >= 0) {
           double w2 = orc_omega2(p, o, d, og, dg, &tau);
-          if (p->sigma * exp(-0.5 * w2) >= op->alpha_min * (1.0 - tol->eps_rel)) *flags |= ORC_F_RECT_EDGE;
+          if (p->sigma * orc_response(op, w2) >= op->alpha_min * (1.0 - tol->eps_rel)) *flags |= ORC_F_RECT_EDGE;
         }
       }
       continue;
     }
     double w2 = orc_omega2(p, o, d, og, dg, &tau);
-    double rho = exp(-0.5 * w2);
+    double rho = orc_response(op, w2);
     double a = p->sigma * rho;
     if (flags && x->edges && !no_rect) {
       const double *e = x->edges + 4 * i;
@@ -808,7 +913,7 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     for (int ch = 0; ch < 3; ++ch) last_col[ch] = col[ch];
     if (rec && nb < cap) {
       orc_contrib *c = &rec[nb];
-      c->i = i; c->alpha = alpha; c->a = a; c->T = T; c->rho = rho; c->tau = tau;
+      c->i = i; c->alpha = alpha; c->a = a; c->T = T; c->rho = rho; c->tau = tau; c->w2 = w2;
       for (int k = 0; k < 3; ++k) { c->og[k] = og[k]; c->dg[k] = dg[k]; c->raw[k] = raw[k]; c->col[k] = col[k]; }
     }
     ++nb;
@@ -822,7 +927,7 @@ static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int 
                             double o[3], double d[3], double *Y, int *valid, int32_t *flags) {
   double em, dp;
   *valid = orc_pixel_ray(c, theta_max, px + 0.5, py + 0.5, o, d, &em, &dp);
-  if (flags && c->model == 1 && fabs(em) < tol->eps_rel) *flags |= ORC_F_PIXEL_EDGE;
+  if (flags && (c->model == 1 || c->model == 3) && fabs(em) < tol->eps_rel) *flags |= ORC_F_PIXEL_EDGE;
   if (!*valid) { if (flags) *flags |= ORC_F_INVALID_PIXEL; return; }
   if (flags && dp < tol->cond_min) *flags |= ORC_F_ILL_COND;
   double nd = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -843,7 +948,7 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
                 double *tfinal, int32_t *nblend, int32_t *flags, double *slack, double *aslack) {
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, edges, tie);
-  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  double theta_max = orc_cam_limit(c);
   if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int q = 0; q < npix; ++q) {
@@ -884,7 +989,7 @@ void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options
   orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
   for (int j = 0; j < nlist; ++j) x.order[j] = (int32_t)list[j];
   x.norder = nlist;
-  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  double theta_max = orc_cam_limit(c);
   if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
   orc_tol tol = {0, 0, 0, 0, 0};
   double o[3], d[3], Y[16];
@@ -920,7 +1025,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
   int n = sc->n, nsh = x.nsh;
-  double theta_max = c->model == 1 ? orc_theta_max(c->k) : 0.5 * ORC_PI;
+  double theta_max = orc_cam_limit(c);
   if (op->colour_mode == 1) orc_ctx_colour(&x, c, theta_max, op);
   /* accumulators: dM (9), dmu (3), dsigma (1), dL/d colour (3, colour_mode 1) */
   double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double));
@@ -965,7 +1070,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
         }
         double da = k->a > op->alpha_max ? 0.0 : dalpha;
         double dsig = da * k->rho;
-        double dw2 = da * (-0.5 * k->a);
+        double dw2 = da * p->sigma * orc_dresponse(op, k->w2, k->rho);
         double pv[3], xw[3];
         for (int j = 0; j < 3; ++j) {
           pv[j] = 2.0 * dw2 * (k->og[j] + k->tau * k->dg[j]); /* dL/d o_g */

@@ -205,14 +205,15 @@ def test_theta_max_is_first_root_of_derivative(orc):
     assert abs(tm - math.sqrt(u)) < 1e-12
 
 
-@pytest.mark.parametrize("model,rs", [("pinhole", 0), ("fisheye", 0), ("pinhole", 1), ("fisheye", 1)])
+@pytest.mark.parametrize("model,rs", [("pinhole", 0), ("fisheye", 0), ("pinhole", 1), ("fisheye", 1),
+                                      ("pinhole_radial", 0), ("pinhole_radial", 1)])
 def test_pixel_ray_passes_through_projected_point(orc, model, rs):
     """Inverse consistency of g: the pixel ray at g(x) passes through x, including under a
     rolling shutter once the row-time fixed point has converged."""
     rng = np.random.default_rng(7)
     qe, te = synth.rs_end_pose(0.05, 2.0)
-    k = [0.02, -0.01, 0.003, -0.0005] if model == "fisheye" else [0, 0, 0, 0]
-    cam = synth.camera(model, 640, 480, fx=300.0 if model == "pinhole" else None, k=k, q_end=qe, t_end=te,
+    k = {"fisheye": [0.02, -0.01, 0.003, -0.0005], "pinhole_radial": [-0.12, 0.03, -0.002, 0.0]}.get(model, [0] * 4)
+    cam = synth.camera(model, 640, 480, fx=300.0 if model != "fisheye" else None, k=k, q_end=qe, t_end=te,
                        rolling_shutter=rs)
     for _ in range(20):
         x = np.array([rng.uniform(-1, 1), rng.uniform(-0.7, 0.7), rng.uniform(2, 4)])
@@ -568,6 +569,93 @@ def test_ewa_projection_option(orc):
     assert ok and np.allclose(pe["mean2d"][i], vmu) and np.allclose(pe["cov2d"][i], cov)
 
 
+# ------------------------------------------------------------------ radial pinhole camera
+
+def test_radial_pinhole_without_distortion_is_the_pinhole(orc):
+    """k = 0: the radial model is the plain pinhole (projection, rays and the rendered image)."""
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    camr = dict(cam, model="pinhole_radial")
+    a = orc.render(sc, cam, op, proj=orc.project(sc, cam, op))
+    pr = orc.project(sc, camr, op)
+    assert np.array_equal(pr["rect"], orc.project(sc, cam, op)["rect"])
+    b = orc.render(sc, camr, op, proj=pr)
+    assert np.max(np.abs(a["rgb"] - b["rgb"])) < 1e-12
+
+
+def test_radial_field_limit_closed_form(orc):
+    """With k2 = k3 = 0 and k1 < 0, r_d = r (1 + k1 r^2) turns over at r = 1 / sqrt(-3 k1): points
+    beyond that radius are not imaged, points inside are, and the image edge is r_d(r_max)."""
+    k1 = -0.2
+    rmax = 1.0 / math.sqrt(-3.0 * k1)
+    cam = synth.camera("pinhole_radial", 640, 480, fx=200.0, k=[k1, 0, 0, 0])
+    for r, ok_expected in ((0.97 * rmax, True), (1.03 * rmax, False)):
+        x = np.array([r * 3.0, 0.0, 3.0])
+        assert orc.project_point(cam, x)[0] == ok_expected
+    rd_max = rmax * (1 + k1 * rmax**2)
+    cx = np.float32(320.0)
+    assert orc.pixel_ray(cam, float(cx) + 200.0 * rd_max * 0.999, 240.0)[0]
+    assert not orc.pixel_ray(cam, float(cx) + 200.0 * rd_max * 1.001, 240.0)[0]
+
+
+# ------------------------------------------------------------------ generalised kernels (degree n)
+
+@pytest.mark.parametrize("n", [3, 4, 5, 8])
+def test_generalised_kernel_max_response_matches_dense_scan(orc, n):
+    """Degree-n kernel rho = exp(-lambda d^n), lambda = 3^(2-n) / 2 (equal to the Gaussian's
+    response at d = 3): the maximum along a pixel ray from a dense 1-D scan of rho(x) equals the
+    oracle's alpha / sigma, and the response is monotone in d so the argmax is the Gaussian's."""
+    rng = np.random.default_rng(22 + n)
+    cam = synth.camera("pinhole", 32, 32, fx=30.0, fy=30.0)
+    lam = 0.5 * 3.0 ** (2 - n)
+    for _ in range(6):
+        mu = np.array([rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), rng.uniform(2, 3)]).astype(np.float32)
+        ls = rng.normal(-2.0, 0.3, 3).astype(np.float32)
+        q = rng.standard_normal(4).astype(np.float32)
+        logit = np.float32(0.3)
+        px, py = int(rng.integers(8, 24)), int(rng.integers(8, 24))
+        sc = one_scene(mu, ls, q, logit, [[0.1, 0.2, 0.3]])
+        out = orc.render(sc, cam, synth.options(t_min=0.0, alpha_min=1e-30, kernel_degree=n),
+                         proj=dict(rect=np.array([[0, 0, 31, 31]], np.int32), depth32=np.array([2.0], np.float32)),
+                         pixels=([px], [py]), no_rect=True)
+        a = out["alpha"][0]
+        sigma = 1 / (1 + math.exp(-float(logit)))
+        R = rot(q.astype(float))
+        Sinv = R @ np.diag(np.exp(-2 * ls.astype(float))) @ R.T
+        d = np.array([(px + 0.5 - 16) / 30, (py + 0.5 - 16) / 30, 1.0])
+        taus = np.linspace(0, 6, 200001)
+        X = taus[:, None] * d[None, :] - mu.astype(float)[None, :]
+        rho = np.exp(-lam * np.einsum("ni,ij,nj->n", X, Sinv, X) ** (n / 2))
+        assert abs(a - sigma * rho.max()) < 1e-6 * max(sigma * rho.max(), 1e-12) + 1e-14
+    # the response at Mahalanobis distance 3 is the Gaussian's
+    assert abs(math.exp(-lam * 3.0**n) - math.exp(-0.5 * 9.0)) < 1e-15
+
+
+def test_generalised_kernel_degree_two_is_the_gaussian(orc):
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    a = orc.render(sc, cam, op, proj=orc.project(sc, cam, op))
+    op2 = dict(op, kernel_degree=2)
+    b = orc.render(sc, cam, op2, proj=orc.project(sc, cam, op2))
+    assert np.array_equal(a["rgb"], b["rgb"])
+    op4 = dict(op, kernel_degree=4)
+    c = orc.render(sc, cam, op4, proj=orc.project(sc, cam, op4))
+    assert np.abs(c["rgb"] - a["rgb"]).max() > 1e-3
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_rect_culling_lossless_for_generalised_kernels(orc, n):
+    """Orthographic camera, cap lifted: the degree-n extent (2 ln(sigma/alpha_min) 3^(n-2))^(1/n)
+    drops only particles below alpha_min, so culled == unculled brute force."""
+    sc = synth.scene_cube(300, 12, log_s=(-2.5, 0.4), deg=1, lo=(-1, -1, 1), hi=(1, 1, 3))
+    cam = synth.camera("ortho", 48, 40, fx=20.0, fy=20.0, cx=24.0, cy=20.0)
+    op = synth.options(extent_sigma=10.0, t_min=0.0, kernel_degree=n)
+    proj = orc.project(sc, cam, op)
+    a = orc.render(sc, cam, op, proj=proj)
+    b = orc.render(sc, cam, op, proj=proj, no_rect=True)
+    assert np.max(np.abs(a["rgb"] - b["rgb"])) < 1e-12
+
+
 # ------------------------------------------------------------------ per-particle colour (colour_mode 1)
 
 def test_per_particle_colour_equals_per_pixel_for_degree_zero(orc):
@@ -616,14 +704,14 @@ def _loss(orc, sc, cam, op, proj, pix, g_rgb, g_a):
     return float(np.sum(o["rgb"] * g_rgb) + np.sum(o["alpha"] * g_a))
 
 
-@pytest.mark.parametrize("colour_mode,deg", [(0, 1), (1, 2)])
-def test_gradients_match_central_differences(orc, colour_mode, deg):
+@pytest.mark.parametrize("colour_mode,deg,kdeg", [(0, 1, 2), (1, 2, 2), (0, 1, 4), (0, 0, 4)])
+def test_gradients_match_central_differences(orc, colour_mode, deg, kdeg):
     """FP64 analytic gradients vs Richardson-extrapolated central differences (steps 2^-9, 2^-10,
     exact in FP32) with the culling decisions held fixed (they carry no gradient, Sec. 4.1).
     colour_mode 1 includes the mean's gradient through the per-particle view direction."""
     sc = _fd_scene(deg=deg)
     cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
-    op = synth.options(t_min=1e-4, colour_mode=colour_mode)
+    op = synth.options(t_min=1e-4, colour_mode=colour_mode, kernel_degree=kdeg)
     proj = orc.project(sc, cam, op)
     yy, xx = np.mgrid[0:20, 0:24]
     px, py = xx.reshape(-1), yy.reshape(-1)
@@ -654,7 +742,41 @@ def test_gradients_match_central_differences(orc, colour_mode, deg):
             fd = (4 * d2 - d1) / 3
             assert abs(fd - ga[j]) <= 1e-6 * max(1.0, abs(ga[j])) + 1e-7, (name, j, fd, ga[j])
             checked += 1
-    assert checked > 200
+    assert checked >= 12 * 14  # every parameter of the 12 particles (SH degree >= 0)
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_odd_degree_kernel_gradient_single_particle(orc, n):
+    """Odd degrees are not twice differentiable where a ray crosses a particle's centre, so the
+    scene-wide difference check above uses even degrees; here one particle and a pixel whose
+    ray passes well off its centre: analytic dL/dmu, dL/dlog_s, dL/dq vs Richardson central
+    differences (exact FP32 steps)."""
+    cam = synth.camera("pinhole", 16, 16, fx=16.0, fy=16.0)
+    base = dict(means=np.array([[0.0625, -0.03125, 2.0]], np.float32),
+                log_scales=np.array([[-1.625, -1.875, -1.25]], np.float32),
+                quats=np.array([[0.8125, 0.1875, -0.3125, 0.40625]], np.float32),
+                opacity_logits=np.array([0.75], np.float32),
+                sh=np.array([[[0.125, 0.25, 0.375]]], np.float32), sh_degree=0)
+    proj = dict(rect=np.array([[0, 0, 15, 15]], np.int32), depth32=np.array([2.0], np.float32))
+    op = synth.options(t_min=0.0, kernel_degree=n)
+    px, py = 10, 6
+    gr = orc.backward(base, cam, op, proj, ([px], [py]), np.ones((1, 3)), np.ones(1))
+    for key in ("means", "log_scales", "quats"):
+        flat = base[key].reshape(-1)
+        for j in range(flat.size):
+            def f(h):
+                s2 = dict(base)
+                b2 = flat.copy()
+                b2[j] = np.float32(float(flat[j]) + h)
+                s2[key] = b2.reshape(base[key].shape)
+                o = orc.render(s2, cam, op, proj=proj, pixels=([px], [py]))
+                return float(o["rgb"].sum() + o["alpha"].sum())
+            h = 2.0**-10
+            d1 = (f(h) - f(-h)) / (2 * h)
+            d2 = (f(h / 2) - f(-h / 2)) / h
+            fd = (4 * d2 - d1) / 3
+            ga = gr[key].reshape(-1)[j]
+            assert abs(fd - ga) <= 1e-5 * max(1.0, abs(ga)), (key, j, fd, ga)
 
 
 def test_dalpha_dmu_matches_printed_chain(orc):
