@@ -49,7 +49,10 @@ typedef enum {
   UT_ERR_UNSUPPORTED = 5  /* a valid request this build does not implement */
 } ut_status;
 
-typedef enum { UT_CAM_PINHOLE = 0, UT_CAM_FISHEYE = 1 } ut_cam_model;
+/* UT_CAM_PINHOLE_RADIAL: u = fx x_n (1 + k1 r^2 + k2 r^4 + k3 r^6) + cx (likewise v) with
+ * (x_n, y_n) = (X, Y) / Z and r = |(x_n, y_n)| (k[3] unused); points beyond the first turning
+ * point of r_d(r) = r (1 + ...) are not imaged, nor pixels beyond r_d there. */
+typedef enum { UT_CAM_PINHOLE = 0, UT_CAM_FISHEYE = 1, UT_CAM_PINHOLE_RADIAL = 2 } ut_cam_model;
 
 /* Camera (the extrinsic W and intrinsic D of Algorithm 1).
  *   pinhole: valid iff z > near_plane; (u,v) = (fx x/z + cx, fy y/z + cy).
@@ -107,7 +110,12 @@ typedef struct {
  *   colour_mode: UT_COLOUR_PER_PIXEL (default; SH at each pixel's ray direction, Sec. 3) or
  *   UT_COLOUR_PER_PARTICLE, a faster mode that evaluates the SH once per particle at the
  *   direction from the camera centre (at the mean's shutter time) to the mean; its gradient
- *   also reaches the mean through that direction. */
+ *   also reaches the mean through that direction.  Under UT_PROJECTION_EWA the radial pinhole
+ *   uses the undistorted pinhole Jacobian (as 3DGS's EWA does). */
+/*   kernel_degree: n = 2 (default) is the Gaussian (eq. gaussian_kernel); n in 3..8 the
+ *   generalised Gaussian of supplementary Sec. A, rho = exp(-1/2 3^(2-n) d^n) of the Mahalanobis
+ *   distance d (the same response as the Gaussian at d = 3), evaluated at the same tau_max;
+ *   combined with UT_COLOUR_PER_PARTICLE it is rejected with UT_ERR_UNSUPPORTED. */
 #define UT_PROJECTION_UT 0
 #define UT_PROJECTION_EWA 1
 #define UT_COLOUR_PER_PIXEL 0
@@ -119,6 +127,7 @@ typedef struct {
   float extent_sigma;
   int32_t projection;
   int32_t colour_mode;
+  int32_t kernel_degree;
 } ut_options;
 
 void ut_default_options(ut_options *opt);

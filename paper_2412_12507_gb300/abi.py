@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libut3d.so")
 
 UT_OK, UT_ERR_INVALID_ARG, UT_ERR_CAPACITY, UT_ERR_CUDA, UT_ERR_TIMEOUT, UT_ERR_UNSUPPORTED = range(6)
-CAM_MODELS = {"pinhole": 0, "fisheye": 1}
+CAM_MODELS = {"pinhole": 0, "fisheye": 1, "pinhole_radial": 2}
 
 
 class UtError(RuntimeError):
@@ -41,7 +41,8 @@ class UtScene(C.Structure):
 class UtOptions(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("t_min", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("rs_iters", C.c_int32), ("newton_iters", C.c_int32),
-                ("extent_sigma", C.c_float), ("projection", C.c_int32), ("colour_mode", C.c_int32)]
+                ("extent_sigma", C.c_float), ("projection", C.c_int32), ("colour_mode", C.c_int32),
+                ("kernel_degree", C.c_int32)]
 
 
 class UtView(C.Structure):
@@ -155,7 +156,7 @@ def make_camera(cam: dict) -> UtCamera:
 def make_options(opts: dict | None = None) -> UtOptions:
     o = default_options()
     for k, v in (opts or {}).items():
-        if k in ("tile_w", "tile_h", "rs_iters", "newton_iters", "projection", "colour_mode"):
+        if k in ("tile_w", "tile_h", "rs_iters", "newton_iters", "projection", "colour_mode", "kernel_degree"):
             setattr(o, k, int(v))
         elif k in ("t_min", "alpha_min", "alpha_max", "extent_sigma"):
             setattr(o, k, float(v))

@@ -63,6 +63,27 @@ double fisheye_theta_max(const double k[4]) {
   return 0.5 * M_PI;
 }
 
+// Radial pinhole: first zero of d r_d / d r = 1 + 3 k1 r^2 + 5 k2 r^4 + 7 k3 r^6 on (0, 10]
+// (scanned in u = r^2, refined by bisection), or infinity when the model is monotone there.
+double radial_rmax(const double k[3]) {
+  auto dr = [&](double u) { return 1.0 + u * (3.0 * k[0] + u * (5.0 * k[1] + u * 7.0 * k[2])); };
+  const int steps = 16384;
+  double prev_u = 0.0;
+  for (int i = 1; i <= steps; ++i) {
+    double u = 100.0 * i / steps;
+    if (dr(u) <= 0.0) {
+      double lo = prev_u, hi = u;
+      for (int it = 0; it < 100; ++it) {
+        double m = 0.5 * (lo + hi);
+        (dr(m) > 0.0 ? lo : hi) = m;
+      }
+      return std::sqrt(lo);
+    }
+    prev_u = u;
+  }
+  return INFINITY;
+}
+
 void quat_rot(const double q[4], double R[9]) {
   double w = q[0], x = q[1], y = q[2], z = q[3];
   R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
@@ -72,7 +93,8 @@ void quat_rot(const double q[4], double R[9]) {
 
 ut_status make_cam(const ut_camera *c, DevCam &d) {
   if (!c) return UT_ERR_INVALID_ARG;
-  if (c->model != UT_CAM_PINHOLE && c->model != UT_CAM_FISHEYE) return UT_ERR_INVALID_ARG;
+  if (c->model != UT_CAM_PINHOLE && c->model != UT_CAM_FISHEYE && c->model != UT_CAM_PINHOLE_RADIAL)
+    return UT_ERR_INVALID_ARG;
   if (c->width < 1 || c->height < 1 || c->width > 32767 || c->height > 32767) return UT_ERR_INVALID_ARG;
   if (c->rolling_shutter != 0 && c->rolling_shutter != 1) return UT_ERR_INVALID_ARG;
   if (c->rolling_shutter && c->height < 2) return UT_ERR_INVALID_ARG;
@@ -135,6 +157,13 @@ ut_status make_cam(const ut_camera *c, DevCam &d) {
     double tm = fisheye_theta_max(k);
     d.theta_max = (float)tm;
     d.rd_max = (float)poly_theta_d(k, tm);
+  } else if (c->model == UT_CAM_PINHOLE_RADIAL) {
+    // theta_max carries the largest imaged normalised radius r_max, rd_max = r_d(r_max)
+    double k[3] = {c->k[0], c->k[1], c->k[2]};
+    double rm = radial_rmax(k);
+    d.theta_max = std::isfinite(rm) ? (float)rm : INFINITY;
+    d.rd_max = std::isfinite(rm) ? (float)(rm * (1.0 + rm * rm * (k[0] + rm * rm * (k[1] + rm * rm * k[2]))))
+                                 : INFINITY;
   } else {
     d.theta_max = (float)(0.5 * M_PI);
     d.rd_max = INFINITY;
@@ -155,8 +184,10 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
     return UT_ERR_INVALID_ARG;
   if (o->rs_iters < 0 || o->rs_iters > 64 || o->newton_iters < 1 || o->newton_iters > 64) return UT_ERR_INVALID_ARG;
   if ((o->projection != UT_PROJECTION_UT && o->projection != UT_PROJECTION_EWA) ||
-      (o->colour_mode != UT_COLOUR_PER_PIXEL && o->colour_mode != UT_COLOUR_PER_PARTICLE))
+      (o->colour_mode != UT_COLOUR_PER_PIXEL && o->colour_mode != UT_COLOUR_PER_PARTICLE) ||
+      o->kernel_degree < 2 || o->kernel_degree > 8)
     return UT_ERR_INVALID_ARG;
+  if (o->kernel_degree != 2 && o->colour_mode == UT_COLOUR_PER_PARTICLE) return UT_ERR_UNSUPPORTED;
   d.tile_w = o->tile_w;
   d.tile_h = o->tile_h;
   d.tiles_x = (c->width + o->tile_w - 1) / o->tile_w;
@@ -169,6 +200,8 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
   d.newton_iters = o->newton_iters;
   d.projection = o->projection;
   d.colour_mode = o->colour_mode;
+  d.kernel_degree = o->kernel_degree;
+  d.kernel_lambda = (float)(0.5 * std::pow(3.0, 2.0 - o->kernel_degree));
   return UT_OK;
 }
 
@@ -335,6 +368,7 @@ void ut_default_options(ut_options *o) {
   o->extent_sigma = 3.f;
   o->projection = UT_PROJECTION_UT;
   o->colour_mode = UT_COLOUR_PER_PIXEL;
+  o->kernel_degree = 2;
 }
 
 uint64_t ut_kernel_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }

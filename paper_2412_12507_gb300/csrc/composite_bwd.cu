@@ -1,14 +1,5 @@
-// composite.cu — tile-based front-to-back compositing with 3D particle evaluation
-// (Sec. 4.2, eq. GaussianMaxResponse; eq. QuadratureVolumeRendering) and its
-// hand-written backward (supplementary Sec. B), for a batch of views.
-//
-// One thread block per image tile (global tile ids over all views of the batch), one thread
-// per pixel.  The tile's depth-sorted particle list is consumed in batches of kBatchF
-// (forward) or kBatch (backward) particles: the block gathers each batch's parameters once,
-// activates them (M = S^-1 R^T, sigma, the alpha_min test threshold, packed rect) into
-// shared memory together with their SH coefficients, and every pixel then walks the batch
-// from shared memory.  The block
-// leaves the list as soon as every pixel's transmittance has dropped below t_min.
+// composite_bwd.cu — hand-written backward of the compositing (supplementary Sec. B) for a
+// batch of views.
 //
 // The backward replays the forward IN FORWARD ORDER: the stored rgb and T_final give the
 // suffix sums S_i = C - sum_{j<=i} c_j alpha_j T_j without dividing transmittances,
@@ -17,358 +8,13 @@
 // partials with a tensor-core contraction over the warp's pixels; both are accumulated
 // across warps in shared memory and pushed to global memory with one atomic per value per
 // (tile, particle).  A final per-particle kernel maps the accumulated dL/dM, dL/dmu,
-// dL/dsigma onto log-scales, quaternions and logits.
-//
-// Template RS selects the general ray-origin path (per-pixel origin, needed when any view
-// has a rolling shutter); without it the origin is the camera centre of the view.
+// dL/dsigma onto log-scales, quaternions and logits.  Tiles run heaviest replay first.
 #include <cuda_bf16.h>
 
-#include "ut3d_device.cuh"
-#include "ut3d_internal.h"
+#include "composite_common.cuh"
 
 namespace ut3d {
 namespace {
-
-constexpr int kBatch = 64;    // particles staged per block step (backward)
-constexpr int kBatchF = 128;  // particles staged per block step (forward)
-constexpr int kOrderBuckets = 1024;  // log buckets of the backward's tile schedule
-
-// Tile schedule of the backward (device scratch): per-tile replay length, the tiles with work
-// ordered by decreasing length, the bucket histogram and scatter cursors, and the count.
-struct TileSched {
-  uint32_t *work, *order, *hist, *cursor, *n_work;
-};
-
-TileSched carve_tile_sched(void *p, int tiles) {
-  const size_t t = (size_t)(tiles > 0 ? tiles : 1);
-  char *c = static_cast<char *>(p);
-  TileSched ts;
-  ts.work = reinterpret_cast<uint32_t *>(c);
-  ts.order = reinterpret_cast<uint32_t *>(c + align256(sizeof(uint32_t) * t));
-  ts.hist = reinterpret_cast<uint32_t *>(c + 2 * align256(sizeof(uint32_t) * t));
-  ts.cursor = ts.hist + kOrderBuckets;
-  ts.n_work = ts.cursor + kOrderBuckets;
-  return ts;
-}
-
-// Staged particle record (4 x float4):
-//   g0 = M00 M01 M02 M10   g1 = M11 M12 M20 M21   g2 = M22 a.x a.y a.z
-//   g3 = sigma, thr = 2 ln(sigma / alpha_min), rect (x0 | y0 << 16), rect (x1 | y1 << 16)
-// where a = M (o - mu) with o the camera centre (RS = false) or a = M mu (RS = true).
-// aux (backward only) = o - mu (RS = false) or mu (RS = true).
-template <bool RS>
-__device__ __forceinline__ void stage_particle(const DevScene &sc, const DevCam &cam, const DevOpts &op, short4 r,
-                                               uint32_t idx, float4 *g, float4 *aux) {
-  float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
-  float3 ls = make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
-  Particle p;
-  activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
-  float3 a;
-  float3 om = make_float3(cam.cen[0] - mu.x, cam.cen[1] - mu.y, cam.cen[2] - mu.z);
-  if (RS) a = mat3_mul(p.M, mu);
-  else a = mat3_mul(p.M, om);
-  float thr = 2.f * logf(p.sigma / op.alpha_min);
-  g[0] = make_float4(p.M[0], p.M[1], p.M[2], p.M[3]);
-  g[1] = make_float4(p.M[4], p.M[5], p.M[6], p.M[7]);
-  g[2] = make_float4(p.M[8], a.x, a.y, a.z);
-  int r0 = ((int)(unsigned short)r.x) | ((int)r.y << 16);
-  int r1 = ((int)(unsigned short)r.z) | ((int)r.w << 16);
-  g[3] = make_float4(p.sigma, thr, __int_as_float(r0), __int_as_float(r1));
-  if (aux) *aux = RS ? make_float4(mu.x, mu.y, mu.z, 0.f) : make_float4(om.x, om.y, om.z, 0.f);
-}
-
-// SH coefficients of the batch's particles into shared memory (float4 when aligned).
-template <int NC>
-__device__ __forceinline__ void stage_sh(const DevScene &sc, const uint32_t *s_idx, int nb, float *s_sh) {
-  if constexpr (NC % 4 == 0) {
-    if (!sc.sh_vec) {
-      for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
-        int b = f / NC;
-        s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
-      }
-      return;
-    }
-    constexpr int N4 = NC / 4;
-    const float4 *src = reinterpret_cast<const float4 *>(sc.sh);
-    float4 *dst = reinterpret_cast<float4 *>(s_sh);
-    for (int f = threadIdx.x; f < nb * N4; f += blockDim.x) {
-      int b = f / N4;
-      dst[f] = src[(size_t)s_idx[b] * N4 + (f - b * N4)];
-    }
-  } else {
-    for (int f = threadIdx.x; f < nb * NC; f += blockDim.x) {
-      int b = f / NC;
-      s_sh[f] = sc.sh[(size_t)s_idx[b] * NC + (f - b * NC)];
-    }
-  }
-}
-
-// Raw colour sum_k beta_k,ch Y_k + 1/2 of one staged particle (before the clamp at 0).
-template <int NSH>
-__device__ __forceinline__ void sh_colour(const float *shb, const float *Y, float &r0, float &r1, float &r2) {
-  constexpr int NC = NSH * 3;
-  r0 = 0.5f; r1 = 0.5f; r2 = 0.5f;
-  if constexpr (NC % 4 == 0) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(shb);
-#pragma unroll
-    for (int j = 0; j < NC / 4; ++j) {
-      float4 c = s4[j];
-      const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int idx = 4 * j + e, k = idx / 3, ch = idx % 3;
-        if (ch == 0) r0 = fmaf(cv[e], Y[k], r0);
-        else if (ch == 1) r1 = fmaf(cv[e], Y[k], r1);
-        else r2 = fmaf(cv[e], Y[k], r2);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NSH; ++k) {
-      r0 = fmaf(shb[3 * k], Y[k], r0);
-      r1 = fmaf(shb[3 * k + 1], Y[k], r1);
-      r2 = fmaf(shb[3 * k + 2], Y[k], r2);
-    }
-  }
-}
-
-// Response of a staged particle for the ray (o, d) of pixel (px, py).  Returns false if the
-// pixel is outside the particle's rect or sigma rho < alpha_min (tested as
-// |o_g x d_g|^2 > thr |d_g|^2).  Otherwise returns a = sigma exp(-omega^2/2) and the
-// canonical-space ray (o_g, d_g) with |d_g|^2.
-template <bool RS>
-__device__ __forceinline__ bool eval_response(const float4 *g, int px, int py, float3 o, float3 d, float3 &og,
-                                              float3 &dg, float &dd, float &a) {
-  float4 g3 = g[3];
-  int r0 = __float_as_int(g3.z), r1 = __float_as_int(g3.w);
-  if (px < (r0 & 0xffff) || px > (r1 & 0xffff) || py < (r0 >> 16) || py > (r1 >> 16)) return false;
-  float4 g0 = g[0], g1 = g[1], g2 = g[2];
-  dg = make_float3(fmaf(g0.x, d.x, fmaf(g0.y, d.y, g0.z * d.z)), fmaf(g0.w, d.x, fmaf(g1.x, d.y, g1.y * d.z)),
-                   fmaf(g1.z, d.x, fmaf(g1.w, d.y, g2.x * d.z)));
-  if (RS) {
-    og = make_float3(fmaf(g0.x, o.x, fmaf(g0.y, o.y, g0.z * o.z)) - g2.y,
-                     fmaf(g0.w, o.x, fmaf(g1.x, o.y, g1.y * o.z)) - g2.z,
-                     fmaf(g1.z, o.x, fmaf(g1.w, o.y, g2.x * o.z)) - g2.w);
-  } else {
-    og = make_float3(g2.y, g2.z, g2.w);
-  }
-  float3 c = cross3(og, dg);
-  float cc = fmaf(c.x, c.x, fmaf(c.y, c.y, c.z * c.z));
-  dd = fmaf(dg.x, dg.x, fmaf(dg.y, dg.y, dg.z * dg.z));
-  if (!(cc <= g3.y * dd)) return false;
-  a = g3.x * __expf(-0.5f * __fdividef(cc, dd));
-  return true;
-}
-
-// Per-particle colour mode: unit view direction of a particle, from the camera centre at the
-// mean's shutter time (the rolling-shutter fixed point; t = 0 for a global shutter) to the
-// mean, and 1 / the distance.
-template <bool RS>
-__device__ __forceinline__ float3 particle_dir(const DevCam &cam, const DevOpts &op, float3 mu, float &inv_len) {
-  float3 c = make_float3(cam.cen[0], cam.cen[1], cam.cen[2]);
-  if (RS && cam.rs) {
-    float2 uv;
-    float t;
-    project_world(cam, op.rs_iters, mat3_mul(cam.R0, mu), uv, t);
-    // centre -R(t)^T T(t) with R(t) = Rot(ax, t phi) R0
-    const float3 Tt = make_float3(fmaf(t, cam.dT[0], cam.T0[0]), fmaf(t, cam.dT[1], cam.T0[1]),
-                                  fmaf(t, cam.dT[2], cam.T0[2]));
-    c = mat3_tmul(cam.R0, rotate_axis(cam.ax, make_float3(-Tt.x, -Tt.y, -Tt.z), -t * cam.phi));
-  }
-  const float3 v = make_float3(mu.x - c.x, mu.y - c.y, mu.z - c.z);
-  inv_len = rsqrtf(dot3(v, v));
-  return make_float3(v.x * inv_len, v.y * inv_len, v.z * inv_len);
-}
-
-// Per-particle colour mode: raw colour sum_k beta_k,ch Y_k(dir) + 1/2 of particle idx.
-template <int DEG, bool RS>
-__device__ __forceinline__ float4 particle_colour(const DevScene &sc, const DevCam &cam, const DevOpts &op,
-                                                  uint32_t idx) {
-  constexpr int NSH = (DEG + 1) * (DEG + 1);
-  const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
-  float il;
-  const float3 dir = particle_dir<RS>(cam, op, mu, il);
-  float Y[NSH];
-  sh_basis<DEG>(dir.x, dir.y, dir.z, Y);
-  const float *beta = sc.sh + (size_t)idx * NSH * 3;
-  float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
-#pragma unroll
-  for (int k = 0; k < NSH; ++k) {
-    r0 = fmaf(beta[3 * k], Y[k], r0);
-    r1 = fmaf(beta[3 * k + 1], Y[k], r1);
-    r2 = fmaf(beta[3 * k + 2], Y[k], r2);
-  }
-  return make_float4(r0, r1, r2, 0.f);
-}
-
-// sum_k a_k grad p_k(x, y, z) for the polynomials p_k that sh_basis evaluates on the unit sphere
-// (differentiated as polynomials in x, y, z; callers project onto the tangent plane).
-template <int DEG>
-__device__ __forceinline__ float3 sh_poly_grad(float x, float y, float z, const float *a) {
-  float gx = 0.f, gy = 0.f, gz = 0.f;
-  if (DEG >= 1) {
-    const float c1 = 0.4886025119029199f;
-    gy -= c1 * a[1];
-    gz += c1 * a[2];
-    gx -= c1 * a[3];
-  }
-  if (DEG >= 2) {
-    const float c4 = 1.0925484305920792f, c6 = 0.31539156525252005f, c8 = 0.5462742152960396f;
-    gx += c4 * y * a[4];
-    gy += c4 * x * a[4];
-    gy -= c4 * z * a[5];
-    gz -= c4 * y * a[5];
-    gx -= 2.f * c6 * x * a[6];
-    gy -= 2.f * c6 * y * a[6];
-    gz += 4.f * c6 * z * a[6];
-    gx -= c4 * z * a[7];
-    gz -= c4 * x * a[7];
-    gx += 2.f * c8 * x * a[8];
-    gy -= 2.f * c8 * y * a[8];
-  }
-  if (DEG >= 3) {
-    const float c9 = 0.5900435899266435f, c10 = 2.890611442640554f, c11 = 0.4570457994644658f,
-                c12 = 0.3731763325901154f, c14 = 1.445305721320277f;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    gx -= 6.f * c9 * x * y * a[9];
-    gy -= 3.f * c9 * (xx - yy) * a[9];
-    gx += c10 * y * z * a[10];
-    gy += c10 * x * z * a[10];
-    gz += c10 * x * y * a[10];
-    gx += 2.f * c11 * x * y * a[11];
-    gy -= c11 * (4.f * zz - xx - 3.f * yy) * a[11];
-    gz -= 8.f * c11 * y * z * a[11];
-    gx -= 6.f * c12 * x * z * a[12];
-    gy -= 6.f * c12 * y * z * a[12];
-    gz += c12 * (6.f * zz - 3.f * xx - 3.f * yy) * a[12];
-    gx -= c11 * (4.f * zz - 3.f * xx - yy) * a[13];
-    gy += 2.f * c11 * x * y * a[13];
-    gz -= 8.f * c11 * x * z * a[13];
-    gx += 2.f * c14 * x * z * a[14];
-    gy -= 2.f * c14 * y * z * a[14];
-    gz += c14 * (xx - yy) * a[14];
-    gx -= 3.f * c9 * (xx - yy) * a[15];
-    gy += 6.f * c9 * x * y * a[15];
-  }
-  return make_float3(gx, gy, gz);
-}
-
-template <int DEG>
-__device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op, int px, int py, bool inside,
-                                            float3 &o, float3 &d, float *Y, bool &valid) {
-  valid = inside && pixel_ray(cam, px, py, op.newton_iters, o, d);
-  if (valid) {
-    float in = rsqrtf(dot3(d, d));
-    sh_basis<DEG>(d.x * in, d.y * in, d.z * in, Y);
-  } else {
-    o = d = make_float3(0.f, 0.f, 1.f);
-#pragma unroll
-    for (int k = 0; k < (DEG + 1) * (DEG + 1); ++k) Y[k] = 0.f;
-  }
-}
-
-// PP: per-particle colour mode (the colour of each staged particle is evaluated once, at its
-// view direction, while staging; pixels read it from shared memory).
-template <int DEG, bool RS, bool STATS, bool PP>
-__global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ BatchDesc bd, DevOpts op,
-                                                       const short4 *__restrict__ rect,
-                                                       const uint32_t *__restrict__ vals,
-                                                       const uint2 *__restrict__ ranges,
-                                                       unsigned long long *__restrict__ stats, TileSched ts) {
-  constexpr int NSH = (DEG + 1) * (DEG + 1);
-  constexpr int NC = NSH * 3;
-  constexpr int PDEG = PP ? 0 : DEG;        // per-pixel SH basis only when colours are per pixel
-  constexpr int NST = PP ? 4 : NC;          // staged colour floats per particle
-  __shared__ float4 s_geo[kBatchF][4];
-  __shared__ __align__(16) float s_sh[kBatchF * NST];
-  __shared__ uint32_t s_idx[kBatchF];
-
-  // tiles in the order k_tile_order gave them (longest predicted walk first); every tile is
-  // in the order, so every pixel is written
-  if (blockIdx.x >= *ts.n_work) return;
-  const int tile = (int)ts.order[blockIdx.x];
-  const DevView &view = bd.v[view_of_tile(bd, tile)];
-  const DevScene &sc = bd.s[view.scene];
-  const DevCam &cam = view.cam;
-  const int lt = tile - view.tile_off;
-  const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
-  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
-  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
-  const bool inside = px < cam.W && py < cam.H;
-  float3 o, d;
-  float Y[(PDEG + 1) * (PDEG + 1)];
-  bool valid;
-  pixel_setup<PDEG>(cam, op, px, py, inside, o, d, Y, valid);
-
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t last = 0;
-  unsigned long long n_eval = 0, n_blend = 0;
-  bool done = !valid;
-  const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatchF) {
-    if (__syncthreads_count(!done) == 0) break;
-    const int nb = min((uint32_t)kBatchF, rg.y - start);
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
-    __syncthreads();
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-      uint32_t idx = s_idx[t];
-      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], nullptr);
-      if (PP) reinterpret_cast<float4 *>(s_sh)[t] = particle_colour<DEG, RS>(sc, cam, op, idx);
-    }
-    if (!PP) stage_sh<NC>(sc, s_idx, nb, s_sh);
-    __syncthreads();
-    if (done) continue;
-    for (int b = 0; b < nb; ++b) {
-      float3 og, dg;
-      float dd, a;
-      if (STATS) {
-        int r0 = __float_as_int(s_geo[b][3].z), r1 = __float_as_int(s_geo[b][3].w);
-        n_eval += !(px < (r0 & 0xffff) || px > (r1 & 0xffff) || py < (r0 >> 16) || py > (r1 >> 16));
-      }
-      if (!eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) continue;
-      float al = fminf(a, op.alpha_max);
-      float Tn = T * (1.f - al);
-      if (Tn < op.t_min) {
-        done = true;
-        break;
-      }
-      if (STATS) ++n_blend;
-      float r0, r1, r2;
-      if (PP) {
-        const float4 c = reinterpret_cast<const float4 *>(s_sh)[b];
-        r0 = c.x; r1 = c.y; r2 = c.z;
-      } else {
-        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
-      }
-      float w = al * T;
-      C0 = fmaf(fmaxf(r0, 0.f), w, C0);
-      C1 = fmaf(fmaxf(r1, 0.f), w, C1);
-      C2 = fmaf(fmaxf(r2, 0.f), w, C2);
-      T = Tn;
-      last = start + b + 1;
-    }
-  }
-  if (inside) {
-    size_t pix = (size_t)py * cam.W + px;
-    size_t plane = (size_t)cam.W * cam.H;
-    view.rgb[pix] = C0;
-    view.rgb[plane + pix] = C1;
-    view.rgb[2 * plane + pix] = C2;
-    view.alpha[pix] = valid ? 1.f - T : 0.f;
-    if (view.tfinal) view.tfinal[pix] = T;
-    if (view.n_used) view.n_used[pix] = last;
-  }
-  if (STATS) {
-    for (int s = 16; s >= 1; s >>= 1) {
-      n_eval += __shfl_xor_sync(0xffffffffu, n_eval, s);
-      n_blend += __shfl_xor_sync(0xffffffffu, n_blend, s);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&stats[0], n_eval);
-      atomicAdd(&stats[1], n_blend);
-    }
-  }
-}
 
 // Reduce-scatter of 16 per-lane values over the 32 lanes: afterwards lanes 2i and 2i+1 hold
 // the warp total of value i.
@@ -449,7 +95,7 @@ struct BwdSmem {
 // in the three spare slots of the reduce-scatter; at the per-(tile, particle) flush it becomes
 // dL/dbeta = dL/dc Y(dir) and the mean's gradient through the view direction.
 // SMALL: tiles of at most 256 pixels, compiled for three resident blocks per SM (80 registers).
-template <int DEG, bool RS, bool SMALL, bool PP>
+template <int DEG, bool RS, bool SMALL, bool PP, bool GEN>
 __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
     k_composite_bwd(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                        const short4 *__restrict__ rect,
@@ -592,7 +238,7 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
       float vv[3] = {0.f, 0.f, 0.f}, xx[3] = {0.f, 0.f, 0.f}, wc[3] = {0.f, 0.f, 0.f}, dsig = 0.f;
       float3 og, dg;
       float dd, a;
-      if (start + b < my_end && eval_response<RS>(s_geo[b], px, py, o, d, og, dg, dd, a)) {
+      if (start + b < my_end && eval_response<RS, GEN>(s_geo[b], px, py, o, d, og, dg, dd, a, op)) {
         contrib = true;
         float al = fminf(a, op.alpha_max);
         float r0, r1, r2;
@@ -618,7 +264,7 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
         float da = a > op.alpha_max ? 0.f : dal;
         float sigma = s_geo[b][3].x;
         dsig = da * a / sigma;
-        float dw2 = -0.5f * a * da;
+        float dw2 = dresponse<GEN>(op, a, og, dg, dd) * da;
         float tau = -dot3(og, dg) / dd;
         float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
         vv[0] = 2.f * dw2 * pp.x;
@@ -703,72 +349,6 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
   }
 }
 
-// Log-spaced bucket (about 1.5 % wide) of a tile's replay length.
-__device__ __forceinline__ int work_bucket(uint32_t w) {
-  return min((int)(48.f * __log2f(1.f + (float)w)), kOrderBuckets - 1);
-}
-
-// Forward schedule estimate, one warp per tile.  A heuristic that only orders the tiles (no
-// result depends on it): a tile's pixels saturate after roughly a fixed optical depth of
-// particles that cover the whole tile, so the estimate is the list position where
-// sum -ln(1 - 0.3 sigma) over particles whose rect contains the tile's pixels reaches
-// kFwdDepth, or the end of the first kFwdCap entries.  Every tile gets work >= 1 so that
-// every tile, even an empty one, is scheduled (its pixels must still be written).
-constexpr int kFwdCap = 512;
-constexpr float kFwdDepth = 40.f;
-
-__global__ void k_fwd_predict(const __grid_constant__ BatchDesc bd, DevOpts op, const short4 *__restrict__ rect,
-                              const uint32_t *__restrict__ vals, const uint2 *__restrict__ ranges, TileSched ts) {
-  const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (tile >= bd.total_tiles) return;
-  const DevView &view = bd.v[view_of_tile(bd, tile)];
-  const float *logits = bd.s[view.scene].logits;
-  const int lt = tile - view.tile_off;
-  const int x0 = (lt % view.tiles_x) * op.tile_w, y0 = (lt / view.tiles_x) * op.tile_h;
-  const int x1 = min(x0 + op.tile_w, view.cam.W) - 1, y1 = min(y0 + op.tile_h, view.cam.H) - 1;
-  const uint2 rg = ranges[tile];
-  const uint32_t end = min(rg.y, rg.x + (uint32_t)kFwdCap);
-  uint32_t pred = end - rg.x;
-  float tau = 0.f;
-  bool found = false;
-  for (uint32_t base = rg.x; base < end && !found; base += 128) {
-    float c[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {  // four chunks of 32 entries in flight per step
-      const uint32_t k = base + 32 * j + lane;
-      c[j] = 0.f;
-      if (k < end) {
-        const uint32_t idx = vals[k];
-        const short4 r = rect[view.part_off + idx];
-        if (r.x <= x0 && r.y <= y0 && r.z >= x1 && r.w >= y1) {
-          const float sg = 1.f / (1.f + __expf(-logits[idx]));
-          c[j] = -__logf(1.f - fminf(0.3f * sg, 0.99f));
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float incl = c[j];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const unsigned hit = __ballot_sync(0xffffffffu, !found && tau + incl >= kFwdDepth);
-      if (hit) {
-        pred = base + 32 * j + (__ffs(hit) - 1) + 1 - rg.x;
-        found = true;
-      }
-      tau += __shfl_sync(0xffffffffu, incl, 31);
-    }
-  }
-  if (lane == 0) {
-    const uint32_t w = (rg.y > rg.x ? pred : 0u) + 1u;
-    ts.work[tile] = w;
-    atomicAdd(&ts.hist[work_bucket(w)], 1u);
-  }
-}
-
 // One warp per tile: work = list entries the backward replays (up to one past the last
 // particle any of the tile's pixels blended, from n_used), and a histogram of the buckets.
 __global__ void k_tile_work(const __grid_constant__ BatchDesc bd, DevOpts op, const uint2 *__restrict__ ranges,
@@ -791,44 +371,6 @@ __global__ void k_tile_work(const __grid_constant__ BatchDesc bd, DevOpts op, co
     const uint32_t w = m > rg.x ? min(m, rg.y) - rg.x : 0u;
     ts.work[tile] = w;
     if (w) atomicAdd(&ts.hist[work_bucket(w)], 1u);
-  }
-}
-
-// Counting sort of the tiles with work by descending bucket (heaviest first, so the longest
-// replays start in the first wave instead of trailing at the end).  1024 threads per block;
-// every block scans the histogram itself and scatters its share of the tiles.
-__global__ void __launch_bounds__(kOrderBuckets) k_tile_order(int total_tiles, TileSched ts) {
-  __shared__ uint32_t s_off[kOrderBuckets];
-  __shared__ uint32_t s_warp[32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint32_t h = ts.hist[kOrderBuckets - 1 - t];  // rank t in descending bucket order
-  uint32_t incl = h;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t v = s_warp[lane], x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    s_warp[lane] = x - v;
-  }
-  __syncthreads();
-  incl += s_warp[warp];
-  s_off[kOrderBuckets - 1 - t] = incl - h;
-  if (blockIdx.x == 0 && t == kOrderBuckets - 1) *ts.n_work = incl;
-  __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + t; i < total_tiles; i += gridDim.x * blockDim.x) {
-    const uint32_t w = ts.work[i];
-    if (!w) continue;
-    const int b = work_bucket(w);
-    ts.order[s_off[b] + atomicAdd(&ts.cursor[b], 1u)] = (uint32_t)i;
   }
 }
 
@@ -882,94 +424,44 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
   }
 }
 
-template <int DEG, bool RS, bool PP>
-void fwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                  const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
-  const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
-  const short4 *r4 = reinterpret_cast<const short4 *>(rect);
-  const uint2 *rg = reinterpret_cast<const uint2 *>(ranges);
-  if (stats)
-    k_composite_fwd<DEG, RS, true, PP><<<blocks, threads, 0, s>>>(bd, op, r4, vals, rg, stats, ts);
-  else
-    k_composite_fwd<DEG, RS, false, PP><<<blocks, threads, 0, s>>>(bd, op, r4, vals, rg, nullptr, ts);
-}
-
-// Degree 0 colours do not depend on the direction: both colour modes run the per-pixel kernel.
-template <int DEG, bool RS>
-void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
-  if constexpr (DEG > 0) {
-    if (op.colour_mode == UT_COLOUR_PER_PARTICLE) {
-      fwd_launch_k<DEG, RS, true>(bd, op, rect, vals, ranges, stats, ts, s);
-      return;
-    }
-  }
-  fwd_launch_k<DEG, RS, false>(bd, op, rect, vals, ranges, stats, ts, s);
-}
-
-template <int DEG, bool RS, bool SMALL, bool PP>
+template <int DEG, bool RS, bool SMALL, bool PP, bool GEN>
 void bwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                   const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
   const int blocks = bd.total_tiles, threads = op.tile_w * op.tile_h;
   const size_t smem = BwdSmem<DEG, PP>::bytes(threads / 32);
-  cudaFuncSetAttribute(k_composite_bwd<DEG, RS, SMALL, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_composite_bwd<DEG, RS, SMALL, PP><<<blocks, threads, smem, s>>>(
+  cudaFuncSetAttribute(k_composite_bwd<DEG, RS, SMALL, PP, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  k_composite_bwd<DEG, RS, SMALL, PP, GEN><<<blocks, threads, smem, s>>>(
       bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
 }
 
-template <int DEG, bool RS, bool PP>
+template <int DEG, bool RS, bool PP, bool GEN>
 void bwd_launch_pp(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                    const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
-  if (op.tile_w * op.tile_h <= 256) bwd_launch_k<DEG, RS, true, PP>(bd, op, rect, vals, ranges, ts, s);
-  else bwd_launch_k<DEG, RS, false, PP>(bd, op, rect, vals, ranges, ts, s);
+  if (op.tile_w * op.tile_h <= 256) bwd_launch_k<DEG, RS, true, PP, GEN>(bd, op, rect, vals, ranges, ts, s);
+  else bwd_launch_k<DEG, RS, false, PP, GEN>(bd, op, rect, vals, ranges, ts, s);
 }
 
 // Degree 0 colours do not depend on the direction: both colour modes run the per-pixel kernel.
+// The degree-n kernels run with per-pixel colours (make_opts rejects the combination with
+// per-particle colours).
 template <int DEG, bool RS>
 void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, const TileSched &ts, cudaStream_t s) {
+  if (op.kernel_degree != 2) {
+    bwd_launch_pp<DEG, RS, false, true>(bd, op, rect, vals, ranges, ts, s);
+    return;
+  }
   if constexpr (DEG > 0) {
     if (op.colour_mode == UT_COLOUR_PER_PARTICLE) {
-      bwd_launch_pp<DEG, RS, true>(bd, op, rect, vals, ranges, ts, s);
+      bwd_launch_pp<DEG, RS, true, false>(bd, op, rect, vals, ranges, ts, s);
       return;
     }
   }
-  bwd_launch_pp<DEG, RS, false>(bd, op, rect, vals, ranges, ts, s);
-}
-
-bool any_rs(const BatchDesc &bd) {
-  for (int v = 0; v < bd.nv; ++v)
-    if (bd.v[v].cam.rs) return true;
-  return false;
+  bwd_launch_pp<DEG, RS, false, false>(bd, op, rect, vals, ranges, ts, s);
 }
 
 }  // namespace
-
-// Predicts each tile's walk, orders the tiles longest first, then composites them in that order.
-ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
-                               const uint32_t *ranges, unsigned long long *stats, void *sched, cudaStream_t s) {
-  if (bd.total_tiles == 0) return UT_OK;
-  const TileSched ts = carve_tile_sched(sched, bd.total_tiles);
-  if (cudaMemsetAsync(ts.hist, 0, sizeof(uint32_t) * (2 * kOrderBuckets + 1), s) != cudaSuccess) return UT_ERR_CUDA;
-  k_fwd_predict<<<(bd.total_tiles + 7) / 8, 256, 0, s>>>(bd, op, reinterpret_cast<const short4 *>(rect), vals,
-                                                         reinterpret_cast<const uint2 *>(ranges), ts);
-  const int ob = (bd.total_tiles + kOrderBuckets - 1) / kOrderBuckets, cap = device_sm_count();
-  k_tile_order<<<ob < cap ? ob : cap, kOrderBuckets, 0, s>>>(bd.total_tiles, ts);
-  count_launches(2);
-  const bool rs = any_rs(bd);
-#define UT3D_FWD(D)                                                     \
-  (rs ? fwd_launch<D, true>(bd, op, rect, vals, ranges, stats, ts, s) \
-      : fwd_launch<D, false>(bd, op, rect, vals, ranges, stats, ts, s))
-  switch (bd.s[0].deg) {
-    case 0: UT3D_FWD(0); break;
-    case 1: UT3D_FWD(1); break;
-    case 2: UT3D_FWD(2); break;
-    default: UT3D_FWD(3); break;
-  }
-#undef UT3D_FWD
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
-}
 
 size_t backward_workspace_bytes(int n) { return align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1)); }
 

@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__
   float dep = sqrtf(fmaf(xc.x, xc.x, fmaf(xc.y, xc.y, xc.z * xc.z)));
 
   // opacity-tightened extent (Algorithm 1) and pixel rectangle
-  float kx = fminf(op.extent_sigma, sqrtf(2.f * logf(p.sigma / op.alpha_min)));
+  // Mahalanobis distance where sigma rho falls to alpha_min: sqrt(2 ln(sigma / alpha_min)) for the
+  // Gaussian, (ln(sigma / alpha_min) / lambda)^(1/n) for the degree-n kernel exp(-lambda d^n)
+  const float lnr = logf(p.sigma / op.alpha_min);
+  float kx = fminf(op.extent_sigma, op.kernel_degree == 2 ? sqrtf(2.f * lnr)
+                                                          : powf(lnr / op.kernel_lambda, 1.f / op.kernel_degree));
   float hx = kx * sqrtf(cxx), hy = kx * sqrtf(cyy);
   ok = ok && isfinite(vm.x) && isfinite(vm.y) && isfinite(hx) && isfinite(hy);
   float fx0 = fmaxf(ceilf(vm.x - hx - 0.5f), 0.f), fx1 = fminf(floorf(vm.x + hx - 0.5f), (float)(cam.W - 1));

@@ -36,6 +36,8 @@ struct DevOpts {
   int rs_iters, newton_iters;
   int projection;   // UT_PROJECTION_UT / UT_PROJECTION_EWA
   int colour_mode;  // UT_COLOUR_PER_PIXEL / UT_COLOUR_PER_PARTICLE
+  int kernel_degree;   // n of the generalised Gaussian (2 = Gaussian)
+  float kernel_lambda; // 1/2 3^(2-n): rho = exp(-kernel_lambda d^n)
 };
 
 // ---------------------------------------------------------------- batches of views
@@ -163,6 +165,15 @@ __device__ __forceinline__ float theta_d_prime(const DevCam &c, float th) {
   return fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 9.f * c.k4, 7.f * c.k3), 5.f * c.k2), 3.f * c.k1), 1.f);
 }
 
+// Radial pinhole: r_d(r) = r (1 + k1 r^2 + k2 r^4 + k3 r^6) and its derivative.
+__device__ __forceinline__ float radial_scale(const DevCam &c, float r2) {
+  return fmaf(r2, fmaf(r2, fmaf(r2, c.k3, c.k2), c.k1), 1.f);
+}
+
+__device__ __forceinline__ float radial_prime(const DevCam &c, float r2) {
+  return fmaf(r2, fmaf(r2, fmaf(r2, 7.f * c.k3, 5.f * c.k2), 3.f * c.k1), 1.f);
+}
+
 // g(x_c): camera-space point to pixel coordinates; returns false when not imaged.
 __device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &uv) {
   if (c.model == UT_CAM_PINHOLE) {
@@ -170,6 +181,16 @@ __device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &u
     uv.x = fmaf(c.fx * p.x, iz, c.cx);
     uv.y = fmaf(c.fy * p.y, iz, c.cy);
     return p.z > c.near_plane;
+  }
+  if (c.model == UT_CAM_PINHOLE_RADIAL) {
+    // theta_max holds the largest imaged normalised radius r_max
+    float iz = 1.f / p.z;
+    float xn = p.x * iz, yn = p.y * iz;
+    float r2 = fmaf(xn, xn, yn * yn);
+    float sd = radial_scale(c, r2);
+    uv.x = fmaf(c.fx * xn, sd, c.cx);
+    uv.y = fmaf(c.fy * yn, sd, c.cy);
+    return p.z > c.near_plane && sqrtf(r2) <= c.theta_max;
   }
   float r2 = fmaf(p.x, p.x, p.y * p.y);
   float rho = sqrtf(r2);
@@ -186,7 +207,7 @@ __device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &u
 // d s = (theta_d'(theta) d theta - s d rho) / rho, d theta = (X Z, Y Z, -rho^2) / (rho r^2),
 // d rho = (X, Y, 0) / rho; on the optical axis the map is the pinhole one.
 __device__ __forceinline__ void cam_jacobian(const DevCam &c, float3 p, float3 &ju, float3 &jv) {
-  if (c.model == UT_CAM_PINHOLE) {
+  if (c.model == UT_CAM_PINHOLE || c.model == UT_CAM_PINHOLE_RADIAL) {  // radial: 3DGS's undistorted one
     const float iz = 1.f / p.z;
     ju = make_float3(c.fx * iz, 0.f, -c.fx * p.x * iz * iz);
     jv = make_float3(0.f, c.fy * iz, -c.fy * p.y * iz * iz);
@@ -235,6 +256,23 @@ __device__ __forceinline__ bool pixel_ray(const DevCam &c, int px, int py, int n
   float3 dc;
   if (c.model == UT_CAM_PINHOLE) {
     dc = make_float3(mx, my, 1.f);
+  } else if (c.model == UT_CAM_PINHOLE_RADIAL) {
+    float rd = sqrtf(fmaf(mx, mx, my * my));
+    if (!(rd <= c.rd_max)) return false;
+    // safeguarded Newton for r_d(r) = rd on the increasing branch [0, r_max]
+    float lo = 0.f, hi = fminf(c.theta_max, fmaxf(2.f * rd, 1.f));
+    for (int it = 0; it < 40 && isinf(c.theta_max) && rd > hi * radial_scale(c, hi * hi); ++it) hi *= 2.f;
+    float r = fminf(rd, hi);
+    for (int it = 0; it < newton_iters; ++it) {
+      float f = fmaf(r, radial_scale(c, r * r), -rd);
+      if (f == 0.f) break;
+      if (f > 0.f) hi = r; else lo = r;
+      float nr = r - f / radial_prime(c, r * r);
+      if (!(nr >= lo && nr <= hi)) nr = 0.5f * (lo + hi);  // Newton left the bracket: bisect
+      if (nr == r) break;
+      r = nr;
+    }
+    dc = rd > 0.f ? make_float3(mx * (r / rd), my * (r / rd), 1.f) : make_float3(0.f, 0.f, 1.f);
   } else {
     float rd = sqrtf(fmaf(mx, mx, my * my));
     if (!(rd <= c.rd_max)) return false;

@@ -145,3 +145,53 @@ def test_per_particle_colour_backward_matches_oracle(name):
     op0 = dict(op, colour_mode=0)
     ref0 = oracle.backward(sc, cam, op0, oracle.project(sc, cam, op0, TOL), (ref_f["px"], ref_f["py"]), w_rgb, w_a)
     assert np.linalg.norm(ref0["sh"] - ref["sh"]) > 1e-3 * np.linalg.norm(ref["sh"])
+
+
+# ------------------------------------------------------------------ radial pinhole, degree-n kernels
+
+def _radial(rs=0):
+    qe, te = synth.rs_end_pose(0.05, 2.0)
+    return dict(scene=synth.scene_cube(6000, 19, deg=3, log_s=(-3.2, 0.4)),
+                camera=synth.camera("pinhole_radial", 320, 240, fx=200.0, fy=200.0, k=[-0.12, 0.03, -0.002, 0.0],
+                                    q_end=qe, t_end=te, rolling_shutter=rs),
+                options=synth.options())
+
+
+@pytest.mark.parametrize("rs,mode", [(0, {}), (1, {}), (0, dict(projection=1)), (0, dict(kernel_degree=4)),
+                                     (1, dict(kernel_degree=3))])
+def test_radial_and_kernel_degree_render_matches_oracle(rs, mode):
+    case = _radial(rs)
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], **mode)
+    g = run_gpu(sc, cam, op)
+    ref_p = oracle.project(sc, cam, op, TOL)
+    assert (to_np(g["proj"].ntiles) > 0).sum() > 0.5 * len(ref_p["ntiles"])
+    ref = oracle.render(sc, cam, op, proj=ref_p, tol=TOL)
+    r = compare_frame(g["frame"], ref)
+    print("radial rs", rs, mode, r)
+    assert r["n_bad"] == 0, r
+    assert r["n_flagged"] <= 0.05 * r["n"], r
+
+
+@pytest.mark.parametrize("kdeg,cam_model", [(4, "pinhole"), (3, "pinhole_radial"), (8, "pinhole")])
+def test_kernel_degree_backward_matches_oracle(kdeg, cam_model):
+    sc = synth.scene_cube(1500, 23, deg=1, log_s=(-2.8, 0.4))
+    cam = synth.camera(cam_model, 96, 80, fx=90.0, fy=90.0,
+                       k=[-0.1, 0.02, 0.0, 0.0] if cam_model == "pinhole_radial" else [0, 0, 0, 0])
+    op = synth.options(kernel_degree=kdeg)
+    W, H = cam["width"], cam["height"]
+    proj_ref = oracle.project(sc, cam, op, TOL)
+    ref_f = oracle.render(sc, cam, op, proj=proj_ref, tol=TOL)
+    flagged = (ref_f["flags"] & (oracle.F_FORWARD_TIES | oracle.F_ALPHA_MAX)) != 0
+    rng = np.random.default_rng(77)
+    w_rgb = rng.standard_normal((H * W, 3)) * ~flagged[:, None]
+    w_a = rng.standard_normal(H * W) * ~flagged
+    ref = oracle.backward(sc, cam, op, proj_ref, (ref_f["px"], ref_f["py"]), w_rgb, w_a)
+    g = run_gpu(sc, cam, op)
+    d_rgb = torch.as_tensor(w_rgb.T.reshape(3, H, W).astype(np.float32)).cuda()
+    d_a = torch.as_tensor(w_a.reshape(H, W).astype(np.float32)).cuda()
+    grads = render.composite_backward(g["scene"], cam, op, g["proj"], g["binning"], g["frame"], d_rgb, d_a)
+    torch.cuda.synchronize()
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        e = _grad_compare(to_np(grads[k]), ref[k], k)
+        print(kdeg, cam_model, k, f"rel err {e:.2e}")
