@@ -158,6 +158,15 @@ ut_status ut_project(const ut_scene *scene, const ut_camera *cam, const ut_param
                      float *mean2d, float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles,
                      ut_stream stream);
 
+/* The camera map g of a batch of world points (no counterpart in the paper's pipeline; the
+ * reference projection of Monte Carlo samples in the UT / EWA accuracy study, and a utility):
+ * uv[i] = g(points[i]) with the model and the rolling-shutter time fixed point of ut_project
+ * (rs_iters from opt); valid[i] = 1 when every projection taken was valid (imaged), else 0 and
+ * uv[i] holds what the last projection gave.  points[n][3], uv[n][2] (float), valid[n] (int32),
+ * all device.  Errors: UT_ERR_INVALID_ARG for a bad camera / options or NULL buffers with n > 0. */
+ut_status ut_project_points(const float *points, int32_t n, const ut_camera *cam, const ut_options *opt, float *uv,
+                            int32_t *valid, ut_stream stream);
+
 /* Bytes of scratch memory bin_and_sort needs for n particles and a key capacity. */
 size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt);
 

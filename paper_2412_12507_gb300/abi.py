@@ -82,6 +82,7 @@ SIGNATURES = {
                                C.c_int64, _P, _P, _P, _P, _P]),
     "bin_and_sort_static": (C.c_int, [C.c_int32, _P, _P, _P, C.POINTER(UtCamera), C.POINTER(UtOptions), C.c_int64,
                                       _P, _P, _P, _P, _P]),
+    "ut_project_points": (C.c_int, [_P, C.c_int32, C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P]),
     "ut_forward_workspace_size": (C.c_size_t, [C.POINTER(UtCamera), C.POINTER(UtOptions)]),
     "composite_forward": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtOptions), _P, _P, _P, _P,
                                     _P, _P, _P, _P, C.c_size_t, _P, _P]),

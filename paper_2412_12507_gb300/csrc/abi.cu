@@ -403,6 +403,17 @@ ut_status ut_project(const ut_scene *scene, const ut_camera *cam, const ut_param
   return launch_project(bd, dop, w, mean2d, cov2d, depth, rect, ntiles, reinterpret_cast<cudaStream_t>(stream));
 }
 
+ut_status ut_project_points(const float *points, int32_t n, const ut_camera *cam, const ut_options *opt, float *uv,
+                            int32_t *valid, ut_stream stream) {
+  DevCam dc;
+  ut_status st = make_cam(cam, dc);
+  if (st != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (n < 0 || (n > 0 && (!points || !uv || !valid || !aligned8(uv)))) return UT_ERR_INVALID_ARG;
+  return launch_project_points(dc, dop, points, n, uv, valid, reinterpret_cast<cudaStream_t>(stream));
+}
+
 size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt) {
   if (n < 0 || key_capacity < 0 || !cam || !opt || opt->tile_w < 1 || opt->tile_h < 1) return 0;
   int tiles = ((cam->width + opt->tile_w - 1) / opt->tile_w) * ((cam->height + opt->tile_h - 1) / opt->tile_h);

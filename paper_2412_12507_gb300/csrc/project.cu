@@ -160,7 +160,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__
   }
 }
 
+__global__ void k_project_points(DevCam cam, DevOpts op, const float *__restrict__ pts, int n,
+                                 float2 *__restrict__ uv, int32_t *__restrict__ valid) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float3 x = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+    float2 v;
+    float t;
+    const bool ok = project_world(cam, op.rs_iters, mat3_mul(cam.R0, x), v, t);
+    uv[i] = v;
+    valid[i] = ok ? 1 : 0;
+  }
+}
+
 }  // namespace
+
+ut_status launch_project_points(const DevCam &cam, const DevOpts &op, const float *points, int n, float *uv,
+                                int32_t *valid, cudaStream_t stream) {
+  if (n == 0) return UT_OK;
+  const int cap = device_sm_count() * 8, g = (n + 255) / 256;
+  k_project_points<<<g < cap ? g : cap, 256, 0, stream>>>(cam, op, points, n, reinterpret_cast<float2 *>(uv),
+                                                          valid);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+}
 
 ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights &w, float *mean2d, float *cov2d,
                          float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream) {

@@ -10,6 +10,7 @@
 namespace ut3d {
 
 struct DevOpts;
+struct DevCam;
 struct BatchDesc;
 
 // Unscented-Transform spread and weights (eq. weights_1/2), computed on the host in FP64.
@@ -30,6 +31,9 @@ void count_launches(int k);
 int device_sm_count();
 
 // Projection of every flattened (view, particle) entry of the batch.
+// g of n world points (one view's camera), with the rolling-shutter fixed point.
+ut_status launch_project_points(const DevCam &cam, const DevOpts &op, const float *points, int n, float *uv,
+                                int32_t *valid, cudaStream_t stream);
 ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights &w, float *mean2d, float *cov2d,
                          float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream);
 

@@ -105,6 +105,18 @@ class Workspace:
         return self.buf[off:off + nbytes]
 
 
+def project_points(points: torch.Tensor, cam: dict, opts: dict | None = None):
+    """ut_project_points: g of world points [n, 3] (float32, device) -> (uv [n, 2], valid [n] bool)."""
+    pts = points.contiguous().float()
+    n = pts.shape[0]
+    uv = torch.empty((n, 2), dtype=torch.float32, device=pts.device)
+    valid = torch.empty(n, dtype=torch.int32, device=pts.device)
+    c, o = abi.make_camera(cam), abi.make_options(opts)
+    abi.check("ut_project_points", abi.lib().ut_project_points(_ptr(pts), n, C.byref(c), C.byref(o), _ptr(uv),
+                                                                _ptr(valid), _stream()))
+    return uv, valid.bool()
+
+
 def bin_and_sort(proj: Projection, cam: dict, opts: dict | None, capacity: int, want_keys: bool = False,
                  ws: Workspace | None = None, out: Binning | None = None) -> Binning:
     """bin_and_sort: duplicate (tile | depth) keys, stable sort, per-tile ranges (Sec. 4.3).
