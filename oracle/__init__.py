@@ -57,7 +57,7 @@ class Options(C.Structure):
                 ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("rs_iters", C.c_int32),
                 ("ut_alpha", C.c_double), ("ut_beta", C.c_double), ("ut_kappa", C.c_double),
                 ("extent_sigma", C.c_double), ("projection", C.c_int32), ("colour_mode", C.c_int32),
-                ("kernel_degree", C.c_int32)]
+                ("kernel_degree", C.c_int32), ("kbuffer", C.c_int32), ("eps_tau", C.c_double)]
 
 
 class Tol(C.Structure):
@@ -152,6 +152,8 @@ def make_options(opts: dict | None = None) -> Options:
     r.projection = int(o.get("projection", 0))    # 0 UT, 1 EWA
     r.colour_mode = int(o.get("colour_mode", 0))  # 0 per pixel, 1 per particle
     r.kernel_degree = int(o.get("kernel_degree", 2))  # generalised Gaussian degree n
+    r.kbuffer = int(o.get("kbuffer", 0))              # 0: tile order; k > 0: per-ray k-buffer
+    r.eps_tau = float(o.get("eps_tau", 1e-5))          # k-buffer near-tie tolerance (flags only)
     return r
 
 

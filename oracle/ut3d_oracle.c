@@ -74,6 +74,8 @@ typedef struct {
   int32_t colour_mode; /* 0: SH at each pixel's ray direction; 1: SH once per particle at the
                           direction from the camera centre (at the mean's shutter time) to the mean */
   int32_t kernel_degree; /* n of the generalised Gaussian (supplementary Sec. A); 2 = Gaussian */
+  int32_t kbuffer;       /* 0: blend in tile (global depth) order; k > 0: per-ray k-buffer (Sec. 4.4, MLAB) */
+  double eps_tau;        /* k-buffer near-tie tolerance on tau (relative), for flags only */
 } orc_options;
 
 /* near-tie tolerances used only to flag pixels whose FP32 result may legitimately differ */
@@ -923,6 +925,91 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
   return nb;
 }
 
+/* "Ours (sorted)" (Sec. 4.4): the per-ray k-buffer of the multi-layer alpha blending
+ * approximation.  Hits (particles with sigma rho >= alpha_min, met in the global depth order)
+ * enter a buffer of at most k entries; when a hit arrives at a full buffer, the closest of the
+ * buffered hits and the new one -- smallest tau_max, earlier arrival on equal tau -- is blended
+ * (front to back, with the same stop rule) and leaves; the new hit takes its place unless it
+ * was itself the closest.  At the end of the list the remaining entries are blended in
+ * ascending tau.  Returns the number of blended particles.  A selection whose runner-up tau is
+ * within eps_tau (relative) of the chosen one may go the other way in FP32: ORC_F_DEPTH_TIE. */
+typedef struct { double tau, alpha, col[3]; int seq; } orc_kb_entry;
+
+static int orc_kb_pick(const orc_kb_entry *e, int n, double eps, int *tie) {
+  int best = 0;
+  for (int j = 1; j < n; ++j)
+    if (e[j].tau < e[best].tau || (e[j].tau == e[best].tau && e[j].seq < e[best].seq)) best = j;
+  for (int j = 0; j < n; ++j)
+    if (j != best && fabs(e[j].tau - e[best].tau) <= eps * fabs(e[best].tau)) *tie = 1;
+  return best;
+}
+
+static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, const orc_options *op,
+                                     const orc_tol *tol, int px, int py, const double o[3], const double d[3],
+                                     const double *Y, double rgb[3], double *Tout, int32_t *flags,
+                                     int *stopped_out) {
+  orc_kb_entry buf[65];
+  int k = op->kbuffer < 64 ? op->kbuffer : 64, nbuf = 0, nb = 0, seq = 0, stopped = 0, tie = 0;
+  double T = 1.0;
+  rgb[0] = rgb[1] = rgb[2] = 0.0;
+  for (int j = 0; j < x->norder && !stopped; ++j) {
+    int i = x->order[j];
+    const orc_particle *p = &x->P[i];
+    const int32_t *r = x->rect + 4 * i;
+    const int inside = px >= r[0] && px <= r[2] && py >= r[1] && py <= r[3];
+    double og[3], dg[3], tau;
+    double w2 = orc_omega2(p, o, d, og, dg, &tau);
+    double a = p->sigma * orc_response(op, w2);
+    if (flags && x->edges) {  /* membership may flip where a rect edge is within eps_px of the pixel */
+      const double *e = x->edges + 4 * i;
+      double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
+      int nx = px >= e[0] - tol->eps_px && px <= e[1] + tol->eps_px;
+      int ny = py >= e[2] - tol->eps_px && py <= e[3] + tol->eps_px;
+      if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel))
+        *flags |= ORC_F_RECT_EDGE;
+    }
+    if (!inside) continue;
+    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) *flags |= ORC_F_ALPHA_MIN;
+    if (a < op->alpha_min) continue;
+    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
+    orc_kb_entry h;
+    h.tau = tau;
+    h.alpha = a < op->alpha_max ? a : op->alpha_max;
+    h.seq = seq++;
+    const float *beta = sc->sh + (size_t)i * x->nsh * 3;
+    const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
+    for (int ch = 0; ch < 3; ++ch) {
+      double s = 0.5;
+      for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Yc[kk];
+      h.col[ch] = s > 0.0 ? s : 0.0;
+    }
+    if (nbuf < k) { buf[nbuf++] = h; continue; }
+    buf[nbuf] = h;  /* the closest of the k buffered hits and the new one is blended */
+    int b = orc_kb_pick(buf, nbuf + 1, op->eps_tau, &tie);
+    double Tn = T * (1.0 - buf[b].alpha);
+    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
+    if (Tn < op->t_min) { stopped = 1; break; }
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
+    T = Tn;
+    ++nb;
+    buf[b] = buf[nbuf];
+  }
+  while (!stopped && nbuf > 0) {  /* end of the list: the rest in ascending tau */
+    int b = orc_kb_pick(buf, nbuf, op->eps_tau, &tie);
+    double Tn = T * (1.0 - buf[b].alpha);
+    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
+    if (Tn < op->t_min) { stopped = 1; break; }
+    for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
+    T = Tn;
+    ++nb;
+    buf[b] = buf[--nbuf];
+  }
+  if (flags && tie) *flags |= ORC_F_DEPTH_TIE;
+  *Tout = T;
+  if (stopped_out) *stopped_out = stopped;
+  return nb;
+}
+
 static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int px, int py, const orc_tol *tol,
                             double o[3], double d[3], double *Y, int *valid, int32_t *flags) {
   double em, dp;
@@ -971,8 +1058,11 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     double T;
     slack[q] = 0.0;
     aslack[q] = 0.0;
-    nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect,
-                                  &slack[q], &aslack[q]);
+    if (op->kbuffer > 0)
+      nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL);
+    else
+      nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect,
+                                    &slack[q], &aslack[q]);
     alpha[q] = 1.0 - T;
     tfinal[q] = T;
     flags[q] = fl;

@@ -136,7 +136,7 @@ def camera(model, width, height, fx=None, fy=None, cx=None, cy=None, k=(0, 0, 0,
 def options(**kw):
     o = dict(tile_w=16, tile_h=16, t_min=1e-4, alpha_min=1.0 / 255.0, alpha_max=0.99, rs_iters=3,
              newton_iters=12, ut_alpha=1.0, ut_beta=2.0, ut_kappa=0.0, extent_sigma=3.0,
-             projection=0, colour_mode=0, kernel_degree=2)
+             projection=0, colour_mode=0, kernel_degree=2, kbuffer=0)
     o.update(kw)
     # FP32 values: both sides see identical thresholds
     for k in ("t_min", "alpha_min", "alpha_max", "ut_alpha", "ut_beta", "ut_kappa", "extent_sigma"):

@@ -656,6 +656,83 @@ def test_rect_culling_lossless_for_generalised_kernels(orc, n):
     assert np.max(np.abs(a["rgb"] - b["rgb"])) < 1e-12
 
 
+# ------------------------------------------------------------------ "Ours (sorted)": per-ray k-buffer
+
+def _two_crossing():
+    """Two isotropic Gaussians where the mean nearer the camera is reached later along one pixel's
+    ray: A sits on the ray at tau = 3.0 (0.05 off it), B at tau = 2.6 but 1.6 off the ray, so
+    |mu_B| > |mu_A| while B's maximum along the ray comes first."""
+    # pinhole 32x32, f = 30: pixel (20, 16) has ray d = (4.5/30, 0.5/30, 1) from the origin
+    d = np.array([4.5 / 30, 0.5 / 30, 1.0])
+    u = np.cross(d, [1.0, 0.0, 0.0])
+    u /= np.linalg.norm(u)
+    mu_a = 3.0 * d + 0.05 * u
+    mu_b = 2.6 * d - 1.6 * u
+    sc = dict(means=np.array([mu_a, mu_b], np.float32),
+              log_scales=np.array([[-0.5, -0.5, -0.5], [0.2, 0.2, 0.2]], np.float32),
+              quats=np.array([[1, 0, 0, 0], [1, 0, 0, 0]], np.float32),
+              opacity_logits=np.array([0.4, 1.5], np.float32),
+              sh=np.array([[[0.8, -0.3, 0.1]], [[-0.4, 0.6, 0.2]]], np.float32), sh_degree=0)
+    return sc
+
+
+def test_kbuffer_composites_in_tau_order():
+    """k >= the number of hits: the k-buffer blends in ascending tau_max, which here is the
+    reverse of the global depth order; the result equals the two-particle quadrature
+    c_1 a_1 + c_2 a_2 (1 - a_1) in tau order, with each a_i taken from a render of particle i
+    alone (an independent route to alpha)."""
+    import oracle as orc
+    sc = _two_crossing()
+    cam = synth.camera("pinhole", 32, 32, fx=30.0, fy=30.0)
+    proj = dict(rect=np.array([[0, 0, 31, 31]] * 2, np.int32),
+                depth32=np.linalg.norm(sc["means"].astype(np.float64), axis=1).astype(np.float32))
+    assert proj["depth32"][0] < proj["depth32"][1]  # A first in depth order
+    px, py = 20, 16
+    op = synth.options(t_min=0.0, kbuffer=16)
+    single = []
+    for i in (0, 1):
+        s1 = {k: (v[i:i + 1] if k != "sh_degree" else v) for k, v in sc.items()}
+        p1 = dict(rect=proj["rect"][i:i + 1], depth32=proj["depth32"][i:i + 1])
+        o = orc.render(s1, cam, synth.options(t_min=0.0), proj=p1, pixels=([px], [py]))
+        single.append((o["alpha"][0], o["rgb"][0] / o["alpha"][0]))
+    (a_a, c_a), (a_b, c_b) = single
+    assert a_a > 0.05 and a_b > 0.05
+    tau_first_is_b = c_b * a_b + c_a * a_a * (1 - a_b)
+    depth_first_is_a = c_a * a_a + c_b * a_b * (1 - a_a)
+    assert np.abs(tau_first_is_b - depth_first_is_a).max() > 1e-3  # the orders differ visibly
+    kb = orc.render(sc, cam, op, proj=proj, pixels=([px], [py]))
+    tile = orc.render(sc, cam, synth.options(t_min=0.0), proj=proj, pixels=([px], [py]))
+    assert np.allclose(kb["rgb"][0], tau_first_is_b, atol=1e-12)
+    assert np.allclose(tile["rgb"][0], depth_first_is_a, atol=1e-12)
+    # k = 1: the two hits compete in the buffer and the closer in tau is blended first as well
+    kb1 = orc.render(sc, cam, synth.options(t_min=0.0, kbuffer=1), proj=proj, pixels=([px], [py]))
+    assert np.allclose(kb1["rgb"][0], tau_first_is_b, atol=1e-12)
+
+
+def test_kbuffer_equals_tile_order_when_depth_and_tau_orders_agree():
+    """Small, well separated particles along the rays: tau_max order = depth order, so the
+    k-buffer image is the tile-order image (any k)."""
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    sc = dict(sc, log_scales=np.full_like(sc["log_scales"], -5.0))
+    import oracle as orc
+    proj = orc.project(sc, cam, op)
+    a = orc.render(sc, cam, op, proj=proj)
+    for k in (1, 4, 16):
+        b = orc.render(sc, cam, dict(op, kbuffer=k), proj=proj)
+        ok = (b["flags"] & orc.F_DEPTH_TIE) == 0
+        assert np.max(np.abs(a["rgb"][ok] - b["rgb"][ok])) < 1e-12, k
+
+
+def test_kbuffer_transmittance_and_alpha_bounds():
+    import oracle as orc
+    case = synth.fisheye_shell(n=3000, width=96, height=64)
+    sc, cam, op = case["scene"], case["camera"], dict(case["options"], kbuffer=16)
+    o = orc.render(sc, cam, op, proj=orc.project(sc, cam, op))
+    assert np.all(o["alpha"] >= 0) and np.all(o["alpha"] <= 1) and np.all(o["tfinal"] >= 0)
+    assert np.all(o["rgb"] >= 0)
+
+
 # ------------------------------------------------------------------ per-particle colour (colour_mode 1)
 
 def test_per_particle_colour_equals_per_pixel_for_degree_zero(orc):
