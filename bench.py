@@ -368,8 +368,8 @@ def run_multiview(dev, steps, warmup, timed):
 def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
     """A/B lines on the bench workload: the UT projection against the first-order EWA one
     (the paper's "Preprocess" comparison with 3DGS; per call, and the whole forward with each),
-    and the per-particle SH colour mode (forward and forward + backward) against the
-    per-pixel one."""
+    the per-ray k-buffer of "Ours (sorted)" (the paper's "Render" comparison), and the
+    per-particle SH colour mode (forward and forward + backward) against the per-pixel one."""
     import torch
     from paper_2412_12507_gb300 import render
     P = cam["width"] * cam["height"]
@@ -401,6 +401,19 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
         out[name] = {"project_ms": proj_ms, "fwd_ms": fwd_ms, "keys": K, "fwd_mpix_s": P / (fwd_ms / 1e3) / 1e6}
         del r
     out["ewa_over_ut_project"] = out["ewa"]["project_ms"] / out["ut"]["project_ms"]
+    # "Ours (sorted)": the per-ray k-buffer (k = 16), forward only
+    o = dict(op, kbuffer=16)
+    r = render.Renderer(cam, o, capacity=1 << 20)
+    r.forward(scene)
+    torch.cuda.synchronize()
+    k_ms = timed(lambda: r.forward(scene, sync_check=False), steps, warmup)
+    calls = {}
+    for k, fn in (("composite_forward", lambda: render.composite_forward(scene, cam, o, r.proj, r.binning, r.frame,
+                                                                         ws=r.fws)),):
+        calls[k] = per_call(fn)
+    out["kbuffer16"] = {"fwd_ms": k_ms, "composite_forward_ms": calls["composite_forward"],
+                        "fwd_mpix_s": P / (k_ms / 1e3) / 1e6}
+    del r
     o = dict(op, colour_mode=1)
     r = render.Renderer(cam, o, capacity=1 << 20)
     r.forward(scene)

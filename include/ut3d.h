@@ -115,7 +115,13 @@ typedef struct {
 /*   kernel_degree: n = 2 (default) is the Gaussian (eq. gaussian_kernel); n in 3..8 the
  *   generalised Gaussian of supplementary Sec. A, rho = exp(-1/2 3^(2-n) d^n) of the Mahalanobis
  *   distance d (the same response as the Gaussian at d = 3), evaluated at the same tau_max;
- *   combined with UT_COLOUR_PER_PARTICLE it is rejected with UT_ERR_UNSUPPORTED. */
+ *   combined with UT_COLOUR_PER_PARTICLE it is rejected with UT_ERR_UNSUPPORTED.
+ *   kbuffer: 0 (default) blends in the tile's depth order; k in 1..16 selects "Ours (sorted)"
+ *   (Sec. 4.4), a per-ray k-buffer: hits enter a buffer of k entries, a full buffer blends the
+ *   closest (by tau_max) of its hits and the arriving one, and the rest are blended in tau_max
+ *   order at the end of the list (the paper uses k = 16).  Forward only (composite_backward and
+ *   render_batch_backward return UT_ERR_UNSUPPORTED, composite_forward too when asked for
+ *   statistics); combined with per-particle colours or kernel_degree != 2 it is unsupported. */
 #define UT_PROJECTION_UT 0
 #define UT_PROJECTION_EWA 1
 #define UT_COLOUR_PER_PIXEL 0
@@ -128,6 +134,7 @@ typedef struct {
   int32_t projection;
   int32_t colour_mode;
   int32_t kernel_degree;
+  int32_t kbuffer;
 } ut_options;
 
 void ut_default_options(ut_options *opt);

@@ -42,7 +42,7 @@ class UtOptions(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("t_min", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("rs_iters", C.c_int32), ("newton_iters", C.c_int32),
                 ("extent_sigma", C.c_float), ("projection", C.c_int32), ("colour_mode", C.c_int32),
-                ("kernel_degree", C.c_int32)]
+                ("kernel_degree", C.c_int32), ("kbuffer", C.c_int32)]
 
 
 class UtView(C.Structure):
@@ -157,7 +157,8 @@ def make_camera(cam: dict) -> UtCamera:
 def make_options(opts: dict | None = None) -> UtOptions:
     o = default_options()
     for k, v in (opts or {}).items():
-        if k in ("tile_w", "tile_h", "rs_iters", "newton_iters", "projection", "colour_mode", "kernel_degree"):
+        if k in ("tile_w", "tile_h", "rs_iters", "newton_iters", "projection", "colour_mode", "kernel_degree",
+                 "kbuffer"):
             setattr(o, k, int(v))
         elif k in ("t_min", "alpha_min", "alpha_max", "extent_sigma"):
             setattr(o, k, float(v))

@@ -187,7 +187,9 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
       (o->colour_mode != UT_COLOUR_PER_PIXEL && o->colour_mode != UT_COLOUR_PER_PARTICLE) ||
       o->kernel_degree < 2 || o->kernel_degree > 8)
     return UT_ERR_INVALID_ARG;
+  if (o->kbuffer < 0 || o->kbuffer > 16) return UT_ERR_INVALID_ARG;
   if (o->kernel_degree != 2 && o->colour_mode == UT_COLOUR_PER_PARTICLE) return UT_ERR_UNSUPPORTED;
+  if (o->kbuffer > 0 && (o->kernel_degree != 2 || o->colour_mode == UT_COLOUR_PER_PARTICLE)) return UT_ERR_UNSUPPORTED;
   d.tile_w = o->tile_w;
   d.tile_h = o->tile_h;
   d.tiles_x = (c->width + o->tile_w - 1) / o->tile_w;
@@ -202,6 +204,7 @@ ut_status make_opts(const ut_options *o, const ut_camera *c, DevOpts &d) {
   d.colour_mode = o->colour_mode;
   d.kernel_degree = o->kernel_degree;
   d.kernel_lambda = (float)(0.5 * std::pow(3.0, 2.0 - o->kernel_degree));
+  d.kbuffer = o->kbuffer;
   return UT_OK;
 }
 
@@ -369,6 +372,7 @@ void ut_default_options(ut_options *o) {
   o->projection = UT_PROJECTION_UT;
   o->colour_mode = UT_COLOUR_PER_PIXEL;
   o->kernel_degree = 2;
+  o->kbuffer = 0;
 }
 
 uint64_t ut_kernel_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }

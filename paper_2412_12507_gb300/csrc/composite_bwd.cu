@@ -475,6 +475,7 @@ size_t tile_sched_bytes(int tiles) {
 // backward over every tile with work, then finalize.
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                                const uint32_t *ranges, void *sched, cudaStream_t s) {
+  if (op.kbuffer > 0) return UT_ERR_UNSUPPORTED;  // the k-buffer variant is forward only
   int total = 0;
   for (int k = 0; k < bd.ns; ++k) {
     const DevScene &sc = bd.s[k];

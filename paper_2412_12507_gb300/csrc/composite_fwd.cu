@@ -110,6 +110,126 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   }
 }
 
+// "Ours (sorted)" (Sec. 4.4): compositing through a per-ray k-buffer (multi-layer alpha
+// blending).  Hits (sigma rho >= alpha_min) met in the tile's depth order enter a buffer of at
+// most k = op.kbuffer entries kept in shared memory (tau_max, alpha, rgb per entry); when a hit
+// meets a full buffer, the closest of the buffered hits and the new one by tau_max is blended
+// front to back (stop rule as in k_composite_fwd) and the new hit takes its slot unless it was
+// itself the closest; at the end of the list the rest are blended in ascending tau_max.
+// n_used is written as 0 (the backward does not replay this variant).
+template <int DEG, bool RS>
+__global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
+                                                               const short4 *__restrict__ rect,
+                                                               const uint32_t *__restrict__ vals,
+                                                               const uint2 *__restrict__ ranges, TileSched ts) {
+  constexpr int NSH = (DEG + 1) * (DEG + 1);
+  constexpr int NC = NSH * 3;
+  __shared__ float4 s_geo[kBatchF][4];
+  __shared__ __align__(16) float s_sh[kBatchF * NC];
+  __shared__ uint32_t s_idx[kBatchF];
+  extern __shared__ float s_kb[];  // [5][k][threads]: tau, alpha, r, g, b of each buffered hit
+
+  if (blockIdx.x >= *ts.n_work) return;
+  const int tile = (int)ts.order[blockIdx.x];
+  const DevView &view = bd.v[view_of_tile(bd, tile)];
+  const DevScene &sc = bd.s[view.scene];
+  const DevCam &cam = view.cam;
+  const int lt = tile - view.tile_off;
+  const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
+  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
+  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  const bool inside = px < cam.W && py < cam.H;
+  const int K = op.kbuffer, nt = blockDim.x;
+  float *kb_tau = s_kb + threadIdx.x, *kb_a = kb_tau + K * nt, *kb_r = kb_a + K * nt, *kb_g = kb_r + K * nt,
+        *kb_b = kb_g + K * nt;  // entry j of this thread at [j * nt]
+  float3 o, d;
+  float Y[NSH];
+  bool valid;
+  pixel_setup<DEG>(cam, op, px, py, inside, o, d, Y, valid);
+
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int nbuf = 0;
+  bool done = !valid;
+  auto blend = [&](float al, float r, float g, float b) {
+    const float Tn = T * (1.f - al);
+    if (Tn < op.t_min) {
+      done = true;
+      return;
+    }
+    const float w = al * T;
+    C0 = fmaf(r, w, C0);
+    C1 = fmaf(g, w, C1);
+    C2 = fmaf(b, w, C2);
+    T = Tn;
+  };
+  const uint2 rg = ranges[tile];
+  for (uint32_t start = rg.x; start < rg.y; start += kBatchF) {
+    if (__syncthreads_count(!done) == 0) break;
+    const int nb = min((uint32_t)kBatchF, rg.y - start);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      uint32_t idx = s_idx[t];
+      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], nullptr);
+    }
+    stage_sh<NC>(sc, s_idx, nb, s_sh);
+    __syncthreads();
+    if (done) continue;
+    for (int b = 0; b < nb && !done; ++b) {
+      float3 og, dg;
+      float dd, a;
+      if (!eval_response<RS, false>(s_geo[b], px, py, o, d, og, dg, dd, a, op)) continue;
+      const float tau = -__fdividef(dot3(og, dg), dd);
+      const float al = fminf(a, op.alpha_max);
+      float r0, r1, r2;
+      sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+      r0 = fmaxf(r0, 0.f); r1 = fmaxf(r1, 0.f); r2 = fmaxf(r2, 0.f);
+      if (nbuf < K) {
+        kb_tau[nbuf * nt] = tau; kb_a[nbuf * nt] = al;
+        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2;
+        ++nbuf;
+        continue;
+      }
+      int bi = -1;  // closest of the buffer and the new hit
+      float bt = tau;
+      for (int j = 0; j < K; ++j) {
+        const float tj = kb_tau[j * nt];
+        if (tj < bt) { bt = tj; bi = j; }
+      }
+      if (bi < 0) {
+        blend(al, r0, r1, r2);
+      } else {
+        blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt]);
+        kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
+        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2;
+      }
+    }
+  }
+  // end of the list: the remaining hits in ascending tau_max
+  while (!done && nbuf > 0) {
+    int bi = 0;
+    float bt = kb_tau[0];
+    for (int j = 1; j < nbuf; ++j) {
+      const float tj = kb_tau[j * nt];
+      if (tj < bt) { bt = tj; bi = j; }
+    }
+    blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt]);
+    --nbuf;
+    kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
+    kb_r[bi * nt] = kb_r[nbuf * nt]; kb_g[bi * nt] = kb_g[nbuf * nt]; kb_b[bi * nt] = kb_b[nbuf * nt];
+  }
+  if (inside) {
+    size_t pix = (size_t)py * cam.W + px;
+    size_t plane = (size_t)cam.W * cam.H;
+    view.rgb[pix] = C0;
+    view.rgb[plane + pix] = C1;
+    view.rgb[2 * plane + pix] = C2;
+    view.alpha[pix] = valid ? 1.f - T : 0.f;
+    if (view.tfinal) view.tfinal[pix] = T;
+    if (view.n_used) view.n_used[pix] = 0;
+  }
+}
+
 // Forward schedule estimate, one warp per tile.  A heuristic that only orders the tiles (no
 // result depends on it): a tile's pixels saturate after roughly a fixed optical depth of
 // particles that cover the whole tile, so the estimate is the list position where
@@ -184,11 +304,19 @@ void fwd_launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, c
 }
 
 // Degree 0 colours do not depend on the direction: both colour modes run the per-pixel kernel.
-// The degree-n kernels run with per-pixel colours (make_opts rejects the combination with
-// per-particle colours).
+// The degree-n kernels and the k-buffer run with per-pixel colours (make_opts rejects the
+// other combinations).
 template <int DEG, bool RS>
 void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                 const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
+  if (op.kbuffer > 0) {
+    const int threads = op.tile_w * op.tile_h;
+    const size_t smem = sizeof(float) * 5 * (size_t)op.kbuffer * threads;
+    cudaFuncSetAttribute(k_composite_fwd_kbuffer<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_composite_fwd_kbuffer<DEG, RS><<<bd.total_tiles, threads, smem, s>>>(
+        bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
+    return;
+  }
   if (op.kernel_degree != 2) {
     fwd_launch_k<DEG, RS, false, true>(bd, op, rect, vals, ranges, stats, ts, s);
     return;
@@ -207,6 +335,7 @@ void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
 // Predicts each tile's walk, orders the tiles longest first, then composites them in that order.
 ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                                const uint32_t *ranges, unsigned long long *stats, void *sched, cudaStream_t s) {
+  if (op.kbuffer > 0 && stats) return UT_ERR_UNSUPPORTED;
   if (bd.total_tiles == 0) return UT_OK;
   const TileSched ts = carve_tile_sched(sched, bd.total_tiles);
   if (cudaMemsetAsync(ts.hist, 0, sizeof(uint32_t) * (2 * kOrderBuckets + 1), s) != cudaSuccess) return UT_ERR_CUDA;

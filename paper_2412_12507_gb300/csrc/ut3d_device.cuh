@@ -38,6 +38,7 @@ struct DevOpts {
   int colour_mode;  // UT_COLOUR_PER_PIXEL / UT_COLOUR_PER_PARTICLE
   int kernel_degree;   // n of the generalised Gaussian (2 = Gaussian)
   float kernel_lambda; // 1/2 3^(2-n): rho = exp(-kernel_lambda d^n)
+  int kbuffer;         // 0: blend in tile order; k: per-ray k-buffer of k entries
 };
 
 // ---------------------------------------------------------------- batches of views

@@ -195,3 +195,37 @@ def test_kernel_degree_backward_matches_oracle(kdeg, cam_model):
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         e = _grad_compare(to_np(grads[k]), ref[k], k)
         print(kdeg, cam_model, k, f"rel err {e:.2e}")
+
+
+# ------------------------------------------------------------------ "Ours (sorted)": per-ray k-buffer
+
+@pytest.mark.parametrize("name,k", [("rs_fisheye", 16), ("fisheye_shell", 16), ("pinhole_deg2_ragged", 4),
+                                    ("pinhole_deg2_ragged", 1)])
+def test_kbuffer_render_matches_oracle(name, k):
+    case = CASES[name]
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], kbuffer=k)
+    g = run_gpu(sc, cam, op)
+    W, H = cam["width"], cam["height"]
+    pix = None if W * H <= 70_000 else sample_pixels(W, H, 20_000, 7)
+    ref = oracle.render(sc, cam, op, proj=oracle.project(sc, cam, op, TOL), pixels=pix, tol=TOL)
+    r = compare_frame(g["frame"], ref)
+    print(name, "k", k, r)
+    assert r["n_bad"] == 0, r
+    assert r["n_flagged"] <= 0.1 * r["n"], r
+    # the k-buffer changes the image (the tau order differs from the tile order somewhere)
+    base = run_gpu(sc, cam, case["options"])["frame"]
+    assert torch.max(torch.abs(base.rgb - g["frame"].rgb)).item() > 1e-4
+
+
+def test_kbuffer_is_forward_only():
+    case = GRAD_CASES["pinhole_deg2"]()
+    sc, cam = case["scene"], case["camera"]
+    op = dict(case["options"], kbuffer=16)
+    g = run_gpu(sc, cam, op)
+    H, W = cam["height"], cam["width"]
+    with pytest.raises(abi.UtError):
+        render.composite_backward(g["scene"], cam, op, g["proj"], g["binning"], g["frame"],
+                                  torch.zeros((3, H, W), device="cuda"), torch.zeros((H, W), device="cuda"))
+    with pytest.raises(abi.UtError):
+        run_gpu(sc, cam, dict(op, colour_mode=1))
