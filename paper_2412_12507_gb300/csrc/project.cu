@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__
   }
   const float4 q4 = sc.quats[i];
   const float logit = sc.logits[i];
-  const DevCam cam = view.cam;
+  const DevCam &cam = view.cam;  // read from the kernel parameter (no register copy)
 
   Particle p;
   bool ok = live && activate(mu, ls, q4, logit, p);
@@ -87,33 +87,42 @@ __global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__
       cyy = fmaf(av, av, cyy);
     }
   } else {
-    // sigma points in start-pose camera rotation: y_0 = R0 mu, y_(1+k) / y_(4+k) = y_0 +- gamma s_k R0 R[:,k]
-    float2 v[7];
-    ok = ok & project_world(cam, op.rs_iters, y0, v[0], t_mu);
+    // sigma points in start-pose camera rotation: y_0 = R0 mu, y = y_0 +- gamma s_k R0 R[:,k].
+    // The six off-centre points go through one (not unrolled) loop, each projection taken
+    // relative to the centre's v_0 (d_j = v_j - v_0), which keeps the moments free of
+    // cancellation: eq. 2d_conic_1 gives v_mu = v_0 + wi sum d_j (the mean weights sum to one)
+    // and eq. 2d_conic_2 gives Sigma' = wi sum d_j d_j^T + (W - 2) dm dm^T with dm = wi sum d_j
+    // and W = wc0 + 6 wi the sum of the covariance weights.
+    float2 v0;
+    ok = ok & project_world(cam, op.rs_iters, y0, v0, t_mu);
+    float3 col[3];  // gamma s_k R0 R[:,k]
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float gs = w.gamma * p.s[k];
-      float3 col = make_float3(gs * p.R[k], gs * p.R[3 + k], gs * p.R[6 + k]);
-      float3 dy = mat3_mul(cam.R0, col);
+      const float gs = w.gamma * p.s[k];
+      col[k] = mat3_mul(cam.R0, make_float3(gs * p.R[k], gs * p.R[3 + k], gs * p.R[6 + k]));
+    }
+    float sx = 0.f, sy = 0.f, pxx = 0.f, pxy = 0.f, pyy = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) {
+      const int k = j < 3 ? j : j - 3;
+      const float3 c3 = k == 0 ? col[0] : (k == 1 ? col[1] : col[2]);  // selects, no local memory
+      const float3 dy = j < 3 ? c3 : make_float3(-c3.x, -c3.y, -c3.z);
+      float2 v;
       float tt;
-      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v[1 + k], tt);
-      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x - dy.x, y0.y - dy.y, y0.z - dy.z), v[4 + k], tt);
+      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v, tt);
+      const float dx = v.x - v0.x, dz = v.y - v0.y;
+      sx += dx;
+      sy += dz;
+      pxx = fmaf(dx, dx, pxx);
+      pxy = fmaf(dx, dz, pxy);
+      pyy = fmaf(dz, dz, pyy);
     }
-    // eq. 2d_conic_1 / 2d_conic_2
-    vm = make_float2(w.wm0 * v[0].x, w.wm0 * v[0].y);
-#pragma unroll
-    for (int j = 1; j < 7; ++j) {
-      vm.x = fmaf(w.wi, v[j].x, vm.x);
-      vm.y = fmaf(w.wi, v[j].y, vm.y);
-    }
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      float ww = j == 0 ? w.wc0 : w.wi;
-      float dx = v[j].x - vm.x, dy = v[j].y - vm.y;
-      cxx = fmaf(ww * dx, dx, cxx);
-      cxy = fmaf(ww * dx, dy, cxy);
-      cyy = fmaf(ww * dy, dy, cyy);
-    }
+    const float dmx = w.wi * sx, dmy = w.wi * sy;
+    const float c = w.wc0 + 6.f * w.wi - 2.f;
+    vm = make_float2(v0.x + dmx, v0.y + dmy);
+    cxx = fmaf(w.wi, pxx, c * dmx * dmx);
+    cxy = fmaf(w.wi, pxy, c * dmx * dmy);
+    cyy = fmaf(w.wi, pyy, c * dmy * dmy);
   }
   float3 xc = cam_point_at(cam, y0, t_mu);
   float dep = sqrtf(fmaf(xc.x, xc.x, fmaf(xc.y, xc.y, xc.z * xc.z)));
