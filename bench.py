@@ -464,12 +464,24 @@ def run_ours(args):
     d_alpha = torch.as_tensor(rng.standard_normal((H, W)).astype(np.float32) / P).to(dev)
     stream = torch.cuda.current_stream()
 
-    def fwd():
+    def fwd_eager():
         r.forward(scene, sync_check=False)
 
-    def fwd_bwd():
+    def fwd_bwd_eager():
         r.forward(scene, sync_check=False)
         r.backward(scene, d_rgb, d_alpha)
+
+    # the timed steps replay the library's own step captured as CUDA graphs (every kernel runs,
+    # no host launch gaps); the eager steps are timed too
+    g_fwd, g_frame, _ = r.capture(scene)
+    g_fb, _, _ = r.capture(scene, d_rgb, d_alpha)
+    torch.cuda.synchronize()
+
+    def fwd():
+        g_fwd.replay()
+
+    def fwd_bwd():
+        g_fb.replay()
 
     def barrier():
         if world > 1:
@@ -488,12 +500,13 @@ def run_ours(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1), world, dev) / steps
 
-    # launches per step (host-side counter of the library)
+    # launches per step (host-side counter of the library, counted on an eager step: a graph
+    # replay runs the same kernels)
     c0 = L.ut_kernel_launch_count()
-    fwd()
+    fwd_eager()
     launches_fwd = L.ut_kernel_launch_count() - c0
     c0 = L.ut_kernel_launch_count()
-    fwd_bwd()
+    fwd_bwd_eager()
     launches_fb = L.ut_kernel_launch_count() - c0
     torch.cuda.synchronize()
 
@@ -502,6 +515,8 @@ def run_ours(args):
     clocks.start()
     fwd_ms = timed(fwd, args.steps, max(3, args.warmup))
     fb_ms = timed(fwd_bwd, args.steps, max(3, args.warmup))
+    fwd_eager_ms = timed(fwd_eager, args.steps, max(3, args.warmup))
+    fb_eager_ms = timed(fwd_bwd_eager, args.steps, max(3, args.warmup))
     if K > r.binning.capacity or r.binning.count() != K:
         raise SystemExit("key count changed during the timed region")
 
@@ -566,9 +581,9 @@ def run_ours(args):
         scene.quats.copy_(host["quats"].view_as(scene.quats), non_blocking=True)
         scene.opacity_logits.copy_(host["opacity_logits"].view_as(scene.opacity_logits), non_blocking=True)
         scene.sh.copy_(host["sh"].view_as(scene.sh), non_blocking=True)
-        f = r.forward(scene, sync_check=False)
-        out_host[:3].copy_(f.rgb, non_blocking=True)
-        out_host[3].copy_(f.alpha, non_blocking=True)
+        g_fwd.replay()
+        out_host[:3].copy_(g_frame.rgb, non_blocking=True)
+        out_host[3].copy_(g_frame.alpha, non_blocking=True)
 
     e2e_ms = timed(e2e_step, max(3, args.steps // 2), 3)
 
@@ -608,8 +623,11 @@ def run_ours(args):
             "config": {"workload": case["name"], "particles": n, "width": W, "height": H,
                        "camera": "fisheye+rolling_shutter", "sh_degree": int(sc_np["sh_degree"]),
                        "tile": f"{op['tile_w']}x{op['tile_h']}", "keys": K, "parallelism": f"replicas{world}",
+                       "launch": "cuda_graph (the library step captured by Renderer.capture)",
                        "l2": "inputs larger than L2 (236 MB scene + 2 x keys), no flush"},
             "fwd_ms": fwd_ms, "fwd_bwd_ms_per_view": fb_ms, "fwd_bwd_mpix_s": job_mpix_s(P, world, fb_ms),
+            "eager": {"fwd_ms": fwd_eager_ms, "fwd_bwd_ms": fb_eager_ms,
+                      "fwd_mpix_s": job_mpix_s(P, world, fwd_eager_ms)},
             "kernels": kernels, "evaluations": n_eval, "blended": n_blend,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "e2e": {"value": job_mpix_s(P, world, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,

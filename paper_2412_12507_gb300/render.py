@@ -227,6 +227,27 @@ class Renderer:
         return composite_backward(scene, self.cam, self.opts, self.proj, self.binning, self.frame, d_rgb, d_alpha,
                                   self.bws)
 
+    def capture(self, scene: Scene, d_rgb: torch.Tensor | None = None, d_alpha: torch.Tensor | None = None):
+        """Records one forward step (and, given dL/drgb and dL/dalpha, one backward) on this
+        renderer's current buffers as a CUDA graph; graph.replay() reruns every kernel of the step
+        (projection, binning, compositing[, backward]) with no host launches.  Returns
+        (graph, frame, grads or None): replays overwrite that frame and those gradient tensors.
+        The key capacity is frozen into the graph: size it with a synchronised forward first
+        (a replay whose key count exceeds it renders black and reports K in binning.k_dev)."""
+        stream = torch.cuda.Stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            self.forward(scene, sync_check=False)  # buffers exist before the capture
+            if d_rgb is not None:
+                self.backward(scene, d_rgb, d_alpha)
+            stream.synchronize()
+            with torch.cuda.graph(graph, stream=stream):
+                frame = self.forward(scene, sync_check=False)
+                grads = self.backward(scene, d_rgb, d_alpha) if d_rgb is not None else None
+        torch.cuda.current_stream().wait_stream(stream)
+        return graph, frame, grads
+
 
 class RenderFunction(torch.autograd.Function):
     """torch.autograd.Function over the C ABI: (means, log_scales, quats, logits, sh) -> (rgb, alpha)."""

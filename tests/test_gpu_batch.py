@@ -198,3 +198,42 @@ def test_autotune_tiles_returns_a_candidate_and_timings():
     assert (best["tile_w"], best["tile_h"]) in render.TILE_CANDIDATES
     assert set(res) == {f"{w}x{h}" for w, h in render.TILE_CANDIDATES}
     assert all(r["ms"] > 0 and r["keys"] > 0 for r in res.values())
+
+
+def test_captured_step_replays_bit_identically_and_follows_new_inputs():
+    """Renderer.capture: the forward (+ backward) step recorded as a CUDA graph gives, on replay,
+    the eager step's image bit for bit and its gradients up to the rounding order of the
+    backward's atomic accumulation, and a replay after the scene's tensors
+    were overwritten in place renders the new values (the graph reads the same buffers)."""
+    sc_np = _scenes()[0]
+    cam = _cams()[2][1]
+    op = synth.options()
+    scene = render.Scene.from_arrays(sc_np)
+    r = render.Renderer(cam, op, capacity=1 << 12)
+    r.forward(scene)
+    torch.cuda.synchronize()
+    H, W = cam["height"], cam["width"]
+    g = torch.Generator().manual_seed(7)
+    d_rgb = torch.randn((3, H, W), generator=g).cuda()
+    d_alpha = torch.randn((H, W), generator=g).cuda()
+    eager_f = {k: getattr(r.forward(scene), k).clone() for k in ("rgb", "alpha", "t_final", "n_used")}
+    eager_g = {k: v.clone() for k, v in r.backward(scene, d_rgb, d_alpha).items()}
+    torch.cuda.synchronize()
+    graph, frame, grads = r.capture(scene, d_rgb, d_alpha)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    for k, v in eager_f.items():
+        assert torch.equal(getattr(frame, k), v), k
+    for k, v in eager_g.items():  # the backward accumulates with float atomics: order-dependent rounding
+        torch.testing.assert_close(grads[k], v, rtol=1e-4, atol=1e-5 * float(v.abs().max()), msg=k)
+    # new opacities in place: the replay must follow them
+    with torch.no_grad():
+        scene.opacity_logits.sub_(1.0)
+    graph.replay()
+    torch.cuda.synchronize()
+    moved = frame.alpha.clone()
+    ref = render.Renderer(cam, op, capacity=1 << 12).forward(scene)
+    torch.cuda.synchronize()
+    assert torch.equal(moved, ref.alpha)
+    assert not torch.equal(moved, eager_f["alpha"])
