@@ -7,11 +7,13 @@
 //   1. a stable LSD radix sort of the N particle depths (bits(depth), index);
 //   2. emission, in that depth order, of one entry per (particle, tile column) it covers,
 //      and a stable radix sort of those entries by global tile column;
-//   3. emission, in that (column, depth) order, of one entry per (particle, tile) — the
-//      rows of each column entry — and a stable radix sort by global tile row.
-// A stable sort by row of a sequence ordered by (column, depth) is ordered by
+//   3. expansion, in that (column, depth) order, of every column entry into its tile rows,
+//      stably ordered by global tile row: scattered straight to the final positions (the row
+//      scatter below) when every view has at most 512 tile rows and the batch at most 16384
+//      tile columns, else emitted and sorted by one more radix pass per 8 row bits.
+// A stable order by row of a sequence ordered by (column, depth) is ordered by
 // (row, column, depth) = (tile, depth), so the outputs are identical, while the K entries
-// pass through one 8-bit radix pass per ceil(log2 rows / 8) (one pass for a 1080p view)
+// are written once (row scatter) or pass through one 8-bit radix pass per ceil(log2 rows / 8)
 // instead of ceil(log2 tiles / 8) passes, and only the shorter column list (one entry per
 // covered column, not per tile) pays for the column order.
 //
@@ -405,8 +407,10 @@ __device__ __forceinline__ int run_owner(uint32_t start, uint32_t p) {
 // Column entries, one warp per 32 particles of the depth order.  The particles' runs are
 // consecutive in the output, so the warp writes their union [start_0, end_31) with all lanes,
 // each lane finding the run of its position.  Key = (tile rows covered << 16) | global tile
-// column (the sort uses the low bits only; the height rides along for the row stage),
-// value = flattened particle index.
+// column, or with PACK global tile column | first tile row << 14 | (rows - 1) << 23 (the sort
+// uses the column bits only; the rest rides along for the row stage), value = flattened
+// particle index.
+template <bool PACK>
 __global__ void __launch_bounds__(kThreads) k_emit_cols(const __grid_constant__ BatchDesc bd, int n,
                                                         const uint32_t *__restrict__ order,
                                                         const uint32_t *__restrict__ offs,
@@ -428,7 +432,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_cols(const __grid_constant__ 
         g = order[j];
         const short4 r = rect[g];
         const uint32_t h = (uint32_t)(r.w / tile_h - r.y / tile_h + 1);
-        key0 = (h << 16) | (uint32_t)(bd.v[view_of_particle(bd, (int)g)].col_off + r.x / tile_w);
+        const uint32_t col = (uint32_t)(bd.v[view_of_particle(bd, (int)g)].col_off + r.x / tile_w);
+        key0 = PACK ? (col | ((uint32_t)(r.y / tile_h) << 14) | ((h - 1u) << 23)) : ((h << 16) | col);
       }
     }
     const uint32_t S = __shfl_sync(0xffffffffu, start, 0);
@@ -533,6 +538,183 @@ __global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *_
   }
 }
 
+// ---------------------------------------------------------------- row scatter
+//
+// The row stage without materialising the row entries.  The column keys carry each entry's
+// first tile row a and row count h next to the column; the column-sorted list is split into
+// CH chunks per tile column, one warp per chunk.  k_row_count counts every chunk's entries per
+// tile row; one exclusive scan over the (tile, chunk) counts in tile order gives each chunk's
+// first position in each tile's run (and the tile ranges); k_row_scatter then walks the chunk
+// 32 entries at a time (lanes in entry order): a lane's rank in row r among the 32 is the
+// number of lower lanes covering r, read off the group's lane mask of r, so every (entry, row)
+// pair lands at its (tile, depth) position.
+
+constexpr int kScatterMaxRows = 512;       // tile rows per view handled by the scatter
+constexpr int kScatterMaxCols = 1 << 14;   // tile columns per batch handled by the scatter
+constexpr int kPackColBits = 14, kPackRowBits = 9;
+
+// Packed column key: global tile column | a << 14 | (h - 1) << 23.
+__device__ __forceinline__ uint32_t pk_col(uint32_t key) { return key & ((1u << kPackColBits) - 1u); }
+__device__ __forceinline__ uint32_t pk_a(uint32_t key) { return (key >> kPackColBits) & ((1u << kPackRowBits) - 1u); }
+__device__ __forceinline__ uint32_t pk_h(uint32_t key) { return (key >> (kPackColBits + kPackRowBits)) + 1u; }
+
+// Warp chunks per tile column: enough warps for the whole GPU on narrow images, eight (one
+// block) per column on wide batches.
+inline int row_chunks(int cols) {
+  const int s = 1024 / (cols > 0 ? cols : 1);
+  return kWarps * (s < 1 ? 1 : (s > 32 ? 32 : s));
+}
+
+// Entry range of chunk k of global tile column c (colb: first / end entry of each column).
+__device__ __forceinline__ void chunk_range(const uint32_t *colb, int c, int k, int ch, uint32_t &lo, uint32_t &hi) {
+  const uint32_t a = colb[2 * c], e = colb[2 * c + 1];
+  const u64 m = e - a;
+  lo = a + (uint32_t)(m * (u64)k / (u64)ch);
+  hi = a + (uint32_t)(m * (u64)(k + 1) / (u64)ch);
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// First and end entry of every global tile column in the sorted packed column keys (columns
+// left at {0, 0} when empty); four keys per thread and their neighbours.
+__global__ void k_col_bounds(const uint32_t *__restrict__ ckeys, Count cc, uint32_t *__restrict__ colb) {
+  const uint32_t M = cc.get();
+  const uint32_t nq = (M + 3) / 4;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint32_t p0 = 4 * q;
+    uint32_t t[6];  // columns of entries p0 - 1 .. p0 + 4 (0xffffffff outside the list)
+    if (p0 + 4 <= M) {
+      const uint4 v = reinterpret_cast<const uint4 *>(ckeys)[q];
+      t[1] = pk_col(v.x); t[2] = pk_col(v.y); t[3] = pk_col(v.z); t[4] = pk_col(v.w);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[1 + i] = p0 + i < M ? pk_col(ckeys[p0 + i]) : 0xffffffffu;
+    }
+    t[0] = p0 > 0 ? pk_col(ckeys[p0 - 1]) : 0xffffffffu;
+    t[5] = p0 + 4 < M ? pk_col(ckeys[p0 + 4]) : 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t p = p0 + i;
+      if (p >= M) break;
+      if (t[i] != t[1 + i]) colb[2 * t[1 + i]] = p;
+      if (t[2 + i] != t[1 + i]) colb[2 * t[1 + i] + 1] = p + 1;
+    }
+  }
+}
+
+// Entries of every warp chunk in every tile of its column: spine[tile * ch + chunk].
+// Block b holds chunks (b % (ch / 8)) * 8 + warp of column b / (ch / 8); dynamic shared
+// memory kWarps x (rows + 1) words.
+__global__ void __launch_bounds__(kThreads) k_row_count(const __grid_constant__ BatchDesc bd,
+                                                        const uint32_t *__restrict__ ck,
+                                                        const uint32_t *__restrict__ colb, int ch,
+                                                        uint32_t *__restrict__ spine) {
+  extern __shared__ uint32_t s_mem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, bpc = ch / kWarps;
+  const int c = blockIdx.x / bpc, k = (blockIdx.x - c * bpc) * kWarps + warp;
+  const DevView &v = bd.v[view_of_col(bd, c)];
+  const int rows = v.tiles_y;
+  uint32_t *D = s_mem + (size_t)warp * (rows + 1);
+  for (int r = lane; r <= rows; r += 32) D[r] = 0;
+  __syncwarp();
+  uint32_t lo, hi;
+  chunk_range(colb, c, k, ch, lo, hi);
+  for (uint32_t i = lo + lane; i < hi; i += 32) {
+    const uint32_t key = ck[i], a = pk_a(key);
+    atomicAdd(&D[a], 1u);
+    atomicAdd(&D[a + pk_h(key)], 0xffffffffu);
+  }
+  __syncwarp();
+  const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off);
+  uint32_t carry = 0;
+  for (int r0 = 0; r0 < rows; r0 += 32) {
+    const int r = r0 + lane;
+    const uint32_t x = warp_incl_scan_u32(r < rows ? D[r] : 0u, lane) + carry;
+    if (r < rows) spine[(size_t)(tile0 + (uint32_t)r * v.tiles_x) * ch + k] = x;
+    carry = __shfl_sync(0xffffffffu, x, 31);
+  }
+}
+
+// Writes every row entry of every warp chunk at its sorted position; chunk 0 of each column
+// also writes the column's tile ranges.  Same block / warp layout as k_row_count.  Per group of
+// 32 entries each lane marks its rows in the group's lane masks (W), then writes its rows at
+// the chunk's next position in the row (G) plus its rank among the group's lanes covering the
+// row.  Dynamic shared memory: per warp 2 x rows words (G, W).
+inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * 2 * (size_t)kWarps * (size_t)max_rows; }
+
+__global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant__ BatchDesc bd,
+                                                          const uint32_t *__restrict__ ck,
+                                                          const uint32_t *__restrict__ cv,
+                                                          const uint32_t *__restrict__ colb, int ch, int max_rows,
+                                                          const uint32_t *__restrict__ spine, Count kcnt,
+                                                          const float *__restrict__ depth,
+                                                          uint32_t *__restrict__ vals, uint32_t *__restrict__ ranges,
+                                                          uint64_t *__restrict__ keys) {
+  extern __shared__ uint32_t s_mem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, bpc = ch / kWarps;
+  const uint32_t full = 0xffffffffu, bit = 1u << lane, lt = bit - 1u;
+  const int c = blockIdx.x / bpc, k = (blockIdx.x - c * bpc) * kWarps + warp;
+  const DevView &v = bd.v[view_of_col(bd, c)];
+  const int rows = v.tiles_y;
+  uint32_t *G = s_mem + (size_t)warp * 2 * max_rows, *W = G + max_rows;
+  const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off), part_off = (uint32_t)v.part_off;
+  const uint32_t kmax = kcnt.get();  // every position is below K; the tests only guard the stores
+  for (int r = lane; r < rows; r += 32) {
+    const uint32_t tile = tile0 + (uint32_t)r * v.tiles_x;
+    G[r] = spine[(size_t)tile * ch + k];
+    W[r] = 0;
+    if (k == 0) {
+      const uint32_t start = spine[(size_t)tile * ch];
+      const uint32_t end = tile + 1 < (uint32_t)bd.total_tiles ? spine[(size_t)(tile + 1) * ch] : kmax;
+      if (start < end) {
+        ranges[2 * tile] = start;
+        ranges[2 * tile + 1] = end;
+      }
+    }
+  }
+  __syncwarp();
+  uint32_t lo, hi;
+  chunk_range(colb, c, k, ch, lo, hi);
+  for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
+    const uint32_t e = g0 + lane;
+    uint32_t a = 0, b = 0, g = 0;  // rows [a, b) of this lane's entry
+    if (e < hi) {
+      const uint32_t key = ck[e];
+      g = cv[e];
+      a = pk_a(key);
+      b = a + pk_h(key);
+    }
+    for (uint32_t r = a; r < b; ++r) atomicOr(&W[r], bit);
+    __syncwarp();
+    const uint32_t loc = g - part_off;
+    for (uint32_t r = a; r < b; ++r) {
+      const uint32_t pos = G[r] + (uint32_t)__popc(W[r] & lt);
+      if (pos < kmax) {
+        vals[pos] = loc;
+        if (keys) keys[pos] = ((u64)(tile0 + r * (uint32_t)v.tiles_x) << 32) | (u64)__float_as_uint(depth[g]);
+      }
+    }
+    __syncwarp();
+    const int rmin = (int)__reduce_min_sync(full, b > a ? a : (uint32_t)rows);
+    const int rmax = (int)__reduce_max_sync(full, b);
+    for (int r = rmin + lane; r < rmax; r += 32) {
+      const uint32_t m = W[r];
+      if (m) {
+        G[r] += (uint32_t)__popc(m);
+        W[r] = 0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------- host orchestration
 
 struct Arena {
@@ -550,11 +732,12 @@ inline uint32_t ceil_div(u64 a, u64 b) { return (uint32_t)((a + b - 1) / b); }
 
 struct Buffers {
   uint32_t *dk[2], *dv[2], *cnt, *offs, *x[3], *spine;
-  u64 *chunk, *total;  // total[0] = column entries, total[1] = K
+  uint32_t *colb, *tspine;  // row scatter: column bounds [2 x cols], (tile, chunk) counts [tiles x S]
+  u64 *chunk, *total;       // total[0] = column entries, total[1] = K
 };
 
 // Workspace layout; with ws == nullptr only the size is accumulated.
-Buffers carve(void *ws, int n, int64_t cap, size_t *bytes = nullptr) {
+Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, size_t *bytes = nullptr) {
   Arena a{static_cast<char *>(ws), 0};
   Buffers b;
   size_t nn = (size_t)(n > 0 ? n : 1);
@@ -567,16 +750,21 @@ Buffers carve(void *ws, int n, int64_t cap, size_t *bytes = nullptr) {
   for (int i = 0; i < 3; ++i) b.x[i] = a.take<uint32_t>(cc);
   size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
   b.spine = a.take<uint32_t>(spine);
+  const size_t tt = (size_t)(tiles > 0 ? tiles : 1), ncol = (size_t)(cols > 0 ? cols : 1);
+  const size_t tsp = tt * (size_t)row_chunks(cols);
+  b.colb = a.take<uint32_t>(2 * ncol);
+  b.tspine = a.take<uint32_t>(tsp);
   size_t maxlen = spine > maxc ? spine : maxc;
+  if (tsp > maxlen) maxlen = tsp;
   b.chunk = a.take<u64>(ceil_div(maxlen, kTile) + 1);
   b.total = a.take<u64>(2);
   if (bytes) *bytes = a.off;
   return b;
 }
 
-size_t carve_bytes(int n, int64_t cap) {
+size_t carve_bytes(int n, int64_t cap, int tiles, int cols) {
   size_t bytes = 0;
-  carve(nullptr, n, cap, &bytes);
+  carve(nullptr, n, cap, tiles, cols, &bytes);
   return bytes;
 }
 
@@ -624,7 +812,7 @@ int bits_for(int tiles) {
 
 }  // namespace
 
-size_t bin_workspace_bytes(int n, int64_t cap, int /*tiles*/) { return carve_bytes(n, cap); }
+size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols) { return carve_bytes(n, cap, tiles, cols); }
 
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
@@ -632,7 +820,7 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
   const int n = bd.total_particles;
   const int tiles = bd.total_tiles;
   const short4 *r4 = reinterpret_cast<const short4 *>(rect);
-  Buffers b = carve(ws, n, cap);
+  Buffers b = carve(ws, n, cap, tiles, bd.total_cols);
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, s) != cudaSuccess) return UT_ERR_CUDA;
   if (cudaMemsetAsync(b.total, 0, 2 * sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
   if (n > 0) {
@@ -645,13 +833,17 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     count_launches(3);
     const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s);
     // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
-    // and the caller's vals, arranged so that the last row pass lands in vals
+    // and the caller's vals, arranged so that the row stage lands in vals: the row scatter
+    // reads the column values from x[2]; the row radix passes end in vals
+    int max_rows = 0;
+    for (int v = 0; v < bd.nv; ++v) max_rows = bd.v[v].tiles_y > max_rows ? bd.v[v].tiles_y : max_rows;
+    const bool scatter = max_rows <= kScatterMaxRows && bd.total_cols <= kScatterMaxCols;
     const int cbits = bits_for(bd.total_cols), rbits = bits_for(bd.total_rows);
     const int cp = (cbits + kRadixBits - 1) / kRadixBits, rp = (rbits + kRadixBits - 1) / kRadixBits;
-    uint32_t *r0 = (rp & 1) ? b.x[2] : vals;           // row values start here ...
-    uint32_t *r1 = r0 == vals ? b.x[2] : vals;         // ... and end in vals
+    uint32_t *r0 = (scatter || (rp & 1)) ? b.x[2] : vals;  // row values start here ...
+    uint32_t *r1 = r0 == vals ? b.x[2] : vals;               // ... and end in vals
     uint32_t *cv[2], *ck[2] = {b.x[0], b.x[1]};
-    cv[0] = (cp & 1) ? r0 : r1;                        // column values end in r1
+    cv[0] = (cp & 1) ? (scatter ? r1 : r0) : (scatter ? r0 : r1);  // column values end in x[2] / r1
     cv[1] = cv[0] == r0 ? r1 : r0;
     // 2. column entries in depth order, sorted by global tile column
     k_gather_widths<<<g, kThreads, 0, s>>>(n, b.dv[r], ntiles, r4, op.tile_w, b.cnt);
@@ -659,13 +851,39 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     scan(b.cnt, b.offs, cn, (u64)n, b.chunk, b.total, s);
     const Count cc{b.total, (u64)cap, 0, b.total + 1};  // nothing is written unless K fits
     const int eg = (int)std::min<u64>((u64)(n + kThreads - 1) / kThreads, (u64)device_sm_count() * 16);
-    k_emit_cols<<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs, b.cnt, r4, cc, op.tile_w, op.tile_h, ck[0], cv[0]);
+    if (scatter)
+      k_emit_cols<true><<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs, b.cnt, r4, cc, op.tile_w, op.tile_h, ck[0],
+                                                cv[0]);
+    else
+      k_emit_cols<false><<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs, b.cnt, r4, cc, op.tile_w, op.tile_h, ck[0],
+                                                 cv[0]);
     count_launches(1);
     const int rc = radix_sort(ck, cv, cc, (u64)cap, 0, cbits, b.spine, b.chunk, s);
+    const Count ck2{b.total + 1, (u64)cap, 0};
+    if (scatter) {
+      // 3. row entries scattered straight into (tile, depth) order
+      const int ch = row_chunks(bd.total_cols), blocks = bd.total_cols * (ch / kWarps);
+      if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
+        return UT_ERR_CUDA;
+      k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ck[rc], cc, b.colb);
+      k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ck[rc], b.colb, ch,
+                                                                                       b.tspine);
+      count_launches(2);
+      const u64 tn = (u64)tiles * (u64)ch;
+      scan(b.tspine, b.tspine, Count{nullptr, 0, (uint32_t)tn}, tn, b.chunk, nullptr, s);
+      const size_t smem = row_scatter_smem(max_rows);
+      if (cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return UT_ERR_CUDA;
+      k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ck[rc], cv[rc], b.colb, ch, max_rows, b.tspine, ck2, depth,
+                                                   vals, ranges, keys);
+      count_launches(1);
+      k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
+      count_launches(1);
+      return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+    }
     // 3. row entries in (column, depth) order, sorted by global tile row; the run lengths are
     //    the heights carried in the column keys
     scan<Count, High16>(ck[rc], b.offs, cc, (u64)cap, b.chunk, nullptr, s);
-    const Count ck2{b.total + 1, (u64)cap, 0};
     uint32_t *rk[2] = {ck[rc ^ 1], ck[rc]}, *rv[2] = {r0, r1};
     const int rg = (int)std::min<u64>(((u64)cap + kThreads - 1) / kThreads, (u64)device_sm_count() * 16);
     k_emit_rows<<<rg, kThreads, 0, s>>>(bd, cc, ck[rc], cv[rc], b.offs, r4, ck2, op.tile_h, rk[0], rv[0]);

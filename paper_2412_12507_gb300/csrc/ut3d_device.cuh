@@ -82,6 +82,16 @@ struct BatchDesc {
   DevScene s[kMaxScenes];
 };
 
+// View owning global tile column c (views are sorted by col_off).
+__device__ __forceinline__ int view_of_col(const BatchDesc &b, int c) {
+  int lo = 0, hi = b.nv - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.v[mid].col_off <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // View owning global tile row r (views are sorted by row_off).
 __device__ __forceinline__ int view_of_row(const BatchDesc &b, int r) {
   int lo = 0, hi = b.nv - 1;
