@@ -335,7 +335,13 @@ struct BatchLayout {
   size_t mean2d, cov2d, depth, rect, ntiles, ranges, vals, sched, bin, total;
 };
 
-BatchLayout batch_layout(long long part, long long tiles, long long cols, long long cap) {
+int max_tiles_y(const BatchDesc &bd) {
+  int m = 0;
+  for (int v = 0; v < bd.nv; ++v) m = bd.v[v].tiles_y > m ? bd.v[v].tiles_y : m;
+  return m;
+}
+
+BatchLayout batch_layout(long long part, long long tiles, long long cols, int max_rows, long long cap) {
   BatchLayout L;
   size_t off = 0;
   size_t p = (size_t)(part > 0 ? part : 1), t = (size_t)(tiles > 0 ? tiles : 1), c = (size_t)(cap > 0 ? cap : 1);
@@ -347,7 +353,7 @@ BatchLayout batch_layout(long long part, long long tiles, long long cols, long l
   L.ranges = off; off += align256(t * 8);
   L.vals = off; off += align256(c * 4);
   L.sched = off; off += tile_sched_bytes((int)t);
-  L.bin = off; off += bin_workspace_bytes((int)p, (int64_t)c, (int)t, (int)cols);
+  L.bin = off; off += bin_workspace_bytes((int)p, (int64_t)c, (int)t, (int)cols, max_rows);
   L.total = off;
   return L;
 }
@@ -420,9 +426,8 @@ ut_status ut_project_points(const float *points, int32_t n, const ut_camera *cam
 
 size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *cam, const ut_options *opt) {
   if (n < 0 || key_capacity < 0 || !cam || !opt || opt->tile_w < 1 || opt->tile_h < 1) return 0;
-  const int cols = (cam->width + opt->tile_w - 1) / opt->tile_w;
-  int tiles = cols * ((cam->height + opt->tile_h - 1) / opt->tile_h);
-  return bin_workspace_bytes(n, key_capacity, tiles, cols);
+  const int cols = (cam->width + opt->tile_w - 1) / opt->tile_w, rows = (cam->height + opt->tile_h - 1) / opt->tile_h;
+  return bin_workspace_bytes(n, key_capacity, cols * rows, cols, rows);
 }
 
 ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
@@ -438,7 +443,7 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
   if (n > 0 && (!depth || !rect || !ntiles || !aligned8(rect))) return UT_ERR_INVALID_ARG;
   if (!tile_ranges || !k_out || (key_capacity > 0 && !vals) || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
   int tiles = dop.tiles_x * dop.tiles_y;
-  size_t need = bin_workspace_bytes(n, key_capacity, tiles, dop.tiles_x);
+  size_t need = bin_workspace_bytes(n, key_capacity, tiles, dop.tiles_x, dop.tiles_y);
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return UT_ERR_INVALID_ARG;
   BatchDesc bd;
   single_view(bd, dc, dop, nullptr, n);
@@ -529,7 +534,7 @@ size_t ut_batch_workspace_size(const ut_scene *scenes, int32_t n_scenes, const u
   BatchDesc bd;
   DevOpts dop;
   if (key_capacity < 0 || make_batch(scenes, n_scenes, views, n_views, opt, bd, dop) != UT_OK) return 0;
-  return batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, key_capacity).total;
+  return batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, max_tiles_y(bd), key_capacity).total;
 }
 
 ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *views, int32_t n_views,
@@ -542,7 +547,7 @@ ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *
   UTWeights w;
   if ((st = make_weights(ut, w)) != UT_OK) return st;
   if (key_capacity < 0 || key_capacity >= (int64_t(1) << 32) || !k_out) return UT_ERR_INVALID_ARG;
-  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, key_capacity);
+  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, max_tiles_y(bd), key_capacity);
   if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
   char *ws = static_cast<char *>(workspace);
@@ -582,7 +587,7 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
   for (int v = 0; v < n_views; ++v)
     if (!views[v].t_final || !views[v].n_used || !views[v].d_rgb || !views[v].d_alpha) return UT_ERR_INVALID_ARG;
   if (key_capacity < 0 || key_capacity >= (int64_t(1) << 32) || !grads) return UT_ERR_INVALID_ARG;
-  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, key_capacity);
+  BatchLayout L = batch_layout(bd.total_particles, bd.total_tiles, bd.total_cols, max_tiles_y(bd), key_capacity);
   if (!workspace || workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
   if (!grad_workspace || grad_workspace_bytes < ut_batch_backward_workspace_size(scenes, n_scenes, views, n_views, opt) ||

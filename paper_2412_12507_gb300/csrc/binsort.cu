@@ -558,15 +558,34 @@ __device__ __forceinline__ uint32_t pk_col(uint32_t key) { return key & ((1u << 
 __device__ __forceinline__ uint32_t pk_a(uint32_t key) { return (key >> kPackColBits) & ((1u << kPackRowBits) - 1u); }
 __device__ __forceinline__ uint32_t pk_h(uint32_t key) { return (key >> (kPackColBits + kPackRowBits)) + 1u; }
 
-// Warp chunks per tile column: enough warps for the whole GPU on narrow images, eight (one
-// block) per column on wide batches.
-inline int row_chunks(int cols) {
-  const int s = 1024 / (cols > 0 ? cols : 1);
-  return kWarps * (s < 1 ? 1 : (s > 32 ? 32 : s));
+// Chunk plan of the row stage (device scratch, written by k_chunk_plan): the column list is
+// cut into about kChunkWarps chunks of similar length (a column of m entries gets
+// ceil(m / target) chunks, target = max(32, ceil(M / kChunkWarps))), one warp each.  The
+// (tile, chunk) counts are laid out in tile order: view v's part starts at voff[v], then per
+// tile row the view's columns in order, each with its chunks, so that position of chunk k of
+// column c in row r = voff[v] + r * vch[v] + (co[c] - co[col_off_v]) + k.
+constexpr int kChunkWarps = 8192;
+
+struct ChunkPlan {
+  uint32_t *ch;         // [cols] chunks of each column
+  uint32_t *co;         // [cols + 1] exclusive prefix of ch
+  uint32_t *chunk_col;  // [kChunkWarps + cols] column of every chunk
+  uint32_t *voff, *vch; // [kMaxViews] spine offset and chunks per tile row of every view
+  u64 *len;             // [2] spine length, number of chunks
+};
+
+inline size_t plan_spine_words(int max_rows, int tiles, int cols) {
+  return (size_t)(max_rows > 0 ? max_rows : 1) * (size_t)kChunkWarps + (size_t)(tiles > 0 ? tiles : 1) +
+         (size_t)(cols > 0 ? cols : 1);
+}
+
+__device__ __forceinline__ uint32_t spine_pos(const ChunkPlan &pl, const DevView &v, int vi, int c, uint32_t r) {
+  return pl.voff[vi] + r * pl.vch[vi] + (pl.co[c] - pl.co[v.col_off]);
 }
 
 // Entry range of chunk k of global tile column c (colb: first / end entry of each column).
-__device__ __forceinline__ void chunk_range(const uint32_t *colb, int c, int k, int ch, uint32_t &lo, uint32_t &hi) {
+__device__ __forceinline__ void chunk_range(const uint32_t *colb, int c, uint32_t k, uint32_t ch, uint32_t &lo,
+                                            uint32_t &hi) {
   const uint32_t a = colb[2 * c], e = colb[2 * c + 1];
   const u64 m = e - a;
   lo = a + (uint32_t)(m * (u64)k / (u64)ch);
@@ -609,70 +628,160 @@ __global__ void k_col_bounds(const uint32_t *__restrict__ ckeys, Count cc, uint3
   }
 }
 
-// Entries of every warp chunk in every tile of its column: spine[tile * ch + chunk].
-// Block b holds chunks (b % (ch / 8)) * 8 + warp of column b / (ch / 8); dynamic shared
-// memory kWarps x (rows + 1) words.
+// The chunk plan from the column bounds (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_chunk_plan(const __grid_constant__ BatchDesc bd,
+                                                     const uint32_t *__restrict__ colb, ChunkPlan pl) {
+  __shared__ u64 s_w[33];
+  __shared__ u64 s_tot;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, cols = bd.total_cols;
+  auto block_sum = [&](u64 x) -> u64 {
+    x = warp_incl_scan_u64(x, lane);
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (t == 0) {
+      u64 a = 0;
+      for (int w = 0; w < 32; ++w) a += s_w[w];
+      s_tot = a;
+    }
+    __syncthreads();
+    const u64 r = s_tot;
+    __syncthreads();
+    return r;
+  };
+  u64 m = 0;
+  for (int c = t; c < cols; c += 1024) m += colb[2 * c + 1] - colb[2 * c];
+  const u64 M = block_sum(m);
+  const u64 target = M / kChunkWarps + 1 > 32 ? M / kChunkWarps + 1 : 32;
+  // chunks per column and their exclusive prefix
+  u64 carry = 0;
+  for (int c0 = 0; c0 < cols; c0 += 1024) {
+    const int c = c0 + t;
+    uint32_t n = 0;
+    if (c < cols) {
+      const u64 mc = colb[2 * c + 1] - colb[2 * c];
+      n = (uint32_t)((mc + target - 1) / target);
+      pl.ch[c] = n;
+    }
+    u64 inc = warp_incl_scan_u64((u64)n, lane);
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const u64 w = s_w[lane];
+      const u64 wi = warp_incl_scan_u64(w, lane);
+      s_w[lane] = wi - w;
+      if (lane == 31) s_w[32] = wi;
+    }
+    __syncthreads();
+    if (c < cols) pl.co[c] = (uint32_t)(carry + s_w[warp] + inc - n);
+    carry += s_w[32];
+    __syncthreads();
+  }
+  if (t == 0) pl.co[cols] = (uint32_t)carry;
+  __syncthreads();
+  if (t == 0) {
+    u64 off = 0;
+    for (int v = 0; v < bd.nv; ++v) {
+      const uint32_t chv = pl.co[bd.v[v].col_off + bd.v[v].tiles_x] - pl.co[bd.v[v].col_off];
+      pl.voff[v] = (uint32_t)off;
+      pl.vch[v] = chv;
+      off += (u64)chv * (u64)bd.v[v].tiles_y;
+    }
+    pl.len[0] = off;
+    pl.len[1] = carry;
+  }
+  for (int c = t; c < cols; c += 1024) {
+    const uint32_t o = pl.co[c], n = pl.ch[c];
+    for (uint32_t k = 0; k < n; ++k) pl.chunk_col[o + k] = (uint32_t)c;
+  }
+}
+
+// Entries of every chunk in every tile of its column, at the chunk's spine positions (one warp
+// per chunk; dynamic shared memory kWarps x (max rows + 1) words).
 __global__ void __launch_bounds__(kThreads) k_row_count(const __grid_constant__ BatchDesc bd,
                                                         const uint32_t *__restrict__ ck,
-                                                        const uint32_t *__restrict__ colb, int ch,
-                                                        uint32_t *__restrict__ spine) {
+                                                        const uint32_t *__restrict__ colb, ChunkPlan pl,
+                                                        int max_rows, uint32_t *__restrict__ spine) {
   extern __shared__ uint32_t s_mem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, bpc = ch / kWarps;
-  const int c = blockIdx.x / bpc, k = (blockIdx.x - c * bpc) * kWarps + warp;
-  const DevView &v = bd.v[view_of_col(bd, c)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t wid = blockIdx.x * kWarps + warp;
+  if (wid >= (uint32_t)pl.len[1]) return;
+  const int c = (int)pl.chunk_col[wid];
+  const uint32_t k = wid - pl.co[c];
+  const int vi = view_of_col(bd, c);
+  const DevView &v = bd.v[vi];
   const int rows = v.tiles_y;
-  uint32_t *D = s_mem + (size_t)warp * (rows + 1);
+  uint32_t *D = s_mem + (size_t)warp * (max_rows + 1);
   for (int r = lane; r <= rows; r += 32) D[r] = 0;
   __syncwarp();
   uint32_t lo, hi;
-  chunk_range(colb, c, k, ch, lo, hi);
+  chunk_range(colb, c, k, pl.ch[c], lo, hi);
   for (uint32_t i = lo + lane; i < hi; i += 32) {
     const uint32_t key = ck[i], a = pk_a(key);
     atomicAdd(&D[a], 1u);
     atomicAdd(&D[a + pk_h(key)], 0xffffffffu);
   }
   __syncwarp();
-  const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off);
+  const uint32_t base = spine_pos(pl, v, vi, c, 0) + k;
   uint32_t carry = 0;
   for (int r0 = 0; r0 < rows; r0 += 32) {
     const int r = r0 + lane;
     const uint32_t x = warp_incl_scan_u32(r < rows ? D[r] : 0u, lane) + carry;
-    if (r < rows) spine[(size_t)(tile0 + (uint32_t)r * v.tiles_x) * ch + k] = x;
+    if (r < rows) spine[base + (uint32_t)r * pl.vch[vi]] = x;
     carry = __shfl_sync(0xffffffffu, x, 31);
   }
 }
 
-// Writes every row entry of every warp chunk at its sorted position; chunk 0 of each column
-// also writes the column's tile ranges.  Same block / warp layout as k_row_count.  Per group of
-// 32 entries each lane marks its rows in the group's lane masks (W), then writes its rows at
-// the chunk's next position in the row (G) plus its rank among the group's lanes covering the
-// row.  Dynamic shared memory: per warp 2 x rows words (G, W).
-inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * 2 * (size_t)kWarps * (size_t)max_rows; }
+// Writes every row entry of every chunk at its sorted position; chunk 0 of each column also
+// writes the column's tile ranges.  One warp per chunk (as k_row_count).  The warp takes
+// windows of consecutive 32-entry groups whose outputs fit kStage: it counts the window's
+// outputs per row, then per group each lane marks its rows in the group's lane masks (W) and
+// places each of its rows at the row's next staging slot plus its rank among the group's lanes
+// covering the row; the staged window, row-major, then goes out in contiguous row runs (a group
+// that alone exceeds kStage is written directly).  Dynamic shared memory per warp: window
+// counts D and row offsets O (rows + 1 each), next global position G and masks W (rows each),
+// kStage staged values and kStage row tags.
+constexpr int kStage = 512;
+
+__host__ __device__ inline size_t row_scatter_words(int max_rows) { return 4 * (size_t)(max_rows + 1) + kStage + kStage / 2; }
+inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * (size_t)kWarps * row_scatter_words(max_rows); }
 
 __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant__ BatchDesc bd,
                                                           const uint32_t *__restrict__ ck,
                                                           const uint32_t *__restrict__ cv,
-                                                          const uint32_t *__restrict__ colb, int ch, int max_rows,
-                                                          const uint32_t *__restrict__ spine, Count kcnt,
-                                                          const float *__restrict__ depth,
+                                                          const uint32_t *__restrict__ colb, ChunkPlan pl,
+                                                          int max_rows, const uint32_t *__restrict__ spine,
+                                                          Count kcnt, const float *__restrict__ depth,
                                                           uint32_t *__restrict__ vals, uint32_t *__restrict__ ranges,
                                                           uint64_t *__restrict__ keys) {
   extern __shared__ uint32_t s_mem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, bpc = ch / kWarps;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t full = 0xffffffffu, bit = 1u << lane, lt = bit - 1u;
-  const int c = blockIdx.x / bpc, k = (blockIdx.x - c * bpc) * kWarps + warp;
-  const DevView &v = bd.v[view_of_col(bd, c)];
+  const uint32_t wid = blockIdx.x * kWarps + warp;
+  if (wid >= (uint32_t)pl.len[1]) return;
+  const int c = (int)pl.chunk_col[wid];
+  const uint32_t k = wid - pl.co[c], nch = pl.ch[c];
+  const int vi = view_of_col(bd, c);
+  const DevView &v = bd.v[vi];
   const int rows = v.tiles_y;
-  uint32_t *G = s_mem + (size_t)warp * 2 * max_rows, *W = G + max_rows;
+  const int rs = max_rows + 1;
+  uint32_t *D = s_mem + (size_t)warp * row_scatter_words(max_rows), *O = D + rs, *G = O + rs, *W = G + rs;
+  uint32_t *sv = W + rs;
+  uint16_t *sr = reinterpret_cast<uint16_t *>(sv + kStage);
   const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off), part_off = (uint32_t)v.part_off;
   const uint32_t kmax = kcnt.get();  // every position is below K; the tests only guard the stores
-  for (int r = lane; r < rows; r += 32) {
-    const uint32_t tile = tile0 + (uint32_t)r * v.tiles_x;
-    G[r] = spine[(size_t)tile * ch + k];
+  const uint32_t base = spine_pos(pl, v, vi, c, 0), rstride = pl.vch[vi];
+  const uint32_t slen = (uint32_t)pl.len[0];
+  for (int r = lane; r <= rows; r += 32) {
+    D[r] = 0;
+    O[r] = 0;
     W[r] = 0;
-    if (k == 0) {
-      const uint32_t start = spine[(size_t)tile * ch];
-      const uint32_t end = tile + 1 < (uint32_t)bd.total_tiles ? spine[(size_t)(tile + 1) * ch] : kmax;
+    if (r == rows) break;
+    const uint32_t sp = base + (uint32_t)r * rstride;
+    G[r] = spine[sp + k];
+    if (k == 0) {  // the tile's run ends where the next tile's (the next spine position's) begins
+      const uint32_t tile = tile0 + (uint32_t)r * v.tiles_x;
+      const uint32_t start = spine[sp];
+      const uint32_t end = sp + nch < slen ? spine[sp + nch] : kmax;
       if (start < end) {
         ranges[2 * tile] = start;
         ranges[2 * tile + 1] = end;
@@ -680,38 +789,101 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
     }
   }
   __syncwarp();
+  auto emit = [&](uint32_t pos, uint32_t g, uint32_t r) {
+    if (pos >= kmax) return;
+    vals[pos] = g - part_off;
+    if (keys) keys[pos] = ((u64)(tile0 + r * (uint32_t)v.tiles_x) << 32) | (u64)__float_as_uint(depth[g]);
+  };
   uint32_t lo, hi;
-  chunk_range(colb, c, k, ch, lo, hi);
-  for (uint32_t g0 = lo; g0 < hi; g0 += 32) {
-    const uint32_t e = g0 + lane;
-    uint32_t a = 0, b = 0, g = 0;  // rows [a, b) of this lane's entry
-    if (e < hi) {
-      const uint32_t key = ck[e];
-      g = cv[e];
-      a = pk_a(key);
-      b = a + pk_h(key);
-    }
-    for (uint32_t r = a; r < b; ++r) atomicOr(&W[r], bit);
-    __syncwarp();
-    const uint32_t loc = g - part_off;
-    for (uint32_t r = a; r < b; ++r) {
-      const uint32_t pos = G[r] + (uint32_t)__popc(W[r] & lt);
-      if (pos < kmax) {
-        vals[pos] = loc;
-        if (keys) keys[pos] = ((u64)(tile0 + r * (uint32_t)v.tiles_x) << 32) | (u64)__float_as_uint(depth[g]);
+  chunk_range(colb, c, k, nch, lo, hi);
+  uint32_t i = lo;
+  while (i < hi) {
+    // the window [i, j): outputs per row (difference array in D), their total, rows [rmin, rend)
+    uint32_t j = i, tot = 0;
+    int rmin = rows, rend = 0;
+    while (j < hi) {
+      const uint32_t e = j + lane;
+      uint32_t a = 0, b = 0;
+      if (e < hi) {
+        const uint32_t key = ck[e];
+        a = pk_a(key);
+        b = a + pk_h(key);
       }
-    }
-    __syncwarp();
-    const int rmin = (int)__reduce_min_sync(full, b > a ? a : (uint32_t)rows);
-    const int rmax = (int)__reduce_max_sync(full, b);
-    for (int r = rmin + lane; r < rmax; r += 32) {
-      const uint32_t m = W[r];
-      if (m) {
-        G[r] += (uint32_t)__popc(m);
-        W[r] = 0;
+      const uint32_t gs = __reduce_add_sync(full, b - a);
+      if (tot > 0 && tot + gs > (uint32_t)kStage) break;
+      if (b > a) {
+        atomicAdd(&D[a], 1u);
+        atomicAdd(&D[b], 0xffffffffu);
       }
+      rmin = min(rmin, (int)__reduce_min_sync(full, b > a ? a : (uint32_t)rows));
+      rend = max(rend, (int)__reduce_max_sync(full, b));
+      tot += gs;
+      j = hi - j > 32u ? j + 32u : hi;
+      if (tot > (uint32_t)kStage) break;
     }
     __syncwarp();
+    const bool direct = tot > (uint32_t)kStage;
+    {  // counts (D) and first staging slot (O: row-major offsets, or G when direct) per row
+      uint32_t carry = 0, run = 0;
+      for (int r0 = rmin; r0 < rend; r0 += 32) {
+        const int r = r0 + lane;
+        const uint32_t cnt = warp_incl_scan_u32(r < rend ? D[r] : 0u, lane) + carry;
+        const uint32_t ci = warp_incl_scan_u32(r < rend ? cnt : 0u, lane);
+        if (r < rend) {
+          D[r] = cnt;
+          O[r] = direct ? G[r] : run + ci - cnt;
+        }
+        carry = __shfl_sync(full, cnt, 31);
+        run += __shfl_sync(full, ci, 31);
+      }
+      __syncwarp();
+      if (lane == 0) D[rend] = 0;
+      __syncwarp();
+    }
+    for (uint32_t g0 = i; g0 < j; g0 += 32) {
+      const uint32_t e = g0 + lane;
+      uint32_t a = 0, b = 0, g = 0;  // rows [a, b) of this lane's entry
+      if (e < j) {
+        const uint32_t key = ck[e];
+        g = cv[e];
+        a = pk_a(key);
+        b = a + pk_h(key);
+      }
+      for (uint32_t r = a; r < b; ++r) atomicOr(&W[r], bit);
+      __syncwarp();
+      for (uint32_t r = a; r < b; ++r) {
+        const uint32_t q = O[r] + (uint32_t)__popc(W[r] & lt);
+        if (direct) {
+          emit(q, g, r);
+        } else if (q < (uint32_t)kStage) {
+          sv[q] = g;
+          sr[q] = (uint16_t)r;
+        }
+      }
+      __syncwarp();
+      for (int r = rmin + lane; r < rend; r += 32) {
+        const uint32_t m = W[r];
+        if (m) {
+          O[r] += (uint32_t)__popc(m);
+          W[r] = 0;
+        }
+      }
+      __syncwarp();
+    }
+    if (!direct) {  // slot q of row r goes to G[r] + (q - row r's first slot)
+      for (uint32_t q = lane; q < tot; q += 32) {
+        const uint32_t r = sr[q];
+        emit(G[r] + q - (O[r] - D[r]), sv[q], r);
+      }
+      __syncwarp();
+    }
+    for (int r = rmin + lane; r < rend; r += 32) {
+      G[r] += D[r];
+      D[r] = 0;
+      O[r] = 0;
+    }
+    __syncwarp();
+    i = j;
   }
 }
 
@@ -732,12 +904,13 @@ inline uint32_t ceil_div(u64 a, u64 b) { return (uint32_t)((a + b - 1) / b); }
 
 struct Buffers {
   uint32_t *dk[2], *dv[2], *cnt, *offs, *x[3], *spine;
-  uint32_t *colb, *tspine;  // row scatter: column bounds [2 x cols], (tile, chunk) counts [tiles x S]
+  uint32_t *colb, *tspine;  // row scatter: column bounds [2 x cols], (tile, chunk) counts
+  ChunkPlan plan;
   u64 *chunk, *total;       // total[0] = column entries, total[1] = K
 };
 
 // Workspace layout; with ws == nullptr only the size is accumulated.
-Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, size_t *bytes = nullptr) {
+Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, int max_rows, size_t *bytes = nullptr) {
   Arena a{static_cast<char *>(ws), 0};
   Buffers b;
   size_t nn = (size_t)(n > 0 ? n : 1);
@@ -750,10 +923,16 @@ Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, size_t *bytes =
   for (int i = 0; i < 3; ++i) b.x[i] = a.take<uint32_t>(cc);
   size_t spine = 256 * (size_t)ceil_div(maxc, kRTile);
   b.spine = a.take<uint32_t>(spine);
-  const size_t tt = (size_t)(tiles > 0 ? tiles : 1), ncol = (size_t)(cols > 0 ? cols : 1);
-  const size_t tsp = tt * (size_t)row_chunks(cols);
+  const size_t ncol = (size_t)(cols > 0 ? cols : 1);
+  const size_t tsp = plan_spine_words(max_rows, tiles, cols);
   b.colb = a.take<uint32_t>(2 * ncol);
   b.tspine = a.take<uint32_t>(tsp);
+  b.plan.ch = a.take<uint32_t>(ncol);
+  b.plan.co = a.take<uint32_t>(ncol + 1);
+  b.plan.chunk_col = a.take<uint32_t>(kChunkWarps + ncol);
+  b.plan.voff = a.take<uint32_t>(kMaxViews);
+  b.plan.vch = a.take<uint32_t>(kMaxViews);
+  b.plan.len = a.take<u64>(2);
   size_t maxlen = spine > maxc ? spine : maxc;
   if (tsp > maxlen) maxlen = tsp;
   b.chunk = a.take<u64>(ceil_div(maxlen, kTile) + 1);
@@ -762,9 +941,9 @@ Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, size_t *bytes =
   return b;
 }
 
-size_t carve_bytes(int n, int64_t cap, int tiles, int cols) {
+size_t carve_bytes(int n, int64_t cap, int tiles, int cols, int max_rows) {
   size_t bytes = 0;
-  carve(nullptr, n, cap, tiles, cols, &bytes);
+  carve(nullptr, n, cap, tiles, cols, max_rows, &bytes);
   return bytes;
 }
 
@@ -812,7 +991,9 @@ int bits_for(int tiles) {
 
 }  // namespace
 
-size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols) { return carve_bytes(n, cap, tiles, cols); }
+size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols, int max_rows) {
+  return carve_bytes(n, cap, tiles, cols, max_rows);
+}
 
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
@@ -820,7 +1001,9 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
   const int n = bd.total_particles;
   const int tiles = bd.total_tiles;
   const short4 *r4 = reinterpret_cast<const short4 *>(rect);
-  Buffers b = carve(ws, n, cap, tiles, bd.total_cols);
+  int max_rows = 0;
+  for (int v = 0; v < bd.nv; ++v) max_rows = bd.v[v].tiles_y > max_rows ? bd.v[v].tiles_y : max_rows;
+  Buffers b = carve(ws, n, cap, tiles, bd.total_cols, max_rows);
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, s) != cudaSuccess) return UT_ERR_CUDA;
   if (cudaMemsetAsync(b.total, 0, 2 * sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
   if (n > 0) {
@@ -835,8 +1018,6 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
     // and the caller's vals, arranged so that the row stage lands in vals: the row scatter
     // reads the column values from x[2]; the row radix passes end in vals
-    int max_rows = 0;
-    for (int v = 0; v < bd.nv; ++v) max_rows = bd.v[v].tiles_y > max_rows ? bd.v[v].tiles_y : max_rows;
     const bool scatter = max_rows <= kScatterMaxRows && bd.total_cols <= kScatterMaxCols;
     const int cbits = bits_for(bd.total_cols), rbits = bits_for(bd.total_rows);
     const int cp = (cbits + kRadixBits - 1) / kRadixBits, rp = (rbits + kRadixBits - 1) / kRadixBits;
@@ -862,20 +1043,21 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     const Count ck2{b.total + 1, (u64)cap, 0};
     if (scatter) {
       // 3. row entries scattered straight into (tile, depth) order
-      const int ch = row_chunks(bd.total_cols), blocks = bd.total_cols * (ch / kWarps);
+      const int blocks = (kChunkWarps + bd.total_cols + kWarps - 1) / kWarps;
       if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
         return UT_ERR_CUDA;
       k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ck[rc], cc, b.colb);
-      k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ck[rc], b.colb, ch,
-                                                                                       b.tspine);
-      count_launches(2);
-      const u64 tn = (u64)tiles * (u64)ch;
-      scan(b.tspine, b.tspine, Count{nullptr, 0, (uint32_t)tn}, tn, b.chunk, nullptr, s);
+      k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan);
+      k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ck[rc], b.colb, b.plan,
+                                                                                       max_rows, b.tspine);
+      count_launches(3);
+      const u64 tmax = plan_spine_words(max_rows, tiles, bd.total_cols);
+      scan(b.tspine, b.tspine, Count{b.plan.len, tmax, 0}, tmax, b.chunk, nullptr, s);
       const size_t smem = row_scatter_smem(max_rows);
       if (cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
-      k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ck[rc], cv[rc], b.colb, ch, max_rows, b.tspine, ck2, depth,
-                                                   vals, ranges, keys);
+      k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ck[rc], cv[rc], b.colb, b.plan, max_rows, b.tspine, ck2,
+                                                   depth, vals, ranges, keys);
       count_launches(1);
       k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
       count_launches(1);

@@ -38,7 +38,7 @@ ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights
                          float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream);
 
 // Duplicate + sort + ranges over the batch's flattened entries and global tiles.
-size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols);
+size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols, int max_rows);
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                      int64_t *k_out, cudaStream_t stream);

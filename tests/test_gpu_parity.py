@@ -92,9 +92,11 @@ BIN_CASES = [
     (70, 33, 16, 16, 500, 40, 20),
     (37, 29, 8, 8, 300, 12, 12),
     (1000, 600, 16, 16, 20_000, 80, 80),        # > one radix tile of keys, 2 tile passes
-    (4096, 4096, 8, 8, 30_000, 60, 60),         # 262144 tiles -> 3 passes
+    (4096, 4096, 8, 8, 30_000, 60, 60),         # 262144 tiles; 512 tile rows, the most the row scatter takes
     (3840, 2160, 32, 8, 10_000, 200, 40),
     (64, 64, 16, 16, 1, 10, 10),
+    (128, 1200, 64, 1, 3_000, 60, 40),          # 1200 tile rows: rows emitted and radix-sorted (2 passes)
+    (17_000, 64, 1, 64, 2_000, 40, 40),         # 17000 tile columns: rows emitted and radix-sorted
 ]
 
 
