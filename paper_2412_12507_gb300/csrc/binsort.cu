@@ -734,15 +734,17 @@ __global__ void __launch_bounds__(kThreads) k_row_count(const __grid_constant__ 
 // Writes every row entry of every chunk at its sorted position; chunk 0 of each column also
 // writes the column's tile ranges.  One warp per chunk (as k_row_count).  The warp takes
 // windows of consecutive 32-entry groups whose outputs fit kStage: it counts the window's
-// outputs per row, then per group each lane marks its rows in the group's lane masks (W) and
+// outputs per row, then per group each lane marks its rows in the group's lane masks and
 // places each of its rows at the row's next staging slot plus its rank among the group's lanes
 // covering the row; the staged window, row-major, then goes out in contiguous row runs (a group
 // that alone exceeds kStage is written directly).  Dynamic shared memory per warp: window
-// counts D and row offsets O (rows + 1 each), next global position G and masks W (rows each),
-// kStage staged values and kStage row tags.
+// counts D (rows + 1), next global position G (rows), per row {next slot, group lane mask} OW
+// (rows), kStage staged {value, row}.
 constexpr int kStage = 512;
 
-__host__ __device__ inline size_t row_scatter_words(int max_rows) { return 4 * (size_t)(max_rows + 1) + kStage + kStage / 2; }
+__host__ __device__ inline size_t row_scatter_words(int max_rows) {
+  return ((2 * (size_t)max_rows + 2) & ~(size_t)1) + 2 * (size_t)max_rows + 2 * (size_t)kStage;
+}
 inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * (size_t)kWarps * row_scatter_words(max_rows); }
 
 __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant__ BatchDesc bd,
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
                                                           Count kcnt, const float *__restrict__ depth,
                                                           uint32_t *__restrict__ vals, uint32_t *__restrict__ ranges,
                                                           uint64_t *__restrict__ keys) {
-  extern __shared__ uint32_t s_mem[];
+  extern __shared__ uint2 s_mem2[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t full = 0xffffffffu, bit = 1u << lane, lt = bit - 1u;
   const uint32_t wid = blockIdx.x * kWarps + warp;
@@ -763,19 +765,18 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
   const int vi = view_of_col(bd, c);
   const DevView &v = bd.v[vi];
   const int rows = v.tiles_y;
-  const int rs = max_rows + 1;
-  uint32_t *D = s_mem + (size_t)warp * row_scatter_words(max_rows), *O = D + rs, *G = O + rs, *W = G + rs;
-  uint32_t *sv = W + rs;
-  uint16_t *sr = reinterpret_cast<uint16_t *>(sv + kStage);
+  uint32_t *D = reinterpret_cast<uint32_t *>(s_mem2) + (size_t)warp * row_scatter_words(max_rows);
+  uint32_t *G = D + max_rows + 1;
+  uint2 *OW = reinterpret_cast<uint2 *>(D + ((2 * (size_t)max_rows + 2) & ~(size_t)1));  // 8-byte aligned
+  uint2 *st = OW + max_rows;
   const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off), part_off = (uint32_t)v.part_off;
   const uint32_t kmax = kcnt.get();  // every position is below K; the tests only guard the stores
   const uint32_t base = spine_pos(pl, v, vi, c, 0), rstride = pl.vch[vi];
   const uint32_t slen = (uint32_t)pl.len[0];
   for (int r = lane; r <= rows; r += 32) {
     D[r] = 0;
-    O[r] = 0;
-    W[r] = 0;
     if (r == rows) break;
+    OW[r] = make_uint2(0u, 0u);
     const uint32_t sp = base + (uint32_t)r * rstride;
     G[r] = spine[sp + k];
     if (k == 0) {  // the tile's run ends where the next tile's (the next spine position's) begins
@@ -823,7 +824,7 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
     }
     __syncwarp();
     const bool direct = tot > (uint32_t)kStage;
-    {  // counts (D) and first staging slot (O: row-major offsets, or G when direct) per row
+    {  // counts (D) and each row's first slot (row-major staging offsets, or G when direct)
       uint32_t carry = 0, run = 0;
       for (int r0 = rmin; r0 < rend; r0 += 32) {
         const int r = r0 + lane;
@@ -831,7 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
         const uint32_t ci = warp_incl_scan_u32(r < rend ? cnt : 0u, lane);
         if (r < rend) {
           D[r] = cnt;
-          O[r] = direct ? G[r] : run + ci - cnt;
+          OW[r].x = direct ? G[r] : run + ci - cnt;
         }
         carry = __shfl_sync(full, cnt, 31);
         run += __shfl_sync(full, ci, 31);
@@ -849,38 +850,35 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
         a = pk_a(key);
         b = a + pk_h(key);
       }
-      for (uint32_t r = a; r < b; ++r) atomicOr(&W[r], bit);
+      for (uint32_t r = a; r < b; ++r) atomicOr(&OW[r].y, bit);
       __syncwarp();
       for (uint32_t r = a; r < b; ++r) {
-        const uint32_t q = O[r] + (uint32_t)__popc(W[r] & lt);
-        if (direct) {
-          emit(q, g, r);
-        } else if (q < (uint32_t)kStage) {
-          sv[q] = g;
-          sr[q] = (uint16_t)r;
-        }
+        const uint2 ow = OW[r];
+        const uint32_t q = ow.x + (uint32_t)__popc(ow.y & lt);
+        if (direct) emit(q, g, r);
+        else if (q < (uint32_t)kStage) st[q] = make_uint2(g, r);
       }
       __syncwarp();
       for (int r = rmin + lane; r < rend; r += 32) {
-        const uint32_t m = W[r];
-        if (m) {
-          O[r] += (uint32_t)__popc(m);
-          W[r] = 0;
-        }
+        const uint2 ow = OW[r];
+        if (ow.y) OW[r] = make_uint2(ow.x + (uint32_t)__popc(ow.y), 0u);
       }
       __syncwarp();
     }
-    if (!direct) {  // slot q of row r goes to G[r] + (q - row r's first slot)
+    if (!direct) {
+      // row r's slots [first, first + D[r]) go to G[r]...: shift = G[r] - first slot
+      for (int r = rmin + lane; r < rend; r += 32) OW[r].x = G[r] - (OW[r].x - D[r]);
+      __syncwarp();
       for (uint32_t q = lane; q < tot; q += 32) {
-        const uint32_t r = sr[q];
-        emit(G[r] + q - (O[r] - D[r]), sv[q], r);
+        const uint2 e = st[q];
+        emit(OW[e.y].x + q, e.x, e.y);
       }
       __syncwarp();
     }
     for (int r = rmin + lane; r < rend; r += 32) {
       G[r] += D[r];
       D[r] = 0;
-      O[r] = 0;
+      OW[r] = make_uint2(0u, 0u);
     }
     __syncwarp();
     i = j;
