@@ -544,6 +544,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     n_eval, n_blend = (int(v) for v in stats.cpu())
     n = scene.n
+    rc = r.proj.rect.long()
+    M_cols = int(torch.where(r.proj.ntiles > 0, rc[:, 2] // op["tile_w"] - rc[:, 0] // op["tile_w"] + 1,
+                             torch.zeros_like(rc[:, 0])).sum())  # column entries of the binning
     hbm, sm_max, src = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
@@ -551,7 +554,9 @@ def run_ours(args):
     F_EVAL, F_BLEND_FWD, F_BLEND_BWD, F_PIX = 40, 110, 230, 120
     work = {
         "ut_project": ("hbm", 80.0 * n / 1e9, "GB"),
-        "bin_and_sort": ("hbm", (44.0 * K + 8.0 * n) / 1e9, "GB"),
+        # binning: the K values written once, 16 B of projection output read per particle, the
+        # column list (8 B per column entry) written and read once
+        "bin_and_sort": ("hbm", (4.0 * K + 16.0 * n + 16.0 * M_cols) / 1e9, "GB"),
         "composite_forward": ("alu", (F_EVAL * n_eval + F_BLEND_FWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
         "composite_backward": ("alu", (F_EVAL * n_eval + F_BLEND_BWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
     }

@@ -731,21 +731,144 @@ __global__ void __launch_bounds__(kThreads) k_row_count(const __grid_constant__ 
   }
 }
 
-// Writes every row entry of every chunk at its sorted position; chunk 0 of each column also
-// writes the column's tile ranges.  One warp per chunk (as k_row_count).  The warp takes
-// windows of consecutive 32-entry groups whose outputs fit kStage: it counts the window's
-// outputs per row, then per group each lane marks its rows in the group's lane masks and
-// places each of its rows at the row's next staging slot plus its rank among the group's lanes
-// covering the row; the staged window, row-major, then goes out in contiguous row runs (a group
-// that alone exceeds kStage is written directly).  Dynamic shared memory per warp: window
-// counts D (rows + 1), next global position G (rows), per row {next slot, group lane mask} OW
-// (rows), kStage staged {value, row}.
+// Stable expansion of a warp's run of entries [lo, hi) — each covering the bins [a, b) — into
+// (entry, bin) outputs at each bin's next output position G[bin] (the row scatter's core).  The
+// warp takes windows of consecutive 32-entry groups whose outputs fit kStage: it counts the
+// window's outputs per bin, then per group each lane marks its bins in the group's lane masks
+// and places each of its bins at the bin's next staging slot plus its rank among the group's
+// lanes covering the bin; the staged window, bin-major, then goes out in contiguous runs (a
+// group that alone exceeds kStage is written directly).  Per-warp shared memory: D (bins + 1)
+// window counts, G (bins) next global positions, OW (bins) {next slot, group lane mask}, st
+// (kStage) staged outputs.  The policy P supplies load(e, a, b, x, y) (bins and two payload
+// words of entry e), stage(x, y, a, bin) (the staged form of one output), bin_of(staged) and
+// emit(pos, staged).
 constexpr int kStage = 512;
 
-__host__ __device__ inline size_t row_scatter_words(int max_rows) {
-  return ((2 * (size_t)max_rows + 2) & ~(size_t)1) + 2 * (size_t)max_rows + 2 * (size_t)kStage;
+__host__ __device__ inline size_t scatter_words(int bins) {
+  return ((2 * (size_t)bins + 2) & ~(size_t)1) + 2 * (size_t)bins + 2 * (size_t)kStage;
 }
-inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * (size_t)kWarps * row_scatter_words(max_rows); }
+
+struct ScatterSmem {
+  uint32_t *D, *G;
+  uint2 *OW, *st;
+  __device__ ScatterSmem(uint32_t *base, int bins) {
+    D = base;
+    G = D + bins + 1;
+    OW = reinterpret_cast<uint2 *>(D + ((2 * (size_t)bins + 2) & ~(size_t)1));  // 8-byte aligned
+    st = OW + bins;
+  }
+};
+
+template <class P>
+__device__ __forceinline__ void scatter_windows(const P &pol, uint32_t lo, uint32_t hi, int nbins, const ScatterSmem &m,
+                                                int lane) {
+  const uint32_t full = 0xffffffffu, bit = 1u << lane, lt = bit - 1u;
+  uint32_t *D = m.D, *G = m.G;
+  uint2 *OW = m.OW, *st = m.st;
+  uint32_t i = lo;
+  while (i < hi) {
+    // the window [i, j): outputs per bin (difference array in D), their total, bins [bmin, bend)
+    uint32_t j = i, tot = 0;
+    int bmin = nbins, bend = 0;
+    while (j < hi) {
+      uint32_t a = 0, b = 0, x, y;
+      if (j + lane < hi) pol.load(j + lane, a, b, x, y);
+      const uint32_t gs = __reduce_add_sync(full, b - a);
+      if (tot > 0 && tot + gs > (uint32_t)kStage) break;
+      if (b > a) {
+        atomicAdd(&D[a], 1u);
+        atomicAdd(&D[b], 0xffffffffu);
+      }
+      bmin = min(bmin, (int)__reduce_min_sync(full, b > a ? a : (uint32_t)nbins));
+      bend = max(bend, (int)__reduce_max_sync(full, b));
+      tot += gs;
+      j = hi - j > 32u ? j + 32u : hi;
+      if (tot > (uint32_t)kStage) break;
+    }
+    __syncwarp();
+    const bool direct = tot > (uint32_t)kStage;
+    {  // counts (D) and each bin's first slot (bin-major staging offsets, or G when direct)
+      uint32_t carry = 0, run = 0;
+      for (int r0 = bmin; r0 < bend; r0 += 32) {
+        const int r = r0 + lane;
+        const uint32_t cnt = warp_incl_scan_u32(r < bend ? D[r] : 0u, lane) + carry;
+        const uint32_t ci = warp_incl_scan_u32(r < bend ? cnt : 0u, lane);
+        if (r < bend) {
+          D[r] = cnt;
+          OW[r].x = direct ? G[r] : run + ci - cnt;
+        }
+        carry = __shfl_sync(full, cnt, 31);
+        run += __shfl_sync(full, ci, 31);
+      }
+      __syncwarp();
+      if (lane == 0) D[bend] = 0;
+      __syncwarp();
+    }
+    for (uint32_t g0 = i; g0 < j; g0 += 32) {
+      uint32_t a = 0, b = 0, x = 0, y = 0;  // bins [a, b) of this lane's entry
+      if (g0 + lane < j) pol.load(g0 + lane, a, b, x, y);
+      for (uint32_t r = a; r < b; ++r) atomicOr(&OW[r].y, bit);
+      __syncwarp();
+      for (uint32_t r = a; r < b; ++r) {
+        const uint2 ow = OW[r];
+        const uint32_t q = ow.x + (uint32_t)__popc(ow.y & lt);
+        if (direct) pol.emit(q, pol.stage(x, y, a, r));
+        else if (q < (uint32_t)kStage) st[q] = pol.stage(x, y, a, r);
+      }
+      __syncwarp();
+      for (int r = bmin + lane; r < bend; r += 32) {
+        const uint2 ow = OW[r];
+        if (ow.y) OW[r] = make_uint2(ow.x + (uint32_t)__popc(ow.y), 0u);
+      }
+      __syncwarp();
+    }
+    if (!direct) {
+      // bin r's slots [first, first + D[r]) go to G[r]...: shift = G[r] - first slot
+      for (int r = bmin + lane; r < bend; r += 32) OW[r].x = G[r] - (OW[r].x - D[r]);
+      __syncwarp();
+      for (uint32_t q = lane; q < tot; q += 32) {
+        const uint2 e = st[q];
+        pol.emit(OW[pol.bin_of(e)].x + q, e);
+      }
+      __syncwarp();
+    }
+    for (int r = bmin + lane; r < bend; r += 32) {
+      G[r] += D[r];
+      D[r] = 0;
+      OW[r] = make_uint2(0u, 0u);
+    }
+    __syncwarp();
+    i = j;
+  }
+}
+
+// Row stage: entries = column entries (packed keys ck, flattened particle cv), bins = the
+// view's tile rows, output = the particle's index within its scene (and the optional key).
+struct RowPolicy {
+  const uint32_t *ck, *cv;
+  uint32_t *vals;
+  uint64_t *keys;
+  const float *depth;
+  uint32_t part_off, tile0, tiles_x, kmax;
+  __device__ void load(uint32_t e, uint32_t &a, uint32_t &b, uint32_t &x, uint32_t &y) const {
+    const uint32_t key = ck[e];
+    x = cv[e];
+    y = 0;
+    a = pk_a(key);
+    b = a + pk_h(key);
+  }
+  __device__ uint2 stage(uint32_t x, uint32_t, uint32_t, uint32_t r) const { return make_uint2(x, r); }
+  __device__ uint32_t bin_of(uint2 s) const { return s.y; }
+  __device__ void emit(uint32_t pos, uint2 s) const {
+    if (pos >= kmax) return;  // every position is below K; the tests only guard the stores
+    vals[pos] = s.x - part_off;
+    if (keys) keys[pos] = ((u64)(tile0 + s.y * tiles_x) << 32) | (u64)__float_as_uint(depth[s.x]);
+  }
+};
+
+// Writes every row entry of every chunk at its sorted position (one warp per chunk, as
+// k_row_count); chunk 0 of each column also writes the column's tile ranges.
+inline size_t row_scatter_smem(int max_rows) { return sizeof(uint32_t) * (size_t)kWarps * scatter_words(max_rows); }
 
 __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant__ BatchDesc bd,
                                                           const uint32_t *__restrict__ ck,
@@ -757,7 +880,6 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
                                                           uint64_t *__restrict__ keys) {
   extern __shared__ uint2 s_mem2[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t full = 0xffffffffu, bit = 1u << lane, lt = bit - 1u;
   const uint32_t wid = blockIdx.x * kWarps + warp;
   if (wid >= (uint32_t)pl.len[1]) return;
   const int c = (int)pl.chunk_col[wid];
@@ -765,20 +887,17 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
   const int vi = view_of_col(bd, c);
   const DevView &v = bd.v[vi];
   const int rows = v.tiles_y;
-  uint32_t *D = reinterpret_cast<uint32_t *>(s_mem2) + (size_t)warp * row_scatter_words(max_rows);
-  uint32_t *G = D + max_rows + 1;
-  uint2 *OW = reinterpret_cast<uint2 *>(D + ((2 * (size_t)max_rows + 2) & ~(size_t)1));  // 8-byte aligned
-  uint2 *st = OW + max_rows;
-  const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off), part_off = (uint32_t)v.part_off;
-  const uint32_t kmax = kcnt.get();  // every position is below K; the tests only guard the stores
+  const ScatterSmem m(reinterpret_cast<uint32_t *>(s_mem2) + (size_t)warp * scatter_words(max_rows), max_rows);
+  const uint32_t tile0 = (uint32_t)v.tile_off + (uint32_t)(c - v.col_off);
+  const uint32_t kmax = kcnt.get();
   const uint32_t base = spine_pos(pl, v, vi, c, 0), rstride = pl.vch[vi];
   const uint32_t slen = (uint32_t)pl.len[0];
   for (int r = lane; r <= rows; r += 32) {
-    D[r] = 0;
+    m.D[r] = 0;
     if (r == rows) break;
-    OW[r] = make_uint2(0u, 0u);
+    m.OW[r] = make_uint2(0u, 0u);
     const uint32_t sp = base + (uint32_t)r * rstride;
-    G[r] = spine[sp + k];
+    m.G[r] = spine[sp + k];
     if (k == 0) {  // the tile's run ends where the next tile's (the next spine position's) begins
       const uint32_t tile = tile0 + (uint32_t)r * v.tiles_x;
       const uint32_t start = spine[sp];
@@ -790,99 +909,10 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
     }
   }
   __syncwarp();
-  auto emit = [&](uint32_t pos, uint32_t g, uint32_t r) {
-    if (pos >= kmax) return;
-    vals[pos] = g - part_off;
-    if (keys) keys[pos] = ((u64)(tile0 + r * (uint32_t)v.tiles_x) << 32) | (u64)__float_as_uint(depth[g]);
-  };
   uint32_t lo, hi;
   chunk_range(colb, c, k, nch, lo, hi);
-  uint32_t i = lo;
-  while (i < hi) {
-    // the window [i, j): outputs per row (difference array in D), their total, rows [rmin, rend)
-    uint32_t j = i, tot = 0;
-    int rmin = rows, rend = 0;
-    while (j < hi) {
-      const uint32_t e = j + lane;
-      uint32_t a = 0, b = 0;
-      if (e < hi) {
-        const uint32_t key = ck[e];
-        a = pk_a(key);
-        b = a + pk_h(key);
-      }
-      const uint32_t gs = __reduce_add_sync(full, b - a);
-      if (tot > 0 && tot + gs > (uint32_t)kStage) break;
-      if (b > a) {
-        atomicAdd(&D[a], 1u);
-        atomicAdd(&D[b], 0xffffffffu);
-      }
-      rmin = min(rmin, (int)__reduce_min_sync(full, b > a ? a : (uint32_t)rows));
-      rend = max(rend, (int)__reduce_max_sync(full, b));
-      tot += gs;
-      j = hi - j > 32u ? j + 32u : hi;
-      if (tot > (uint32_t)kStage) break;
-    }
-    __syncwarp();
-    const bool direct = tot > (uint32_t)kStage;
-    {  // counts (D) and each row's first slot (row-major staging offsets, or G when direct)
-      uint32_t carry = 0, run = 0;
-      for (int r0 = rmin; r0 < rend; r0 += 32) {
-        const int r = r0 + lane;
-        const uint32_t cnt = warp_incl_scan_u32(r < rend ? D[r] : 0u, lane) + carry;
-        const uint32_t ci = warp_incl_scan_u32(r < rend ? cnt : 0u, lane);
-        if (r < rend) {
-          D[r] = cnt;
-          OW[r].x = direct ? G[r] : run + ci - cnt;
-        }
-        carry = __shfl_sync(full, cnt, 31);
-        run += __shfl_sync(full, ci, 31);
-      }
-      __syncwarp();
-      if (lane == 0) D[rend] = 0;
-      __syncwarp();
-    }
-    for (uint32_t g0 = i; g0 < j; g0 += 32) {
-      const uint32_t e = g0 + lane;
-      uint32_t a = 0, b = 0, g = 0;  // rows [a, b) of this lane's entry
-      if (e < j) {
-        const uint32_t key = ck[e];
-        g = cv[e];
-        a = pk_a(key);
-        b = a + pk_h(key);
-      }
-      for (uint32_t r = a; r < b; ++r) atomicOr(&OW[r].y, bit);
-      __syncwarp();
-      for (uint32_t r = a; r < b; ++r) {
-        const uint2 ow = OW[r];
-        const uint32_t q = ow.x + (uint32_t)__popc(ow.y & lt);
-        if (direct) emit(q, g, r);
-        else if (q < (uint32_t)kStage) st[q] = make_uint2(g, r);
-      }
-      __syncwarp();
-      for (int r = rmin + lane; r < rend; r += 32) {
-        const uint2 ow = OW[r];
-        if (ow.y) OW[r] = make_uint2(ow.x + (uint32_t)__popc(ow.y), 0u);
-      }
-      __syncwarp();
-    }
-    if (!direct) {
-      // row r's slots [first, first + D[r]) go to G[r]...: shift = G[r] - first slot
-      for (int r = rmin + lane; r < rend; r += 32) OW[r].x = G[r] - (OW[r].x - D[r]);
-      __syncwarp();
-      for (uint32_t q = lane; q < tot; q += 32) {
-        const uint2 e = st[q];
-        emit(OW[e.y].x + q, e.x, e.y);
-      }
-      __syncwarp();
-    }
-    for (int r = rmin + lane; r < rend; r += 32) {
-      G[r] += D[r];
-      D[r] = 0;
-      OW[r] = make_uint2(0u, 0u);
-    }
-    __syncwarp();
-    i = j;
-  }
+  const RowPolicy pol{ck, cv, vals, keys, depth, (uint32_t)v.part_off, tile0, (uint32_t)v.tiles_x, kmax};
+  scatter_windows(pol, lo, hi, rows, m, lane);
 }
 
 // ---------------------------------------------------------------- host orchestration
@@ -1041,12 +1071,13 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     const Count ck2{b.total + 1, (u64)cap, 0};
     if (scatter) {
       // 3. row entries scattered straight into (tile, depth) order
+      const uint32_t *ckc = ck[rc], *cvc = cv[rc];
       const int blocks = (kChunkWarps + bd.total_cols + kWarps - 1) / kWarps;
       if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
         return UT_ERR_CUDA;
-      k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ck[rc], cc, b.colb);
+      k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ckc, cc, b.colb);
       k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan);
-      k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ck[rc], b.colb, b.plan,
+      k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ckc, b.colb, b.plan,
                                                                                        max_rows, b.tspine);
       count_launches(3);
       const u64 tmax = plan_spine_words(max_rows, tiles, bd.total_cols);
@@ -1054,8 +1085,8 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
       const size_t smem = row_scatter_smem(max_rows);
       if (cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
-      k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ck[rc], cv[rc], b.colb, b.plan, max_rows, b.tspine, ck2,
-                                                   depth, vals, ranges, keys);
+      k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ckc, cvc, b.colb, b.plan, max_rows, b.tspine, ck2, depth,
+                                                   vals, ranges, keys);
       count_launches(1);
       k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
       count_launches(1);

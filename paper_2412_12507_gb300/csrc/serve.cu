@@ -268,7 +268,25 @@ bool schedule(ut_server *s) {
       return true;
     }
     size_t off;
-    if (!s->arena.alloc(need + 256, &off)) continue;
+    if (!s->arena.alloc(need + 256, &off)) {
+      if (nb > 1) continue;
+      // one view whose estimated keys do not fit: run it with the largest capacity the arena can
+      // hold now (an overflow re-runs it with the observed count); the estimate may be inflated
+      const size_t avail = s->arena.largest();
+      int64_t lo = 0, hi = capacity;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        const size_t nm = ut_batch_workspace_size(s->scenes.data(), (int)s->scenes.size(), views.data(), 1,
+                                                  &s->cfg.options, mid);
+        if (nm != 0 && ((nm + 256 + 255) & ~(size_t)255) <= avail) lo = mid;
+        else hi = mid - 1;
+      }
+      if (lo < 1024) break;
+      capacity = lo;
+      need = ut_batch_workspace_size(s->scenes.data(), (int)s->scenes.size(), views.data(), 1, &s->cfg.options,
+                                     capacity);
+      if (need == 0 || !s->arena.alloc(need + 256, &off)) break;
+    }
     sl.ws_off = off;
     sl.ws_bytes = need + 256;
     sl.cap = capacity;

@@ -99,6 +99,26 @@ def test_first_request_of_a_class_may_overflow_and_is_retried():
         srv.close()
 
 
+def test_overestimated_request_runs_with_the_capacity_the_arena_holds():
+    """A request whose estimated key count needs more scratch than the arena holds still runs
+    (with the largest capacity that fits; an overflow would re-run it with the observed count)."""
+    op = synth.options()
+    scenes = [render.Scene.from_arrays(synth.scene_cube(50, 53, log_s=(-3.0, 0.3), deg=3, lo=(-1, -1, -1),
+                                                        hi=(1, 1, 1)))]
+    cam = synth.orbit_cameras(5, [("pinhole", 256, 256, 0)])[0]
+    # first estimate: 2 keys / pixel x 65536 pixels x headroom 8 = ~1M keys, ~25 MB of scratch
+    srv = render.Server(scenes, op, arena_bytes=8 << 20, key_headroom=8.0)
+    try:
+        rid = srv.submit(0, cam)
+        rgb, alpha, _ = srv.wait(rid, 60_000)
+        rgb_p, a_p = _plain(scenes[0], cam, op)
+        assert torch.max(torch.abs(rgb - rgb_p)).item() <= RGB_TOL
+        assert torch.max(torch.abs(alpha - a_p)).item() <= RGB_TOL
+        srv.release(rid)
+    finally:
+        srv.close()
+
+
 def test_request_larger_than_the_arena_is_rejected():
     op = synth.options()
     scenes = [render.Scene.from_arrays(_scenes()[0])]
