@@ -249,6 +249,83 @@ class Renderer:
         return graph, frame, grads
 
 
+_SCENE_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+class FramePipeline:
+    """Renders a stream of frames whose particle parameters arrive in host memory (pinned, for
+    asynchronous copies), overlapping each frame's host-to-device copy and image read-back with
+    the neighbouring frames' rendering.
+
+    Two device copies of the scene, each with its own renderer (workspaces, frame) and its
+    captured forward step, alternate: frame i's parameters are copied in on a copy stream while
+    frame i - 1 renders on the current stream, and frame i - 1's image is copied out on a
+    read-back stream while frame i renders.  `submit` returns the pinned [4][H][W] buffer (rgb,
+    alpha) that receives the frame; it holds that frame once `done(buffer)` has been
+    synchronised and until the submit two frames later.  The key capacity is sized on the
+    first frame (one synchronisation in the constructor); a later frame with more keys than it
+    renders black (its count is in renderers[b].binning.k_dev)."""
+
+    def __init__(self, cam: dict, opts: dict | None, first: dict, sh_degree: int, headroom: float = 1.25):
+        n = int(first["means"].numel() // 3)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.bufs = []
+        for _ in range(2):
+            sc = Scene(torch.empty((n, 3), dtype=torch.float32, device=dev),
+                       torch.empty((n, 3), dtype=torch.float32, device=dev),
+                       torch.empty((n, 4), dtype=torch.float32, device=dev),
+                       torch.empty(n, dtype=torch.float32, device=dev),
+                       torch.empty((n, (sh_degree + 1) ** 2, 3), dtype=torch.float32, device=dev), sh_degree)
+            for k in _SCENE_FIELDS:
+                getattr(sc, k).copy_(first[k].view_as(getattr(sc, k)))
+            self.bufs.append(sc)
+        probe = Renderer(cam, opts)
+        probe.forward(self.bufs[0])
+        cap = int(probe.binning.count() * headroom) + 1024
+        del probe
+        self.renderers = [Renderer(cam, opts, capacity=cap) for _ in range(2)]
+        self.graphs = [r.capture(b)[:2] for r, b in zip(self.renderers, self.bufs)]
+        H, W = int(cam["height"]), int(cam["width"])
+        self.host_out = [torch.empty((4, H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.copy_stream, self.read_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.rendered = [torch.cuda.Event() for _ in range(2)]
+        self.freed = [torch.cuda.Event() for _ in range(2)]
+        self.i = 0
+        torch.cuda.synchronize()
+
+    def submit(self, host: dict) -> torch.Tensor:
+        b = self.i % 2
+        self.i += 1
+        sc, cs = self.bufs[b], torch.cuda.current_stream()
+        self.copy_stream.wait_event(self.freed[b])  # frame i - 2 no longer reads this buffer
+        with torch.cuda.stream(self.copy_stream):
+            for k in _SCENE_FIELDS:
+                getattr(sc, k).copy_(host[k].view_as(getattr(sc, k)), non_blocking=True)
+            self.copied[b].record(self.copy_stream)
+        cs.wait_event(self.copied[b])
+        graph, frame = self.graphs[b]
+        graph.replay()
+        self.rendered[b].record(cs)
+        out = self.host_out[b]
+        self.read_stream.wait_event(self.rendered[b])
+        with torch.cuda.stream(self.read_stream):
+            out[:3].copy_(frame.rgb, non_blocking=True)
+            out[3].copy_(frame.alpha, non_blocking=True)
+            self.freed[b].record(self.read_stream)
+        return out
+
+    def done(self, out: torch.Tensor) -> torch.cuda.Event:
+        """The event after which `out` (a buffer submit returned) holds its frame."""
+        return self.freed[0] if out is self.host_out[0] else self.freed[1]
+
+    def join(self, stream: torch.cuda.Stream | None = None):
+        """Makes `stream` (default: the current one) wait for every copy submitted so far."""
+        s = stream or torch.cuda.current_stream()
+        s.wait_stream(self.copy_stream)
+        s.wait_stream(self.read_stream)
+
+
 class RenderFunction(torch.autograd.Function):
     """torch.autograd.Function over the C ABI: (means, log_scales, quats, logits, sh) -> (rgb, alpha)."""
 

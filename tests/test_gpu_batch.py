@@ -237,3 +237,30 @@ def test_captured_step_replays_bit_identically_and_follows_new_inputs():
     torch.cuda.synchronize()
     assert torch.equal(moved, ref.alpha)
     assert not torch.equal(moved, eager_f["alpha"])
+
+
+def test_frame_pipeline_matches_plain_renders_of_each_frame():
+    """render.FramePipeline: frames whose parameters arrive from pinned host memory, rendered
+    with overlapped copies, give exactly the images of plain renders of the same parameters."""
+    sc_np = dict(_scenes()[1])
+    cam = _cams()[1][1]
+    op = synth.options()
+    fields = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    frames = []
+    for f in range(4):
+        d = {k: np.array(sc_np[k], np.float32, copy=True) for k in fields}
+        d["opacity_logits"] = d["opacity_logits"] - 0.3 * f
+        d["means"] = d["means"] + np.float32(0.01 * f)
+        frames.append({k: torch.as_tensor(v).pin_memory() for k, v in d.items()})
+    pipe = render.FramePipeline(cam, op, frames[0], sc_np["sh_degree"])
+    got = []
+    for fr in frames:
+        out = pipe.submit(fr)
+        pipe.done(out).synchronize()
+        got.append(out.clone())
+    for fr, img in zip(frames, got):
+        scene = render.Scene.from_arrays(dict({k: v.numpy() for k, v in fr.items()}, sh_degree=sc_np["sh_degree"]))
+        f = render.Renderer(cam, op, capacity=1 << 12).forward(scene)
+        torch.cuda.synchronize()
+        assert torch.equal(img[:3], f.rgb.cpu())
+        assert torch.equal(img[3], f.alpha.cpu())
