@@ -550,8 +550,11 @@ def run_ours(args):
     hbm, sm_max, src = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-    # per-evaluation / per-blend FP32 operation counts of the compositing arithmetic (see the design notes)
-    F_EVAL, F_BLEND_FWD, F_BLEND_BWD, F_PIX = 40, 110, 230, 120
+    # per-evaluation / per-blend FP32 operation counts of the compositing arithmetic, term by
+    # term in the design notes; a rolling-shutter view adds the per-pixel origin's canonical
+    # image M o - M mu to every evaluation (9 FMA + 3 subtractions)
+    F_EVAL = 40 + (21 if cam.get("rolling_shutter", 0) else 0)
+    F_BLEND_FWD, F_BLEND_BWD, F_PIX = 110, 275, 120
     work = {
         "ut_project": ("hbm", 80.0 * n / 1e9, "GB"),
         # binning: the K values written once, 16 B of projection output read per particle, the
