@@ -95,6 +95,8 @@ BIN_CASES = [
     (4096, 4096, 8, 8, 30_000, 60, 60),         # 262144 tiles; 512 tile rows, the most the row scatter takes
     (3840, 2160, 32, 8, 10_000, 200, 40),
     (64, 64, 16, 16, 1, 10, 10),
+    (256, 2048, 16, 4, 3_000, 40, 400),         # tall rects (up to 100 tile rows): scatter groups past the window
+    (512, 512, 32, 8, 20_000, 20, 6),           # one or two tile rows per entry: windows of many groups
     (128, 1200, 64, 1, 3_000, 60, 40),          # 1200 tile rows: rows emitted and radix-sorted (2 passes)
     (17_000, 64, 1, 64, 2_000, 40, 40),         # 17000 tile columns: rows emitted and radix-sorted
 ]
