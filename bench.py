@@ -458,10 +458,13 @@ def run_ours(args):
     K = r.binning.count()
     r.capacity = int(K * 1.05) + 1024
     r.binning = None
-    r.forward(scene)
+    frame0 = r.forward(scene)
+    # upstream gradient of the training step's loss L = mean((rgb - target)^2) against a seeded
+    # U(0, 1) target, taken at the rendered image (fixed over the timed steps; no alpha term)
     rng = np.random.default_rng(77)
-    d_rgb = torch.as_tensor(rng.standard_normal((3, H, W)).astype(np.float32) / P).to(dev)
-    d_alpha = torch.as_tensor(rng.standard_normal((H, W)).astype(np.float32) / P).to(dev)
+    target = torch.as_tensor(rng.uniform(0.0, 1.0, (3, H, W)).astype(np.float32)).to(dev)
+    d_rgb = (2.0 / (3 * P)) * (frame0.rgb - target)
+    d_alpha = torch.zeros((H, W), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def fwd_eager():

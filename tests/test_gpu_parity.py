@@ -291,6 +291,8 @@ def _grad_compare(got, ref, name, rel=1e-3):
 
 GRAD_CASES = {
     "rs_fisheye_crop": lambda: synth.rs_fisheye(n=2000, width=320, height=180),
+    # the headline camera (1920x1080 rolling-shutter fisheye) with 2000 Gaussians of its scene
+    "rs_fisheye_1080p_2k": lambda: synth.rs_fisheye(n=2000),
     "pinhole_deg2": lambda: dict(scene=synth.scene_cube(1500, 13, deg=2, log_s=(-2.8, 0.4)),
                                  camera=synth.camera("pinhole", 96, 80, fx=90.0, fy=90.0),
                                  options=synth.options()),
