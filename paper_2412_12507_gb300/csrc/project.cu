@@ -21,7 +21,7 @@ constexpr int kWarps = 8;
 // baseline: the mean projects through g and the covariance through the Jacobian of g at the
 // camera-space mean (under a rolling shutter, at the pose of the mean's own shutter time).
 template <bool EWA>
-__global__ void __launch_bounds__(kWarps * 32) k_project(const __grid_constant__ BatchDesc bd, DevOpts op, UTWeights w,
+__global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constant__ BatchDesc bd, DevOpts op, UTWeights w,
                                                          float2 *__restrict__ mean2d, float *__restrict__ cov2d,
                                                          float *__restrict__ depth, short4 *__restrict__ rect,
                                                          uint32_t *__restrict__ ntiles) {
