@@ -257,20 +257,23 @@ class FramePipeline:
     asynchronous copies), overlapping each frame's host-to-device copy and image read-back with
     the neighbouring frames' rendering.
 
-    Two device copies of the scene, each with its own renderer (workspaces, frame) and its
-    captured forward step, alternate: frame i's parameters are copied in on a copy stream while
-    frame i - 1 renders on the current stream, and frame i - 1's image is copied out on a
-    read-back stream while frame i renders.  `submit` returns the pinned [4][H][W] buffer (rgb,
-    alpha) that receives the frame; it holds that frame once `done(buffer)` has been
-    synchronised and until the submit two frames later.  The key capacity is sized on the
-    first frame (one synchronisation in the constructor); a later frame with more keys than it
-    renders black (its count is in renderers[b].binning.k_dev)."""
+    `depth` device copies of the scene, each with its own renderer (workspaces, frame) and its
+    captured forward step, rotate: frame i's parameters are copied in on a copy stream while
+    earlier frames render on the current stream, and each finished image is copied out on a
+    read-back stream while the next frame renders; frame i's copy waits only for the read-back
+    of frame i - depth.  `submit` returns the pinned [4][H][W] buffer (rgb, alpha) that
+    receives the frame; it holds that frame once `done(buffer)` has been synchronised and until
+    the submit `depth` frames later.  The key capacity is sized on the first frame (one
+    synchronisation in the constructor); a later frame with more keys than it renders black
+    (its count is in renderers[b].binning.k_dev)."""
 
-    def __init__(self, cam: dict, opts: dict | None, first: dict, sh_degree: int, headroom: float = 1.25):
+    def __init__(self, cam: dict, opts: dict | None, first: dict, sh_degree: int, headroom: float = 1.25,
+                 depth: int = 3):
         n = int(first["means"].numel() // 3)
         dev = torch.device("cuda", torch.cuda.current_device())
+        self.depth = int(depth)
         self.bufs = []
-        for _ in range(2):
+        for _ in range(self.depth):
             sc = Scene(torch.empty((n, 3), dtype=torch.float32, device=dev),
                        torch.empty((n, 3), dtype=torch.float32, device=dev),
                        torch.empty((n, 4), dtype=torch.float32, device=dev),
@@ -283,22 +286,22 @@ class FramePipeline:
         probe.forward(self.bufs[0])
         cap = int(probe.binning.count() * headroom) + 1024
         del probe
-        self.renderers = [Renderer(cam, opts, capacity=cap) for _ in range(2)]
+        self.renderers = [Renderer(cam, opts, capacity=cap) for _ in range(self.depth)]
         self.graphs = [r.capture(b)[:2] for r, b in zip(self.renderers, self.bufs)]
         H, W = int(cam["height"]), int(cam["width"])
-        self.host_out = [torch.empty((4, H, W), dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.host_out = [torch.empty((4, H, W), dtype=torch.float32).pin_memory() for _ in range(self.depth)]
         self.copy_stream, self.read_stream = torch.cuda.Stream(), torch.cuda.Stream()
-        self.copied = [torch.cuda.Event() for _ in range(2)]
-        self.rendered = [torch.cuda.Event() for _ in range(2)]
-        self.freed = [torch.cuda.Event() for _ in range(2)]
+        self.copied = [torch.cuda.Event() for _ in range(self.depth)]
+        self.rendered = [torch.cuda.Event() for _ in range(self.depth)]
+        self.freed = [torch.cuda.Event() for _ in range(self.depth)]
         self.i = 0
         torch.cuda.synchronize()
 
     def submit(self, host: dict) -> torch.Tensor:
-        b = self.i % 2
+        b = self.i % self.depth
         self.i += 1
         sc, cs = self.bufs[b], torch.cuda.current_stream()
-        self.copy_stream.wait_event(self.freed[b])  # frame i - 2 no longer reads this buffer
+        self.copy_stream.wait_event(self.freed[b])  # frame i - depth no longer reads this buffer
         with torch.cuda.stream(self.copy_stream):
             for k in _SCENE_FIELDS:
                 getattr(sc, k).copy_(host[k].view_as(getattr(sc, k)), non_blocking=True)
@@ -317,7 +320,7 @@ class FramePipeline:
 
     def done(self, out: torch.Tensor) -> torch.cuda.Event:
         """The event after which `out` (a buffer submit returned) holds its frame."""
-        return self.freed[0] if out is self.host_out[0] else self.freed[1]
+        return self.freed[next(i for i, h in enumerate(self.host_out) if h is out)]
 
     def join(self, stream: torch.cuda.Stream | None = None):
         """Makes `stream` (default: the current one) wait for every copy submitted so far."""

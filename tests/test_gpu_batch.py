@@ -252,12 +252,18 @@ def test_frame_pipeline_matches_plain_renders_of_each_frame():
         d["opacity_logits"] = d["opacity_logits"] - 0.3 * f
         d["means"] = d["means"] + np.float32(0.01 * f)
         frames.append({k: torch.as_tensor(v).pin_memory() for k, v in d.items()})
-    pipe = render.FramePipeline(cam, op, frames[0], sc_np["sh_degree"])
     got = []
-    for fr in frames:
-        out = pipe.submit(fr)
-        pipe.done(out).synchronize()
-        got.append(out.clone())
+    for depth in (2, 3):
+        pipe = render.FramePipeline(cam, op, frames[0], sc_np["sh_degree"], depth=depth)
+        outs = [pipe.submit(fr) for fr in frames[:depth]]  # `depth` frames in flight at once
+        for out in outs:
+            pipe.done(out).synchronize()
+            got.append(out.clone())
+        for fr in frames[depth:]:
+            out = pipe.submit(fr)
+            pipe.done(out).synchronize()
+            got.append(out.clone())
+    frames = frames + frames
     for fr, img in zip(frames, got):
         scene = render.Scene.from_arrays(dict({k: v.numpy() for k, v in fr.items()}, sh_degree=sc_np["sh_degree"]))
         f = render.Renderer(cam, op, capacity=1 << 12).forward(scene)
