@@ -195,6 +195,63 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint
   }
 }
 
+// k_scan_down for short chunk lists (kSelfPrefixChunks or fewer): `chunk` holds each chunk's raw
+// total (from k_scan_reduce) and every block sums the totals before its chunk itself, so no
+// separate spine pass is needed; block 0 writes the grand total when `total` is given.
+constexpr uint32_t kSelfPrefixChunks = 1024;
+
+template <class L, class X = Ident>
+__global__ void __launch_bounds__(kThreads) k_scan_down_self(const uint32_t *in, uint32_t *out, L len,
+                                                             const u64 *__restrict__ chunk, u64 *__restrict__ total) {
+  __shared__ uint32_t s_v[kTile + kTile / 32];
+  __shared__ u64 s_warp[kWarps + 1];
+  const uint32_t n = len.get();
+  const uint32_t nchunks = (n + kTile - 1) / kTile;
+  if (blockIdx.x == 0 && total) {
+    u64 a = 0;
+    for (uint32_t c = threadIdx.x; c < nchunks; c += blockDim.x) a += chunk[c];
+    u64 ex;
+    const u64 t = block_excl_scan_u64(a, s_warp, ex);
+    if (threadIdx.x == 0) *total = t;
+  }
+  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    u64 a = 0;
+    for (uint32_t cc = threadIdx.x; cc < c; cc += blockDim.x) a += chunk[cc];
+    u64 ex;
+    const u64 prefix = block_excl_scan_u64(a, s_warp, ex);
+    uint32_t base = c * kTile;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+      int q = i * kThreads + threadIdx.x;
+      uint32_t p = base + q;
+      s_v[skew(q)] = p < n ? X()(in[p]) : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kIPT];
+    u64 sum = 0;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+      v[i] = s_v[skew(threadIdx.x * kIPT + i)];
+      sum += v[i];
+    }
+    block_excl_scan_u64(sum, s_warp, ex);
+    u64 run = prefix + ex;
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+      s_v[skew(threadIdx.x * kIPT + i)] = (uint32_t)run;
+      run += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kIPT; ++i) {
+      int q = i * kThreads + threadIdx.x;
+      uint32_t p = base + q;
+      if (p < n) out[p] = s_v[skew(q)];
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- radix sort passes
 
 
@@ -986,6 +1043,11 @@ template <class L, class X = Ident>
 void scan(const uint32_t *in, uint32_t *out, L len, u64 max_len, u64 *chunk, u64 *total, cudaStream_t s) {
   int g = grid_for(max_len, kTile);
   k_scan_reduce<L, X><<<g, kThreads, 0, s>>>(in, len, chunk);
+  if (ceil_div(max_len, kTile) <= kSelfPrefixChunks) {  // short chunk lists: no spine pass
+    k_scan_down_self<L, X><<<g, kThreads, 0, s>>>(in, out, len, chunk, total);
+    count_launches(2);
+    return;
+  }
   k_scan_spine<L><<<1, 1024, 0, s>>>(chunk, len, total);
   k_scan_down<L, X><<<g, kThreads, 0, s>>>(in, out, len, chunk);
   count_launches(3);
