@@ -195,10 +195,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint
   }
 }
 
-// k_scan_down for short chunk lists (kSelfPrefixChunks or fewer): `chunk` holds each chunk's raw
+// k_scan_down for chunk lists of up to kSelfPrefixChunks: `chunk` holds each chunk's raw
 // total (from k_scan_reduce) and every block sums the totals before its chunk itself, so no
 // separate spine pass is needed; block 0 writes the grand total when `total` is given.
-constexpr uint32_t kSelfPrefixChunks = 1024;
+constexpr uint32_t kSelfPrefixChunks = 4096;
 
 template <class L, class X = Ident>
 __global__ void __launch_bounds__(kThreads) k_scan_down_self(const uint32_t *in, uint32_t *out, L len,
@@ -424,12 +424,23 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
 
 // ---------------------------------------------------------------- binning kernels
 
-__global__ void k_depth_init(int n, const float *__restrict__ depth, const uint32_t *__restrict__ ntiles,
-                             uint32_t *__restrict__ dk, uint32_t *__restrict__ dv) {
+// Depth keys (culled particles last) and the particle indices, and K = sum of ntiles added to
+// *ksum (zeroed beforehand) with one atomic per block.
+__global__ void __launch_bounds__(kThreads) k_depth_init(int n, const float *__restrict__ depth,
+                                                         const uint32_t *__restrict__ ntiles,
+                                                         uint32_t *__restrict__ dk, uint32_t *__restrict__ dv,
+                                                         u64 *__restrict__ ksum) {
+  __shared__ u64 s_warp[kWarps + 1];
+  u64 k = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    dk[i] = ntiles[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
+    const uint32_t t = ntiles[i];
+    dk[i] = t > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
     dv[i] = (uint32_t)i;
+    k += t;
   }
+  u64 ex;
+  const u64 tot = block_excl_scan_u64(k, s_warp, ex);
+  if (threadIdx.x == 0 && tot) atomicAdd(reinterpret_cast<unsigned long long *>(ksum), (unsigned long long)tot);
 }
 
 // Depth order -> number of tile columns each particle covers (0 if culled).
@@ -1099,11 +1110,9 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
   if (n > 0) {
     const int g = grid_for(n, kThreads);
     const Count cn{nullptr, 0, (uint32_t)n};
-    // K = sum of ntiles (reported even when it exceeds the capacity)
-    k_scan_reduce<Count><<<grid_for(n, kTile), kThreads, 0, s>>>(ntiles, cn, b.chunk);
-    k_scan_spine<Count><<<1, 1024, 0, s>>>(b.chunk, cn, b.total + 1);
-    k_depth_init<<<g, kThreads, 0, s>>>(n, depth, ntiles, b.dk[0], b.dv[0]);
-    count_launches(3);
+    // depth keys, and K = sum of ntiles (reported even when it exceeds the capacity)
+    k_depth_init<<<g, kThreads, 0, s>>>(n, depth, ntiles, b.dk[0], b.dv[0], b.total + 1);
+    count_launches(1);
     const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s);
     // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
     // and the caller's vals, arranged so that the row stage lands in vals: the row scatter
