@@ -696,12 +696,26 @@ __global__ void k_col_bounds(const uint32_t *__restrict__ ckeys, Count cc, uint3
   }
 }
 
-// The chunk plan from the column bounds (one block of 1024 threads).
-__global__ void __launch_bounds__(1024) k_chunk_plan(const __grid_constant__ BatchDesc bd,
-                                                     const uint32_t *__restrict__ colb, ChunkPlan pl) {
+// The chunk plan from the column bounds (one block of 1024 threads).  With dspine, the column
+// order came from one radix pass over all column bits, and the bounds are read off its scanned
+// digit-major counts instead (column c starts at dspine[c * tiles], tiles = radix tiles of the
+// M column entries) and written to colb here.
+__global__ void __launch_bounds__(1024) k_chunk_plan(const __grid_constant__ BatchDesc bd, uint32_t *__restrict__ colb,
+                                                     ChunkPlan pl, const uint32_t *__restrict__ dspine, int ndigits,
+                                                     Count mcnt) {
   __shared__ u64 s_w[33];
   __shared__ u64 s_tot;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, cols = bd.total_cols;
+  if (dspine) {
+    const uint32_t M = mcnt.get(), nt = (M + kRTile - 1) / kRTile;
+    for (int c = t; c < cols; c += 1024) {
+      const uint32_t a = M ? dspine[(size_t)c * nt] : 0u;
+      const uint32_t e = !M ? 0u : (c + 1 < ndigits ? dspine[(size_t)(c + 1) * nt] : M);
+      colb[2 * c] = a;
+      colb[2 * c + 1] = e;
+    }
+    __syncthreads();
+  }
   auto block_sum = [&](u64 x) -> u64 {
     x = warp_incl_scan_u64(x, lane);
     if (lane == 31) s_w[warp] = x;
@@ -945,10 +959,12 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
                                                           int max_rows, const uint32_t *__restrict__ spine,
                                                           Count kcnt, const float *__restrict__ depth,
                                                           uint32_t *__restrict__ vals, uint32_t *__restrict__ ranges,
-                                                          uint64_t *__restrict__ keys) {
+                                                          uint64_t *__restrict__ keys, const u64 *__restrict__ ktotal,
+                                                          int64_t *__restrict__ k_out) {
   extern __shared__ uint2 s_mem2[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t wid = blockIdx.x * kWarps + warp;
+  if (wid == 0 && lane == 0) *k_out = (int64_t)*ktotal;  // K, also when it exceeds the capacity
   if (wid >= (uint32_t)pl.len[1]) return;
   const int c = (int)pl.chunk_col[wid];
   const uint32_t k = wid - pl.co[c], nch = pl.ch[c];
@@ -1144,22 +1160,25 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
       // 3. row entries scattered straight into (tile, depth) order
       const uint32_t *ckc = ck[rc], *cvc = cv[rc];
       const int blocks = (kChunkWarps + bd.total_cols + kWarps - 1) / kWarps;
-      if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
-        return UT_ERR_CUDA;
-      k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ckc, cc, b.colb);
-      k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan);
+      if (cp == 1) {  // bounds from the single column pass's digit counts
+        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, b.spine, 1 << cbits, cc);
+      } else {
+        if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
+          return UT_ERR_CUDA;
+        k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ckc, cc, b.colb);
+        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, nullptr, 0, cc);
+        count_launches(1);
+      }
       k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ckc, b.colb, b.plan,
                                                                                        max_rows, b.tspine);
-      count_launches(3);
+      count_launches(2);
       const u64 tmax = plan_spine_words(max_rows, tiles, bd.total_cols);
       scan(b.tspine, b.tspine, Count{b.plan.len, tmax, 0}, tmax, b.chunk, nullptr, s);
       const size_t smem = row_scatter_smem(max_rows);
       if (cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return UT_ERR_CUDA;
       k_row_scatter<<<blocks, kThreads, smem, s>>>(bd, ckc, cvc, b.colb, b.plan, max_rows, b.tspine, ck2, depth,
-                                                   vals, ranges, keys);
-      count_launches(1);
-      k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
+                                                   vals, ranges, keys, b.total + 1, k_out);
       count_launches(1);
       return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
     }
