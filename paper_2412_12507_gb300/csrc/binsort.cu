@@ -18,7 +18,8 @@
 // covered column, not per tile) pays for the column order.
 //
 // The radix sort is the project's own: per 8-bit digit pass an upsweep (per-warp shared
-// histograms fed by uint4 key loads), a digit-major exclusive scan, and a downsweep that
+// histograms fed by uint4 key loads), a digit-major exclusive scan (per-chunk totals, then a
+// down-sweep whose blocks add up the totals before their chunk), and a downsweep that
 // ranks keys stably in shared memory (same-digit lanes found with 8 ballots per 32-key group,
 // per-warp running digit counters) and writes them out digit-grouped for coalescing.
 // No kernel waits on another block, so nothing in here can spin.
