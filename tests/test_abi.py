@@ -58,6 +58,26 @@ def test_workspace_sizes(L):
     assert L.ut_forward_workspace_size(None, C.byref(o)) == 0
 
 
+def test_workspace_sizes_never_shrink_as_the_key_capacity_grows(L):
+    """The serving loop searches for the largest key capacity whose scratch fits its arena,
+    which relies on the workspace size being non-decreasing in the capacity."""
+    o = abi.default_options()
+    caps = (0, 1, 1023, 1024, 4096, 1 << 16, 1 << 20, 12_345_678, 1 << 31)
+    cams = (synth.camera("fisheye", 1920, 1080), synth.camera("pinhole", 64, 48, fx=60.0),
+            synth.camera("pinhole", 3840, 2160, fx=2000.0))
+    for cam in cams:
+        c = abi.make_camera(cam)
+        sizes = [L.ut_bin_workspace_size(5000, k, C.byref(c), C.byref(o)) for k in caps]
+        assert sizes[0] > 0 and all(a <= b for a, b in zip(sizes, sizes[1:])), sizes
+    dummy = 256  # a 256-byte aligned stand-in address: the size query never dereferences it
+    sc = abi.UtScene(dummy, dummy, dummy, dummy, dummy, 5000, 3)
+    views = (abi.UtView * len(cams))()
+    for v, cam in zip(views, cams):
+        v.scene, v.camera, v.rgb, v.alpha = 0, abi.make_camera(cam), dummy, dummy
+    sizes = [L.ut_batch_workspace_size(C.byref(sc), 1, views, len(cams), C.byref(o), k) for k in caps]
+    assert sizes[0] > 0 and all(a <= b for a, b in zip(sizes, sizes[1:])), sizes
+
+
 def _project(L, cam, opts=None, n=0, params=None):
     sc = abi.UtScene(None, None, None, None, None, n, 0)
     c = abi.make_camera(cam)
