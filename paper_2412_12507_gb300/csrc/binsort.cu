@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t *in, uint
 // k_scan_down for chunk lists of up to kSelfPrefixChunks: `chunk` holds each chunk's raw
 // total (from k_scan_reduce) and every block sums the totals before its chunk itself, so no
 // separate spine pass is needed; block 0 writes the grand total when `total` is given.
-constexpr uint32_t kSelfPrefixChunks = 4096;
+constexpr uint32_t kSelfPrefixChunks = 65536;  // also keeps the launch sequence independent of the capacity
 
 template <class L, class X = Ident>
 __global__ void __launch_bounds__(kThreads) k_scan_down_self(const uint32_t *in, uint32_t *out, L len,

@@ -270,8 +270,12 @@ bool schedule(ut_server *s) {
     size_t off;
     if (!s->arena.alloc(need + 256, &off)) {
       if (nb > 1) continue;
-      // one view whose estimated keys do not fit: run it with the largest capacity the arena can
-      // hold now (an overflow re-runs it with the observed count); the estimate may be inflated
+      // one view whose estimated keys do not fit while nothing else holds arena memory: run it
+      // with the largest capacity the arena can hold (an overflow re-runs it with the observed
+      // count; the estimate may be inflated).  With batches in flight, wait for their memory.
+      bool any_busy = false;
+      for (auto &x : s->slots) any_busy |= x.busy;
+      if (any_busy) break;
       const size_t avail = s->arena.largest();
       int64_t lo = 0, hi = capacity;
       while (lo < hi) {
