@@ -933,7 +933,11 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
  * was itself the closest.  At the end of the list the remaining entries are blended in
  * ascending tau.  Returns the number of blended particles.  A selection whose runner-up tau is
  * within eps_tau (relative) of the chosen one may go the other way in FP32: ORC_F_DEPTH_TIE. */
-typedef struct { double tau, alpha, col[3]; int seq; } orc_kb_entry;
+typedef struct {
+  double tau, alpha, col[3];
+  int seq;
+  orc_contrib c; /* everything the backward needs of this (pixel, particle) pair */
+} orc_kb_entry;
 
 static int orc_kb_pick(const orc_kb_entry *e, int n, double eps, int *tie) {
   int best = 0;
@@ -947,7 +951,7 @@ static int orc_kb_pick(const orc_kb_entry *e, int n, double eps, int *tie) {
 static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, const orc_options *op,
                                      const orc_tol *tol, int px, int py, const double o[3], const double d[3],
                                      const double *Y, double rgb[3], double *Tout, int32_t *flags,
-                                     int *stopped_out) {
+                                     int *stopped_out, orc_contrib *rec, int cap) {
   orc_kb_entry buf[65];
   int k = op->kbuffer < 64 ? op->kbuffer : 64, nbuf = 0, nb = 0, seq = 0, stopped = 0, tie = 0;
   double T = 1.0;
@@ -959,7 +963,8 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
     const int inside = px >= r[0] && px <= r[2] && py >= r[1] && py <= r[3];
     double og[3], dg[3], tau;
     double w2 = orc_omega2(p, o, d, og, dg, &tau);
-    double a = p->sigma * orc_response(op, w2);
+    double rho = orc_response(op, w2);
+    double a = p->sigma * rho;
     if (flags && x->edges) {  /* membership may flip where a rect edge is within eps_px of the pixel */
       const double *e = x->edges + 4 * i;
       double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
@@ -982,7 +987,11 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
       double s = 0.5;
       for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Yc[kk];
       h.col[ch] = s > 0.0 ? s : 0.0;
+      h.c.raw[ch] = s;
+      h.c.col[ch] = h.col[ch];
     }
+    h.c.i = i; h.c.alpha = h.alpha; h.c.a = a; h.c.rho = rho; h.c.tau = tau; h.c.w2 = w2;
+    for (int kk = 0; kk < 3; ++kk) { h.c.og[kk] = og[kk]; h.c.dg[kk] = dg[kk]; }
     if (nbuf < k) { buf[nbuf++] = h; continue; }
     buf[nbuf] = h;  /* the closest of the k buffered hits and the new one is blended */
     int b = orc_kb_pick(buf, nbuf + 1, op->eps_tau, &tie);
@@ -990,6 +999,7 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
     if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
     if (Tn < op->t_min) { stopped = 1; break; }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
+    if (rec && nb < cap) { rec[nb] = buf[b].c; rec[nb].T = T; }
     T = Tn;
     ++nb;
     buf[b] = buf[nbuf];
@@ -1000,6 +1010,7 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
     if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
     if (Tn < op->t_min) { stopped = 1; break; }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
+    if (rec && nb < cap) { rec[nb] = buf[b].c; rec[nb].T = T; }
     T = Tn;
     ++nb;
     buf[b] = buf[--nbuf];
@@ -1059,7 +1070,7 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     slack[q] = 0.0;
     aslack[q] = 0.0;
     if (op->kbuffer > 0)
-      nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL);
+      nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, NULL, 0);
     else
       nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect,
                                     &slack[q], &aslack[q]);
@@ -1102,7 +1113,9 @@ static void orc_rot_grad(const double q[4], const double G[9], double gq[4]) {
 }
 
 /* Reverse-mode gradient of L with respect to every particle parameter, given dL/drgb and
- * dL/dalpha at the listed pixels (supplementary Sec. B: d alpha / d omega^2 = -1/2 sigma
+ * dL/dalpha at the listed pixels, over each pixel's blended pairs in the order they were
+ * blended (tile order, or the k-buffer's order with op->kbuffer > 0, whose selection decisions
+ * are piecewise constant and carry no gradient) (supplementary Sec. B: d alpha / d omega^2 = -1/2 sigma
  * exp(-omega^2/2); d omega^2 / d o_g = 2 (o_g + tau d_g); d o_g / d mu = -S^-1 R^T; the S, R
  * terms follow from d omega^2 / d d_g = 2 tau (o_g + tau d_g) and M = S^-1 R^T).  The 2D
  * projection contributes no gradient: it only selects particles (Sec. 4.1).
@@ -1132,7 +1145,10 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
       orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
       if (!valid) continue;
       double rgb[3], Tf;
-      int nb = orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL, NULL);
+      /* the blended pairs in blending order: the tile (depth) order, or the k-buffer's order */
+      int nb = op->kbuffer > 0
+                   ? orc_composite_ray_kbuffer(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, NULL, rec, x.norder)
+                   : orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL, NULL);
       const double *g = g_rgb + 3 * q;
       double gA = g_alpha[q];
       double S[3] = {0, 0, 0}; /* sum over later blended particles of c alpha T */

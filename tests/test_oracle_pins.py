@@ -822,6 +822,68 @@ def test_gradients_match_central_differences(orc, colour_mode, deg, kdeg):
     assert checked >= 12 * 14  # every parameter of the 12 particles (SH degree >= 0)
 
 
+@pytest.mark.parametrize("k", [2, 16])
+def test_kbuffer_gradients_match_central_differences(orc, k):
+    """The k-buffer ("Ours (sorted)") backward: analytic gradients over each pixel's blended pairs
+    in the buffer's blending order vs Richardson central differences (exact FP32 steps).  The
+    selection by tau_max is piecewise constant; pixels where a selection is within 2 % of a tie
+    (it could flip under the steps), near alpha_min / alpha_max or near the stop are left out."""
+    sc = _fd_scene(deg=1)
+    cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
+    op = synth.options(t_min=1e-4, kbuffer=k)
+    proj = orc.project(sc, cam, op)
+    yy, xx = np.mgrid[0:20, 0:24]
+    px, py = xx.reshape(-1), yy.reshape(-1)
+    fl = orc.render(sc, cam, dict(op, eps_tau=0.02), proj=proj, tol=dict(eps_rel=0.1, eps_px=0.0),
+                    pixels=(px, py))["flags"]
+    keep = (fl & (orc.F_ALPHA_MIN | orc.F_TSTOP | orc.F_ALPHA_MAX | orc.F_DEPTH_TIE)) == 0
+    assert keep.mean() > 0.5
+    rng = np.random.default_rng(1)
+    g_rgb = rng.standard_normal((len(px), 3)) * keep[:, None]
+    g_a = rng.standard_normal(len(px)) * keep
+    pix = (px, py)
+    gr = orc.backward(sc, cam, op, proj, pix, g_rgb, g_a)
+    checked = 0
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        base = sc[name]
+        flat = base.reshape(-1)
+        ga = gr[name].reshape(-1)
+        for j in range(flat.size):
+            def f(h):
+                b2 = base.copy().reshape(-1)
+                b2[j] = np.float32(float(flat[j]) + h)
+                assert float(b2[j]) == float(flat[j]) + h
+                return _loss(orc, dict(sc, **{name: b2.reshape(base.shape)}), cam, op, proj, pix, g_rgb, g_a)
+            h = 2.0**-9
+            d1 = (f(h) - f(-h)) / (2 * h)
+            d2 = (f(h / 2) - f(-h / 2)) / h
+            fd = (4 * d2 - d1) / 3
+            assert abs(fd - ga[j]) <= 1e-6 * max(1.0, abs(ga[j])) + 1e-7, (name, j, fd, ga[j])
+            checked += 1
+    assert checked >= 12 * 14
+
+
+def test_kbuffer_gradients_equal_tile_order_when_the_orders_agree(orc):
+    """Small, well separated particles along the rays: tau_max order = depth order, so the
+    k-buffer blends the tile order and its gradients are the tile-order gradients (any k)."""
+    case = synth.small_pinhole()
+    sc, cam, op = case["scene"], case["camera"], case["options"]
+    sc = dict(sc, log_scales=np.full_like(sc["log_scales"], -5.0))
+    proj = orc.project(sc, cam, op)
+    H, W = cam["height"], cam["width"]
+    yy, xx = np.mgrid[0:H, 0:W]
+    pix = (xx.reshape(-1), yy.reshape(-1))
+    rng = np.random.default_rng(2)
+    g_rgb, g_a = rng.standard_normal((H * W, 3)), rng.standard_normal(H * W)
+    ref = orc.backward(sc, cam, op, proj, pix, g_rgb, g_a)
+    for k in (1, 16):
+        opk = dict(op, kbuffer=k)
+        assert not np.any(orc.render(sc, cam, opk, proj=proj)["flags"] & orc.F_DEPTH_TIE)
+        got = orc.backward(sc, cam, opk, proj, pix, g_rgb, g_a)
+        for name in ref:
+            assert np.allclose(got[name], ref[name], rtol=1e-12, atol=1e-12 * np.abs(ref[name]).max()), (k, name)
+
+
 @pytest.mark.parametrize("n", [3, 5])
 def test_odd_degree_kernel_gradient_single_particle(orc, n):
     """Odd degrees are not twice differentiable where a ray crosses a particle's centre, so the
