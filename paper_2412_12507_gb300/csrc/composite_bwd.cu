@@ -475,7 +475,6 @@ size_t tile_sched_bytes(int tiles) {
 // backward over every tile with work, then finalize.
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                                const uint32_t *ranges, void *sched, cudaStream_t s) {
-  if (op.kbuffer > 0) return UT_ERR_UNSUPPORTED;  // the k-buffer variant is forward only
   int total = 0;
   for (int k = 0; k < bd.ns; ++k) {
     const DevScene &sc = bd.s[k];
@@ -485,7 +484,10 @@ ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int
     if (cudaMemsetAsync(sc.d_sh, 0, sizeof(float) * nc * sc.n, s) != cudaSuccess) return UT_ERR_CUDA;
     total = sc.grad_off + sc.n > total ? sc.grad_off + sc.n : total;
   }
-  if (bd.total_tiles > 0) {
+  if (op.kbuffer > 0) {  // "Ours (sorted)": its own replay of the per-ray k-buffer
+    const ut_status st = launch_composite_bwd_kbuffer(bd, op, rect, vals, ranges, s);
+    if (st != UT_OK) return st;
+  } else if (bd.total_tiles > 0) {
     const TileSched ts = carve_tile_sched(sched, bd.total_tiles);
     if (cudaMemsetAsync(ts.hist, 0, sizeof(uint32_t) * (2 * kOrderBuckets + 1), s) != cudaSuccess) return UT_ERR_CUDA;
     const auto *rg = reinterpret_cast<const uint2 *>(ranges);

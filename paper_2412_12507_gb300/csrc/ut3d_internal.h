@@ -54,5 +54,8 @@ size_t backward_workspace_bytes(int n);
 size_t tile_sched_bytes(int tiles);
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
                                const uint32_t *ranges, void *sched, cudaStream_t stream);
+// The backward of the per-ray k-buffer compositing (accumulators cleared by the caller).
+ut_status launch_composite_bwd_kbuffer(const BatchDesc &bd, const DevOpts &op, const int16_t *rect,
+                                       const uint32_t *vals, const uint32_t *ranges, cudaStream_t stream);
 
 }  // namespace ut3d
