@@ -401,7 +401,7 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
         out[name] = {"project_ms": proj_ms, "fwd_ms": fwd_ms, "keys": K, "fwd_mpix_s": P / (fwd_ms / 1e3) / 1e6}
         del r
     out["ewa_over_ut_project"] = out["ewa"]["project_ms"] / out["ut"]["project_ms"]
-    # "Ours (sorted)": the per-ray k-buffer (k = 16), forward only
+    # "Ours (sorted)": the per-ray k-buffer (k = 16), forward and backward
     o = dict(op, kbuffer=16)
     r = render.Renderer(cam, o, capacity=1 << 20)
     r.forward(scene)
@@ -409,9 +409,11 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
     k_ms = timed(lambda: r.forward(scene, sync_check=False), steps, warmup)
     calls = {}
     for k, fn in (("composite_forward", lambda: render.composite_forward(scene, cam, o, r.proj, r.binning, r.frame,
-                                                                         ws=r.fws)),):
+                                                                         ws=r.fws)),
+                  ("composite_backward", lambda: r.backward(scene, d_rgb, d_alpha))):
         calls[k] = per_call(fn)
     out["kbuffer16"] = {"fwd_ms": k_ms, "composite_forward_ms": calls["composite_forward"],
+                        "composite_backward_ms": calls["composite_backward"],
                         "fwd_mpix_s": P / (k_ms / 1e3) / 1e6}
     del r
     o = dict(op, colour_mode=1)
