@@ -119,9 +119,11 @@ typedef struct {
  *   kbuffer: 0 (default) blends in the tile's depth order; k in 1..16 selects "Ours (sorted)"
  *   (Sec. 4.4), a per-ray k-buffer: hits enter a buffer of k entries, a full buffer blends the
  *   closest (by tau_max) of its hits and the arriving one, and the rest are blended in tau_max
- *   order at the end of the list (the paper uses k = 16).  Forward only (composite_backward and
- *   render_batch_backward return UT_ERR_UNSUPPORTED, composite_forward too when asked for
- *   statistics); combined with per-particle colours or kernel_degree != 2 it is unsupported. */
+ *   order at the end of the list (the paper uses k = 16).  composite_backward and
+ *   render_batch_backward differentiate through the same blending order (the selections carry
+ *   no gradient); a tile of 512 pixels with k = 16 is the largest buffer one block holds, larger
+ *   ones return UT_ERR_UNSUPPORTED from the backward.  composite_forward rejects statistics
+ *   with a k-buffer; combined with per-particle colours or kernel_degree != 2 it is unsupported. */
 #define UT_PROJECTION_UT 0
 #define UT_PROJECTION_EWA 1
 #define UT_COLOUR_PER_PIXEL 0
