@@ -121,8 +121,8 @@ typedef struct {
  *   closest (by tau_max) of its hits and the arriving one, and the rest are blended in tau_max
  *   order at the end of the list (the paper uses k = 16).  composite_backward and
  *   render_batch_backward differentiate through the same blending order (the selections carry
- *   no gradient); a tile of 512 pixels with k = 16 is the largest buffer one block holds, larger
- *   ones return UT_ERR_UNSUPPORTED from the backward.  composite_forward rejects statistics
+ *   no gradient; every allowed tile size and k fits one block's shared memory).
+ *   composite_forward rejects statistics
  *   with a k-buffer; combined with per-particle colours or kernel_degree != 2 it is unsupported. */
 #define UT_PROJECTION_UT 0
 #define UT_PROJECTION_EWA 1
