@@ -46,7 +46,7 @@ typedef enum {
   UT_ERR_CAPACITY = 2,    /* a caller buffer is too small (see bin_and_sort) */
   UT_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
   UT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
-  UT_ERR_UNSUPPORTED = 5  /* a valid request this build does not implement */
+  UT_ERR_UNSUPPORTED = 5  /* a valid request the library does not implement */
 } ut_status;
 
 /* UT_CAM_PINHOLE_RADIAL: u = fx x_n (1 + k1 r^2 + k2 r^4 + k3 r^6) + cx (likewise v) with
