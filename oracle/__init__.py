@@ -81,6 +81,7 @@ def lib():
         L.orc_ut_estimate.restype = C.c_int
         L.orc_ut_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, C.c_double, C.c_double,
                                       C.c_double, P, P, P, P, P, P, P]
+        L.orc_pose.argtypes = [C.POINTER(Camera), C.c_double, P, P]
         L.orc_cam_limit.restype = C.c_double
         L.orc_cam_limit.argtypes = [C.POINTER(Camera)]
         L.orc_ewa_estimate.restype = C.c_int
@@ -205,6 +206,15 @@ def project_point(cam: dict, x, rs_iters: int = 3):
     m = np.zeros(1)
     v = lib().orc_project_world(C.byref(c), tm, rs_iters, _p(_f64(x)), _p(uv), _p(t), _p(m))
     return bool(v), uv, float(t[0])
+
+
+def pose_at(cam: dict, t: float):
+    """World->camera rotation (3x3) and translation of the camera at shutter time t."""
+    c = make_camera(cam)
+    R = np.zeros(9)
+    T = np.zeros(3)
+    lib().orc_pose(C.byref(c), float(t), _p(R), _p(T))
+    return R.reshape(3, 3), T
 
 
 def pixel_ray(cam: dict, px: float, py: float):

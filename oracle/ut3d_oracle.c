@@ -141,6 +141,9 @@ static void orc_pose_at(const orc_camera *c, double t, double R[9], double T[3])
   for (int i = 0; i < 3; ++i) T[i] = (1.0 - t) * c->t_start[i] + t * c->t_end[i];
 }
 
+/* The pose at shutter time t as the tests see it (same function, exported). */
+void orc_pose(const orc_camera *c, double t, double R[9], double T[3]) { orc_pose_at(c, t, R, T); }
+
 /* ------------------------------------------------------------------ fisheye polynomial */
 
 static double orc_theta_d(const double k[4], double th) {

@@ -252,6 +252,96 @@ def test_rolling_shutter_fixed_point_converges_to_row_time(orc):
         assert abs(t - np.clip((uv[1] - 0.5) / 1079, 0, 1)) < 1e-12
 
 
+def _geodesic_pose(Ra, Ta, Rb, Tb, t):
+    """Pose at time t along the rotation geodesic from Ra to Rb, by axis-angle (scipy), and
+    the straight segment from Ta to Tb: an independent route to the interpolated pose."""
+    from scipy.spatial.transform import Rotation
+    rv = Rotation.from_matrix(Ra.T @ Rb).as_rotvec()  # angle in [0, pi]: the shorter way round
+    return Ra @ Rotation.from_rotvec(t * rv).as_matrix(), (1.0 - t) * np.asarray(Ta) + t * np.asarray(Tb)
+
+
+def _big_rs_camera(model="pinhole", flip=False):
+    """Rolling-shutter camera whose end pose is 120 degrees from its start pose (large enough
+    that a normalised lerp of the quaternions, or t read backwards, is far off the geodesic)."""
+    qa = np.array([0.9, 0.1, -0.3, 0.2])
+    qa /= np.linalg.norm(qa)
+    axis = np.array([0.3, -0.8, 0.5]) / np.linalg.norm([0.3, -0.8, 0.5])
+    rel = np.concatenate([[math.cos(math.radians(60))], math.sin(math.radians(60)) * axis])
+    w1, v1 = qa[0], qa[1:]
+    w2, v2 = rel[0], rel[1:]
+    qb = np.concatenate([[w1 * w2 - v1 @ v2], w1 * v2 + w2 * v1 + np.cross(v1, v2)])  # qa (x) rel
+    if flip:
+        qb = -qb  # the same rotation on the other sheet of the double cover
+    return synth.camera(model, 640, 480, fx=300.0, q=qa, t=(0.1, -0.2, 0.3), q_end=qb, t_end=(0.6, 0.1, -0.4),
+                        rolling_shutter=1)
+
+
+@pytest.mark.parametrize("flip", [False, True])
+def test_rolling_shutter_pose_follows_the_geodesic(orc, flip):
+    """The pose at shutter time t (Sec. 1: each sigma point seen through its own extrinsic
+    matrix): t = 0 and t = 1 give the start and end poses exactly; in between the rotation lies
+    on the shorter geodesic at the fraction t of its angle and the translation on the segment.
+    Checked at t = 1/4 and 3/4, where a normalised lerp, a reversed time axis or swapped end
+    poses are far off."""
+    cam = _big_rs_camera(flip=flip)
+    Ra, Rb = rot(cam["q_start"]), rot(cam["q_end"])
+    Ta, Tb = cam["t_start"], cam["t_end"]
+    R0, T0 = orc.pose_at(cam, 0.0)
+    R1, T1 = orc.pose_at(cam, 1.0)
+    assert np.allclose(R0, Ra, atol=1e-14) and np.allclose(T0, Ta, atol=1e-15)
+    assert np.allclose(R1, Rb, atol=1e-14) and np.allclose(T1, Tb, atol=1e-15)
+    for t in (0.25, 0.5, 0.75, 0.1, 0.9):
+        R, T = orc.pose_at(cam, t)
+        Rg, Tg = _geodesic_pose(Ra, Ta, Rb, Tb, t)
+        assert np.allclose(R, Rg, atol=1e-12), t
+        assert np.allclose(T, Tg, atol=1e-15), t
+        # the rotation angle from the start grows linearly in t (120 degrees in all, up to the
+        # FP32 rounding of the camera's quaternions)
+        ang = math.degrees(math.acos(np.clip((np.trace(Ra.T @ R) - 1) / 2, -1, 1)))
+        total = math.degrees(math.acos(np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1)))
+        assert abs(total - 120.0) < 1e-4
+        assert abs(ang - total * t) < 1e-9, (t, ang)
+    # a global-shutter camera ignores the end pose
+    R, T = orc.pose_at(dict(cam, rolling_shutter=0), 0.7)
+    assert np.allclose(R, Ra, atol=1e-14) and np.allclose(T, Ta, atol=1e-15)
+
+
+def test_rolling_shutter_projection_and_rays_use_the_row_pose(orc):
+    """g(x) under a rolling shutter equals the plain pinhole map through the geodesic pose at
+    the point's shutter time, and a pixel's ray is the camera centre and direction of the pose
+    at its row's time (t = (y - 1/2) / (H - 1))."""
+    cam = _big_rs_camera()
+    Ra, Rb = rot(cam["q_start"]), rot(cam["q_end"])
+    Ta, Tb = cam["t_start"], cam["t_end"]
+    H = cam["height"]
+    rng = np.random.default_rng(17)
+    n_ok = 0
+    for _ in range(200):
+        # points in front of the camera at a random shutter time
+        t0 = rng.uniform(0, 1)
+        R, T = _geodesic_pose(Ra, Ta, Rb, Tb, t0)
+        xc = np.array([rng.uniform(-1, 1), rng.uniform(-0.7, 0.7), rng.uniform(2, 4)])
+        x = R.T @ (xc - T)
+        ok, uv, t = orc.project_point(cam, x, rs_iters=3)
+        if not ok:
+            continue
+        n_ok += 1
+        R, T = _geodesic_pose(Ra, Ta, Rb, Tb, t)
+        y = R @ x + T
+        assert np.allclose(uv, [cam["fx"] * y[0] / y[2] + cam["cx"], cam["fy"] * y[1] / y[2] + cam["cy"]],
+                           atol=1e-9)
+    assert n_ok > 50
+    for py in (0.5, 120.5, 239.5, 400.0, 479.5):
+        px = rng.uniform(0, 640)
+        ok, o, d = orc.pixel_ray(cam, px, py)
+        assert ok
+        R, T = _geodesic_pose(Ra, Ta, Rb, Tb, min(max((py - 0.5) / (H - 1), 0.0), 1.0))
+        assert np.allclose(o, -R.T @ T, atol=1e-12)
+        dc = np.array([(px - cam["cx"]) / cam["fx"], (py - cam["cy"]) / cam["fy"], 1.0])
+        dw = R.T @ dc
+        assert np.allclose(d / np.linalg.norm(d), dw / np.linalg.norm(dw), atol=1e-12)
+
+
 # ------------------------------------------------------------------ spherical harmonics
 
 def test_sh_orthonormal(orc):
