@@ -208,11 +208,15 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
  * Same inputs, outputs, asynchrony and capacity contract as bin_and_sort; the scratch comes
  * from a fixed array of UT_BIN_STATIC_SCRATCH_BYTES (32 MiB) compiled into the library,
  * which every GPU that loads the library holds until the process exits.
- *   - Returns UT_ERR_CAPACITY, launching nothing, when
- *     ut_bin_workspace_size(n, key_capacity, cam, opt) > UT_BIN_STATIC_SCRATCH_BYTES
- *     (for example n = 100k particles with key_capacity = 2M fits).
- *   - The first call on each device looks up the array's device address (once per device,
- *     with that device current); make that first call before capturing any stream.
+ *   - Arguments bin_and_sort rejects are rejected with the same status.  Then, launching
+ *     nothing, UT_ERR_CAPACITY when
+ *     ut_bin_workspace_size(n, key_capacity, cam, opt) > UT_BIN_STATIC_SCRATCH_BYTES.
+ *     The scratch takes about 16 B per particle plus 22 B per unit of key capacity, so the
+ *     largest key_capacity that fits is 1,446,400 for n = 100k particles on a 1920x1080
+ *     camera with 16x16 tiles (562,816 for n = 1M; 1,524,480 for n = 0).
+ *   - Every call looks up the array's device address with the calling thread's device
+ *     current; the first call on a device also loads the library's device code there, so
+ *     make that first call before capturing any stream.
  *   - Allocates nothing.  All calls share the one array and it keeps the last call's
  *     contents; calls whose work overlaps on the GPU race on it: order them (one stream). */
 #define UT_BIN_STATIC_SCRATCH_BYTES (32u << 20)

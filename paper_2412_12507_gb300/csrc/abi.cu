@@ -430,20 +430,37 @@ size_t ut_bin_workspace_size(int32_t n, int64_t key_capacity, const ut_camera *c
   return bin_workspace_bytes(n, key_capacity, cols * rows, cols, rows);
 }
 
+}  // extern "C"
+
+namespace ut3d {
+// Every check bin_and_sort makes on its arguments except the workspace's; on success *need is
+// the workspace size.  bin_and_sort_static shares it, so both give the same status.
+ut_status bin_check_args(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                         const ut_camera *cam, const ut_options *opt, int64_t key_capacity, const uint32_t *vals,
+                         const uint32_t *tile_ranges, const int64_t *k_out, DevCam &dc, DevOpts &dop, size_t *need) {
+  ut_status st = make_cam(cam, dc);
+  if (st != UT_OK) return st;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 32)) return UT_ERR_INVALID_ARG;
+  if (n > 0 && (!depth || !rect || !ntiles || !aligned8(rect))) return UT_ERR_INVALID_ARG;
+  if (!tile_ranges || !k_out || (key_capacity > 0 && !vals) || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
+  *need = bin_workspace_bytes(n, key_capacity, dop.tiles_x * dop.tiles_y, dop.tiles_x, dop.tiles_y);
+  return UT_OK;
+}
+}  // namespace ut3d
+
+extern "C" {
+
 ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                        const ut_camera *cam, const ut_options *opt, void *workspace, size_t workspace_bytes,
                        int64_t key_capacity, uint64_t *keys, uint32_t *vals, uint32_t *tile_ranges,
                        int64_t *k_out, ut_stream stream) {
   DevCam dc;
-  ut_status st = make_cam(cam, dc);
-  if (st != UT_OK) return st;
   DevOpts dop;
-  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
-  if (n < 0 || key_capacity < 0 || key_capacity >= (int64_t(1) << 32)) return UT_ERR_INVALID_ARG;
-  if (n > 0 && (!depth || !rect || !ntiles || !aligned8(rect))) return UT_ERR_INVALID_ARG;
-  if (!tile_ranges || !k_out || (key_capacity > 0 && !vals) || !aligned8(tile_ranges)) return UT_ERR_INVALID_ARG;
-  int tiles = dop.tiles_x * dop.tiles_y;
-  size_t need = bin_workspace_bytes(n, key_capacity, tiles, dop.tiles_x, dop.tiles_y);
+  size_t need = 0;
+  ut_status st = bin_check_args(n, depth, rect, ntiles, cam, opt, key_capacity, vals, tile_ranges, k_out, dc, dop,
+                                &need);
+  if (st != UT_OK) return st;
   if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return UT_ERR_INVALID_ARG;
   BatchDesc bd;
   single_view(bd, dc, dop, nullptr, n);

@@ -11,14 +11,14 @@
 // The array g_bin_scratch is a file-scope __device__ variable of UT_BIN_STATIC_SCRATCH_BYTES
 // bytes: every GPU that loads the library keeps it until the process exits.  In host code
 // its name is only a host-side stand-in for the device symbol, never a device address, so
-// the real address is looked up once per device with cudaGetSymbolAddress (with that device
-// current) and cached.  That lookup happens on the first call on each device; make that
-// first call before capturing any stream.  All calls share the one array and it keeps the
-// last call's contents; nothing in it has to start at zero (the kernels clear what they
-// accumulate into), but calls whose work overlaps on the GPU race on it, so issue them on
-// one stream or otherwise order them.
-#include <mutex>
-
+// every call looks the real address up with cudaGetSymbolAddress, with the calling thread's
+// device current, and checks the result.  The first call on a device also loads this
+// module there; make that first call before capturing any stream.  Later lookups are cheap,
+// and because nothing is cached, a device reset or a re-created primary context can never
+// leave a stale address behind.  All calls share the one array and it keeps the last call's
+// contents; nothing in it has to start at zero (the kernels clear what they accumulate
+// into), but calls whose work overlaps on the GPU race on it, so issue them on one stream
+// or otherwise order them.
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -27,21 +27,14 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_bin_scratch[UT_BIN_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-// Device address of g_bin_scratch on the current device (set up once per device).
+// Device address of g_bin_scratch in the current context.
 ut_status scratch_address(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return UT_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || !p) return UT_ERR_CUDA;
-    g_scratch_addr[dev] = p;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_bin_scratch) != cudaSuccess || !p) {
+    (void)cudaGetLastError();  // the failed lookup must not be reported by a later call
+    return UT_ERR_CUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return UT_OK;
 }
 
@@ -54,13 +47,17 @@ extern "C" ut_status bin_and_sort_static(int32_t n, const float *depth, const in
                                          const uint32_t *ntiles, const ut_camera *cam, const ut_options *opt,
                                          int64_t key_capacity, uint64_t *keys, uint32_t *vals,
                                          uint32_t *tile_ranges, int64_t *k_out, ut_stream stream) {
-  if (n < 0 || key_capacity < 0 || !cam || !opt) return UT_ERR_INVALID_ARG;
-  size_t need = ut_bin_workspace_size(n, key_capacity, cam, opt);
-  if (need == 0) return UT_ERR_INVALID_ARG;
+  // bin_and_sort's own argument checks come first, so that both entry points give the same
+  // status for the same arguments; only then the size limit of the fixed array
+  DevCam dc;
+  DevOpts dop;
+  size_t need = 0;
+  ut_status st = bin_check_args(n, depth, rect, ntiles, cam, opt, key_capacity, vals, tile_ranges, k_out, dc, dop,
+                                &need);
+  if (st != UT_OK) return st;
   if (need > (size_t)UT_BIN_STATIC_SCRATCH_BYTES) return UT_ERR_CAPACITY;
   void *ws = nullptr;
-  ut_status st = scratch_address(&ws);
-  if (st != UT_OK) return st;
+  if ((st = scratch_address(&ws)) != UT_OK) return st;
   return bin_and_sort(n, depth, rect, ntiles, cam, opt, ws, (size_t)UT_BIN_STATIC_SCRATCH_BYTES, key_capacity, keys,
                       vals, tile_ranges, k_out, stream);
 }

@@ -39,6 +39,10 @@ ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights
 
 // Duplicate + sort + ranges over the batch's flattened entries and global tiles.
 size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols, int max_rows);
+// bin_and_sort's argument checks other than the workspace's; *need = the workspace size.
+ut_status bin_check_args(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
+                         const ut_camera *cam, const ut_options *opt, int64_t key_capacity, const uint32_t *vals,
+                         const uint32_t *tile_ranges, const int64_t *k_out, DevCam &dc, DevOpts &dop, size_t *need);
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
                      int64_t *k_out, cudaStream_t stream);

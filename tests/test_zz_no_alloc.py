@@ -72,15 +72,60 @@ def test_static_scratch_matches_workspace_version_on_two_calls():
         assert torch.equal(ranges, ref.ranges)
 
 
+def _largest_capacity(n, cam, op):
+    """Largest key capacity whose workspace fits the fixed array (host query only)."""
+    c, o = abi.make_camera(cam), abi.make_options(op)
+    size = lambda cap: abi.lib().ut_bin_workspace_size(n, cap, C.byref(c), C.byref(o))  # noqa: E731
+    lo, hi = 0, 1 << 31
+    while lo < hi:
+        mid = (lo + hi + 1) // 2
+        lo, hi = (mid, hi) if size(mid) <= STATIC_BYTES else (lo, mid - 1)
+    return lo
+
+
+STATIC_BYTES = 32 << 20
+
+
+def test_static_scratch_limit_is_the_documented_one():
+    """The header states the largest capacity for 100k particles on a 1080p camera with 16x16
+    tiles; at that capacity the call runs and matches bin_and_sort, one key more is refused."""
+    W, H, n = 1920, 1080, 100_000
+    cam = synth.camera("pinhole", W, H, fx=float(W))
+    op = synth.options()
+    cap = _largest_capacity(n, cam, op)
+    assert cap == 1_446_400
+    depth, rect, nt, K = _inputs(34, n, W, H, 16, 16)
+    assert K <= cap
+    T = render.tile_count(cam, op)
+    proj = render.Projection(None, None, depth, rect, nt)
+    ref = render.bin_and_sort(proj, cam, op, cap, want_keys=True)
+    keys, vals, ranges, k_out = _outputs(cap, T)
+    st = _static_call(n, depth, rect, nt, cam, op, cap, keys, vals, ranges, k_out)
+    assert st == abi.UT_OK, abi.lib().ut_status_string(st)
+    torch.cuda.synchronize()
+    assert int(k_out.item()) == ref.count() == K
+    assert torch.equal(vals[:K], ref.vals[:K]) and torch.equal(ranges, ref.ranges)
+    k_out.fill_(-1)
+    ranges.fill_(-1)
+    st = _static_call(n, depth, rect, nt, cam, op, cap + 1, keys, vals, ranges, k_out)
+    assert st == abi.UT_ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert int(k_out.item()) == -1 and torch.all(ranges == -1)  # nothing was launched
+
+
 def test_static_scratch_rejects_sizes_beyond_its_maximum():
     cam = synth.camera("pinhole", 1920, 1080, fx=1920.0)
     op = synth.options()
     depth, rect, nt, K = _inputs(33, 1000, 1920, 1080, 16, 16)
     cap = 10_000_000  # needs far more than the fixed scratch array
     c, o = abi.make_camera(cam), abi.make_options(op)
-    assert abi.lib().ut_bin_workspace_size(1000, cap, C.byref(c), C.byref(o)) > (32 << 20)
+    assert abi.lib().ut_bin_workspace_size(1000, cap, C.byref(c), C.byref(o)) > STATIC_BYTES
     keys, vals, ranges, k_out = _outputs(16, render.tile_count(cam, op))
+    k_out.fill_(-1)  # a sentinel no launch would leave in place
     st = _static_call(1000, depth, rect, nt, cam, op, cap, keys, vals, ranges, k_out)
     assert st == abi.UT_ERR_CAPACITY
     torch.cuda.synchronize()
-    assert int(k_out.item()) == 0 and torch.all(ranges == -1)  # nothing was launched
+    assert int(k_out.item()) == -1 and torch.all(ranges == -1)  # nothing was launched
+    # a capacity bin_and_sort rejects as invalid is rejected the same way here
+    st = _static_call(1000, depth, rect, nt, cam, op, 1 << 32, keys, vals, ranges, k_out)
+    assert st == abi.UT_ERR_INVALID_ARG
