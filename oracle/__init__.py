@@ -92,11 +92,11 @@ def lib():
         L.orc_count_keys.argtypes = [C.c_int, P, C.c_int, C.c_int]
         L.orc_bin.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_render.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), C.POINTER(Tol),
-                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, P]
+                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, P, P, P]
         L.orc_render_list.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P,
                                       C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_backward.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P, C.c_int,
-                                   P, P, P, P, P, P, P, P, P]
+                                   P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -281,7 +281,8 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
 
     proj: output of project() (or a dict with rect / depth32 and optionally edges / tie,
     e.g. synthetic arrays).  Returns rgb[P,3], alpha[P], tfinal[P], nblend[P], flags[P],
-    slack (the colour change depth-tied pairs can cause when reordered), and px, py."""
+    slack / aslack (the colour / opacity change depth-tied pairs and stop ties can cause),
+    fslack / faslack (a bound on what flipping the other flagged decisions can change), and px, py."""
     S = _SceneArrays(scene)
     if proj is None:
         proj = project(scene, cam, opts, tol)
@@ -298,12 +299,13 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
     edges = _f64(proj["edges"]).reshape(-1, 4) if proj.get("edges") is not None else None
     tie = _i32(proj["tie"]) if proj.get("tie") is not None else None
     out = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), tfinal=np.zeros(P), nblend=np.zeros(P, np.int32),
-               flags=np.zeros(P, np.int32), slack=np.zeros(P), aslack=np.zeros(P), px=px, py=py)
+               flags=np.zeros(P, np.int32), slack=np.zeros(P), aslack=np.zeros(P), fslack=np.zeros(P),
+               faslack=np.zeros(P), px=px, py=py)
     c, o, t = make_camera(cam), make_options(opts), make_tol(tol)
     lib().orc_render(C.byref(S.s), C.byref(c), C.byref(o), C.byref(t), _p(rect), _p(depth32), _p(edges),
                      _p(tie), P, _p(px), _p(py), int(no_rect), _p(out["rgb"]), _p(out["alpha"]),
                      _p(out["tfinal"]), _p(out["nblend"]), _p(out["flags"]), _p(out["slack"]),
-                     _p(out["aslack"]))
+                     _p(out["aslack"]), _p(out["fslack"]), _p(out["faslack"]))
     return out
 
 
@@ -318,19 +320,30 @@ def render_list(scene: dict, cam: dict, opts: dict | None, rect, depth32, px: in
     return rgb, float(tf[0])
 
 
-def backward(scene: dict, cam: dict, opts: dict | None, proj: dict, pixels, g_rgb, g_alpha) -> dict:
-    """FP64 reverse-mode gradients of sum(g_rgb * rgb) + sum(g_alpha * alpha) over the listed pixels."""
+def backward(scene: dict, cam: dict, opts: dict | None, proj: dict, pixels, g_rgb, g_alpha,
+             magnitudes: bool = False) -> dict:
+    """FP64 reverse-mode gradients of sum(g_rgb * rgb) + sum(g_alpha * alpha) over the listed pixels.
+
+    magnitudes=True also returns, under "mag", the same sums taken over the absolute values of
+    every pair's term (with the linear maps made entry-wise absolute): the scale of the rounding
+    error of a floating-point evaluation of each gradient element."""
     S = _SceneArrays(scene)
     px, py = _i32(pixels[0]), _i32(pixels[1])
     P = px.shape[0]
     n, nsh = S.n, (S.deg + 1) ** 2
-    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-               opacity_logits=np.zeros(n), sh=np.zeros((n, nsh, 3)))
+
+    def zeros():
+        return dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+                    opacity_logits=np.zeros(n), sh=np.zeros((n, nsh, 3)))
+    out = zeros()
+    mag = zeros() if magnitudes else None
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
     c, o = make_camera(cam), make_options(opts)
     lib().orc_backward(C.byref(S.s), C.byref(c), C.byref(o), _p(_i32(proj["rect"])), _p(_f32(proj["depth32"])),
                        P, _p(px), _p(py), _p(_f64(g_rgb).reshape(-1)), _p(_f64(g_alpha).reshape(-1)),
-                       _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
-                       _p(out["sh"]))
+                       *(_p(out[k]) for k in keys), *((_p(mag[k]) for k in keys) if mag else (None,) * 5))
+    if mag is not None:
+        out["mag"] = mag
     return out
 
 

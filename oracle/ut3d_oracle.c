@@ -832,30 +832,49 @@ typedef struct {
   double alpha, a, T, rho, tau, w2, og[3], dg[3], raw[3], col[3];
 } orc_contrib;
 
+/* Bounds a pixel's FP32 result may legitimately differ by from this FP64 one (all >= 0):
+ * slack / aslack for reorderings of depth-tied pairs and stop-threshold ties (exact effects),
+ * fslack / faslack for the other flagged decisions (a bound on what flipping them can do). */
+typedef struct {
+  double slack, aslack, fslack, faslack;
+} orc_slack;
+
 /* Composites one pixel ray over the particles in `order` (eq. QuadratureVolumeRendering with
  * alpha_i = sigma_i rho_i at tau_max).  Returns the number of blended particles; fills rgb, T.
  * When `rec` is given, records every blended particle (up to cap).
  * Depth near-ties: two consecutive blended particles whose FP32 depth keys are within
  * depth_ulps may legitimately come in either order from an FP32 depth; swapping them changes
- * the colour by exactly T_i alpha_i alpha_j (c_j - c_i), which is added to *slack.  Three or more
- * in a row set ORC_F_DEPTH_TIE instead.  A transmittance T (1 - alpha) within eps_t of t_min may
- * stop one particle earlier or later: its T alpha c is added to *slack and T alpha to *aslack. */
+ * the colour by exactly T_i alpha_i alpha_j (c_j - c_i), which is added to sl->slack.  Three or
+ * more in a row set ORC_F_DEPTH_TIE instead.  A transmittance T (1 - alpha) within eps_t of t_min
+ * may stop one particle earlier or later: its T alpha c is added to sl->slack and T alpha to
+ * sl->aslack.
+ * Flip bounds: a flagged decision about one particle (membership at a rect edge, alpha_min,
+ * the alpha_max clamp, the order inside a run of three or more depth ties) changes what that
+ * particle adds, T alpha c, by at most T dalpha c (dalpha = its alpha, or the clamp's change),
+ * and scales what comes after it, T (1 - alpha) S with S <= the largest colour c_max among the
+ * particles this ray evaluates, by at most T dalpha c_max; so sl->fslack = sum over flagged
+ * decisions of T dalpha (c + c_max) (+ t_min c_max for a stop that moves), and sl->faslack =
+ * sum of T dalpha (+ t_min). */
 static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_options *op, const orc_tol *tol,
                              int px, int py, const double o[3], const double d[3], const double *Y, double rgb[3],
-                             double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect, double *slack,
-                             double *aslack) {
+                             double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect, orc_slack *sl) {
   double T = 1.0;
   int nb = 0;
   uint32_t last_bits = 0;
   int have_last = 0, last_tie = 0;
-  double last_alpha = 0.0, last_T = 1.0, last_col[3] = {0, 0, 0};
+  double last_alpha = 0.0, last_T = 1.0, last_col[3] = {0, 0, 0}, last_cmax = 0.0;
+  double fb_c = 0.0, fb_a = 0.0, cmax_seen = 0.0;
+  int n_events = 0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
+  if (sl) sl->slack = sl->aslack = sl->fslack = sl->faslack = 0.0;
   for (int j = 0; j < x->norder; ++j) {
     int i = x->order[j];
     const orc_particle *p = &x->P[i];
     const int32_t *r = x->rect + 4 * i;
     int inside = px >= r[0] && px <= r[2] && py >= r[1] && py <= r[3];
     double og[3], dg[3], tau;
+    const float *beta = sc->sh + (size_t)i * x->nsh * 3;
+    const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
     if (!inside && !no_rect) {
       /* only a rect edge within eps of this pixel could flip membership */
       if (x->edges && flags) {
@@ -865,7 +884,21 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
         int ny = py >= e[2] - tol->eps_px && py <= e[3] + tol->eps_px;
         if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && px >= 0 && py >= 0) {
           double w2 = orc_omega2(p, o, d, og, dg, &tau);
-          if (p->sigma * orc_response(op, w2) >= op->alpha_min * (1.0 - tol->eps_rel)) *flags |= ORC_F_RECT_EDGE;
+          double ao = p->sigma * orc_response(op, w2);
+          if (ao >= op->alpha_min * (1.0 - tol->eps_rel)) {
+            *flags |= ORC_F_RECT_EDGE;
+            double co = 0.0;
+            for (int ch = 0; ch < 3; ++ch) {
+              double v = 0.5;
+              for (int kk = 0; kk < x->nsh; ++kk) v += beta[3 * kk + ch] * Yc[kk];
+              co = fmax(co, v);
+            }
+            double al = ao < op->alpha_max ? ao : op->alpha_max;
+            fb_c += T * al * co;
+            fb_a += T * al;
+            cmax_seen = fmax(cmax_seen, co);
+            ++n_events;
+          }
         }
       }
       continue;
@@ -873,48 +906,72 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     double w2 = orc_omega2(p, o, d, og, dg, &tau);
     double rho = orc_response(op, w2);
     double a = p->sigma * rho;
+    double raw[3], col[3], cmax = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
+      double v = 0.5;
+      for (int kk = 0; kk < x->nsh; ++kk) v += beta[3 * kk + ch] * Yc[kk];
+      raw[ch] = v;
+      col[ch] = v > 0.0 ? v : 0.0;
+      cmax = fmax(cmax, col[ch]);
+    }
+    double alpha = a < op->alpha_max ? a : op->alpha_max;
+    int event = 0;
     if (flags && x->edges && !no_rect) {
       const double *e = x->edges + 4 * i;
       double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
-      if ((ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel))
+      if ((ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel)) {
         *flags |= ORC_F_RECT_EDGE;
+        event = 1;
+      }
     }
-    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) *flags |= ORC_F_ALPHA_MIN;
+    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) {
+      *flags |= ORC_F_ALPHA_MIN;
+      event = 1;
+    }
+    if (a >= op->alpha_min * (1.0 - tol->eps_rel)) cmax_seen = fmax(cmax_seen, cmax);
+    if (event) {
+      fb_c += T * alpha * cmax;
+      fb_a += T * alpha;
+      ++n_events;
+    }
     if (a < op->alpha_min) continue;
-    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
-    double alpha = a < op->alpha_max ? a : op->alpha_max;
-    double Tn = T * (1.0 - alpha);
-    const float *beta = sc->sh + (size_t)i * x->nsh * 3;
-    const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
-    double raw[3], col[3], cmax = 0.0;
-    for (int ch = 0; ch < 3; ++ch) {
-      double s = 0.5;
-      for (int kk = 0; kk < x->nsh; ++kk) s += beta[3 * kk + ch] * Yc[kk];
-      raw[ch] = s;
-      col[ch] = s > 0.0 ? s : 0.0;
-      cmax = fmax(cmax, col[ch]);
+    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) {
+      *flags |= ORC_F_ALPHA_MAX;
+      double da = fabs(a - op->alpha_max);
+      fb_c += T * da * cmax;
+      fb_a += T * da;
+      ++n_events;
     }
+    double Tn = T * (1.0 - alpha);
     if (fabs(Tn - op->t_min) < tol->eps_t * op->t_min) {
       /* the stop decision may flip: this one particle is blended or not (and at most one more
        * after it, whose T is already below t_min) */
       if (flags) *flags |= ORC_F_TSTOP;
-      if (slack) *slack += T * alpha * cmax;
-      if (aslack) *aslack += T * alpha;
+      if (sl) {
+        sl->slack += T * alpha * cmax;
+        sl->aslack += T * alpha;
+      }
     }
     if (Tn < op->t_min) break;
     uint32_t bits = orc_f32_bits(x->depth32[i]);
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += col[ch] * alpha * T;
     if (have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) {
-      if (flags && last_tie) *flags |= ORC_F_DEPTH_TIE;
+      if (flags && last_tie) {
+        /* a run of three or more: the order inside it is bounded, not tracked */
+        *flags |= ORC_F_DEPTH_TIE;
+        fb_c += T * alpha * cmax + last_T * last_alpha * last_cmax;
+        fb_a += T * alpha + last_T * last_alpha;
+        ++n_events;
+      }
       double dc = 0.0;
       for (int ch = 0; ch < 3; ++ch) dc = fmax(dc, fabs(col[ch] - last_col[ch]));
-      if (slack) *slack += last_T * last_alpha * alpha * dc;
+      if (sl) sl->slack += last_T * last_alpha * alpha * dc;
       last_tie = 1;
     } else {
       last_tie = 0;
     }
     last_bits = bits; have_last = 1;
-    last_alpha = alpha; last_T = T;
+    last_alpha = alpha; last_T = T; last_cmax = cmax;
     for (int ch = 0; ch < 3; ++ch) last_col[ch] = col[ch];
     if (rec && nb < cap) {
       orc_contrib *c = &rec[nb];
@@ -923,6 +980,10 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
     }
     ++nb;
     T = Tn;
+  }
+  if (sl && n_events) {
+    sl->fslack = fb_c + fb_a * cmax_seen + op->t_min * cmax_seen;
+    sl->faslack = fb_a + op->t_min;
   }
   *Tout = T;
   return nb;
@@ -1040,13 +1101,15 @@ static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int 
  * rect / depth32 / valid come from orc_project or are given directly (synthetic).
  * edges / tie may be NULL (then no near-tie flags of those kinds).  no_rect != 0 evaluates
  * every particle at every pixel (culling disabled).
- * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags, and slack / aslack =
- * the largest colour / opacity change that FP32 depth ties and stop-threshold ties can cause
- * (see orc_composite_ray). */
+ * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags, slack / aslack =
+ * the largest colour / opacity change that FP32 depth ties and stop-threshold ties can cause, and
+ * fslack / faslack (nullable) = a bound on what the other flagged decisions can change (see
+ * orc_composite_ray; the k-buffer path leaves both at 0). */
 void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
                 const int32_t *rect, const float *depth32, const double *edges, const int32_t *tie, int npix,
                 const int32_t *pix_x, const int32_t *pix_y, int no_rect, double *rgb, double *alpha,
-                double *tfinal, int32_t *nblend, int32_t *flags, double *slack, double *aslack) {
+                double *tfinal, int32_t *nblend, int32_t *flags, double *slack, double *aslack, double *fslack,
+                double *faslack) {
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, edges, tie);
   double theta_max = orc_cam_limit(c);
@@ -1061,6 +1124,8 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     if (!valid) {
       rgb[3 * q] = rgb[3 * q + 1] = rgb[3 * q + 2] = 0.0;
       alpha[q] = 0.0; tfinal[q] = 1.0; nblend[q] = 0; flags[q] = fl; slack[q] = 0.0; aslack[q] = 0.0;
+      if (fslack) fslack[q] = 0.0;
+      if (faslack) faslack[q] = 0.0;
       continue;
     }
     for (int t = 0; t < x.ntie; ++t) {
@@ -1072,11 +1137,18 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     double T;
     slack[q] = 0.0;
     aslack[q] = 0.0;
-    if (op->kbuffer > 0)
+    if (fslack) fslack[q] = 0.0;
+    if (faslack) faslack[q] = 0.0;
+    if (op->kbuffer > 0) {
       nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, NULL, 0);
-    else
-      nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect,
-                                    &slack[q], &aslack[q]);
+    } else {
+      orc_slack sl;
+      nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect, &sl);
+      slack[q] = sl.slack;
+      aslack[q] = sl.aslack;
+      if (fslack) fslack[q] = sl.fslack;
+      if (faslack) faslack[q] = sl.faslack;
+    }
     alpha[q] = 1.0 - T;
     tfinal[q] = T;
     flags[q] = fl;
@@ -1100,7 +1172,7 @@ void orc_render_list(const orc_scene *sc, const orc_camera *c, const orc_options
   int valid;
   orc_pixel_setup(c, theta_max, x.deg, px, py, &tol, o, d, Y, &valid, NULL);
   if (!valid) { rgb[0] = rgb[1] = rgb[2] = 0; *tfinal = 1.0; }
-  else orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, tfinal, NULL, NULL, 0, 0, NULL, NULL);
+  else orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, tfinal, NULL, NULL, 0, 0, NULL);
   orc_ctx_free(&x);
 }
 
@@ -1127,7 +1199,8 @@ static void orc_rot_grad(const double q[4], const double G[9], double gq[4]) {
 void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *op, const int32_t *rect,
                   const float *depth32, int npix, const int32_t *pix_x, const int32_t *pix_y, const double *g_rgb,
                   const double *g_alpha, double *d_means, double *d_log_scales, double *d_quats,
-                  double *d_logits, double *d_sh) {
+                  double *d_logits, double *d_sh, double *m_means, double *m_log_scales, double *m_quats,
+                  double *m_logits, double *m_sh) {
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, NULL, NULL);
   int n = sc->n, nsh = x.nsh;
@@ -1136,6 +1209,14 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   /* accumulators: dM (9), dmu (3), dsigma (1), dL/d colour (3, colour_mode 1) */
   double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double));
   memset(d_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
+  /* Optional magnitudes (m_* non-NULL): the same sums with every pair's term replaced by its
+   * absolute value and every linear map by its entry-wise absolute value.  A sum computed in
+   * floating point with unit roundoff u deviates from the exact one by at most about
+   * n u sum |x_i| (the classical summation bound, Higham, "Accuracy and Stability of
+   * Numerical Algorithms", Sec. 4.2), so these give the scale of an FP32 result's error. */
+  const int want_mag = m_means && m_log_scales && m_quats && m_logits && m_sh;
+  double *macc = want_mag ? (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double)) : NULL;
+  if (want_mag) memset(m_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
   orc_tol tol = {0, 0, 0, 0, 0};
 #pragma omp parallel
   {
@@ -1151,7 +1232,7 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
       /* the blended pairs in blending order: the tile (depth) order, or the k-buffer's order */
       int nb = op->kbuffer > 0
                    ? orc_composite_ray_kbuffer(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, NULL, rec, x.norder)
-                   : orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL, NULL);
+                   : orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL);
       const double *g = g_rgb + 3 * q;
       double gA = g_alpha[q];
       double S[3] = {0, 0, 0}; /* sum over later blended particles of c alpha T */
@@ -1170,11 +1251,19 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
           if (op->colour_mode == 1) {
 #pragma omp atomic
             acc[16 * (size_t)k->i + 13 + ch] += gc;
+            if (want_mag) {
+#pragma omp atomic
+              macc[16 * (size_t)k->i + 13 + ch] += fabs(gc);
+            }
             continue;
           }
           for (int kk = 0; kk < nsh; ++kk) {
 #pragma omp atomic
             d_sh[((size_t)k->i * nsh + kk) * 3 + ch] += gc * Y[kk];
+            if (want_mag) {
+#pragma omp atomic
+              m_sh[((size_t)k->i * nsh + kk) * 3 + ch] += fabs(gc * Y[kk]);
+            }
           }
         }
         double da = k->a > op->alpha_max ? 0.0 : dalpha;
@@ -1198,6 +1287,21 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
         }
 #pragma omp atomic
         A[12] += dsig;
+        if (want_mag) {
+          double *MA = macc + 16 * (size_t)k->i;
+          for (int r = 0; r < 3; ++r)
+            for (int j = 0; j < 3; ++j) {
+#pragma omp atomic
+              MA[3 * r + j] += fabs(pv[r] * xw[j]);
+            }
+          for (int j = 0; j < 3; ++j) {
+            double dm = fabs(p->M[j] * pv[0]) + fabs(p->M[3 + j] * pv[1]) + fabs(p->M[6 + j] * pv[2]);
+#pragma omp atomic
+            MA[9 + j] += dm;
+          }
+#pragma omp atomic
+          MA[12] += fabs(dsig);
+        }
       }
     }
     free(rec);
@@ -1234,8 +1338,49 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
     double dot = gq[0] * p->qn[0] + gq[1] * p->qn[1] + gq[2] * p->qn[2] + gq[3] * p->qn[3];
     for (int j = 0; j < 4; ++j) d_quats[4 * i + j] = (gq[j] - p->qn[j] * dot) / p->qnorm;
     d_logits[i] = A[12] * p->sigma * (1.0 - p->sigma);
+    if (want_mag) {
+      /* the same maps, entry-wise absolute, applied to the absolute sums */
+      const double *MA = macc + 16 * (size_t)i;
+      for (int j = 0; j < 3; ++j) m_means[3 * i + j] = MA[9 + j];
+      if (op->colour_mode == 1) {
+        const float *beta = sc->sh + (size_t)i * nsh * 3;
+        for (int ch = 0; ch < 3; ++ch) {
+          double gc = MA[13 + ch];
+          for (int kk = 0; kk < nsh; ++kk) {
+            m_sh[((size_t)i * nsh + kk) * 3 + ch] += gc * fabs(x.Yp[16 * (size_t)i + kk]);
+            for (int j = 0; j < 3; ++j)
+              m_means[3 * i + j] += gc * fabs(beta[3 * kk + ch] * x.dYdmu[48 * (size_t)i + 16 * j + kk]);
+          }
+        }
+      }
+      double Ga[9];
+      for (int k = 0; k < 3; ++k) {
+        double acc_l = 0;
+        for (int j = 0; j < 3; ++j) {
+          acc_l += MA[3 * k + j] * fabs(p->M[3 * k + j]);
+          Ga[3 * j + k] = MA[3 * k + j] / p->s[k];
+        }
+        m_log_scales[3 * i + k] = acc_l;
+      }
+      /* quaternion map L = (I - q q^T) J / |q| with J = d gq / d G, column by column */
+      double L[4][9];
+      for (int m = 0; m < 9; ++m) {
+        double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gj[4];
+        e[m] = 1.0;
+        orc_rot_grad(p->qn, e, gj);
+        double dj = gj[0] * p->qn[0] + gj[1] * p->qn[1] + gj[2] * p->qn[2] + gj[3] * p->qn[3];
+        for (int j = 0; j < 4; ++j) L[j][m] = (gj[j] - p->qn[j] * dj) / p->qnorm;
+      }
+      for (int j = 0; j < 4; ++j) {
+        double mq = 0.0;
+        for (int m = 0; m < 9; ++m) mq += fabs(L[j][m]) * Ga[m];
+        m_quats[4 * i + j] = mq;
+      }
+      m_logits[i] = MA[12] * p->sigma * (1.0 - p->sigma);
+    }
   }
   free(acc);
+  free(macc);
   orc_ctx_free(&x);
 }
 

@@ -1036,3 +1036,67 @@ def test_dalpha_dmu_matches_printed_chain(orc):
     dog_dmu = -M
     expect = dalpha_dw2 * dw2_dog @ dog_dmu
     assert np.allclose(gr["means"][0], expect, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ error-scale outputs of the oracle
+
+def test_gradient_magnitudes_bound_the_gradients(orc):
+    """The backward's magnitudes (the gradient sums taken over absolute values) bound every
+    gradient element (triangle inequality), and with a single particle seen by a single pixel
+    (one term in every sum) they equal the absolute gradients."""
+    sc = _fd_scene(deg=1)
+    cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
+    op = synth.options()
+    proj = orc.project(sc, cam, op)
+    yy, xx = np.mgrid[0:20, 0:24]
+    pix = (xx.reshape(-1), yy.reshape(-1))
+    rng = np.random.default_rng(3)
+    g_rgb = rng.standard_normal((pix[0].size, 3))
+    g_a = rng.standard_normal(pix[0].size)
+    gr = orc.backward(sc, cam, op, proj, pix, g_rgb, g_a, magnitudes=True)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert np.all(gr["mag"][k] >= np.abs(gr[k]) * (1 - 1e-12) - 1e-300), k
+        assert np.any(gr["mag"][k] > 1.5 * np.abs(gr[k])), k  # cancellation happens somewhere
+    one = one_scene([0.05, -0.02, 3.0], [-1.2, -1.5, -1.4], [0.9, 0.2, -0.3, 0.1], 0.3,
+                    [[0.3, -0.2, 0.1], [0.1, 0.05, -0.1], [0.02, -0.03, 0.04], [-0.05, 0.01, 0.02]], deg=1)
+    p1 = orc.project(one, cam, op)
+    px, py = np.array([12]), np.array([10])
+    g1 = orc.backward(one, cam, op, p1, (px, py), np.array([[0.7, -0.4, 0.2]]), np.array([0.3]), magnitudes=True)
+    assert abs(g1["mag"]["opacity_logits"][0] - abs(g1["opacity_logits"][0])) < 1e-15
+    assert np.allclose(g1["mag"]["sh"], np.abs(g1["sh"]), rtol=1e-15, atol=0)
+
+
+def test_flip_bound_covers_an_alpha_min_decision(orc):
+    """Where a particle's sigma rho sits at alpha_min, rendering with alpha_min just above and just
+    below it includes and excludes the particle: the colour and opacity change between the two
+    must stay within the flip bounds (fslack / faslack) the oracle reports for that pixel."""
+    sc = _fd_scene(deg=1)
+    cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
+    op = synth.options()
+    proj = orc.project(sc, cam, op)
+    yy, xx = np.mgrid[0:20, 0:24]
+    px, py = xx.reshape(-1), yy.reshape(-1)
+    checked = 0
+    for j in range(sc["means"].shape[0]):
+        single = {k: (v[j:j + 1] if k != "sh_degree" else v) for k, v in sc.items()}
+        pj = dict(rect=proj["rect"][j:j + 1], depth32=proj["depth32"][j:j + 1])
+        a1 = orc.render(single, cam, op, proj=pj, pixels=(px, py), tol=dict(eps_px=0.0))["alpha"]
+        q = int(np.argmax(np.where(a1 < 0.5, a1, 0)))  # a pixel where it is partly transparent
+        a = a1[q]
+        if not (0.01 < a < 0.5):
+            continue
+        renders = []
+        for amin in (a * (1 - 1e-6), a * (1 + 1e-6)):
+            o2 = dict(op, alpha_min=float(amin))
+            renders.append(orc.render(sc, cam, o2, proj=proj, pixels=(px[q:q + 1], py[q:q + 1]),
+                                      tol=dict(eps_px=0.0, eps_rel=1e-4)))
+        dc = np.abs(renders[0]["rgb"] - renders[1]["rgb"]).max()
+        da = abs(renders[0]["alpha"][0] - renders[1]["alpha"][0])
+        assert renders[0]["flags"][0] & orc.F_ALPHA_MIN and renders[1]["flags"][0] & orc.F_ALPHA_MIN
+        assert dc > 1e-4  # the decision matters
+        for r in renders:
+            assert dc <= r["fslack"][0] + r["slack"][0] + 1e-12, (dc, r["fslack"][0])
+            assert da <= r["faslack"][0] + r["aslack"][0] + 1e-12, (da, r["faslack"][0])
+            assert r["fslack"][0] < 20 * dc + 4e-4  # and the bound is not vacuous
+        checked += 1
+    assert checked >= 4
