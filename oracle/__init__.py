@@ -22,11 +22,15 @@ _lib = None
 
 # pixel flag bits (mirror the enum in ut3d_oracle.c)
 F_RECT_EDGE, F_ALPHA_MIN, F_TSTOP, F_DEPTH_TIE = 1, 2, 4, 8
-F_CULL_TIE, F_PIXEL_EDGE, F_ILL_COND, F_ALPHA_MAX, F_INVALID_PIXEL = 16, 32, 64, 128, 256
+F_CULL_TIE, F_PIXEL_EDGE, F_ILL_COND, F_ALPHA_MAX, F_INVALID_PIXEL, F_CLAMP = 16, 32, 64, 128, 256, 512
 # flags that can change the forward result between an FP32 and an FP64 evaluation
 # (depth-tied pairs and stop-threshold ties are not in this set: their effect is bounded by the
 # per-pixel slack / aslack that render() returns)
 F_FORWARD_TIES = (F_RECT_EDGE | F_ALPHA_MIN | F_DEPTH_TIE | F_CULL_TIE | F_PIXEL_EDGE | F_ILL_COND)
+# flags whose decisions can change a gradient between an FP32 and an FP64 evaluation: the
+# forward's, the alpha_max clamp and the stop (both change which terms are differentiated),
+# and a colour channel at its clamp at 0 (the colour is continuous there, its derivative not)
+F_BACKWARD_TIES = F_FORWARD_TIES | F_ALPHA_MAX | F_TSTOP | F_CLAMP
 
 
 def build(force: bool = False) -> str:
@@ -92,7 +96,7 @@ def lib():
         L.orc_count_keys.argtypes = [C.c_int, P, C.c_int, C.c_int]
         L.orc_bin.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_render.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), C.POINTER(Tol),
-                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, P, P, P]
+                                 P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_render_list.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P,
                                       C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_backward.argtypes = [C.POINTER(Scene), C.POINTER(Camera), C.POINTER(Options), P, P, C.c_int,
@@ -282,7 +286,8 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
     proj: output of project() (or a dict with rect / depth32 and optionally edges / tie,
     e.g. synthetic arrays).  Returns rgb[P,3], alpha[P], tfinal[P], nblend[P], flags[P],
     slack / aslack (the colour / opacity change depth-tied pairs and stop ties can cause),
-    fslack / faslack (a bound on what flipping the other flagged decisions can change), and px, py."""
+    fslack / faslack (a bound on what flipping the other flagged decisions can change),
+    rslack / raslack (the FP32 rounding bound of the blended particles' alphas), and px, py."""
     S = _SceneArrays(scene)
     if proj is None:
         proj = project(scene, cam, opts, tol)
@@ -300,12 +305,13 @@ def render(scene: dict, cam: dict, opts: dict | None = None, proj: dict | None =
     tie = _i32(proj["tie"]) if proj.get("tie") is not None else None
     out = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), tfinal=np.zeros(P), nblend=np.zeros(P, np.int32),
                flags=np.zeros(P, np.int32), slack=np.zeros(P), aslack=np.zeros(P), fslack=np.zeros(P),
-               faslack=np.zeros(P), px=px, py=py)
+               faslack=np.zeros(P), rslack=np.zeros(P), raslack=np.zeros(P), px=px, py=py)
     c, o, t = make_camera(cam), make_options(opts), make_tol(tol)
     lib().orc_render(C.byref(S.s), C.byref(c), C.byref(o), C.byref(t), _p(rect), _p(depth32), _p(edges),
                      _p(tie), P, _p(px), _p(py), int(no_rect), _p(out["rgb"]), _p(out["alpha"]),
                      _p(out["tfinal"]), _p(out["nblend"]), _p(out["flags"]), _p(out["slack"]),
-                     _p(out["aslack"]), _p(out["fslack"]), _p(out["faslack"]))
+                     _p(out["aslack"]), _p(out["fslack"]), _p(out["faslack"]), _p(out["rslack"]),
+                     _p(out["raslack"]))
     return out
 
 

@@ -91,8 +91,21 @@ typedef struct {
 enum {
   ORC_F_RECT_EDGE = 1, ORC_F_ALPHA_MIN = 2, ORC_F_TSTOP = 4, ORC_F_DEPTH_TIE = 8,
   ORC_F_CULL_TIE = 16, ORC_F_PIXEL_EDGE = 32, ORC_F_ILL_COND = 64, ORC_F_ALPHA_MAX = 128,
-  ORC_F_INVALID_PIXEL = 256
+  ORC_F_INVALID_PIXEL = 256, ORC_F_CLAMP = 512
 };
+
+/* A blended particle's colour channel sum_k beta_k Y_k + 1/2 within eps_rel of 0, relative to
+ * the size of its terms: the clamp max(., 0) may go either way in FP32.  The colour itself is
+ * continuous there (it is ~0 on both sides), but its derivative is not, so a gradient through
+ * such a pixel may legitimately differ: ORC_F_CLAMP (it does not concern the forward). */
+static int orc_clamp_tie(const float *beta, const double *Yc, int nsh, const double raw[3], double eps) {
+  for (int ch = 0; ch < 3; ++ch) {
+    double scale = 0.5;
+    for (int kk = 0; kk < nsh; ++kk) scale += fabs(beta[3 * kk + ch] * Yc[kk]);
+    if (fabs(raw[ch]) < eps * scale) return 1;
+  }
+  return 0;
+}
 
 /* ------------------------------------------------------------------ rotations */
 
@@ -836,8 +849,29 @@ typedef struct {
  * slack / aslack for reorderings of depth-tied pairs and stop-threshold ties (exact effects),
  * fslack / faslack for the other flagged decisions (a bound on what flipping them can do). */
 typedef struct {
-  double slack, aslack, fslack, faslack;
+  double slack, aslack, fslack, faslack, rslack, raslack;
 } orc_slack;
+
+/* Bound on the FP32 rounding of a blended particle's alpha.  The response is evaluated from the
+ * canonical-frame ray o_g = M (o - mu), d_g = M d: o - mu (and the ray) are known to about
+ * u (|o| + |mu|) in FP32 (u = 2^-24), so the ray's Mahalanobis distance omega carries an
+ * absolute error of about u |M|_F (|o| + |mu|), which the response's slope turns into
+ * |d alpha| = |d alpha / d omega^2| 2 omega |d omega|.  For a particle much smaller than its
+ * distance (|M| large) this dominates every other rounding.  The factor 2 covers the two
+ * roundings on the way (o - mu, then M times it); |M|_F >= |M|_2 and |o| + |mu| >= |o - mu|
+ * already make the estimate an upper one. */
+static double orc_alpha_rounding(const orc_options *op, const orc_particle *p, const double o[3], double w2,
+                                 double rho) {
+  double mf = 0.0, on = 0.0, mn = 0.0;
+  for (int j = 0; j < 9; ++j) mf += p->M[j] * p->M[j];
+  for (int j = 0; j < 3; ++j) {
+    on += o[j] * o[j];
+    mn += p->mu[j] * p->mu[j];
+  }
+  const double u = ldexp(1.0, -24);
+  const double dw = 2.0 * u * sqrt(mf) * (sqrt(on) + sqrt(mn));
+  return fabs(p->sigma * orc_dresponse(op, w2, rho)) * 2.0 * sqrt(w2) * dw;
+}
 
 /* Composites one pixel ray over the particles in `order` (eq. QuadratureVolumeRendering with
  * alpha_i = sigma_i rho_i at tau_max).  Returns the number of blended particles; fills rgb, T.
@@ -854,7 +888,8 @@ typedef struct {
  * and scales what comes after it, T (1 - alpha) S with S <= the largest colour c_max among the
  * particles this ray evaluates, by at most T dalpha c_max; so sl->fslack = sum over flagged
  * decisions of T dalpha (c + c_max) (+ t_min c_max for a stop that moves), and sl->faslack =
- * sum of T dalpha (+ t_min). */
+ * sum of T dalpha (+ t_min).  The same two terms with dalpha = the FP32 rounding bound of each
+ * blended particle's alpha (orc_alpha_rounding) give sl->rslack / sl->raslack. */
 static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_options *op, const orc_tol *tol,
                              int px, int py, const double o[3], const double d[3], const double *Y, double rgb[3],
                              double *Tout, int32_t *flags, orc_contrib *rec, int cap, int no_rect, orc_slack *sl) {
@@ -863,10 +898,10 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
   uint32_t last_bits = 0;
   int have_last = 0, last_tie = 0;
   double last_alpha = 0.0, last_T = 1.0, last_col[3] = {0, 0, 0}, last_cmax = 0.0;
-  double fb_c = 0.0, fb_a = 0.0, cmax_seen = 0.0;
+  double fb_c = 0.0, fb_a = 0.0, cmax_seen = 0.0, rb_c = 0.0, rb_a = 0.0;
   int n_events = 0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
-  if (sl) sl->slack = sl->aslack = sl->fslack = sl->faslack = 0.0;
+  if (sl) sl->slack = sl->aslack = sl->fslack = sl->faslack = sl->rslack = sl->raslack = 0.0;
   for (int j = 0; j < x->norder; ++j) {
     int i = x->order[j];
     const orc_particle *p = &x->P[i];
@@ -953,8 +988,14 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
       }
     }
     if (Tn < op->t_min) break;
+    if (flags && orc_clamp_tie(beta, Yc, x->nsh, raw, tol->eps_rel)) *flags |= ORC_F_CLAMP;
     uint32_t bits = orc_f32_bits(x->depth32[i]);
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += col[ch] * alpha * T;
+    if (sl && a <= op->alpha_max) {
+      const double dr = orc_alpha_rounding(op, p, o, w2, rho);
+      rb_c += T * dr * cmax;
+      rb_a += T * dr;
+    }
     if (have_last && (int64_t)bits - (int64_t)last_bits <= tol->depth_ulps) {
       if (flags && last_tie) {
         /* a run of three or more: the order inside it is bounded, not tracked */
@@ -984,6 +1025,10 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
   if (sl && n_events) {
     sl->fslack = fb_c + fb_a * cmax_seen + op->t_min * cmax_seen;
     sl->faslack = fb_a + op->t_min;
+  }
+  if (sl) {
+    sl->rslack = rb_c + rb_a * cmax_seen;
+    sl->raslack = rb_a;
   }
   *Tout = T;
   return nb;
@@ -1054,6 +1099,7 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
       h.c.raw[ch] = s;
       h.c.col[ch] = h.col[ch];
     }
+    if (flags && orc_clamp_tie(beta, Yc, x->nsh, h.c.raw, tol->eps_rel)) *flags |= ORC_F_CLAMP;
     h.c.i = i; h.c.alpha = h.alpha; h.c.a = a; h.c.rho = rho; h.c.tau = tau; h.c.w2 = w2;
     for (int kk = 0; kk < 3; ++kk) { h.c.og[kk] = og[kk]; h.c.dg[kk] = dg[kk]; }
     if (nbuf < k) { buf[nbuf++] = h; continue; }
@@ -1103,13 +1149,14 @@ static void orc_pixel_setup(const orc_camera *c, double theta_max, int deg, int 
  * every particle at every pixel (culling disabled).
  * Outputs per listed pixel: rgb[3], alpha = 1 - T_final, tfinal, nblend, flags, slack / aslack =
  * the largest colour / opacity change that FP32 depth ties and stop-threshold ties can cause, and
- * fslack / faslack (nullable) = a bound on what the other flagged decisions can change (see
- * orc_composite_ray; the k-buffer path leaves both at 0). */
+ * fslack / faslack (nullable) = a bound on what the other flagged decisions can change, and
+ * rslack / raslack (nullable) = the FP32 rounding bound of the blended particles' alphas (see
+ * orc_composite_ray; the k-buffer path leaves these at 0). */
 void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op, const orc_tol *tol,
                 const int32_t *rect, const float *depth32, const double *edges, const int32_t *tie, int npix,
                 const int32_t *pix_x, const int32_t *pix_y, int no_rect, double *rgb, double *alpha,
                 double *tfinal, int32_t *nblend, int32_t *flags, double *slack, double *aslack, double *fslack,
-                double *faslack) {
+                double *faslack, double *rslack, double *raslack) {
   orc_ctx x;
   orc_ctx_init(&x, sc, rect, depth32, edges, tie);
   double theta_max = orc_cam_limit(c);
@@ -1126,6 +1173,8 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
       alpha[q] = 0.0; tfinal[q] = 1.0; nblend[q] = 0; flags[q] = fl; slack[q] = 0.0; aslack[q] = 0.0;
       if (fslack) fslack[q] = 0.0;
       if (faslack) faslack[q] = 0.0;
+      if (rslack) rslack[q] = 0.0;
+      if (raslack) raslack[q] = 0.0;
       continue;
     }
     for (int t = 0; t < x.ntie; ++t) {
@@ -1139,6 +1188,8 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     aslack[q] = 0.0;
     if (fslack) fslack[q] = 0.0;
     if (faslack) faslack[q] = 0.0;
+    if (rslack) rslack[q] = 0.0;
+    if (raslack) raslack[q] = 0.0;
     if (op->kbuffer > 0) {
       nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, NULL, 0);
     } else {
@@ -1148,6 +1199,8 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
       aslack[q] = sl.aslack;
       if (fslack) fslack[q] = sl.fslack;
       if (faslack) faslack[q] = sl.faslack;
+      if (rslack) rslack[q] = sl.rslack;
+      if (raslack) raslack[q] = sl.raslack;
     }
     alpha[q] = 1.0 - T;
     tfinal[q] = T;
@@ -1209,11 +1262,15 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
   /* accumulators: dM (9), dmu (3), dsigma (1), dL/d colour (3, colour_mode 1) */
   double *acc = (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double));
   memset(d_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
-  /* Optional magnitudes (m_* non-NULL): the same sums with every pair's term replaced by its
-   * absolute value and every linear map by its entry-wise absolute value.  A sum computed in
-   * floating point with unit roundoff u deviates from the exact one by at most about
-   * n u sum |x_i| (the classical summation bound, Higham, "Accuracy and Stability of
-   * Numerical Algorithms", Sec. 4.2), so these give the scale of an FP32 result's error. */
+  /* Optional magnitudes (m_* non-NULL): the whole computation evaluated on absolute values --
+   * every sum (and difference) of the per-pair chain, the sums over pairs and the final linear
+   * maps taken over the absolute values of their operands.  A floating-point evaluation with
+   * unit roundoff u deviates from the exact value by at most about (number of rounding steps)
+   * u times this magnitude (the running error bound of forward error analysis; Higham,
+   * "Accuracy and Stability of Numerical Algorithms", Sec. 3.1 and 4.2), whatever the order of
+   * the sums, so it gives the scale of an FP32 result's error.  The suffix colour of a pair is
+   * bounded by twice the pixel's final colour, which covers an evaluation that forms it as the
+   * final colour minus a running prefix. */
   const int want_mag = m_means && m_log_scales && m_quats && m_logits && m_sh;
   double *macc = want_mag ? (double *)calloc((size_t)(n > 0 ? n : 1) * 16, sizeof(double)) : NULL;
   if (want_mag) memset(m_sh, 0, sizeof(double) * (size_t)n * nsh * 3);
@@ -1288,19 +1345,40 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
 #pragma omp atomic
         A[12] += dsig;
         if (want_mag) {
+          /* the per-pair chain on absolute values */
+          double dal_a = fabs(gA) * Tf / om1;
+          for (int ch = 0; ch < 3; ++ch) dal_a += fabs(g[ch]) * (k->col[ch] * k->T + 2.0 * rgb[ch] / om1);
+          const double da_a = k->a > op->alpha_max ? 0.0 : dal_a;
+          const double dw2_a = da_a * p->sigma * fabs(orc_dresponse(op, k->w2, k->rho));
+          double og_a[3], dg_a[3], dd = 0.0, num = 0.0;
+          for (int r = 0; r < 3; ++r) {
+            og_a[r] = dg_a[r] = 0.0;
+            for (int j = 0; j < 3; ++j) {
+              og_a[r] += fabs(p->M[3 * r + j]) * (fabs(o[j]) + fabs(p->mu[j]));
+              dg_a[r] += fabs(p->M[3 * r + j]) * fabs(d[j]);
+            }
+            dd += k->dg[r] * k->dg[r];
+            num += og_a[r] * dg_a[r];
+          }
+          const double tau_a = num / dd;
+          double pv_a[3], xw_a[3];
+          for (int j = 0; j < 3; ++j) {
+            pv_a[j] = 2.0 * dw2_a * (og_a[j] + tau_a * dg_a[j]);
+            xw_a[j] = fabs(o[j]) + fabs(p->mu[j]) + tau_a * fabs(d[j]);
+          }
           double *MA = macc + 16 * (size_t)k->i;
           for (int r = 0; r < 3; ++r)
             for (int j = 0; j < 3; ++j) {
 #pragma omp atomic
-              MA[3 * r + j] += fabs(pv[r] * xw[j]);
+              MA[3 * r + j] += pv_a[r] * xw_a[j];
             }
           for (int j = 0; j < 3; ++j) {
-            double dm = fabs(p->M[j] * pv[0]) + fabs(p->M[3 + j] * pv[1]) + fabs(p->M[6 + j] * pv[2]);
+            double dm = fabs(p->M[j]) * pv_a[0] + fabs(p->M[3 + j]) * pv_a[1] + fabs(p->M[6 + j]) * pv_a[2];
 #pragma omp atomic
             MA[9 + j] += dm;
           }
 #pragma omp atomic
-          MA[12] += fabs(dsig);
+          MA[12] += da_a * k->rho;
         }
       }
     }

@@ -43,20 +43,76 @@ def frame_at(frame, px, py):
     return rgb[:, py, px].T, to_np(frame.alpha)[py, px], tf
 
 
-def compare_frame(frame, ref, tol=RGB_TOL):
-    """Max |rgb - oracle| and |alpha - oracle| over pixels without a forward near-tie flag."""
+# flags whose pixels carry no bound: a particle whose culling is a near tie may be present on one
+# side only, and the oracle does not evaluate a culled particle
+UNBOUNDED = oracle.F_CULL_TIE
+
+
+def compare_frame(frame, ref, tol=RGB_TOL, unbounded=None):
+    """Per-pixel error of the GPU frame beyond what the oracle bounds:
+    err = max(|rgb - oracle| - slack - fslack - rslack, |alpha - oracle| - aslack - faslack - raslack),
+    where slack covers depth-tied pairs and stop-threshold ties, fslack the other flagged decisions
+    and rslack the FP32 rounding of the blended particles' alphas.  Every pixel without an
+    `unbounded` flag (default: a culling near-tie) is compared against tol."""
+    unb = UNBOUNDED if unbounded is None else unbounded
     got_rgb, got_a, _ = frame_at(frame, ref["px"], ref["py"])
-    flagged = (ref["flags"] & oracle.F_FORWARD_TIES) != 0
-    # reordering depth-tied pairs changes the colour by at most the oracle's slack
-    err = np.maximum(np.abs(got_rgb - ref["rgb"]).max(axis=1) - ref["slack"],
-                     np.abs(got_a - ref["alpha"]) - ref["aslack"])
-    ok = ~flagged
-    return dict(max_err=float(err[ok].max()) if ok.any() else 0.0, n=int(err.size), n_flagged=int(flagged.sum()),
-                n_slack=int((ref["slack"] > 0).sum()),
-                n_bad=int((err[ok] > tol).sum()), max_err_flagged=float(err[flagged].max()) if flagged.any() else 0.0)
+    flags = ref["flags"]
+    flagged = (flags & oracle.F_FORWARD_TIES) != 0
+    bounded = (flags & unb) == 0
+    raw = np.maximum(np.abs(got_rgb - ref["rgb"]).max(axis=1), np.abs(got_a - ref["alpha"]))
+    err = np.maximum(np.abs(got_rgb - ref["rgb"]).max(axis=1) - ref["slack"] - ref["fslack"] - ref["rslack"],
+                     np.abs(got_a - ref["alpha"]) - ref["aslack"] - ref["faslack"] - ref["raslack"])
+    fb = flagged & bounded
+    out = dict(max_err=float(err[bounded].max()) if bounded.any() else 0.0, n=int(err.size),
+               n_flagged=int(flagged.sum()), n_unbounded=int((~bounded).sum()),
+               n_slack=int((ref["slack"] > 0).sum()), n_bad=int((err[bounded] > tol).sum()),
+               max_err_flagged=float(err[fb].max()) if fb.any() else 0.0, max_raw=float(raw.max()),
+               max_rslack=float(ref["rslack"].max()))
+    if bounded.any():
+        q = int(np.argmax(np.where(bounded, err, -np.inf)))
+        out["worst"] = dict(px=int(ref["px"][q]), py=int(ref["py"][q]), flags=int(flags[q]), raw=float(raw[q]),
+                            slack=float(ref["slack"][q]), fslack=float(ref["fslack"][q]),
+                            rslack=float(ref["rslack"][q]))
+    return out
+
+
+def gpu_decisions(g):
+    """The GPU projection's discrete decisions (rects and FP32 depth bits) for the oracle: with
+    them the oracle composites exactly the per-pixel lists the kernels composite."""
+    return dict(rect=to_np(g["proj"].rect).astype(np.int32), depth32=to_np(g["proj"].depth))
+
+
+# the oracle's tolerances in decision-injected mode: rects and depth order come from the GPU,
+# so no rect-edge, culling or depth-order flags remain
+TOL_INJECTED = dict(TOL, depth_ulps=-1)
 
 
 def sample_pixels(W, H, n, seed):
     rng = np.random.default_rng(seed)
     q = rng.choice(W * H, size=min(n, W * H), replace=False)
     return (q % W).astype(np.int32), (q // W).astype(np.int32)
+
+# Element-wise gradient bar: |g - g_ref| <= 1e-3 |g_ref| + 1e-6 max |g_ref| + KAPPA mag, where mag
+# is the oracle's magnitude of that element (its whole computation evaluated on absolute values).
+# A floating-point evaluation errs by at most about (rounding steps) x u x mag (u = 2^-24, the
+# running error bound).  The SH coefficients' gradients are contracted on the tensor cores with
+# BF16 hi / lo operands, whose three-term products carry a relative error up to 2^-15 each;
+# KAPPA = 2^-14 covers that and the sums' own rounding (1024 u).
+KAPPA = 2.0 ** -14
+
+
+def grad_compare(got, ref, mag, name, rel=1e-3):
+    """Per tensor ||g - g_ref|| / ||g_ref|| <= rel, and every element within the bar above."""
+    g = got.reshape(-1).astype(np.float64)
+    r = ref.reshape(-1)
+    m = mag.reshape(-1)
+    nrm = np.linalg.norm(r)
+    assert nrm > 0, name
+    e = np.linalg.norm(g - r) / nrm
+    assert e <= rel, (name, e)
+    bound = rel * np.abs(r) + 1e-6 * np.max(np.abs(r)) + KAPPA * m
+    bad = np.abs(g - r) > bound
+    if bad.any():
+        j = int(np.argmax(np.abs(g - r) / bound))
+        raise AssertionError((name, int(bad.sum()), "worst", j, float(g[j]), float(r[j]), float(m[j])))
+    return e

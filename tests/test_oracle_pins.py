@@ -1041,9 +1041,10 @@ def test_dalpha_dmu_matches_printed_chain(orc):
 # ------------------------------------------------------------------ error-scale outputs of the oracle
 
 def test_gradient_magnitudes_bound_the_gradients(orc):
-    """The backward's magnitudes (the gradient sums taken over absolute values) bound every
-    gradient element (triangle inequality), and with a single particle seen by a single pixel
-    (one term in every sum) they equal the absolute gradients."""
+    """The backward's magnitudes (the computation evaluated on absolute values) bound every
+    gradient element (triangle inequality), and where a single term remains -- one particle, one
+    pixel, an opacity-only loss for the logit, a colour-only loss for the SH coefficients -- they
+    equal the absolute gradients."""
     sc = _fd_scene(deg=1)
     cam = synth.camera("pinhole", 24, 20, fx=30.0, fy=30.0, cx=12.0, cy=10.0)
     op = synth.options()
@@ -1061,9 +1062,14 @@ def test_gradient_magnitudes_bound_the_gradients(orc):
                     [[0.3, -0.2, 0.1], [0.1, 0.05, -0.1], [0.02, -0.03, 0.04], [-0.05, 0.01, 0.02]], deg=1)
     p1 = orc.project(one, cam, op)
     px, py = np.array([12]), np.array([10])
-    g1 = orc.backward(one, cam, op, p1, (px, py), np.array([[0.7, -0.4, 0.2]]), np.array([0.3]), magnitudes=True)
-    assert abs(g1["mag"]["opacity_logits"][0] - abs(g1["opacity_logits"][0])) < 1e-15
-    assert np.allclose(g1["mag"]["sh"], np.abs(g1["sh"]), rtol=1e-15, atol=0)
+    g1 = orc.backward(one, cam, op, p1, (px, py), np.zeros((1, 3)), np.array([0.3]), magnitudes=True)
+    assert g1["opacity_logits"][0] != 0
+    assert abs(g1["mag"]["opacity_logits"][0] - abs(g1["opacity_logits"][0])) < 1e-15 * abs(g1["opacity_logits"][0])
+    g2 = orc.backward(one, cam, op, p1, (px, py), np.array([[0.7, -0.4, 0.2]]), np.zeros(1), magnitudes=True)
+    assert np.abs(g2["sh"]).max() > 0
+    assert np.allclose(g2["mag"]["sh"], np.abs(g2["sh"]), rtol=1e-15, atol=0)
+    for k in ("means", "log_scales", "quats", "opacity_logits"):
+        assert np.all(g2["mag"][k] >= np.abs(g2[k]) * (1 - 1e-12)), k
 
 
 def test_flip_bound_covers_an_alpha_min_decision(orc):
@@ -1100,3 +1106,62 @@ def test_flip_bound_covers_an_alpha_min_decision(orc):
             assert r["fslack"][0] < 20 * dc + 4e-4  # and the bound is not vacuous
         checked += 1
     assert checked >= 4
+
+
+def test_colour_clamp_flag(orc):
+    """A colour channel whose SH sum sits at 0 (where the clamp max(., 0) switches) is flagged at
+    every pixel that blends the particle; 0.1 away from it, it is not."""
+    C0 = 0.28209479177387814
+    for off, want in ((0.0, True), (0.1, False)):
+        one = one_scene([0.0, 0.0, 3.0], [-1.0, -1.0, -1.0], [1.0, 0.0, 0.0, 0.0], 2.0,
+                        [[(-0.5 + off) / C0, 0.3, 0.2]], deg=0)
+        cam = synth.camera("pinhole", 16, 16, fx=20.0, fy=20.0)
+        r = orc.render(one, cam, synth.options(), tol=dict(eps_rel=1e-4))
+        hit = r["nblend"] > 0
+        assert hit.sum() > 20
+        got = (r["flags"] & orc.F_CLAMP) != 0
+        assert np.all(got[hit] == want) and not got[~hit].any()
+
+
+def test_alpha_rounding_bound_covers_an_fp32_evaluation(orc):
+    """The oracle's FP32 rounding bound of a blended particle's alpha (raslack of a one-particle
+    render) covers the alpha an FP32 evaluation of eq. GaussianMaxResponse gives (canonical ray
+    o_g = M (o - mu), d_g = M d, omega^2 = |o_g x d_g|^2 / |d_g|^2, all in numpy float32) for tiny
+    particles far from the camera, where the evaluation is worst conditioned -- and stays within a
+    small factor of the largest deviation seen."""
+    f32 = np.float32
+    rng = np.random.default_rng(23)
+    cam = synth.camera("pinhole", 64, 64, fx=3000.0, fy=3000.0, t=(0.3, -0.2, 0.5))
+    op = synth.options()
+    worst_ratio, worst_dev = 0.0, 0.0
+    for _ in range(40):
+        mu = np.array([-0.3 + rng.uniform(-0.004, 0.004), 0.2 + rng.uniform(-0.004, 0.004), rng.uniform(7.0, 9.0)])
+        ls = rng.normal(-6.0, 0.3, 3)
+        q = rng.standard_normal(4)
+        sc = one_scene(mu, ls, q, 3.0, [[0.3, 0.3, 0.3]], deg=0)
+        okp, uv, _ = orc.project_point(cam, sc["means"][0].astype(np.float64))
+        px, py = int(uv[0]), int(uv[1])
+        if not (okp and 0 <= px < 64 and 0 <= py < 64):
+            continue
+        r = orc.render(sc, cam, op, pixels=(np.array([px]), np.array([py])))
+        if r["nblend"][0] != 1 or r["alpha"][0] > 0.98:
+            continue
+        ok, o, d = orc.pixel_ray(cam, px + 0.5, py + 0.5)
+        m32 = sc["means"][0].astype(f32)
+        s32 = np.exp(sc["log_scales"][0].astype(f32))
+        qq = sc["quats"][0].astype(np.float64)
+        R = rot(qq).astype(f32)
+        M = (R.T / s32[:, None]).astype(f32)  # S^-1 R^T
+        og = M @ (o.astype(f32) - m32)
+        dg = M @ d.astype(f32)
+        c = np.cross(og, dg).astype(f32)
+        w2 = f32(np.dot(c, c) / np.dot(dg, dg))
+        sig = f32(1.0 / (1.0 + np.exp(-f32(3.0))))
+        a32 = float(sig * np.exp(-f32(0.5) * w2))
+        dev = abs(a32 - r["alpha"][0])
+        bound = r["raslack"][0]
+        assert dev <= bound, (dev, bound)
+        worst_dev = max(worst_dev, dev)
+        worst_ratio = max(worst_ratio, dev / bound)
+    assert worst_dev > 1e-6          # the case is ill-conditioned enough to matter
+    assert worst_ratio > 0.05        # and the bound is within 20x of the worst deviation
