@@ -118,8 +118,8 @@ typedef struct {
  *   combined with UT_COLOUR_PER_PARTICLE it is rejected with UT_ERR_UNSUPPORTED.
  *   kbuffer: 0 (default) blends in the tile's depth order; k in 1..16 selects "Ours (sorted)"
  *   (Sec. 4.4), a per-ray k-buffer: hits enter a buffer of k entries, a full buffer blends the
- *   closest (by tau_max) of its hits and the arriving one, and the rest are blended in tau_max
- *   order at the end of the list (the paper uses k = 16).  composite_backward and
+ *   closest (by tau_max; the earlier arrival on equal tau_max) of its hits and the arriving one,
+ *   and the rest are blended in that order at the end of the list (the paper uses k = 16).  composite_backward and
  *   render_batch_backward differentiate through the same blending order (the selections carry
  *   no gradient; every allowed tile size and k fits one block's shared memory).
  *   composite_forward rejects statistics
@@ -146,6 +146,19 @@ const char *ut_status_string(ut_status s);
  * all threads).  A measurement aid with no counterpart in the paper: benchmarks read it
  * before and after a step to report how many of the library's kernels the step ran. */
 uint64_t ut_kernel_launch_count(void);
+
+/* Peak-throughput probes (a measurement aid with no counterpart in the paper: the compositing
+ * kernels' roofline fractions divide by peaks measured on the same GPU).  Launches blocks x
+ * threads threads (threads a multiple of 32, at most 256), each running `iters` iterations of 8
+ * independent dependency chains of one operation:
+ *   UT_PROBE_FMA: fma.rn.f32 (2 FP32 flop each),
+ *   UT_PROBE_EX2: ex2.approx.ftz.f32 (the special-function unit's base-2 exponential).
+ * Operations launched = blocks * threads * iters * 8; time the launch with events on `stream`.
+ * out[blocks * threads] (device, caller-owned) receives each thread's chain sum.
+ * Errors: UT_ERR_INVALID_ARG for an unknown kind, bad sizes or a NULL out. */
+#define UT_PROBE_FMA 0
+#define UT_PROBE_EX2 1
+ut_status ut_peak_probe(int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float *out, ut_stream stream);
 
 /* UT projection of every particle (Algorithm 1 and Algorithm 2; eq. sigma_points,
  * weights_1, weights_2, 2d_conic_1, 2d_conic_2).

@@ -112,10 +112,12 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
 
 // "Ours (sorted)" (Sec. 4.4): compositing through a per-ray k-buffer (multi-layer alpha
 // blending).  Hits (sigma rho >= alpha_min) met in the tile's depth order enter a buffer of at
-// most k = op.kbuffer entries kept in shared memory (tau_max, alpha, rgb per entry); when a hit
-// meets a full buffer, the closest of the buffered hits and the new one by tau_max is blended
-// front to back (stop rule as in k_composite_fwd) and the new hit takes its slot unless it was
-// itself the closest; at the end of the list the rest are blended in ascending tau_max.
+// most k = op.kbuffer entries kept in shared memory (tau_max, alpha, rgb and the hit's position
+// in the tile's list per entry); when a hit meets a full buffer, the closest of the buffered
+// hits and the new one by tau_max -- the earlier arrival, i.e. the smaller list position, on
+// equal tau_max -- is blended front to back (stop rule as in k_composite_fwd) and the new hit
+// takes its slot unless it was itself the closest; at the end of the list the rest are blended
+// in ascending (tau_max, arrival).
 // n_used is written as 0 (the backward does not replay this variant).
 template <int DEG, bool RS>
 __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
   __shared__ float4 s_geo[kBatchF][4];
   __shared__ __align__(16) float s_sh[kBatchF * NC];
   __shared__ uint32_t s_idx[kBatchF];
-  extern __shared__ float s_kb[];  // [5][k][threads]: tau, alpha, r, g, b of each buffered hit
+  extern __shared__ float s_kb[];  // [6][k][threads]: tau, alpha, r, g, b, list position of each hit
 
   if (blockIdx.x >= *ts.n_work) return;
   const int tile = (int)ts.order[blockIdx.x];
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
   const int K = op.kbuffer, nt = blockDim.x;
   float *kb_tau = s_kb + threadIdx.x, *kb_a = kb_tau + K * nt, *kb_r = kb_a + K * nt, *kb_g = kb_r + K * nt,
         *kb_b = kb_g + K * nt;  // entry j of this thread at [j * nt]
+  uint32_t *kb_p = reinterpret_cast<uint32_t *>(kb_b + K * nt);
   float3 o, d;
   float Y[NSH];
   bool valid;
@@ -184,39 +187,47 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
       float r0, r1, r2;
       sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
       r0 = fmaxf(r0, 0.f); r1 = fmaxf(r1, 0.f); r2 = fmaxf(r2, 0.f);
+      const uint32_t pos = start + b;
       if (nbuf < K) {
         kb_tau[nbuf * nt] = tau; kb_a[nbuf * nt] = al;
-        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2;
+        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_p[nbuf * nt] = pos;
         ++nbuf;
         continue;
       }
-      int bi = -1;  // closest of the buffer and the new hit
+      // closest of the buffer and the new hit; on equal tau the earlier arrival (the new hit
+      // arrived last, so it wins only with a strictly smaller tau)
+      int bi = -1;
       float bt = tau;
+      uint32_t bp = pos;
       for (int j = 0; j < K; ++j) {
         const float tj = kb_tau[j * nt];
-        if (tj < bt) { bt = tj; bi = j; }
+        const uint32_t pj = kb_p[j * nt];
+        if (tj < bt || (tj == bt && pj < bp)) { bt = tj; bp = pj; bi = j; }
       }
       if (bi < 0) {
         blend(al, r0, r1, r2);
       } else {
         blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt]);
         kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
-        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2;
+        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_p[bi * nt] = pos;
       }
     }
   }
-  // end of the list: the remaining hits in ascending tau_max
+  // end of the list: the remaining hits in ascending (tau_max, arrival)
   while (!done && nbuf > 0) {
     int bi = 0;
     float bt = kb_tau[0];
+    uint32_t bp = kb_p[0];
     for (int j = 1; j < nbuf; ++j) {
       const float tj = kb_tau[j * nt];
-      if (tj < bt) { bt = tj; bi = j; }
+      const uint32_t pj = kb_p[j * nt];
+      if (tj < bt || (tj == bt && pj < bp)) { bt = tj; bp = pj; bi = j; }
     }
     blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt]);
     --nbuf;
     kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
     kb_r[bi * nt] = kb_r[nbuf * nt]; kb_g[bi * nt] = kb_g[nbuf * nt]; kb_b[bi * nt] = kb_b[nbuf * nt];
+    kb_p[bi * nt] = kb_p[nbuf * nt];
   }
   if (inside) {
     size_t pix = (size_t)py * cam.W + px;
@@ -311,7 +322,7 @@ void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
                 const uint32_t *ranges, unsigned long long *stats, const TileSched &ts, cudaStream_t s) {
   if (op.kbuffer > 0) {
     const int threads = op.tile_w * op.tile_h;
-    const size_t smem = sizeof(float) * 5 * (size_t)op.kbuffer * threads;
+    const size_t smem = sizeof(float) * 6 * (size_t)op.kbuffer * threads;
     cudaFuncSetAttribute(k_composite_fwd_kbuffer<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_composite_fwd_kbuffer<DEG, RS><<<bd.total_tiles, threads, smem, s>>>(
         bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
