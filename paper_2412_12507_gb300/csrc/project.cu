@@ -17,10 +17,25 @@ namespace {
 
 constexpr int kWarps = 8;
 
+// The camera map of the kernel: CAM = 2 model + rolling shutter when every view of the launch
+// shares them (a specialised kernel with no camera branches), or -1 for a batch that mixes them
+// (the runtime dispatch of project_world / cam_point_at).
+template <int CAM>
+__device__ __forceinline__ bool proj_world(const DevCam &c, int rs_iters, float3 y, float2 &uv, float &t) {
+  if constexpr (CAM < 0) return project_world(c, rs_iters, y, uv, t);
+  else return project_world_t<CAM / 2, (CAM & 1) != 0>(c, rs_iters, y, uv, t);
+}
+
+template <int CAM>
+__device__ __forceinline__ float3 point_at(const DevCam &c, float3 y, float t) {
+  if constexpr (CAM < 0) return cam_point_at(c, y, t);
+  else return cam_point_at_t<(CAM & 1) != 0>(c, y, t);
+}
+
 // EWA: the first-order projection of 3DGS (eq. ewa_splatting) instead of the UT, as an A/B
 // baseline: the mean projects through g and the covariance through the Jacobian of g at the
 // camera-space mean (under a rolling shutter, at the pose of the mean's own shutter time).
-template <bool EWA>
+template <bool EWA, int CAM>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constant__ BatchDesc bd, DevOpts op, UTWeights w,
                                                          float2 *__restrict__ mean2d, float *__restrict__ cov2d,
                                                          float *__restrict__ depth, short4 *__restrict__ rect,
@@ -94,7 +109,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constan
     // and eq. 2d_conic_2 gives Sigma' = wi sum d_j d_j^T + (W - 2) dm dm^T with dm = wi sum d_j
     // and W = wc0 + 6 wi the sum of the covariance weights.
     float2 v0;
-    ok = ok & project_world(cam, op.rs_iters, y0, v0, t_mu);
+    ok = ok & proj_world<CAM>(cam, op.rs_iters, y0, v0, t_mu);
     float3 col[3];  // gamma s_k R0 R[:,k]
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -109,7 +124,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constan
       const float3 dy = j < 3 ? c3 : make_float3(-c3.x, -c3.y, -c3.z);
       float2 v;
       float tt;
-      ok = ok & project_world(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v, tt);
+      ok = ok & proj_world<CAM>(cam, op.rs_iters, make_float3(y0.x + dy.x, y0.y + dy.y, y0.z + dy.z), v, tt);
       const float dx = v.x - v0.x, dz = v.y - v0.y;
       sx += dx;
       sy += dz;
@@ -124,7 +139,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constan
     cxy = fmaf(w.wi, pxy, c * dmx * dmy);
     cyy = fmaf(w.wi, pyy, c * dmy * dmy);
   }
-  float3 xc = cam_point_at(cam, y0, t_mu);
+  float3 xc = point_at<CAM>(cam, y0, t_mu);
   float dep = sqrtf(fmaf(xc.x, xc.x, fmaf(xc.y, xc.y, xc.z * xc.z)));
 
   // opacity-tightened extent (Algorithm 1) and pixel rectangle
@@ -181,6 +196,13 @@ __global__ void k_project_points(DevCam cam, DevOpts op, const float *__restrict
   }
 }
 
+template <bool EWA, int CAM>
+void project_launch(int blocks, const BatchDesc &bd, const DevOpts &op, const UTWeights &w, float *mean2d,
+                    float *cov2d, float *depth, int16_t *rect, uint32_t *ntiles, cudaStream_t stream) {
+  k_project<EWA, CAM><<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d,
+                                                         depth, reinterpret_cast<short4 *>(rect), ntiles);
+}
+
 }  // namespace
 
 ut_status launch_project_points(const DevCam &cam, const DevOpts &op, const float *points, int n, float *uv,
@@ -198,12 +220,23 @@ ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights
   const int n = bd.total_particles;
   if (n == 0) return UT_OK;
   int blocks = (n + kWarps * 32 - 1) / (kWarps * 32);
-  if (op.projection == UT_PROJECTION_EWA)
-    k_project<true><<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d, depth,
-                                                        reinterpret_cast<short4 *>(rect), ntiles);
-  else
-    k_project<false><<<blocks, kWarps * 32, 0, stream>>>(bd, op, w, reinterpret_cast<float2 *>(mean2d), cov2d,
-                                                         depth, reinterpret_cast<short4 *>(rect), ntiles);
+  // one camera map for every view: the specialised UT kernel
+  int cam = 2 * bd.v[0].cam.model + (bd.v[0].cam.rs ? 1 : 0);
+  for (int v = 1; v < bd.nv; ++v)
+    if (2 * bd.v[v].cam.model + (bd.v[v].cam.rs ? 1 : 0) != cam) cam = -1;
+  if (op.projection == UT_PROJECTION_EWA) {
+    project_launch<true, -1>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream);
+  } else {
+    switch (cam) {
+      case 2 * UT_CAM_PINHOLE: project_launch<false, 2 * UT_CAM_PINHOLE>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      case 2 * UT_CAM_PINHOLE + 1: project_launch<false, 2 * UT_CAM_PINHOLE + 1>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      case 2 * UT_CAM_FISHEYE: project_launch<false, 2 * UT_CAM_FISHEYE>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      case 2 * UT_CAM_FISHEYE + 1: project_launch<false, 2 * UT_CAM_FISHEYE + 1>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      case 2 * UT_CAM_PINHOLE_RADIAL: project_launch<false, 2 * UT_CAM_PINHOLE_RADIAL>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      case 2 * UT_CAM_PINHOLE_RADIAL + 1: project_launch<false, 2 * UT_CAM_PINHOLE_RADIAL + 1>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+      default: project_launch<false, -1>(blocks, bd, op, w, mean2d, cov2d, depth, rect, ntiles, stream); break;
+    }
+  }
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }

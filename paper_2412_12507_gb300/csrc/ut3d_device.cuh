@@ -148,10 +148,30 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 
-// Rodrigues rotation of y by angle th about the unit axis a.
+// sin and cos of th for |th| <= pi (rotation angles between two poses): Cody-Waite reduction by
+// pi/2 (k = rint(2 th / pi) in -2..2, r = th - k pi/2 with pi/2 split into two floats, so r is
+// exact to about 1e-15), then odd / even polynomials on [-pi/4, pi/4] -- sin r = r + r^3 P(r^2),
+// cos r = 1 - r^2 / 2 + r^4 Q(r^2), coefficients fitted to sin and cos by least squares with
+// minimax reweighting (absolute error <= 2e-9 before rounding) -- and the quadrant by selects.
+// Within about an ulp, like sincosf, without its path for huge arguments.
+__device__ __forceinline__ void sincos_pi(float th, float &s, float &c) {
+  const float k = rintf(th * 0.63661977236758134f);
+  float r = fmaf(-k, 1.5707963705062866f, th);
+  r = fmaf(-k, -4.371139000186243e-08f, r);
+  const float r2 = r * r;
+  const float sr = fmaf(r * r2, fmaf(r2, fmaf(r2, -1.9496e-4f, 8.33198e-3f), -0.16666651f), r);
+  const float cr = fmaf(r2 * r2, fmaf(r2, fmaf(r2, 2.44385385e-05f, -1.38873683e-03f), 4.16666469e-02f),
+                        fmaf(-0.5f, r2, 1.f));
+  const int q = ((int)k) & 3;
+  const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+  s = (q & 2) ? -ss : ss;
+  c = (q == 1 || q == 2) ? -cc : cc;
+}
+
+// Rodrigues rotation of y by angle th (|th| <= pi) about the unit axis a.
 __device__ __forceinline__ float3 rotate_axis(const float *a, float3 y, float th) {
   float s, c;
-  sincosf(th, &s, &c);
+  sincos_pi(th, s, c);
   float ad = a[0] * y.x + a[1] * y.y + a[2] * y.z;
   float3 axy = make_float3(a[1] * y.z - a[2] * y.y, a[2] * y.x - a[0] * y.z, a[0] * y.y - a[1] * y.x);
   float oc = (1.f - c) * ad;
@@ -159,11 +179,52 @@ __device__ __forceinline__ float3 rotate_axis(const float *a, float3 y, float th
                      fmaf(y.z, c, fmaf(axy.z, s, a[2] * oc)));
 }
 
-// x_c(t) for a point whose start-pose camera coordinates rotated part is y = R0 x.
-__device__ __forceinline__ float3 cam_point_at(const DevCam &c, float3 y, float t) {
-  float3 r = c.rs ? rotate_axis(c.ax, y, t * c.phi) : y;
+// Rodrigues rotation with the fast hardware sine / cosine (absolute error about 4e-7 for
+// |th| <= pi): used only inside the rolling-shutter time fixed point, whose iterates feed nothing
+// but the next time estimate (see project_world_t).
+__device__ __forceinline__ float3 rotate_axis_fast(const float *a, float3 y, float th) {
+  float s, c;
+  __sincosf(th, &s, &c);
+  float ad = a[0] * y.x + a[1] * y.y + a[2] * y.z;
+  float3 axy = make_float3(a[1] * y.z - a[2] * y.y, a[2] * y.x - a[0] * y.z, a[0] * y.y - a[1] * y.x);
+  float oc = (1.f - c) * ad;
+  return make_float3(fmaf(y.x, c, fmaf(axy.x, s, a[0] * oc)), fmaf(y.y, c, fmaf(axy.y, s, a[1] * oc)),
+                     fmaf(y.z, c, fmaf(axy.z, s, a[2] * oc)));
+}
+
+// atan2(y, x) for y >= 0, in [0, pi]: atan of a = min(y, |x|) / max(y, |x|) in [0, 1] by an odd
+// polynomial a P(a^2) of degree 15 (coefficients fitted to atan on [0, 1] by least squares with
+// minimax reweighting; |error| <= 1.2e-7 in FP32), then the octant by selects.  For the
+// rolling-shutter fixed point's iterates (see project_world_t).
+__device__ __forceinline__ float atan2_pos_fast(float y, float x) {
+  const float ax = fabsf(x);
+  const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+  const float a = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+  const float a2 = a * a;
+  float p = -0.004054596647620201f;
+  p = fmaf(p, a2, 0.021863065659999847f);
+  p = fmaf(p, a2, -0.05591248348355293f);
+  p = fmaf(p, a2, 0.09642209112644196f);
+  p = fmaf(p, a2, -0.13908633589744568f);
+  p = fmaf(p, a2, 0.19946566224098206f);
+  p = fmaf(p, a2, -0.33329862356185913f);
+  p = fmaf(p, a2, 0.9999993443489075f);
+  float r = p * a;
+  r = y > ax ? 1.5707963267948966f - r : r;
+  return x < 0.f ? 3.141592653589793f - r : r;
+}
+
+// x_c(t) for a point whose start-pose camera coordinates rotated part is y = R0 x.  RS: the
+// camera has a rolling shutter (c.rs != 0); the runtime form below tests c.rs itself.
+template <bool RS>
+__device__ __forceinline__ float3 cam_point_at_t(const DevCam &c, float3 y, float t) {
+  float3 r = RS ? rotate_axis(c.ax, y, t * c.phi) : y;
   return make_float3(r.x + fmaf(t, c.dT[0], c.T0[0]), r.y + fmaf(t, c.dT[1], c.T0[1]),
                      r.z + fmaf(t, c.dT[2], c.T0[2]));
+}
+
+__device__ __forceinline__ float3 cam_point_at(const DevCam &c, float3 y, float t) {
+  return c.rs ? cam_point_at_t<true>(c, y, t) : cam_point_at_t<false>(c, y, t);
 }
 
 __device__ __forceinline__ float theta_d_poly(const DevCam &c, float th) {
@@ -185,15 +246,16 @@ __device__ __forceinline__ float radial_prime(const DevCam &c, float r2) {
   return fmaf(r2, fmaf(r2, fmaf(r2, 7.f * c.k3, 5.f * c.k2), 3.f * c.k1), 1.f);
 }
 
-// g(x_c): camera-space point to pixel coordinates; returns false when not imaged.
-__device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &uv) {
-  if (c.model == UT_CAM_PINHOLE) {
+// g(x_c): camera-space point to pixel coordinates; returns false when not imaged.  MODEL is the
+// camera model (ut_cam_model); cam_project dispatches on c.model at run time.
+template <int MODEL>
+__device__ __forceinline__ bool cam_project_t(const DevCam &c, float3 p, float2 &uv) {
+  if constexpr (MODEL == UT_CAM_PINHOLE) {
     float iz = 1.f / p.z;
     uv.x = fmaf(c.fx * p.x, iz, c.cx);
     uv.y = fmaf(c.fy * p.y, iz, c.cy);
     return p.z > c.near_plane;
-  }
-  if (c.model == UT_CAM_PINHOLE_RADIAL) {
+  } else if constexpr (MODEL == UT_CAM_PINHOLE_RADIAL) {
     // theta_max holds the largest imaged normalised radius r_max
     float iz = 1.f / p.z;
     float xn = p.x * iz, yn = p.y * iz;
@@ -202,15 +264,54 @@ __device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &u
     uv.x = fmaf(c.fx * xn, sd, c.cx);
     uv.y = fmaf(c.fy * yn, sd, c.cy);
     return p.z > c.near_plane && sqrtf(r2) <= c.theta_max;
+  } else {
+    // 1 / rho by the reciprocal square root and one Newton step (within about an ulp, like the
+    // IEEE square root and division it replaces); the near-plane test on squares
+    const float r2 = fmaf(p.x, p.x, p.y * p.y);
+    float rq = rsqrtf(r2);
+    rq = rq * fmaf(-0.5f * r2, rq * rq, 1.5f);
+    const bool axis = !(r2 > 0.f);
+    const float th = atan2f(axis ? 0.f : r2 * rq, p.z);
+    const float s = axis ? 1.f / p.z : theta_d_poly(c, th) * rq;
+    uv.x = fmaf(c.fx * s, p.x, c.cx);
+    uv.y = fmaf(c.fy * s, p.y, c.cy);
+    return (fmaf(p.z, p.z, r2) > c.near_plane * c.near_plane) && (th <= c.theta_max);
   }
-  float r2 = fmaf(p.x, p.x, p.y * p.y);
-  float rho = sqrtf(r2);
-  float r3 = sqrtf(fmaf(p.z, p.z, r2));
-  float th = atan2f(rho, p.z);
-  float s = rho > 0.f ? theta_d_poly(c, th) / rho : 1.f / p.z;
-  uv.x = fmaf(c.fx * s, p.x, c.cx);
-  uv.y = fmaf(c.fy * s, p.y, c.cy);
-  return (r3 > c.near_plane) && (th <= c.theta_max);
+}
+
+// g(x_c) with fast reciprocal square root / division and atan2_pos_fast: for the rolling-shutter
+// fixed point's iterates only (see project_world_t).  Same validity tests as cam_project_t.
+template <int MODEL>
+__device__ __forceinline__ bool cam_project_fast_t(const DevCam &c, float3 p, float2 &uv) {
+  if constexpr (MODEL == UT_CAM_FISHEYE) {
+    const float r2 = fmaf(p.x, p.x, p.y * p.y);
+    const float rq = rsqrtf(r2);
+    const bool axis = !(r2 > 0.f);
+    const float th = atan2_pos_fast(axis ? 0.f : r2 * rq, p.z);
+    const float s = axis ? __fdividef(1.f, p.z) : theta_d_poly(c, th) * rq;
+    uv.x = fmaf(c.fx * s, p.x, c.cx);
+    uv.y = fmaf(c.fy * s, p.y, c.cy);
+    return (fmaf(p.z, p.z, r2) > c.near_plane * c.near_plane) && (th <= c.theta_max);
+  } else if constexpr (MODEL == UT_CAM_PINHOLE_RADIAL) {
+    const float iz = __fdividef(1.f, p.z);
+    const float xn = p.x * iz, yn = p.y * iz;
+    const float r2 = fmaf(xn, xn, yn * yn);
+    const float sd = radial_scale(c, r2);
+    uv.x = fmaf(c.fx * xn, sd, c.cx);
+    uv.y = fmaf(c.fy * yn, sd, c.cy);
+    return p.z > c.near_plane && r2 <= c.theta_max * c.theta_max;
+  } else {
+    const float iz = __fdividef(1.f, p.z);
+    uv.x = fmaf(c.fx * p.x, iz, c.cx);
+    uv.y = fmaf(c.fy * p.y, iz, c.cy);
+    return p.z > c.near_plane;
+  }
+}
+
+__device__ __forceinline__ bool cam_project(const DevCam &c, float3 p, float2 &uv) {
+  if (c.model == UT_CAM_PINHOLE) return cam_project_t<UT_CAM_PINHOLE>(c, p, uv);
+  if (c.model == UT_CAM_PINHOLE_RADIAL) return cam_project_t<UT_CAM_PINHOLE_RADIAL>(c, p, uv);
+  return cam_project_t<UT_CAM_FISHEYE>(c, p, uv);
 }
 
 // Jacobian d g / d x_c (rows u, v) of the camera map at a camera-space point.  Fisheye:
@@ -244,19 +345,39 @@ __device__ __forceinline__ void cam_jacobian(const DevCam &c, float3 p, float3 &
 // Projection of a world point with the rolling-shutter time fixed point
 // (t = 1/2, rs_iters updates t <- clamp((v - 1/2)/(H-1)), final projection).
 // y = R0 x.  Returns validity of every projection taken; t_out = the final time.
-__device__ __forceinline__ bool project_world(const DevCam &c, int rs_iters, float3 y, float2 &uv, float &t_out) {
+// The iterates only produce the next time estimate: an error dv in their row moves t by
+// dv / (H - 1) and the final projection by (dv / dt) dv / (H - 1), five orders of magnitude less
+// for any camera that moves less than a frame height over the exposure, so they take the fast
+// camera map (rotation with the hardware sine / cosine, fast reciprocal square root and atan2;
+// a few 1e-4 px each); the final projection, which alone sets the result, takes the IEEE one.
+template <int MODEL, bool RS>
+__device__ __forceinline__ bool project_world_t(const DevCam &c, int rs_iters, float3 y, float2 &uv, float &t_out) {
   bool ok = true;
   float t = 0.f;
-  if (c.rs) {
+  if (RS) {
     t = 0.5f;
     for (int it = 0; it < rs_iters; ++it) {
-      ok &= cam_project(c, cam_point_at(c, y, t), uv);
+      const float3 r = rotate_axis_fast(c.ax, y, t * c.phi);
+      const float3 p = make_float3(r.x + fmaf(t, c.dT[0], c.T0[0]), r.y + fmaf(t, c.dT[1], c.T0[1]),
+                                   r.z + fmaf(t, c.dT[2], c.T0[2]));
+      ok &= cam_project_fast_t<MODEL>(c, p, uv);
       t = fminf(fmaxf((uv.y - 0.5f) * c.inv_hm1, 0.f), 1.f);
     }
   }
-  ok &= cam_project(c, cam_point_at(c, y, t), uv);
+  ok &= cam_project_t<MODEL>(c, cam_point_at_t<RS>(c, y, t), uv);
   t_out = t;
   return ok;
+}
+
+__device__ __forceinline__ bool project_world(const DevCam &c, int rs_iters, float3 y, float2 &uv, float &t_out) {
+  if (c.model == UT_CAM_PINHOLE)
+    return c.rs ? project_world_t<UT_CAM_PINHOLE, true>(c, rs_iters, y, uv, t_out)
+                : project_world_t<UT_CAM_PINHOLE, false>(c, rs_iters, y, uv, t_out);
+  if (c.model == UT_CAM_PINHOLE_RADIAL)
+    return c.rs ? project_world_t<UT_CAM_PINHOLE_RADIAL, true>(c, rs_iters, y, uv, t_out)
+                : project_world_t<UT_CAM_PINHOLE_RADIAL, false>(c, rs_iters, y, uv, t_out);
+  return c.rs ? project_world_t<UT_CAM_FISHEYE, true>(c, rs_iters, y, uv, t_out)
+              : project_world_t<UT_CAM_FISHEYE, false>(c, rs_iters, y, uv, t_out);
 }
 
 // World ray of pixel (px, py) (integer indices; the ray goes through the pixel centre).
