@@ -3,7 +3,7 @@
 //
 // Host-side only.  A worker thread owns all GPU submission:
 //   1. admission: pending requests, in arrival order, receive their output image (rgb + alpha)
-//      from the caller's device arena as long as it fits;
+//      from the caller's device arena as long as it fits, at most one batch ahead of the GPU;
 //   2. batching: admitted requests are grouped (up to max_batch_views, at most
 //      UT_MAX_BATCH_SCENES distinct scenes) into one render_batch call whose key capacity is a
 //      learned per-(scene, resolution) estimate times the headroom, and whose workspace is also
@@ -222,8 +222,10 @@ void fail_slot(ut_server *s, Slot &sl, ut_status err) {
 
 // Admission and batching (called with the lock held).  Returns true if it launched something.
 bool schedule(ut_server *s) {
-  // admit pending requests in arrival order while their outputs fit
-  while (!s->pending.empty()) {
+  // admit pending requests in arrival order while their outputs fit, at most one batch ahead of
+  // the GPU: admitting further ahead gains nothing (the slots are busy) and, under a burst,
+  // would fill the arena with waiting outputs and leave no room for any batch's workspace
+  while (!s->pending.empty() && s->admitted.size() < (size_t)s->cfg.max_batch_views) {
     Request &r = s->reqs[s->pending.front()];
     size_t off;
     if (!s->arena.alloc(r.out_bytes, &off)) break;

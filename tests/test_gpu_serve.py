@@ -145,3 +145,25 @@ def test_wait_times_out_without_blocking_forever():
         srv.release(rid)
     finally:
         srv.close()
+
+
+def test_burst_larger_than_the_arena_completes_in_order():
+    """A burst of requests whose outputs together exceed the arena: admission stays at most one
+    batch ahead of the GPU, so waiting outputs never crowd out the workspaces, and a client that
+    waits for and releases the requests in arrival order sees every one of them complete."""
+    op = synth.options()
+    scenes = [render.Scene.from_arrays(_scenes()[1])]
+    cams = synth.orbit_cameras(12, [("fisheye", 480, 270, j % 2) for j in range(60)])
+    out_mb = 16 * 480 * 270 / 2**20
+    arena = 80 << 20
+    assert len(cams) * out_mb > arena / 2**20  # the outputs alone would not fit together
+    srv = render.Server(scenes, op, arena_bytes=arena, max_batch_views=4, max_in_flight=3)
+    try:
+        ids = [srv.submit(0, c) for c in cams]
+        for rid in ids:
+            out = srv.wait(rid, 60_000)
+            assert out is not None, "a request of the burst did not complete"
+            srv.release(rid)
+        assert srv.stats()["completed"] == len(ids)
+    finally:
+        srv.close()
