@@ -40,10 +40,16 @@ def parse():
     ap.add_argument("--workload", default="rs_fisheye_1m_1080p")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle's CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="leave out the forward-only fisheye-shell line (100k Gaussians, 1280x720)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="measured serving requests (0: skip)")
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests / s")
     ap.add_argument("--serve-arena-gb", type=float, default=64.0)
+    ap.add_argument("--serve-saturated-requests", type=int, default=600,
+                    help="measured requests of the saturated serving run (0: skip)")
+    ap.add_argument("--serve-saturated-rate", type=float, default=2000.0,
+                    help="arrival rate of the saturated serving run, requests / s (above capacity)")
     ap.add_argument("--multiview-steps", type=int, default=5,
                     help="timed steps of the 8-view 3M-particle fwd+bwd batch (0: skip)")
     return ap.parse_args()
@@ -111,6 +117,58 @@ def measured_traffic(kernel, workload_name):
     if h.hexdigest() != rec["sources_sha256"] or rec["workload"] != workload_name:
         return None
     return float(rec["bytes_per_launch"])
+
+
+def measure_alu_peaks(L, dev, stream, sms):
+    """FP32 FMA and special-function (ex2) throughput of this GPU, from the library's probe
+    kernels (ut_peak_probe: 8 independent chains per thread, 8 blocks of 256 per SM, a few ms
+    per launch); the median of 5 launches timed with events on the launching stream."""
+    import torch
+
+    from paper_2412_12507_gb300 import abi
+    blocks, threads = sms * 8, 256
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    res = {}
+    for kind, name, iters, flop_per_op in ((0, "fp32", 40000, 2.0), (1, "ex2", 5000, 1.0)):
+        def launch():
+            abi.check("ut_peak_probe", L.ut_peak_probe(kind, blocks, threads, iters, out.data_ptr(), stream.cuda_stream))
+        launch()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        res[name] = (blocks * threads * iters * 8 * flop_per_op / (ms / 1e3), ms)
+    return {"fp32_tflops": res["fp32"][0] / 1e12, "ex2_gops": res["ex2"][0] / 1e9,
+            "fp32_ms": res["fp32"][1], "ex2_ms": res["ex2"][1],
+            "how": f"ut_peak_probe: {blocks} x {threads} threads x 8 chains of fma.rn.f32 / ex2.approx.ftz.f32, "
+                   "median of 5 launches"}
+
+
+def projection_work(cam, rs_iters=3):
+    """FP32 operations and transcendental calls (sqrt, atan2, sin / cos, exp, log, division:
+    one each) of the UT projection of one particle, counted from the arithmetic the method
+    needs (term by term in the design notes): 7 sigma points, each projected 1 + rs_iters
+    times under a rolling shutter, plus activation, moments, depth, extent and rectangle."""
+    rs = bool(cam.get("rolling_shutter", 0))
+    if cam["model"] == "fisheye":
+        cam_f, cam_s = 23, 4  # |x|, rho, theta = atan2, theta_d polynomial, scale and (u, v)
+    elif cam["model"] == "pinhole_radial":
+        cam_f, cam_s = 17, 2
+    else:
+        cam_f, cam_s = 6, 1
+    # per projection: the pose at time t (rotation about the fixed axis 31 + sin / cos,
+    # translation 9) and the time update 4 under a rolling shutter, else the translation 9
+    per_f, per_s, per_pt = (cam_f + 44, cam_s + 2, 1 + rs_iters) if rs else (cam_f + 9, cam_s, 1)
+    # per particle: activation 49, R0 mu 15, sigma-point columns 57 and points 18, moments 78,
+    # depth (pose 9 / 40, norm 5), extent 5, rectangle 16, tile count 8
+    base_f, base_s = 254 + (31 if rs else 0), 12 + (2 if rs else 0)
+    return 7 * per_pt * per_f + base_f, 7 * per_pt * per_s + base_s
 
 
 class ClockSampler:
@@ -202,19 +260,26 @@ def run_reference(args):
         return
     case = workload(args.workload)
     W, H = case["camera"]["width"], case["camera"]["height"]
-    frames = []
+    frames, walls = [], []
     desc, thr = "", 1
     per = max(2.0, args.cpu_seconds / max(1, args.steps))
     for _ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         f, desc, thr = oracle_frame_time(case, per)
+        walls.append(time.perf_counter() - t0)
         frames.append(f)
-    frames = frames[args.warmup:]
-    ms = 1e3 * statistics.median(frames)
-    v = W * H / (ms / 1e3) / 1e6
+    frames, walls = frames[args.warmup:], walls[args.warmup:]
+    frame_ms = 1e3 * statistics.median(frames)
+    v = W * H / (frame_ms / 1e3) / 1e6
+    # a step is one bounded sample (the projection of every particle and a seeded pixel sample):
+    # ms_per_step is its measured wall time, so steps x ms_per_step is what ran; value is the
+    # per-frame rate extrapolated from the sample
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": case["name"]},
+            "value_basis": "extrapolated: full-frame time estimated from each step's sample",
+            "frame_ms_extrapolated": frame_ms,
             "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": thr, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -295,6 +360,19 @@ def run_serving(scenes, opts, reqs, n_warm, arena_bytes, max_batch_views=8, max_
     return np.array(lat[meas]), wall, stats
 
 
+def latency_breakdown(lat, reqs, sizes):
+    """p50 / p99 latency of the measured requests grouped by resolution and by scene."""
+    out = {"by_resolution": {}, "by_scene": {}}
+    res = [f"{c['width']}x{c['height']}" for _, _, c in reqs]
+    sc = [f"{sizes[s] // 1000}k" for _, s, _ in reqs]
+    for key, labels in (("by_resolution", res), ("by_scene", sc)):
+        for lab in sorted(set(labels), key=lambda x: (len(x), x)):
+            v = np.array([l for l, g in zip(lat, labels) if g == lab])
+            out[key][lab] = {"n": int(v.size), "p50_ms": float(np.percentile(v, 50)),
+                             "p99_ms": float(np.percentile(v, 99))}
+    return out
+
+
 def run_plain(scenes, opts, reqs, n_warm):
     """The same trace through one plain single-view render call per request, in arrival order."""
     import torch
@@ -356,10 +434,45 @@ def run_multiview(dev, steps, warmup, timed):
     if int(br.k_dev.item()) != K:
         raise SystemExit("multiview key count changed during the timed region")
     nv = len(views)
+    # where the batch's time goes: every view rendered on its own through the single-view calls
+    # (same tile shape), each ABI call timed with events on the stream
+    stream = torch.cuda.current_stream()
+    per_view = []
+    for (si, cam), g_rgb, g_a in zip(views, d_rgb, d_a):
+        r = render.Renderer(cam, best, capacity=1 << 20)
+        r.forward(scene)
+        torch.cuda.synchronize()
+        calls = {"ut_project": [], "bin_and_sort": [], "composite_forward": [], "composite_backward": []}
+        for _ in range(3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record(stream)
+            render.project(scene, cam, best, r.proj)
+            ev[1].record(stream)
+            render.bin_and_sort(r.proj, cam, best, r.capacity, ws=r.ws, out=r.binning)
+            ev[2].record(stream)
+            render.composite_forward(scene, cam, best, r.proj, r.binning, r.frame, ws=r.fws)
+            ev[3].record(stream)
+            r.backward(scene, g_rgb, g_a)
+            ev[4].record(stream)
+            torch.cuda.synchronize()
+            for j, k in enumerate(calls):
+                calls[k].append(ev[j].elapsed_time(ev[j + 1]))
+        cm = {k: statistics.median(v) for k, v in calls.items()}
+        stats = torch.zeros(2, dtype=torch.int64, device=dev)
+        render.composite_forward(scene, cam, best, r.proj, r.binning, r.frame, stats=stats, ws=r.fws)
+        torch.cuda.synchronize()
+        per_view.append({"model": cam["model"] + ("+rs" if cam.get("rolling_shutter") else ""),
+                         "width": cam["width"], "height": cam["height"], "keys": r.binning.count(),
+                         "evaluations": int(stats[0]), "blended": int(stats[1]), "ms": cm})
+        del r
+    single_f = sum(v["ms"]["ut_project"] + v["ms"]["bin_and_sort"] + v["ms"]["composite_forward"] for v in per_view)
+    single_b = sum(v["ms"]["composite_backward"] for v in per_view)
     out = {"workload": case["name"], "particles": scene.n, "views": nv, "pixels": pix, "keys": K,
            "tile": f"{best['tile_w']}x{best['tile_h']}", "autotune_ms_per_batch": tuned,
            "fwd_ms_per_view": f_ms / nv, "fwd_bwd_ms_per_view": fb_ms / nv,
-           "fwd_mpix_s": pix / (f_ms / 1e3) / 1e6, "fwd_bwd_mpix_s": pix / (fb_ms / 1e3) / 1e6, "steps": steps}
+           "fwd_mpix_s": pix / (f_ms / 1e3) / 1e6, "fwd_bwd_mpix_s": pix / (fb_ms / 1e3) / 1e6, "steps": steps,
+           "single_view_calls": per_view, "single_view_sum_fwd_ms": single_f,
+           "single_view_sum_bwd_ms": single_b}
     del br, frames, scene
     torch.cuda.empty_cache()
     return out
@@ -430,6 +543,105 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
     out["per_particle_colour"] = {"fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "fwd_mpix_s": P / (f_ms / 1e3) / 1e6,
                                   "fwd_bwd_mpix_s": P / (fb_ms / 1e3) / 1e6}
     del r
+    torch.cuda.empty_cache()
+    return out
+
+
+def call_fractions(call_ms, n, K, M_cols, n_eval, n_blend, P, cam, op, hbm, alu):
+    """Roofline fraction of each ABI call from its measured duration and its algorithmic work:
+    bytes for the projection (HBM side) and the binning, FP32 operations for the compositing,
+    plus the projection's arithmetic and the compositing's special-function side against the
+    FP32 and ex2 peaks measured in the same run."""
+    fp32_peak, ex2_peak = alu["fp32_tflops"], alu["ex2_gops"]
+    # per-evaluation / per-blend FP32 operation counts of the compositing arithmetic, term by
+    # term in the design notes; a rolling-shutter view adds the per-pixel origin's canonical
+    # image M o - M mu to every evaluation (9 FMA + 3 subtractions)
+    F_EVAL = 40 + (21 if cam.get("rolling_shutter", 0) else 0)
+    F_BLEND_FWD, F_BLEND_BWD, F_PIX = 110, 275, 120
+    work = {
+        "ut_project": ("hbm", 80.0 * n / 1e9),
+        # binning: the K values written once, 16 B of projection output read per particle, the
+        # column list (8 B per column entry) written and read once
+        "bin_and_sort": ("hbm", (4.0 * K + 16.0 * n + 16.0 * M_cols) / 1e9),
+        "composite_forward": ("alu", (F_EVAL * n_eval + F_BLEND_FWD * n_blend + F_PIX * P) / 1e12),
+        "composite_backward": ("alu", (F_EVAL * n_eval + F_BLEND_BWD * n_blend + F_PIX * P) / 1e12),
+    }
+    kernels = {}
+    for k, (bound, amount) in work.items():
+        if k not in call_ms:
+            continue
+        ach = amount / (call_ms[k] / 1e3)
+        peak = hbm if bound == "hbm" else fp32_peak
+        kernels[k] = {"ms": call_ms[k], "bound": bound, "achieved": ach, "peak": peak,
+                      "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / peak}
+    # the binning also against the survey's algorithmic model: every key (8 B key + 4 B value)
+    # emitted, sorted (read + written) and scanned for ranges (44 B / key), 8 B per particle
+    kernels["bin_and_sort"]["model_44B_per_key"] = {
+        "achieved_gbs": (44.0 * K + 8.0 * n) / 1e9 / (call_ms["bin_and_sort"] / 1e3),
+        "frac": (44.0 * K + 8.0 * n) / 1e9 / (call_ms["bin_and_sort"] / 1e3) / hbm}
+    # the special-function side of the compositing (one ex2 and one reciprocal per evaluation)
+    # and the arithmetic side of the projection
+    for k in ("composite_forward", "composite_backward"):
+        if k in kernels:
+            g = 2.0 * n_eval / (call_ms[k] / 1e3) / 1e9
+            kernels[k]["sfu"] = {"ops": 2 * n_eval, "achieved_gops": g, "peak_gops": ex2_peak, "frac": g / ex2_peak}
+    pf, ps = projection_work(cam, op["rs_iters"])
+    sec = call_ms["ut_project"] / 1e3
+    kernels["ut_project"]["fp32"] = {"flop_per_particle": pf, "achieved_tflops": pf * n / sec / 1e12,
+                                     "peak_tflops": fp32_peak, "frac": pf * n / sec / 1e12 / fp32_peak}
+    kernels["ut_project"]["transcendental"] = {"per_particle": ps, "achieved_gops": ps * n / sec / 1e9,
+                                               "ex2_peak_gops": ex2_peak, "frac": ps * n / sec / 1e9 / ex2_peak}
+    return kernels
+
+
+def run_forward_workload(name, dev, steps, warmup, timed, alu, hbm):
+    """A forward-only workload (the fisheye shell: 100k Gaussians on a radius-5 shell around a
+    1280x720 180-degree polynomial fisheye, SH degree 3): the captured forward step timed over
+    `steps`, each ABI call timed with events, and the calls' roofline fractions."""
+    import torch
+
+    from paper_2412_12507_gb300 import render
+    case = workload(name)
+    sc_np, cam, op = case["scene"], case["camera"], case["options"]
+    W, H = cam["width"], cam["height"]
+    scene = render.Scene.from_arrays(sc_np, dev)
+    r = render.Renderer(cam, op, capacity=1 << 20)
+    r.forward(scene)
+    torch.cuda.synchronize()
+    K = r.binning.count()
+    r.capacity = int(K * 1.05) + 1024
+    r.binning = None
+    r.forward(scene)
+    g, _, _ = r.capture(scene)
+    torch.cuda.synchronize()
+    fwd_ms = timed(lambda: g.replay(), steps, warmup)
+    stream = torch.cuda.current_stream()
+    calls = {"ut_project": [], "bin_and_sort": [], "composite_forward": []}
+    for _ in range(max(5, steps)):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        render.project(scene, cam, op, r.proj)
+        ev[1].record(stream)
+        render.bin_and_sort(r.proj, cam, op, r.capacity, ws=r.ws, out=r.binning)
+        ev[2].record(stream)
+        render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, ws=r.fws)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        for j, k in enumerate(calls):
+            calls[k].append(ev[j].elapsed_time(ev[j + 1]))
+    call_ms = {k: statistics.median(v) for k, v in calls.items()}
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    render.composite_forward(scene, cam, op, r.proj, r.binning, r.frame, stats=stats, ws=r.fws)
+    torch.cuda.synchronize()
+    n_eval, n_blend = (int(v) for v in stats.cpu())
+    rc = r.proj.rect.long()
+    M_cols = int(torch.where(r.proj.ntiles > 0, rc[:, 2] // op["tile_w"] - rc[:, 0] // op["tile_w"] + 1,
+                             torch.zeros_like(rc[:, 0])).sum())
+    kernels = call_fractions(call_ms, scene.n, K, M_cols, n_eval, n_blend, W * H, cam, op, hbm, alu)
+    out = {"workload": case["name"], "particles": scene.n, "width": W, "height": H, "keys": K,
+           "fwd_ms": fwd_ms, "fwd_mpix_s": W * H / (fwd_ms / 1e3) / 1e6, "evaluations": n_eval,
+           "blended": n_blend, "kernels": kernels, "launch": "cuda_graph", "steps": steps}
+    del r, g, scene
     torch.cuda.empty_cache()
     return out
 
@@ -520,6 +732,8 @@ def run_ours(args):
     clocks.start()
     fwd_ms = timed(fwd, args.steps, max(3, args.warmup))
     fb_ms = timed(fwd_bwd, args.steps, max(3, args.warmup))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu = measure_alu_peaks(L, dev, stream, sms)
     fwd_eager_ms = timed(fwd_eager, args.steps, max(3, args.warmup))
     fb_eager_ms = timed(fwd_bwd_eager, args.steps, max(3, args.warmup))
     if K > r.binning.capacity or r.binning.count() != K:
@@ -553,34 +767,16 @@ def run_ours(args):
     M_cols = int(torch.where(r.proj.ntiles > 0, rc[:, 2] // op["tile_w"] - rc[:, 0] // op["tile_w"] + 1,
                              torch.zeros_like(rc[:, 0])).sum())  # column entries of the binning
     hbm, sm_max, src = peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-    # per-evaluation / per-blend FP32 operation counts of the compositing arithmetic, term by
-    # term in the design notes; a rolling-shutter view adds the per-pixel origin's canonical
-    # image M o - M mu to every evaluation (9 FMA + 3 subtractions)
-    F_EVAL = 40 + (21 if cam.get("rolling_shutter", 0) else 0)
-    F_BLEND_FWD, F_BLEND_BWD, F_PIX = 110, 275, 120
-    work = {
-        "ut_project": ("hbm", 80.0 * n / 1e9, "GB"),
-        # binning: the K values written once, 16 B of projection output read per particle, the
-        # column list (8 B per column entry) written and read once
-        "bin_and_sort": ("hbm", (4.0 * K + 16.0 * n + 16.0 * M_cols) / 1e9, "GB"),
-        "composite_forward": ("alu", (F_EVAL * n_eval + F_BLEND_FWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
-        "composite_backward": ("alu", (F_EVAL * n_eval + F_BLEND_BWD * n_blend + F_PIX * P) / 1e12, "TFLOP"),
-    }
-    kernels = {}
-    for k, (bound, amount, unit) in work.items():
-        sec = call_ms[k] / 1e3
-        ach = amount / sec
-        peak = hbm if bound == "hbm" else fp32_peak
-        kernels[k] = {"ms": call_ms[k], "bound": bound, "achieved": ach, "peak": peak,
-                      "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / peak}
+    fp32_peak = alu["fp32_tflops"]  # measured in this run
+    fp32_nominal = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    kernels = call_fractions(call_ms, n, K, M_cols, n_eval, n_blend, P, cam, op, hbm, alu)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": measured_traffic(dom, case["name"]),
                 "peak_source": (f"{src} HBM copy" if d["bound"] == "hbm" else
-                                f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz")}
+                                f"measured FP32 FMA-chain probe in this run ({alu['how']}; nominal "
+                                f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz = {fp32_nominal:.1f})")}
 
     # end to end through the public API with host buffers: every step copies the scene in from
     # pinned host memory and the image (rgb, alpha) back out; render.FramePipeline overlaps a
@@ -608,6 +804,10 @@ def run_ours(args):
     del pipe
 
     variants = run_variants(scene, cam, op, d_rgb, d_alpha, timed, args.steps, max(3, args.warmup))
+    fisheye_shell = None
+    if args.workload != "fisheye_shell_100k_720p" and not args.no_extra_workloads:
+        fisheye_shell = run_forward_workload("fisheye_shell_100k_720p", dev, args.steps, max(3, args.warmup), timed,
+                                             alu, peaks()[0])
 
     multiview = None
     if args.multiview_steps > 0:
@@ -621,12 +821,29 @@ def run_ours(args):
         pix = sum(c["width"] * c["height"] for _, _, c in reqs[args.serve_warmup:])
         lat_s, wall_s, st = run_serving(sc_list, op, reqs, args.serve_warmup, int(args.serve_arena_gb * (1 << 30)))
         lat_p, wall_p = run_plain(sc_list, op, reqs, args.serve_warmup)
+        sizes = [s.n for s in sc_list]
+        meas = reqs[args.serve_warmup:]
         serve = {"requests": args.serve_requests, "warmup_requests": args.serve_warmup, "rate_req_s": args.serve_rate,
                  "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
                  "mean_ms": float(lat_s.mean()), "mpix_s": pix / wall_s / 1e6,
                  "plain_p50_ms": float(np.percentile(lat_p, 50)), "plain_p99_ms": float(np.percentile(lat_p, 99)),
                  "plain_mpix_s": pix / wall_p / 1e6, "offered_mpix_s": pix / (reqs[-1][0] - reqs[args.serve_warmup][0]) / 1e6,
-                 "server": st, "scenes": [s.n for s in sc_list]}
+                 "server": st, "scenes": sizes, "server_latency": latency_breakdown(lat_s, meas, sizes),
+                 "plain_latency": latency_breakdown(lat_p, meas, sizes)}
+        if args.serve_saturated_requests > 0:
+            # the same kind of trace offered far above capacity: the sustained throughput of each arm
+            n_w = min(100, args.serve_saturated_requests // 4)
+            sreqs = serving_requests(n_w + args.serve_saturated_requests, args.serve_saturated_rate, seed=5)
+            spix = sum(c["width"] * c["height"] for _, _, c in sreqs[n_w:])
+            lat_s2, wall_s2, st2 = run_serving(sc_list, op, sreqs, n_w, int(args.serve_arena_gb * (1 << 30)))
+            lat_p2, wall_p2 = run_plain(sc_list, op, sreqs, n_w)
+            serve["saturated"] = {
+                "requests": args.serve_saturated_requests, "rate_req_s": args.serve_saturated_rate,
+                "offered_mpix_s": spix / (sreqs[-1][0] - sreqs[n_w][0]) / 1e6,
+                "mpix_s": spix / wall_s2 / 1e6, "plain_mpix_s": spix / wall_p2 / 1e6,
+                "p50_ms": float(np.percentile(lat_s2, 50)), "p99_ms": float(np.percentile(lat_s2, 99)),
+                "plain_p50_ms": float(np.percentile(lat_p2, 50)), "plain_p99_ms": float(np.percentile(lat_p2, 99)),
+                "server": st2}
         del sc_list
         torch.cuda.empty_cache()
 
@@ -648,7 +865,7 @@ def run_ours(args):
             "fwd_ms": fwd_ms, "fwd_bwd_ms_per_view": fb_ms, "fwd_bwd_mpix_s": job_mpix_s(P, world, fb_ms),
             "eager": {"fwd_ms": fwd_eager_ms, "fwd_bwd_ms": fb_eager_ms,
                       "fwd_mpix_s": job_mpix_s(P, world, fwd_eager_ms)},
-            "kernels": kernels, "evaluations": n_eval, "blended": n_blend,
+            "kernels": kernels, "evaluations": n_eval, "blended": n_blend, "alu_peaks": alu,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "e2e": {"value": job_mpix_s(P, world, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
@@ -656,6 +873,7 @@ def run_ours(args):
             "gpu_launches": int(launches_fwd * args.steps + launches_fb * args.steps),
             "launches_per_step": {"fwd": int(launches_fwd), "fwd_bwd": int(launches_fb)},
             "variants": variants,
+            "fisheye_shell_100k_720p": fisheye_shell,
             "multiview": multiview,
             "serve": serve,
         }

@@ -125,3 +125,10 @@ def test_bin_and_sort_validation(L):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         abi.lib(str(tmp_path / "nope.so"))
+
+
+def test_peak_probe_validates_arguments(L):
+    """The throughput probe rejects bad arguments on the host, before any launch."""
+    for args in ((7, 1, 256, 10), (0, 0, 256, 10), (0, 1, 48, 10), (0, 1, 512, 10), (1, 1, 256, 0)):
+        assert L.ut_peak_probe(*args, C.c_void_p(16), None) == abi.UT_ERR_INVALID_ARG
+    assert L.ut_peak_probe(0, 1, 256, 10, None, None) == abi.UT_ERR_INVALID_ARG
