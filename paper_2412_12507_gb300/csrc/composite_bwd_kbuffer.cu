@@ -1,34 +1,37 @@
 // composite_bwd_kbuffer.cu — backward of the "Ours (sorted)" compositing (Sec. 4.4): per-ray
 // k-buffer (multi-layer alpha blending) with per-pixel SH colour and the Gaussian kernel.
 //
-// The blending order of a k-buffer ray is decided per pixel (the closest buffered hit by tau_max
-// leaves when a new hit meets a full buffer, the rest leave in tau order at the end), so a
-// particle is usually blended long after its batch has left shared memory.  The kernel replays
-// the forward kernel's buffer logic exactly (same staging, same FP32 decisions), and at each
-// blend it takes the gradient of that (pixel, particle) pair in the forward order, as the
-// tile-order backward does: the stored final colour gives the colour still to come,
-// S = C_final - A after the pair's own contribution, so
+// The blending order of a k-buffer ray is decided per pixel (the closest buffered hit by tau_max,
+// the earlier arrival on equal tau_max, leaves when a new hit meets a full buffer, the rest leave
+// in that order at the end), so a particle is often blended after its batch has left shared
+// memory.  The kernel replays the forward kernel's buffer logic exactly (same staging, same FP32
+// decisions), and at each blend it takes the gradient of that (pixel, particle) pair in the
+// forward order, as the tile-order backward does: the stored final colour gives the colour still
+// to come, S = C_final - A after the pair's own contribution, so
 // dL/dalpha = sum_c g_c (c_c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha).  The pair's
 // canonical ray (o_g, d_g) is recomputed from the particle's parameters in global memory, and
-// its contributions go to the particle's accumulators (the 13 geometry partials of k_finalize's
-// layout, and dL/dbeta for the unclamped channels) with one global atomic each.  Selection by
-// tau_max is piecewise constant and carries no gradient.
+// its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
+// unclamped channels) go to the particle's accumulators with one global atomic each (a window of
+// per-list-position accumulators in shared memory was measured 5x slower: the lanes of a warp
+// blend the same particle at nearly the same time, and shared-memory atomics on one address
+// serialise, while the L2's reductions absorb them).
+// Selection by tau_max is piecewise constant and carries no gradient.
 #include "composite_common.cuh"
 
 namespace ut3d {
 namespace {
 
 template <int DEG, bool RS>
-__global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
+__global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                                const short4 *__restrict__ rect,
                                                                const uint32_t *__restrict__ vals,
                                                                const uint2 *__restrict__ ranges) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
-  __shared__ float4 s_geo[kBatchF][4];
-  __shared__ __align__(16) float s_sh[kBatchF * NC];
-  __shared__ uint32_t s_idx[kBatchF];
-  extern __shared__ float s_kb[];  // [6][k][threads]: tau, alpha, r, g, b, particle index
+  __shared__ float4 s_geo[kBatchK][4];
+  __shared__ __align__(16) float s_sh[kBatchK * NC];
+  __shared__ uint32_t s_idx[kBatchK];
+  extern __shared__ float s_kb[];  // [6][k][threads]: tau, alpha, r, g, b, list position
 
   const int tile = blockIdx.x;
   const DevView &view = bd.v[view_of_tile(bd, tile)];
@@ -42,7 +45,7 @@ __global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_cons
   const int K = op.kbuffer, nt = blockDim.x;
   float *kb_tau = s_kb + threadIdx.x, *kb_a = kb_tau + K * nt, *kb_r = kb_a + K * nt, *kb_g = kb_r + K * nt,
         *kb_b = kb_g + K * nt;
-  uint32_t *kb_i = reinterpret_cast<uint32_t *>(kb_b + K * nt);  // entry j of this thread at [j * nt]
+  uint32_t *kb_p = reinterpret_cast<uint32_t *>(kb_b + K * nt);  // entry j of this thread at [j * nt]
   float3 o, d;
   float Y[NSH];
   bool valid;
@@ -59,9 +62,9 @@ __global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_cons
   int nbuf = 0;
   bool done = !valid;
 
-  // blends the pair (particle idx, alpha al, clamped colour c) at transmittance T, with the stop
-  // rule of the forward, and adds its gradient contributions
-  auto blend = [&](float al, float c0, float c1, float c2, uint32_t idx) {
+  // blends the pair (the particle at list position pos, alpha al, clamped colour c) at
+  // transmittance T, with the stop rule of the forward, and adds its gradient contributions
+  auto blend = [&](float al, float c0, float c1, float c2, uint32_t pos) {
     const float Tn = T * (1.f - al);
     if (Tn < op.t_min) {
       done = true;
@@ -75,6 +78,8 @@ __global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_cons
     const float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
                       g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
     T = Tn;
+    const uint32_t idx = vals[pos];
+    UT_DBG_CHECK(idx < (uint32_t)sc.n, UT_DBG_PARTICLE, idx, sc.n, 1);
     if (idx >= (uint32_t)sc.n) return;  // every index is a particle of the scene; the test only guards
     // SH coefficients: dL/dbeta_k,ch = g_ch w Y_k where the colour's clamp is inactive
     const float gc[3] = {c0 > 0.f ? g0 * w : 0.f, c1 > 0.f ? g1 * w : 0.f, c2 > 0.f ? g2 * w : 0.f};
@@ -113,9 +118,9 @@ __global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_cons
   };
 
   const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatchF) {
+  for (uint32_t start = rg.x; start < rg.y; start += kBatchK) {
     if (__syncthreads_count(!done) == 0) break;
-    const int nb = min((uint32_t)kBatchF, rg.y - start);
+    const int nb = min((uint32_t)kBatchK, rg.y - start);
     for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
@@ -134,41 +139,32 @@ __global__ void __launch_bounds__(512) k_composite_bwd_kbuffer(const __grid_cons
       float r0, r1, r2;
       sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
       r0 = fmaxf(r0, 0.f); r1 = fmaxf(r1, 0.f); r2 = fmaxf(r2, 0.f);
-      const uint32_t idx = s_idx[b];
+      const uint32_t pos = start + b;
       if (nbuf < K) {
         kb_tau[nbuf * nt] = tau; kb_a[nbuf * nt] = al;
-        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_i[nbuf * nt] = idx;
+        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_p[nbuf * nt] = pos;
         ++nbuf;
         continue;
       }
-      int bi = -1;  // closest of the buffer and the new hit (the forward kernel's choice)
-      float bt = tau;
-      for (int j = 0; j < K; ++j) {
-        const float tj = kb_tau[j * nt];
-        if (tj < bt) { bt = tj; bi = j; }
-      }
+      // closest of the buffer and the new hit (the forward kernel's choice)
+      const int bi = kb_select(kb_tau, kb_p, nt, K, tau, true);
       if (bi < 0) {
-        blend(al, r0, r1, r2, idx);
+        blend(al, r0, r1, r2, pos);
       } else {
-        blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_i[bi * nt]);
+        blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
         kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
-        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_i[bi * nt] = idx;
+        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_p[bi * nt] = pos;
       }
     }
   }
-  // end of the list: the remaining hits in ascending tau_max
+  // end of the list: the remaining hits in ascending (tau_max, arrival)
   while (!done && nbuf > 0) {
-    int bi = 0;
-    float bt = kb_tau[0];
-    for (int j = 1; j < nbuf; ++j) {
-      const float tj = kb_tau[j * nt];
-      if (tj < bt) { bt = tj; bi = j; }
-    }
-    blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_i[bi * nt]);
+    const int bi = kb_select(kb_tau, kb_p, nt, nbuf, 0.f, false);
+    blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
     --nbuf;
     kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
     kb_r[bi * nt] = kb_r[nbuf * nt]; kb_g[bi * nt] = kb_g[nbuf * nt]; kb_b[bi * nt] = kb_b[nbuf * nt];
-    kb_i[bi * nt] = kb_i[nbuf * nt];
+    kb_p[bi * nt] = kb_p[nbuf * nt];
   }
 }
 
@@ -177,11 +173,13 @@ ut_status launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, 
                    const uint32_t *ranges, cudaStream_t s) {
   const int threads = op.tile_w * op.tile_h;
   const size_t smem = sizeof(float) * 6 * (size_t)op.kbuffer * threads;
-  constexpr size_t kStatic = sizeof(float4) * kBatchF * 4 + sizeof(float) * kBatchF * 3 * (DEG + 1) * (DEG + 1) +
-                             sizeof(uint32_t) * kBatchF;
+  constexpr size_t kStatic = sizeof(float4) * kBatchK * 4 + sizeof(float) * kBatchK * 3 * (DEG + 1) * (DEG + 1) +
+                             sizeof(uint32_t) * kBatchK;
   if (smem + kStatic > 227 * 1024) return UT_ERR_UNSUPPORTED;  // the buffer does not fit one block
   if (cudaFuncSetAttribute(k_composite_bwd_kbuffer<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_composite_bwd_kbuffer<DEG, RS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     return UT_ERR_CUDA;
   k_composite_bwd_kbuffer<DEG, RS><<<bd.total_tiles, threads, smem, s>>>(
       bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges));
@@ -203,5 +201,7 @@ ut_status launch_composite_bwd_kbuffer(const BatchDesc &bd, const DevOpts &op, c
     default: return rs ? launch_k<3, true>(bd, op, rect, vals, ranges, s) : launch_k<3, false>(bd, op, rect, vals, ranges, s);
   }
 }
+
+UT_DBG_READER(dbg_read_kbuffer)
 
 }  // namespace ut3d

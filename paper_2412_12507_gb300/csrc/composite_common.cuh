@@ -14,6 +14,7 @@
 // has a rolling shutter); without it the origin is the camera centre of the view.
 #pragma once
 
+#include "ut3d_debug.cuh"
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -22,6 +23,7 @@ namespace {
 
 constexpr int kBatch = 64;    // particles staged per block step (backward)
 constexpr int kBatchF = 128;  // particles staged per block step (forward)
+constexpr int kBatchK = 64;   // particles staged per block step (k-buffer): two blocks of 256 fit an SM
 constexpr int kOrderBuckets = 1024;  // log buckets of the backward's tile schedule
 
 // Tile schedule of the backward (device scratch): per-tile replay length, the tiles with work
@@ -50,6 +52,10 @@ TileSched carve_tile_sched(void *p, int tiles) {
 template <bool RS>
 __device__ __forceinline__ void stage_particle(const DevScene &sc, const DevCam &cam, const DevOpts &op, short4 r,
                                                uint32_t idx, float4 *g, float4 *aux) {
+  // debug build: a listed particle belongs to the scene and its rectangle lies in the image
+  UT_DBG_CHECK(idx < (uint32_t)sc.n, UT_DBG_PARTICLE, idx, sc.n, 0);
+  UT_DBG_CHECK(r.x >= 0 && r.y >= 0 && r.x <= r.z && r.y <= r.w && r.z < cam.W && r.w < cam.H, UT_DBG_RECT, idx,
+               (uint16_t)r.x | ((uint32_t)(uint16_t)r.y << 16), (uint16_t)r.z | ((uint32_t)(uint16_t)r.w << 16));
   float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
   float3 ls = make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
   Particle p;
@@ -322,6 +328,37 @@ __global__ void __launch_bounds__(kOrderBuckets) k_tile_order(int total_tiles, T
     const int b = work_bucket(w);
     ts.order[s_off[b] + atomicAdd(&ts.cursor[b], 1u)] = (uint32_t)i;
   }
+}
+
+// The k-buffer's closest hit among entries [0, n) of a thread's buffer (tau_max at tau[j * nt],
+// list position at pos[j * nt]) and, with with_new, a new hit of tau_max tau0 that arrived last:
+// the smallest tau_max, the earlier arrival (smaller list position) on equal tau_max.  Returns
+// -1 for the new hit, else the entry.  One pass over tau_max finds the minimum and whether it is
+// tied; only a tie (rare: equal FP32 values) takes a second pass over the list positions.
+__device__ __forceinline__ int kb_select(const float *tau, const uint32_t *pos, int nt, int n, float tau0,
+                                         bool with_new) {
+  float bt = with_new ? tau0 : tau[0];
+  int bi = with_new ? -1 : 0;
+  bool tie = false;
+  for (int j = with_new ? 0 : 1; j < n; ++j) {
+    const float tj = tau[j * nt];
+    tie = tj == bt ? true : (tj < bt ? false : tie);
+    if (tj < bt) {
+      bt = tj;
+      bi = j;
+    }
+  }
+  if (tie) {  // the new hit (arrived last) loses every tie
+    uint32_t bp = 0xffffffffu;
+    for (int j = 0; j < n; ++j) {
+      const uint32_t pj = pos[j * nt];
+      if (tau[j * nt] == bt && pj < bp) {
+        bp = pj;
+        bi = j;
+      }
+    }
+  }
+  return bi;
 }
 
 bool any_rs(const BatchDesc &bd) {

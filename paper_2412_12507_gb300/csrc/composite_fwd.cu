@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   // in the order, so every pixel is written
   if (blockIdx.x >= *ts.n_work) return;
   const int tile = (int)ts.order[blockIdx.x];
+  UT_DBG_CHECK(tile < bd.total_tiles, UT_DBG_TILE_ID, tile, bd.total_tiles, 2);
   const DevView &view = bd.v[view_of_tile(bd, tile)];
   const DevScene &sc = bd.s[view.scene];
   const DevCam &cam = view.cam;
@@ -120,19 +121,20 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
 // in ascending (tau_max, arrival).
 // n_used is written as 0 (the backward does not replay this variant).
 template <int DEG, bool RS>
-__global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
+__global__ void __launch_bounds__(512, 1) k_composite_fwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                                const short4 *__restrict__ rect,
                                                                const uint32_t *__restrict__ vals,
                                                                const uint2 *__restrict__ ranges, TileSched ts) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
-  __shared__ float4 s_geo[kBatchF][4];
-  __shared__ __align__(16) float s_sh[kBatchF * NC];
-  __shared__ uint32_t s_idx[kBatchF];
+  __shared__ float4 s_geo[kBatchK][4];
+  __shared__ __align__(16) float s_sh[kBatchK * NC];
+  __shared__ uint32_t s_idx[kBatchK];
   extern __shared__ float s_kb[];  // [6][k][threads]: tau, alpha, r, g, b, list position of each hit
 
   if (blockIdx.x >= *ts.n_work) return;
   const int tile = (int)ts.order[blockIdx.x];
+  UT_DBG_CHECK(tile < bd.total_tiles, UT_DBG_TILE_ID, tile, bd.total_tiles, 2);
   const DevView &view = bd.v[view_of_tile(bd, tile)];
   const DevScene &sc = bd.s[view.scene];
   const DevCam &cam = view.cam;
@@ -166,9 +168,9 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
     T = Tn;
   };
   const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatchF) {
+  for (uint32_t start = rg.x; start < rg.y; start += kBatchK) {
     if (__syncthreads_count(!done) == 0) break;
-    const int nb = min((uint32_t)kBatchF, rg.y - start);
+    const int nb = min((uint32_t)kBatchK, rg.y - start);
     for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
@@ -194,16 +196,9 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
         ++nbuf;
         continue;
       }
-      // closest of the buffer and the new hit; on equal tau the earlier arrival (the new hit
-      // arrived last, so it wins only with a strictly smaller tau)
-      int bi = -1;
-      float bt = tau;
-      uint32_t bp = pos;
-      for (int j = 0; j < K; ++j) {
-        const float tj = kb_tau[j * nt];
-        const uint32_t pj = kb_p[j * nt];
-        if (tj < bt || (tj == bt && pj < bp)) { bt = tj; bp = pj; bi = j; }
-      }
+      // closest of the buffer and the new hit (the new hit arrived last: it wins only with a
+      // strictly smaller tau_max)
+      const int bi = kb_select(kb_tau, kb_p, nt, K, tau, true);
       if (bi < 0) {
         blend(al, r0, r1, r2);
       } else {
@@ -215,14 +210,7 @@ __global__ void __launch_bounds__(512) k_composite_fwd_kbuffer(const __grid_cons
   }
   // end of the list: the remaining hits in ascending (tau_max, arrival)
   while (!done && nbuf > 0) {
-    int bi = 0;
-    float bt = kb_tau[0];
-    uint32_t bp = kb_p[0];
-    for (int j = 1; j < nbuf; ++j) {
-      const float tj = kb_tau[j * nt];
-      const uint32_t pj = kb_p[j * nt];
-      if (tj < bt || (tj == bt && pj < bp)) { bt = tj; bp = pj; bi = j; }
-    }
+    const int bi = kb_select(kb_tau, kb_p, nt, nbuf, 0.f, false);
     blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt]);
     --nbuf;
     kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
@@ -324,6 +312,8 @@ void fwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
     const int threads = op.tile_w * op.tile_h;
     const size_t smem = sizeof(float) * 6 * (size_t)op.kbuffer * threads;
     cudaFuncSetAttribute(k_composite_fwd_kbuffer<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_composite_fwd_kbuffer<DEG, RS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     k_composite_fwd_kbuffer<DEG, RS><<<bd.total_tiles, threads, smem, s>>>(
         bd, op, reinterpret_cast<const short4 *>(rect), vals, reinterpret_cast<const uint2 *>(ranges), ts);
     return;
@@ -369,5 +359,7 @@ ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }
+
+UT_DBG_READER(dbg_read_fwd)
 
 }  // namespace ut3d
