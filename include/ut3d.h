@@ -160,6 +160,32 @@ uint64_t ut_kernel_launch_count(void);
 #define UT_PROBE_EX2 1
 ut_status ut_peak_probe(int32_t kind, int32_t blocks, int32_t threads, int32_t iters, float *out, ut_stream stream);
 
+/* Debug builds (a testing aid with no counterpart in the paper).  A library compiled with
+ * UT_DEBUG checks, where a wrong index would write outside a buffer, that key and value positions
+ * are below the key capacity, tile ids below the number of tiles, particle indices below the
+ * scene's count and rectangles inside the image, and records the first violation instead of
+ * faulting; its binning workspace carries guard bytes after every sub-buffer (so its
+ * ut_bin_workspace_size is larger), filled at the start of each bin_and_sort and checked at its
+ * end.  A release build compiles all of this away.
+ *   ut_debug_enabled: 1 in a debug build, else 0.
+ *   ut_debug_read: record[4] = {code, a, b, c} of the first violation since the last reset
+ *     (code UT_DBG_NONE = 0 when there is none); reset != 0 clears it.  Synchronises with the
+ *     device.  UT_ERR_UNSUPPORTED in a release build.
+ *   ut_debug_check_bin_workspace: checks the guard bytes of a binning workspace that bin_and_sort
+ *     used with the same n, key_capacity, camera and options (recording UT_DBG_CANARY with a =
+ *     the sub-buffer, b = the byte offset in its guard, c = the byte found).  UT_ERR_UNSUPPORTED
+ *     in a release build. */
+#define UT_DBG_NONE 0
+#define UT_DBG_KEY_INDEX 1 /* a = position, b = capacity */
+#define UT_DBG_TILE_ID 2   /* a = tile, b = number of tiles */
+#define UT_DBG_RECT 3      /* a = particle, b = x0 | y0 << 16, c = x1 | y1 << 16 */
+#define UT_DBG_PARTICLE 4  /* a = particle index, b = the scene's count */
+#define UT_DBG_CANARY 5
+int32_t ut_debug_enabled(void);
+ut_status ut_debug_read(uint32_t record[4], int32_t reset);
+ut_status ut_debug_check_bin_workspace(const void *workspace, int32_t n, int64_t key_capacity, const ut_camera *cam,
+                                       const ut_options *opt, ut_stream stream);
+
 /* UT projection of every particle (Algorithm 1 and Algorithm 2; eq. sigma_points,
  * weights_1, weights_2, 2d_conic_1, 2d_conic_2).
  *   Sigma points: mu, mu +- sqrt(3+lambda) s_k R[:,k] (the square root R S of

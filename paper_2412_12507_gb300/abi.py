@@ -76,6 +76,10 @@ SIGNATURES = {
     "ut_status_string": (C.c_char_p, [C.c_int]),
     "ut_kernel_launch_count": (C.c_uint64, []),
     "ut_peak_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P]),
+    "ut_debug_enabled": (C.c_int32, []),
+    "ut_debug_read": (C.c_int, [C.POINTER(C.c_uint32), C.c_int32]),
+    "ut_debug_check_bin_workspace": (C.c_int, [_P, C.c_int32, C.c_int64, C.POINTER(UtCamera), C.POINTER(UtOptions),
+                                               _P]),
     "ut_project": (C.c_int, [C.POINTER(UtScene), C.POINTER(UtCamera), C.POINTER(UtParams), C.POINTER(UtOptions),
                              _P, _P, _P, _P, _P, _P]),
     "ut_bin_workspace_size": (C.c_size_t, [C.c_int32, C.c_int64, C.POINTER(UtCamera), C.POINTER(UtOptions)]),

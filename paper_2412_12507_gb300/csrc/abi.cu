@@ -383,6 +383,48 @@ void ut_default_options(ut_options *o) {
 
 uint64_t ut_kernel_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
+int32_t ut_debug_enabled(void) {
+#ifdef UT_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+ut_status ut_debug_read(uint32_t record[4], int32_t reset) {
+#ifdef UT_DEBUG
+  if (!record) return UT_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return UT_ERR_CUDA;
+  ut_status (*readers[])(uint32_t *, bool) = {dbg_read_binsort, dbg_read_project, dbg_read_fwd, dbg_read_bwd,
+                                              dbg_read_kbuffer};
+  record[0] = record[1] = record[2] = record[3] = 0u;
+  for (auto rd : readers) {  // the first unit with a record reports; every record is read (and reset)
+    uint32_t r[4];
+    const ut_status st = rd(r, reset != 0);
+    if (st != UT_OK) return st;
+    if (record[0] == 0u && r[0] != 0u)
+      for (int i = 0; i < 4; ++i) record[i] = r[i];
+  }
+  return UT_OK;
+#else
+  (void)record;
+  (void)reset;
+  return UT_ERR_UNSUPPORTED;
+#endif
+}
+
+ut_status ut_debug_check_bin_workspace(const void *workspace, int32_t n, int64_t key_capacity, const ut_camera *cam,
+                                       const ut_options *opt, ut_stream stream) {
+  DevCam dc;
+  ut_status st = make_cam(cam, dc);
+  if (st != UT_OK) return st;
+  DevOpts dop;
+  if ((st = make_opts(opt, cam, dop)) != UT_OK) return st;
+  if (!workspace || n < 0 || key_capacity < 0) return UT_ERR_INVALID_ARG;
+  return dbg_check_bin_guards(workspace, n, key_capacity, dop.tiles_x * dop.tiles_y, dop.tiles_x, dop.tiles_y,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
 const char *ut_status_string(ut_status s) {
   switch (s) {
     case UT_OK: return "ok";

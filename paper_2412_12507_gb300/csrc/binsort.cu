@@ -23,6 +23,7 @@
 // ranks keys stably in shared memory (same-digit lanes found with 8 ballots per 32-key group,
 // per-warp running digit counters) and writes them out digit-grouped for coalescing.
 // No kernel waits on another block, so nothing in here can spin.
+#include "ut3d_debug.cuh"
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -514,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_cols(const __grid_constant__ 
       const uint32_t k0 = __shfl_sync(0xffffffffu, key0, l);
       const uint32_t g0 = __shfl_sync(0xffffffffu, g, l);
       if (p < E) {
+        UT_DBG_CHECK(p < total.cap, UT_DBG_KEY_INDEX, p, total.cap, 0);
         ckeys[p] = k0 + (p - s0);
         cvals[p] = g0;
       }
@@ -556,6 +558,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_rows(const __grid_constant__ 
       const uint32_t k0 = __shfl_sync(0xffffffffu, key0, l);
       const uint32_t l0 = __shfl_sync(0xffffffffu, local, l);
       if (p < E) {
+        UT_DBG_CHECK(p < total.cap, UT_DBG_KEY_INDEX, p, total.cap, 1);
         rkeys[p] = k0 + ((p - s0) << bd.col_bits);
         rvals[p] = l0;
       }
@@ -597,6 +600,7 @@ __global__ void k_ranges(const __grid_constant__ BatchDesc bd, const uint32_t *_
       const bool first = t[i] != cur, last = t[2 + i] != cur;
       if (!(first || last || keys)) continue;
       const uint32_t tile = tile_of_key(bd, cur);
+      UT_DBG_CHECK(tile < (uint32_t)bd.total_tiles, UT_DBG_TILE_ID, tile, bd.total_tiles, 0);
       if (first) ranges[2 * tile] = p;
       if (last) ranges[2 * tile + 1] = p + 1;
       if (keys) {
@@ -943,6 +947,7 @@ struct RowPolicy {
   __device__ uint2 stage(uint32_t x, uint32_t, uint32_t, uint32_t r) const { return make_uint2(x, r); }
   __device__ uint32_t bin_of(uint2 s) const { return s.y; }
   __device__ void emit(uint32_t pos, uint2 s) const {
+    UT_DBG_CHECK(pos < kmax, UT_DBG_KEY_INDEX, pos, kmax, 2);
     if (pos >= kmax) return;  // every position is below K; the tests only guard the stores
     vals[pos] = s.x - part_off;
     if (keys) keys[pos] = ((u64)(tile0 + s.y * tiles_x) << 32) | (u64)__float_as_uint(depth[s.x]);
@@ -988,6 +993,7 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
       const uint32_t start = spine[sp];
       const uint32_t end = sp + nch < slen ? spine[sp + nch] : kmax;
       if (start < end) {
+        UT_DBG_CHECK(tile < (uint32_t)bd.total_tiles, UT_DBG_TILE_ID, tile, bd.total_tiles, 1);
         ranges[2 * tile] = start;
         ranges[2 * tile + 1] = end;
       }
@@ -1002,20 +1008,48 @@ __global__ void __launch_bounds__(kThreads) k_row_scatter(const __grid_constant_
 
 // ---------------------------------------------------------------- host orchestration
 
+// Guard bytes after every sub-buffer of a debug build's binning workspace (their offsets).
+constexpr int kMaxGuards = 48;
+#ifdef UT_DEBUG
+constexpr uint32_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xa5;
+#endif
+struct GuardList {
+  int n = 0;
+  uint32_t off[kMaxGuards];
+};
+
 struct Arena {
   char *p;
   size_t off;
+  GuardList *guards = nullptr;
   template <class T>
   T *take(size_t count) {
     T *r = reinterpret_cast<T *>(p ? p + off : nullptr);
     off += align256(count * sizeof(T));
+#ifdef UT_DEBUG
+    if (guards && guards->n < kMaxGuards) guards->off[guards->n++] = (uint32_t)off;
+    off += kGuardBytes;
+#endif
     return r;
   }
 };
 
+#ifdef UT_DEBUG
+// Debug build: every guard byte still kGuardByte, else UT_DBG_CANARY (guard, offset, byte).
+__global__ void k_check_guards(const unsigned char *__restrict__ ws, GuardList g) {
+  for (int i = 0; i < g.n; ++i)
+    for (uint32_t b = threadIdx.x; b < kGuardBytes; b += blockDim.x) {
+      const unsigned char v = ws[(size_t)g.off[i] + b];
+      UT_DBG_CHECK(v == kGuardByte, UT_DBG_CANARY, i, b, v);
+    }
+}
+#endif
+
 inline uint32_t ceil_div(u64 a, u64 b) { return (uint32_t)((a + b - 1) / b); }
 
 struct Buffers {
+  GuardList guards;
   uint32_t *dk[2], *dv[2], *cnt, *offs, *x[3], *spine;
   uint32_t *colb, *tspine;  // row scatter: column bounds [2 x cols], (tile, chunk) counts
   ChunkPlan plan;
@@ -1024,8 +1058,8 @@ struct Buffers {
 
 // Workspace layout; with ws == nullptr only the size is accumulated.
 Buffers carve(void *ws, int n, int64_t cap, int tiles, int cols, int max_rows, size_t *bytes = nullptr) {
-  Arena a{static_cast<char *>(ws), 0};
   Buffers b;
+  Arena a{static_cast<char *>(ws), 0, &b.guards};
   size_t nn = (size_t)(n > 0 ? n : 1);
   size_t cc = (size_t)(cap > 0 ? cap : 1);
   size_t maxc = nn > cc ? nn : cc;
@@ -1122,6 +1156,17 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
   int max_rows = 0;
   for (int v = 0; v < bd.nv; ++v) max_rows = bd.v[v].tiles_y > max_rows ? bd.v[v].tiles_y : max_rows;
   Buffers b = carve(ws, n, cap, tiles, bd.total_cols, max_rows);
+#ifdef UT_DEBUG
+  for (int i = 0; i < b.guards.n; ++i)
+    if (cudaMemsetAsync(static_cast<char *>(ws) + b.guards.off[i], kGuardByte, kGuardBytes, s) != cudaSuccess)
+      return UT_ERR_CUDA;
+  struct GuardCheck {  // checks the guards when launch_bin returns
+    const Buffers &b;
+    void *ws;
+    cudaStream_t s;
+    ~GuardCheck() { k_check_guards<<<1, 256, 0, s>>>(static_cast<const unsigned char *>(ws), b.guards); }
+  } guard_check{b, ws, s};
+#endif
   if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)tiles, s) != cudaSuccess) return UT_ERR_CUDA;
   if (cudaMemsetAsync(b.total, 0, 2 * sizeof(u64), s) != cudaSuccess) return UT_ERR_CUDA;
   if (n > 0) {
@@ -1197,6 +1242,20 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
   k_write_kout<<<1, 1, 0, s>>>(b.total + 1, k_out);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+}
+
+UT_DBG_READER(dbg_read_binsort)
+
+ut_status dbg_check_bin_guards(const void *ws, int n, int64_t cap, int tiles, int cols, int max_rows,
+                               cudaStream_t stream) {
+#ifdef UT_DEBUG
+  const Buffers b = carve(const_cast<void *>(ws), n, cap, tiles, cols, max_rows);
+  k_check_guards<<<1, 256, 0, stream>>>(static_cast<const unsigned char *>(ws), b.guards);
+  return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+#else
+  (void)ws; (void)n; (void)cap; (void)tiles; (void)cols; (void)max_rows; (void)stream;
+  return UT_ERR_UNSUPPORTED;
+#endif
 }
 
 }  // namespace ut3d

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
   // tiles in the order k_tile_order gave them (most list entries to replay first)
   if (blockIdx.x >= *ts.n_work) return;
   const int tile = (int)ts.order[blockIdx.x];
+  UT_DBG_CHECK(tile < bd.total_tiles, UT_DBG_TILE_ID, tile, bd.total_tiles, 3);
   const DevView &view = bd.v[view_of_tile(bd, tile)];
   const DevScene &sc = bd.s[view.scene];
   const DevCam &cam = view.cam;
@@ -516,5 +517,7 @@ ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int
   }
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }
+
+UT_DBG_READER(dbg_read_bwd)
 
 }  // namespace ut3d

@@ -8,6 +8,7 @@
 // coalesced vector accesses.  The 7 sigma points are projected through the view's camera
 // (with the rolling-shutter time fixed point), and the weighted mean / covariance, depth,
 // opacity-tightened rectangle and tile count are written out.
+#include "ut3d_debug.cuh"
 #include "ut3d_device.cuh"
 #include "ut3d_internal.h"
 
@@ -158,6 +159,8 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_project(const __grid_constan
   uint32_t nt = 0;
   if (ok) {
     int x0 = (int)fx0, x1 = (int)fx1, y0i = (int)fy0, y1 = (int)fy1;
+    UT_DBG_CHECK(x0 >= 0 && y0i >= 0 && x0 <= x1 && y0i <= y1 && x1 < cam.W && y1 < cam.H, UT_DBG_RECT,
+                 blockIdx.x * blockDim.x + threadIdx.x, x0 | (y0i << 16), x1 | (y1 << 16));
     r = make_short4((short)x0, (short)y0i, (short)x1, (short)y1);
     nt = (uint32_t)((x1 / op.tile_w - x0 / op.tile_w + 1) * (y1 / op.tile_h - y0i / op.tile_h + 1));
   } else {
@@ -240,5 +243,7 @@ ut_status launch_project(const BatchDesc &bd, const DevOpts &op, const UTWeights
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;
 }
+
+UT_DBG_READER(dbg_read_project)
 
 }  // namespace ut3d

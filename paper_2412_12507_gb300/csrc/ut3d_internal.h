@@ -24,6 +24,17 @@ struct UTWeights {
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Debug-build records of the translation units with checks (ut3d_debug.cuh); all zero in a
+// release build.
+ut_status dbg_read_binsort(uint32_t out[4], bool reset);
+ut_status dbg_read_project(uint32_t out[4], bool reset);
+ut_status dbg_read_fwd(uint32_t out[4], bool reset);
+ut_status dbg_read_bwd(uint32_t out[4], bool reset);
+ut_status dbg_read_kbuffer(uint32_t out[4], bool reset);
+// Debug build: checks the guard bytes of a binning workspace (records UT_DBG_CANARY).
+ut_status dbg_check_bin_guards(const void *ws, int n, int64_t cap, int tiles, int cols, int max_rows,
+                               cudaStream_t stream);
+
 // Process-wide count of kernel launches (ut_kernel_launch_count); every launch site adds to it.
 void count_launches(int k);
 

@@ -132,3 +132,14 @@ def test_peak_probe_validates_arguments(L):
     for args in ((7, 1, 256, 10), (0, 0, 256, 10), (0, 1, 48, 10), (0, 1, 512, 10), (1, 1, 256, 0)):
         assert L.ut_peak_probe(*args, C.c_void_p(16), None) == abi.UT_ERR_INVALID_ARG
     assert L.ut_peak_probe(0, 1, 256, 10, None, None) == abi.UT_ERR_INVALID_ARG
+
+
+def test_release_build_has_no_debug_checks(L):
+    """The release library reports no debug build and refuses the debug entry points."""
+    assert L.ut_debug_enabled() == 0
+    rec = (C.c_uint32 * 4)()
+    assert L.ut_debug_read(rec, 1) == abi.UT_ERR_UNSUPPORTED
+    cam = abi.make_camera(synth.camera("pinhole", 32, 32, fx=32.0))
+    o = abi.default_options()
+    st = L.ut_debug_check_bin_workspace(C.c_void_p(256), 10, 100, C.byref(cam), C.byref(o), None)
+    assert st == abi.UT_ERR_UNSUPPORTED
