@@ -411,9 +411,10 @@ ut_status ut_server_wait(ut_server *s, uint64_t id, int32_t timeout_ms, int32_t 
 ut_status ut_server_release(ut_server *s, uint64_t id);
 
 /* Counters since creation: completed requests, batches launched, key-capacity retries, graph
- * replays, graph (re)instantiations. */
+ * replays, graph (re)instantiations, retries whose batch went back to the queue (no memory for
+ * the larger workspace yet), and failed requests. */
 typedef struct {
-  uint64_t completed, batches, retries, graph_launches, graph_instantiations;
+  uint64_t completed, batches, retries, graph_launches, graph_instantiations, requeued, failed;
 } ut_server_stats;
 ut_status ut_server_get_stats(ut_server *s, ut_server_stats *stats);
 

@@ -62,7 +62,8 @@ class UtServerConfig(C.Structure):
 
 class UtServerStats(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("batches", C.c_uint64), ("retries", C.c_uint64),
-                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64), ("requeued", C.c_uint64),
+                ("failed", C.c_uint64)]
 
 
 MAX_BATCH_VIEWS = 32

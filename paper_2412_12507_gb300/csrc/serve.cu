@@ -37,7 +37,9 @@ double ms_since(Clock::time_point t0, Clock::time_point t1) {
   return std::chrono::duration<double, std::milli>(t1 - t0).count();
 }
 
-// First-fit allocator over [0, size) with 256-byte granularity.
+// Allocator over [0, size) with 256-byte granularity: workspaces first-fit from the bottom,
+// request outputs (which live until the client releases them) last-fit from the top, so that the
+// long-lived outputs do not scatter holes through the space the large workspaces need.
 class Arena {
  public:
   void init(size_t size) {
@@ -53,6 +55,18 @@ class Arena {
         size_t start = it->first + bytes;
         free_.erase(it);
         if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  bool alloc_high(size_t bytes, size_t *off) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.rbegin(); it != free_.rend(); ++it) {
+      if (it->second >= bytes) {
+        it->second -= bytes;  // the block keeps its start and gives up its top
+        *off = it->first + it->second;
+        if (it->second == 0) free_.erase(std::next(it).base());
         return true;
       }
     }
@@ -96,7 +110,12 @@ struct Request {
   size_t out_off = 0, out_bytes = 0;
   bool has_out = false;  // output image carved from the arena
   uint64_t key_class = 0;
+  int overflows = 0;  // key-capacity overflows of the batches it was in
 };
+
+// A request whose batches overflowed this often (the arena cannot hold the workspace its key
+// count needs) fails with UT_ERR_CAPACITY instead of being retried for ever.
+constexpr int kMaxOverflows = 6;
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -134,6 +153,9 @@ struct ut_server {
 namespace {
 
 size_t out_bytes(const ut_camera &c) { return (size_t)16 * (size_t)c.width * (size_t)c.height; }
+
+// Largest key capacity of one batch (render_batch needs key_capacity < 2^32).
+constexpr double kMaxBatchKeys = 4.0e9;
 
 uint64_t key_class(int scene, const ut_camera &c) {
   return ((uint64_t)scene << 40) ^ ((uint64_t)c.model << 36) ^ ((uint64_t)c.width << 18) ^ (uint64_t)c.height;
@@ -213,11 +235,13 @@ void fail_slot(ut_server *s, Slot &sl, ut_status err) {
     r.state = FAILED;
     r.status = err;
     r.t_done = now;
+    s->stats.failed++;
   }
   if (sl.ws_bytes) s->arena.release(sl.ws_off, sl.ws_bytes);
   sl.ws_bytes = 0;
   sl.reqs.clear();
   sl.busy = false;
+  s->cv_done.notify_all();  // waiters of the failed requests
 }
 
 // Admission and batching (called with the lock held).  Returns true if it launched something.
@@ -228,7 +252,7 @@ bool schedule(ut_server *s) {
   while (!s->pending.empty() && s->admitted.size() < (size_t)s->cfg.max_batch_views) {
     Request &r = s->reqs[s->pending.front()];
     size_t off;
-    if (!s->arena.alloc(r.out_bytes, &off)) break;
+    if (!s->arena.alloc_high(r.out_bytes, &off)) break;
     r.out_off = off;
     r.has_out = true;
     r.state = ADMITTED;
@@ -256,7 +280,9 @@ bool schedule(ut_server *s) {
       est.push_back(key_estimate(s, r));
       cap += est.back();
     }
-    int64_t capacity = (int64_t)std::min(cap * (double)s->cfg.key_headroom, 4.0e9);
+    const double want = cap * (double)s->cfg.key_headroom;
+    if (want > kMaxBatchKeys && nb > 1) continue;  // more keys than one batch can sort: fewer views
+    int64_t capacity = (int64_t)std::min(want, kMaxBatchKeys);
     size_t need = ut_batch_workspace_size(s->scenes.data(), (int)s->scenes.size(), views.data(), (int)nb,
                                           &s->cfg.options, capacity);
     if (need == 0) {
@@ -264,6 +290,7 @@ bool schedule(ut_server *s) {
       Request &r = s->reqs[s->admitted.front()];
       r.state = FAILED;
       r.status = UT_ERR_INVALID_ARG;
+      s->stats.failed++;
       r.t_done = Clock::now();
       s->admitted.pop_front();
       s->cv_done.notify_all();
@@ -312,6 +339,7 @@ bool schedule(ut_server *s) {
     Request &r = s->reqs[s->admitted.front()];
     r.state = FAILED;
     r.status = UT_ERR_CAPACITY;
+    s->stats.failed++;
     r.t_done = Clock::now();
     s->admitted.pop_front();
     s->cv_done.notify_all();
@@ -352,14 +380,28 @@ bool reap(ut_server *s) {
       // overflow: re-run the same batch with the observed key count
       s->stats.retries++;
       s->arena.release(sl.ws_off, sl.ws_bytes);
+      sl.ws_bytes = 0;
       std::vector<ut_view> views;
       for (uint64_t id : sl.reqs) views.push_back(make_view(s, s->reqs[id]));
-      int64_t capacity = (int64_t)((double)K * s->cfg.key_headroom) + 1024;
-      size_t need = ut_batch_workspace_size(s->scenes.data(), (int)s->scenes.size(), views.data(),
-                                            (int)views.size(), &s->cfg.options, capacity);
+      const double want = (double)K * s->cfg.key_headroom + 1024.0;
+      int worst = 0;
+      for (uint64_t id : sl.reqs) worst = std::max(worst, ++s->reqs[id].overflows);
+      if ((want > kMaxBatchKeys || worst > kMaxOverflows) && sl.reqs.size() == 1) {
+        // one view with more keys than any batch can sort, or than the arena could ever give it
+        fail_slot(s, sl, UT_ERR_CAPACITY);
+        continue;
+      }
+      // (a batch of several views whose keys exceed one batch goes back to the queue; its views'
+      // learned key estimates now split it)
+      int64_t capacity = (int64_t)std::min(want, kMaxBatchKeys);
+      size_t need = want > kMaxBatchKeys ? 0
+                                         : ut_batch_workspace_size(s->scenes.data(), (int)s->scenes.size(),
+                                                                   views.data(), (int)views.size(), &s->cfg.options,
+                                                                   capacity);
       size_t off;
       if (need == 0 || !s->arena.alloc(need + 256, &off)) {
         // put the requests back at the head of the queue, to be re-batched when memory frees up
+        s->stats.requeued++;
         sl.ws_bytes = 0;
         for (auto it = sl.reqs.rbegin(); it != sl.reqs.rend(); ++it) {
           s->reqs[*it].state = ADMITTED;
