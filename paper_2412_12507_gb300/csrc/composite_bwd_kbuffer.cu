@@ -11,7 +11,11 @@
 // dL/dalpha = sum_c g_c (c_c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha).  The pair's
 // canonical ray (o_g, d_g) is recomputed from the particle's parameters in global memory, and
 // its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
-// unclamped channels) go to the particle's accumulators with one global atomic each (a window of
+// unclamped channels) go to the particle's accumulators.  The lanes of a warp blend in step (one
+// blend event per lane per staged particle, and per step of the final drain); when every event of
+// a step concerns the same particle -- the common case, neighbouring pixels' buffers evolve
+// alike -- the warp sums the events' contributions with reduce-scatters and adds each value with
+// one atomic, otherwise every lane adds its own, one global atomic per value (a window of
 // per-list-position accumulators in shared memory was measured 5x slower: the lanes of a warp
 // blend the same particle at nearly the same time, and shared-memory atomics on one address
 // serialise, while the L2's reductions absorb them).
@@ -21,6 +25,24 @@
 namespace ut3d {
 namespace {
 
+constexpr int kBatchKB = 48;  // particles staged per block step: two blocks of 256 fit an SM at k = 16
+
+// Reduce-scatter of 16 per-lane values over the 32 lanes: afterwards lanes 2i and 2i+1 hold the
+// warp total of value i.
+__device__ __forceinline__ void kb_reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 16, L = 8; L >= 1; o >>= 1, L >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+      const float send = up ? v[j] : v[j + L];
+      const float keep = up ? v[j + L] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <int DEG, bool RS>
 __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_constant__ BatchDesc bd, DevOpts op,
                                                                const short4 *__restrict__ rect,
@@ -28,9 +50,10 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
                                                                const uint2 *__restrict__ ranges) {
   constexpr int NSH = (DEG + 1) * (DEG + 1);
   constexpr int NC = NSH * 3;
-  __shared__ float4 s_geo[kBatchK][4];
-  __shared__ __align__(16) float s_sh[kBatchK * NC];
-  __shared__ uint32_t s_idx[kBatchK];
+  __shared__ float4 s_geo[kBatchKB][4];
+  __shared__ float4 s_aux[kBatchKB];
+  __shared__ __align__(16) float s_sh[kBatchKB * NC];
+  __shared__ uint32_t s_idx[kBatchKB];
   extern __shared__ float s_kb[];  // [6][k][threads]: tau, alpha, r, g, b, list position
 
   const int tile = blockIdx.x;
@@ -61,6 +84,13 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
   float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;  // running prefix of the composited colour
   int nbuf = 0;
   bool done = !valid;
+  uint32_t sb = 0;  // list position of the batch staged in shared memory
+  int snb = 0;      // and its length
+  // this lane's blend event of the current step: particle, SH weights g_c w, the geometry partial
+  // v = 2 dL/domega^2 (o_g + tau d_g), x = o - mu + tau d, and dL/dsigma
+  bool has_ev = false;
+  uint32_t ev_idx = 0;
+  float ev_gc[3] = {0.f, 0.f, 0.f}, ev_v[3] = {0.f, 0.f, 0.f}, ev_x[3] = {0.f, 0.f, 0.f}, ev_dsig = 0.f;
 
   // blends the pair (the particle at list position pos, alpha al, clamped colour c) at
   // transmittance T, with the stop rule of the forward, and adds its gradient contributions
@@ -78,93 +108,170 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
     const float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
                       g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
     T = Tn;
-    const uint32_t idx = vals[pos];
+    // a particle of the staged batch is read from shared memory (its staged record and o - mu or
+    // mu), an older one from its parameters in global memory
+    const bool staged = pos >= sb && pos < sb + (uint32_t)snb;
+    const uint32_t idx = staged ? s_idx[pos - sb] : vals[pos];
     UT_DBG_CHECK(idx < (uint32_t)sc.n, UT_DBG_PARTICLE, idx, sc.n, 1);
     if (idx >= (uint32_t)sc.n) return;  // every index is a particle of the scene; the test only guards
     // SH coefficients: dL/dbeta_k,ch = g_ch w Y_k where the colour's clamp is inactive
-    const float gc[3] = {c0 > 0.f ? g0 * w : 0.f, c1 > 0.f ? g1 * w : 0.f, c2 > 0.f ? g2 * w : 0.f};
-    float *dsh = sc.d_sh + (size_t)idx * NC;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      if (gc[ch] == 0.f) continue;
-#pragma unroll
-      for (int k = 0; k < NSH; ++k) atomicAdd(&dsh[3 * k + ch], gc[ch] * Y[k]);
+    ev_gc[0] = c0 > 0.f ? g0 * w : 0.f;
+    ev_gc[1] = c1 > 0.f ? g1 * w : 0.f;
+    ev_gc[2] = c2 > 0.f ? g2 * w : 0.f;
+    // geometry: the pair's canonical ray
+    float3 og, dg, om;
+    float sigma;
+    if (staged) {
+      const float4 *g = s_geo[pos - sb];
+      const float4 g0r = g[0], g1r = g[1], g2r = g[2], ax = s_aux[pos - sb];
+      dg = make_float3(fmaf(g0r.x, d.x, fmaf(g0r.y, d.y, g0r.z * d.z)),
+                       fmaf(g0r.w, d.x, fmaf(g1r.x, d.y, g1r.y * d.z)),
+                       fmaf(g1r.z, d.x, fmaf(g1r.w, d.y, g2r.x * d.z)));
+      if (RS) {
+        og = make_float3(fmaf(g0r.x, o.x, fmaf(g0r.y, o.y, g0r.z * o.z)) - g2r.y,
+                         fmaf(g0r.w, o.x, fmaf(g1r.x, o.y, g1r.y * o.z)) - g2r.z,
+                         fmaf(g1r.z, o.x, fmaf(g1r.w, o.y, g2r.x * o.z)) - g2r.w);
+        om = make_float3(o.x - ax.x, o.y - ax.y, o.z - ax.z);
+      } else {
+        og = make_float3(g2r.y, g2r.z, g2r.w);
+        om = make_float3(ax.x, ax.y, ax.z);
+      }
+      sigma = g[3].x;
+    } else {
+      const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
+      const float3 ls =
+          make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
+      Particle p;
+      activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
+      om = make_float3(o.x - mu.x, o.y - mu.y, o.z - mu.z);
+      og = mat3_mul(p.M, om);
+      dg = mat3_mul(p.M, d);
+      sigma = p.sigma;
     }
-    // geometry: the pair's canonical ray from the particle's parameters
-    const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
-    const float3 ls = make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
-    Particle p;
-    activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
-    const float3 om = make_float3(o.x - mu.x, o.y - mu.y, o.z - mu.z);
-    const float3 og = mat3_mul(p.M, om), dg = mat3_mul(p.M, d);
     const float3 cr = cross3(og, dg);
     const float cc = dot3(cr, cr), dd = dot3(dg, dg);
-    const float a = p.sigma * __expf(-0.5f * __fdividef(cc, dd));
+    const float a = sigma * __expf(-0.5f * __fdividef(cc, dd));
     const float da = a > op.alpha_max ? 0.f : dal;
-    const float dsig = da * a / p.sigma;
+    ev_dsig = da * a / sigma;
     const float dw2 = -0.5f * a * da;
     const float tau = -dot3(og, dg) / dd;
     const float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
-    const float vv[3] = {2.f * dw2 * pp.x, 2.f * dw2 * pp.y, 2.f * dw2 * pp.z};
-    const float xx[3] = {fmaf(tau, d.x, om.x), fmaf(tau, d.y, om.y), fmaf(tau, d.z, om.z)};
-    float *acc = sc.gacc + (size_t)idx * 16;
+    ev_v[0] = 2.f * dw2 * pp.x;
+    ev_v[1] = 2.f * dw2 * pp.y;
+    ev_v[2] = 2.f * dw2 * pp.z;
+    ev_x[0] = fmaf(tau, d.x, om.x);
+    ev_x[1] = fmaf(tau, d.y, om.y);
+    ev_x[2] = fmaf(tau, d.z, om.z);
+    ev_idx = idx;
+    has_ev = true;
+  };
+
+  // adds this step's blend events to the particles' accumulators; every lane of the warp calls it
+  const int lane = threadIdx.x & 31;
+  auto emit = [&]() {
+    const unsigned act = __ballot_sync(0xffffffffu, has_ev);
+    if (!act) return;
+    const uint32_t p0 = __shfl_sync(0xffffffffu, ev_idx, __ffs(act) - 1);
+    if (__all_sync(0xffffffffu, !has_ev || ev_idx == p0)) {
+      // one particle: the warp's sums, one atomic per value
+      float v[16];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      atomicAdd(&acc[r], vv[r]);
+      for (int r = 0; r < 3; ++r) {
+        v[r] = has_ev ? ev_v[r] : 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) atomicAdd(&acc[3 + 3 * r + c], vv[r] * xx[c]);
+        for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = has_ev ? ev_v[r] * ev_x[c] : 0.f;
+      }
+      v[12] = has_ev ? ev_dsig : 0.f;
+      v[13] = v[14] = v[15] = 0.f;
+      kb_reduce_scatter16(v, lane);
+      const int vi = lane >> 1;
+      if (!(lane & 1) && vi < 13) atomicAdd(&sc.gacc[(size_t)p0 * 16 + vi], v[0]);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        if (!__any_sync(0xffffffffu, has_ev && ev_gc[ch] != 0.f)) continue;
+        float u[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) u[k] = (has_ev && k < NSH) ? ev_gc[ch] * Y[k < NSH ? k : 0] : 0.f;
+        kb_reduce_scatter16(u, lane);
+        if (!(lane & 1) && vi < NSH && u[0] != 0.f) atomicAdd(&sc.d_sh[(size_t)p0 * NC + 3 * vi + ch], u[0]);
+      }
+    } else if (has_ev) {
+      float *dsh = sc.d_sh + (size_t)ev_idx * NC;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        if (ev_gc[ch] == 0.f) continue;
+#pragma unroll
+        for (int k = 0; k < NSH; ++k) atomicAdd(&dsh[3 * k + ch], ev_gc[ch] * Y[k]);
+      }
+      float *acc = sc.gacc + (size_t)ev_idx * 16;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        atomicAdd(&acc[r], ev_v[r]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(&acc[3 + 3 * r + c], ev_v[r] * ev_x[c]);
+      }
+      atomicAdd(&acc[12], ev_dsig);
     }
-    atomicAdd(&acc[12], dsig);
+    has_ev = false;
   };
 
   const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatchK) {
+  for (uint32_t start = rg.x; start < rg.y; start += kBatchKB) {
     if (__syncthreads_count(!done) == 0) break;
-    const int nb = min((uint32_t)kBatchK, rg.y - start);
+    const int nb = (int)min((uint32_t)kBatchKB, rg.y - start);
     for (int t = threadIdx.x; t < nb; t += blockDim.x) s_idx[t] = vals[start + t];
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
       uint32_t idx = s_idx[t];
-      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], nullptr);
+      stage_particle<RS>(sc, cam, op, rect[view.part_off + idx], idx, s_geo[t], &s_aux[t]);
     }
     stage_sh<NC>(sc, s_idx, nb, s_sh);
     __syncthreads();
-    if (done) continue;
-    for (int b = 0; b < nb && !done; ++b) {
+    sb = start;
+    snb = nb;
+    if (__all_sync(0xffffffffu, done)) continue;
+    // every lane of the warp walks every staged particle (the emit steps are warp-wide)
+    for (int b = 0; b < nb; ++b) {
       float3 og, dg;
       float dd, a;
-      if (!eval_response<RS, false>(s_geo[b], px, py, o, d, og, dg, dd, a, op)) continue;
-      const float tau = -__fdividef(dot3(og, dg), dd);
-      const float al = fminf(a, op.alpha_max);
-      float r0, r1, r2;
-      sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
-      r0 = fmaxf(r0, 0.f); r1 = fmaxf(r1, 0.f); r2 = fmaxf(r2, 0.f);
-      const uint32_t pos = start + b;
-      if (nbuf < K) {
-        kb_tau[nbuf * nt] = tau; kb_a[nbuf * nt] = al;
-        kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_p[nbuf * nt] = pos;
-        ++nbuf;
-        continue;
+      if (!done && eval_response<RS, false>(s_geo[b], px, py, o, d, og, dg, dd, a, op)) {
+        const float tau = -__fdividef(dot3(og, dg), dd);
+        const float al = fminf(a, op.alpha_max);
+        float r0, r1, r2;
+        sh_colour<NSH>(s_sh + b * NC, Y, r0, r1, r2);
+        r0 = fmaxf(r0, 0.f); r1 = fmaxf(r1, 0.f); r2 = fmaxf(r2, 0.f);
+        const uint32_t pos = start + b;
+        if (nbuf < K) {
+          kb_tau[nbuf * nt] = tau; kb_a[nbuf * nt] = al;
+          kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_p[nbuf * nt] = pos;
+          ++nbuf;
+        } else {
+          // closest of the buffer and the new hit (the forward kernel's choice)
+          const int bi = kb_select(kb_tau, kb_p, nt, K, tau, true);
+          if (bi < 0) {
+            blend(al, r0, r1, r2, pos);
+          } else {
+            blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
+            kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
+            kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_p[bi * nt] = pos;
+          }
+        }
       }
-      // closest of the buffer and the new hit (the forward kernel's choice)
-      const int bi = kb_select(kb_tau, kb_p, nt, K, tau, true);
-      if (bi < 0) {
-        blend(al, r0, r1, r2, pos);
-      } else {
-        blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
-        kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
-        kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_p[bi * nt] = pos;
-      }
+      emit();
+      if (__all_sync(0xffffffffu, done)) break;
     }
   }
-  // end of the list: the remaining hits in ascending (tau_max, arrival)
-  while (!done && nbuf > 0) {
-    const int bi = kb_select(kb_tau, kb_p, nt, nbuf, 0.f, false);
-    blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
-    --nbuf;
-    kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
-    kb_r[bi * nt] = kb_r[nbuf * nt]; kb_g[bi * nt] = kb_g[nbuf * nt]; kb_b[bi * nt] = kb_b[nbuf * nt];
-    kb_p[bi * nt] = kb_p[nbuf * nt];
+  // end of the list: the remaining hits in ascending (tau_max, arrival), the warp in step
+  while (__any_sync(0xffffffffu, !done && nbuf > 0)) {
+    if (!done && nbuf > 0) {
+      const int bi = kb_select(kb_tau, kb_p, nt, nbuf, 0.f, false);
+      blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
+      --nbuf;
+      kb_tau[bi * nt] = kb_tau[nbuf * nt]; kb_a[bi * nt] = kb_a[nbuf * nt];
+      kb_r[bi * nt] = kb_r[nbuf * nt]; kb_g[bi * nt] = kb_g[nbuf * nt]; kb_b[bi * nt] = kb_b[nbuf * nt];
+      kb_p[bi * nt] = kb_p[nbuf * nt];
+    }
+    emit();
   }
 }
 
@@ -173,8 +280,8 @@ ut_status launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, 
                    const uint32_t *ranges, cudaStream_t s) {
   const int threads = op.tile_w * op.tile_h;
   const size_t smem = sizeof(float) * 6 * (size_t)op.kbuffer * threads;
-  constexpr size_t kStatic = sizeof(float4) * kBatchK * 4 + sizeof(float) * kBatchK * 3 * (DEG + 1) * (DEG + 1) +
-                             sizeof(uint32_t) * kBatchK;
+  constexpr size_t kStatic = sizeof(float4) * kBatchKB * 5 + sizeof(float) * kBatchKB * 3 * (DEG + 1) * (DEG + 1) +
+                             sizeof(uint32_t) * kBatchKB;
   if (smem + kStatic > 227 * 1024) return UT_ERR_UNSUPPORTED;  // the buffer does not fit one block
   if (cudaFuncSetAttribute(k_composite_bwd_kbuffer<DEG, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess ||
