@@ -291,8 +291,8 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
                             size_t workspace_bytes, unsigned long long *stats, ut_stream stream);
 
 /* Bytes of scratch memory composite_backward needs for n particles rendered with this camera
- * and these options (per-particle accumulators and a per-tile schedule); 0 for invalid
- * arguments. */
+ * and these options (per-particle accumulators, with opt->kbuffer > 0 a per-particle record
+ * table of the same size, and a per-tile schedule); 0 for invalid arguments. */
 size_t ut_backward_workspace_size(int32_t n, const ut_camera *cam, const ut_options *opt);
 
 /* Gradient of a scalar loss L through composite_forward (supplementary Sec. B):
@@ -353,7 +353,8 @@ typedef struct {
 } ut_scene_grads;
 
 /* Bytes of scratch render_batch_backward needs for these scenes and views (per-particle
- * accumulators of every scene and a per-tile schedule over all views); 0 for invalid arguments. */
+ * accumulators of every scene, with opt->kbuffer > 0 a per-particle record table of the same
+ * size, and a per-tile schedule over all views); 0 for invalid arguments. */
 size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes, const ut_view *views,
                                         int32_t n_views, const ut_options *opt);
 

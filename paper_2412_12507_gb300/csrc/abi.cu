@@ -544,7 +544,7 @@ ut_status composite_forward(const ut_scene *scene, const ut_camera *cam, const u
 size_t ut_backward_workspace_size(int32_t n, const ut_camera *cam, const ut_options *opt) {
   if (n < 0 || !cam || !opt || opt->tile_w < 1 || opt->tile_h < 1 || cam->width < 1 || cam->height < 1) return 0;
   int tiles = ((cam->width + opt->tile_w - 1) / opt->tile_w) * ((cam->height + opt->tile_h - 1) / opt->tile_h);
-  return backward_workspace_bytes(n) + tile_sched_bytes(tiles);
+  return backward_workspace_bytes(n, opt->kbuffer > 0) + tile_sched_bytes(tiles);
 }
 
 ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const ut_options *opt,
@@ -564,7 +564,7 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
   if (scene->n > 0 && (!rect || !aligned8(rect) || !d_means || !d_log_scales || !d_quats || !d_opacity_logits ||
                        !d_sh))
     return UT_ERR_INVALID_ARG;
-  const size_t acc_bytes = backward_workspace_bytes(scene->n);
+  const size_t acc_bytes = backward_workspace_bytes(scene->n, dop.kbuffer > 0);
   if (!workspace || workspace_bytes < acc_bytes + tile_sched_bytes(dop.tiles_x * dop.tiles_y) ||
       (reinterpret_cast<uintptr_t>(workspace) & 255))
     return UT_ERR_INVALID_ARG;
@@ -578,6 +578,7 @@ ut_status composite_backward(const ut_scene *scene, const ut_camera *cam, const 
   v.d_alpha = d_alpha;
   DevScene &s = bd.s[0];
   s.gacc = static_cast<float *>(workspace);
+  s.kbrec = dop.kbuffer > 0 ? reinterpret_cast<float4 *>(static_cast<char *>(workspace) + acc_bytes / 2) : nullptr;
   s.d_means = d_means;
   s.d_log_scales = d_log_scales;
   s.d_quats = d_quats;
@@ -631,7 +632,7 @@ size_t ut_batch_backward_workspace_size(const ut_scene *scenes, int32_t n_scenes
   DevOpts dop;
   if (make_batch(scenes, n_scenes, views, n_views, opt, bd, dop) != UT_OK) return 0;
   size_t total = 0;
-  for (int k = 0; k < n_scenes; ++k) total += backward_workspace_bytes(scenes[k].n);
+  for (int k = 0; k < n_scenes; ++k) total += backward_workspace_bytes(scenes[k].n, dop.kbuffer > 0);
   return total + tile_sched_bytes(bd.total_tiles);
 }
 
@@ -660,7 +661,9 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
       return UT_ERR_INVALID_ARG;
     DevScene &s = bd.s[k];
     s.gacc = reinterpret_cast<float *>(gw);
-    gw += backward_workspace_bytes(scenes[k].n);
+    const size_t acc_bytes = backward_workspace_bytes(scenes[k].n, dop.kbuffer > 0);
+    s.kbrec = dop.kbuffer > 0 ? reinterpret_cast<float4 *>(gw + acc_bytes / 2) : nullptr;
+    gw += acc_bytes;
     s.d_means = g.d_means;
     s.d_log_scales = g.d_log_scales;
     s.d_quats = g.d_quats;

@@ -464,7 +464,10 @@ void bwd_launch(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, con
 
 }  // namespace
 
-size_t backward_workspace_bytes(int n) { return align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1)); }
+size_t backward_workspace_bytes(int n, bool kbuffer) {
+  const size_t part = align256(sizeof(float) * 16 * (size_t)(n > 0 ? n : 1));
+  return kbuffer ? 2 * part : part;
+}
 
 size_t tile_sched_bytes(int tiles) {
   const size_t t = (size_t)(tiles > 0 ? tiles : 1);

@@ -9,13 +9,15 @@
 // forward order, as the tile-order backward does: the stored final colour gives the colour still
 // to come, S = C_final - A after the pair's own contribution, so
 // dL/dalpha = sum_c g_c (c_c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha).  The pair's
-// canonical ray (o_g, d_g) is recomputed from the particle's parameters in global memory, and
-// its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
+// canonical ray (o_g, d_g) is recomputed from the particle's staged record while its batch is in
+// shared memory (about 70% of the blends at k = 16), else from its parameters in global memory,
+// and its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
 // unclamped channels) go to the particle's accumulators.  The lanes of a warp blend in step (one
-// blend event per lane per staged particle, and per step of the final drain); when every event of
-// a step concerns the same particle -- the common case, neighbouring pixels' buffers evolve
-// alike -- the warp sums the events' contributions with reduce-scatters and adds each value with
-// one atomic, otherwise every lane adds its own, one global atomic per value (a window of
+// blend event per lane per staged particle, and per step of the final drain), and the events of a
+// step are grouped by particle: neighbouring pixels' buffers evolve alike, so a step's 20 or so
+// events name three or four particles.  A group of four or more lanes sums its contributions with
+// reduce-scatters over the warp and adds each value with one atomic; the lanes of smaller groups
+// add their own, one global atomic per value (a window of
 // per-list-position accumulators in shared memory was measured 5x slower: the lanes of a warp
 // blend the same particle at nearly the same time, and shared-memory atomics on one address
 // serialise, while the L2's reductions absorb them).
@@ -41,6 +43,22 @@ __device__ __forceinline__ void kb_reduce_scatter16(float (&v)[16], int lane) {
     }
   }
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// The record table of the scene's particles: M (row-major, 9), M mu, mu and sigma, 16 floats.
+__global__ void k_kb_records(const DevScene sc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sc.n; i += gridDim.x * blockDim.x) {
+    const float3 mu = make_float3(sc.means[3 * i], sc.means[3 * i + 1], sc.means[3 * i + 2]);
+    const float3 ls = make_float3(sc.log_scales[3 * i], sc.log_scales[3 * i + 1], sc.log_scales[3 * i + 2]);
+    Particle p;
+    activate(mu, ls, sc.quats[i], sc.logits[i], p);
+    const float3 a = mat3_mul(p.M, mu);
+    float4 *rec = sc.kbrec + 4 * (size_t)i;
+    rec[0] = make_float4(p.M[0], p.M[1], p.M[2], p.M[3]);
+    rec[1] = make_float4(p.M[4], p.M[5], p.M[6], p.M[7]);
+    rec[2] = make_float4(p.M[8], a.x, a.y, a.z);
+    rec[3] = make_float4(mu.x, mu.y, mu.z, p.sigma);
+  }
 }
 
 template <int DEG, bool RS>
@@ -109,7 +127,7 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
                       g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
     T = Tn;
     // a particle of the staged batch is read from shared memory (its staged record and o - mu or
-    // mu), an older one from its parameters in global memory
+    // mu), an older one from the call's record table (M, M mu, mu, sigma)
     const bool staged = pos >= sb && pos < sb + (uint32_t)snb;
     const uint32_t idx = staged ? s_idx[pos - sb] : vals[pos];
     UT_DBG_CHECK(idx < (uint32_t)sc.n, UT_DBG_PARTICLE, idx, sc.n, 1);
@@ -119,35 +137,30 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
     ev_gc[1] = c1 > 0.f ? g1 * w : 0.f;
     ev_gc[2] = c2 > 0.f ? g2 * w : 0.f;
     // geometry: the pair's canonical ray
-    float3 og, dg, om;
-    float sigma;
+    float4 q0, q1, q2, q3;  // M row-major in q0, q1, q2.x; then M mu (or M (o - mu)), mu (or o - mu), sigma
     if (staged) {
       const float4 *g = s_geo[pos - sb];
-      const float4 g0r = g[0], g1r = g[1], g2r = g[2], ax = s_aux[pos - sb];
-      dg = make_float3(fmaf(g0r.x, d.x, fmaf(g0r.y, d.y, g0r.z * d.z)),
-                       fmaf(g0r.w, d.x, fmaf(g1r.x, d.y, g1r.y * d.z)),
-                       fmaf(g1r.z, d.x, fmaf(g1r.w, d.y, g2r.x * d.z)));
-      if (RS) {
-        og = make_float3(fmaf(g0r.x, o.x, fmaf(g0r.y, o.y, g0r.z * o.z)) - g2r.y,
-                         fmaf(g0r.w, o.x, fmaf(g1r.x, o.y, g1r.y * o.z)) - g2r.z,
-                         fmaf(g1r.z, o.x, fmaf(g1r.w, o.y, g2r.x * o.z)) - g2r.w);
-        om = make_float3(o.x - ax.x, o.y - ax.y, o.z - ax.z);
-      } else {
-        og = make_float3(g2r.y, g2r.z, g2r.w);
-        om = make_float3(ax.x, ax.y, ax.z);
-      }
-      sigma = g[3].x;
+      q0 = g[0]; q1 = g[1]; q2 = g[2];
+      q3 = s_aux[pos - sb];
+      q3.w = g[3].x;
     } else {
-      const float3 mu = make_float3(sc.means[3 * idx], sc.means[3 * idx + 1], sc.means[3 * idx + 2]);
-      const float3 ls =
-          make_float3(sc.log_scales[3 * idx], sc.log_scales[3 * idx + 1], sc.log_scales[3 * idx + 2]);
-      Particle p;
-      activate(mu, ls, sc.quats[idx], sc.logits[idx], p);
-      om = make_float3(o.x - mu.x, o.y - mu.y, o.z - mu.z);
-      og = mat3_mul(p.M, om);
-      dg = mat3_mul(p.M, d);
-      sigma = p.sigma;
+      const float4 *rec = sc.kbrec + 4 * (size_t)idx;
+      q0 = __ldg(rec); q1 = __ldg(rec + 1); q2 = __ldg(rec + 2); q3 = __ldg(rec + 3);
     }
+    const float3 dg = make_float3(fmaf(q0.x, d.x, fmaf(q0.y, d.y, q0.z * d.z)),
+                                  fmaf(q0.w, d.x, fmaf(q1.x, d.y, q1.y * d.z)),
+                                  fmaf(q1.z, d.x, fmaf(q1.w, d.y, q2.x * d.z)));
+    float3 og, om;
+    if (RS || !staged) {  // the record holds M mu and mu
+      og = make_float3(fmaf(q0.x, o.x, fmaf(q0.y, o.y, q0.z * o.z)) - q2.y,
+                       fmaf(q0.w, o.x, fmaf(q1.x, o.y, q1.y * o.z)) - q2.z,
+                       fmaf(q1.z, o.x, fmaf(q1.w, o.y, q2.x * o.z)) - q2.w);
+      om = make_float3(o.x - q3.x, o.y - q3.y, o.z - q3.z);
+    } else {  // the staged record of a global-shutter view holds M (o - mu) and o - mu
+      og = make_float3(q2.y, q2.z, q2.w);
+      om = make_float3(q3.x, q3.y, q3.z);
+    }
+    const float sigma = q3.w;
     const float3 cr = cross3(og, dg);
     const float cc = dot3(cr, cr), dd = dot3(dg, dg);
     const float a = sigma * __expf(-0.5f * __fdividef(cc, dd));
@@ -171,31 +184,37 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
   auto emit = [&]() {
     const unsigned act = __ballot_sync(0xffffffffu, has_ev);
     if (!act) return;
-    const uint32_t p0 = __shfl_sync(0xffffffffu, ev_idx, __ffs(act) - 1);
-    if (__all_sync(0xffffffffu, !has_ev || ev_idx == p0)) {
-      // one particle: the warp's sums, one atomic per value
+    const unsigned grp = __match_any_sync(0xffffffffu, has_ev ? ev_idx : 0xffffffffu);
+    unsigned big = __ballot_sync(0xffffffffu, has_ev && (int)(__ffs(grp) - 1) == lane && __popc(grp) >= 4);
+    const int vi = lane >> 1;
+    while (big) {
+      const int l = __ffs(big) - 1;
+      big &= big - 1;
+      const unsigned gm = __shfl_sync(0xffffffffu, grp, l);
+      const uint32_t p0 = __shfl_sync(0xffffffffu, ev_idx, l);
+      const bool in = (gm >> lane) & 1u;
       float v[16];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        v[r] = has_ev ? ev_v[r] : 0.f;
+        v[r] = in ? ev_v[r] : 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = has_ev ? ev_v[r] * ev_x[c] : 0.f;
+        for (int c = 0; c < 3; ++c) v[3 + 3 * r + c] = in ? ev_v[r] * ev_x[c] : 0.f;
       }
-      v[12] = has_ev ? ev_dsig : 0.f;
+      v[12] = in ? ev_dsig : 0.f;
       v[13] = v[14] = v[15] = 0.f;
       kb_reduce_scatter16(v, lane);
-      const int vi = lane >> 1;
       if (!(lane & 1) && vi < 13) atomicAdd(&sc.gacc[(size_t)p0 * 16 + vi], v[0]);
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        if (!__any_sync(0xffffffffu, has_ev && ev_gc[ch] != 0.f)) continue;
+        if (!__any_sync(0xffffffffu, in && ev_gc[ch] != 0.f)) continue;
         float u[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) u[k] = (has_ev && k < NSH) ? ev_gc[ch] * Y[k < NSH ? k : 0] : 0.f;
+        for (int k = 0; k < 16; ++k) u[k] = (in && k < NSH) ? ev_gc[ch] * Y[k < NSH ? k : 0] : 0.f;
         kb_reduce_scatter16(u, lane);
         if (!(lane & 1) && vi < NSH && u[0] != 0.f) atomicAdd(&sc.d_sh[(size_t)p0 * NC + 3 * vi + ch], u[0]);
       }
-    } else if (has_ev) {
+    }
+    if (has_ev && __popc(grp) < 4) {
       float *dsh = sc.d_sh + (size_t)ev_idx * NC;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
@@ -234,6 +253,9 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
     for (int b = 0; b < nb; ++b) {
       float3 og, dg;
       float dd, a;
+      bool leave = false;
+      float l_a = 0.f, l_r = 0.f, l_g = 0.f, l_b = 0.f;
+      uint32_t l_p = 0;
       if (!done && eval_response<RS, false>(s_geo[b], px, py, o, d, og, dg, dd, a, op)) {
         const float tau = -__fdividef(dot3(og, dg), dd);
         const float al = fminf(a, op.alpha_max);
@@ -246,17 +268,20 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
           kb_r[nbuf * nt] = r0; kb_g[nbuf * nt] = r1; kb_b[nbuf * nt] = r2; kb_p[nbuf * nt] = pos;
           ++nbuf;
         } else {
-          // closest of the buffer and the new hit (the forward kernel's choice)
+          // closest of the buffer and the new hit (the forward kernel's choice) leaves
           const int bi = kb_select(kb_tau, kb_p, nt, K, tau, true);
+          leave = true;
           if (bi < 0) {
-            blend(al, r0, r1, r2, pos);
+            l_a = al; l_r = r0; l_g = r1; l_b = r2; l_p = pos;
           } else {
-            blend(kb_a[bi * nt], kb_r[bi * nt], kb_g[bi * nt], kb_b[bi * nt], kb_p[bi * nt]);
+            l_a = kb_a[bi * nt]; l_r = kb_r[bi * nt]; l_g = kb_g[bi * nt]; l_b = kb_b[bi * nt]; l_p = kb_p[bi * nt];
             kb_tau[bi * nt] = tau; kb_a[bi * nt] = al;
             kb_r[bi * nt] = r0; kb_g[bi * nt] = r1; kb_b[bi * nt] = r2; kb_p[bi * nt] = pos;
           }
         }
       }
+      // one blend site for the warp, whichever way its lanes' hits went
+      if (leave) blend(l_a, l_r, l_g, l_b, l_p);
       emit();
       if (__all_sync(0xffffffffu, done)) break;
     }
@@ -300,6 +325,14 @@ ut_status launch_k(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, 
 ut_status launch_composite_bwd_kbuffer(const BatchDesc &bd, const DevOpts &op, const int16_t *rect,
                                        const uint32_t *vals, const uint32_t *ranges, cudaStream_t s) {
   if (bd.total_tiles == 0) return UT_OK;
+  for (int k = 0; k < bd.ns; ++k) {
+    const DevScene &sc = bd.s[k];
+    if (sc.n <= 0) continue;
+    if (!sc.kbrec) return UT_ERR_INVALID_ARG;
+    const int g = (sc.n + 255) / 256, cap = device_sm_count() * 8;
+    k_kb_records<<<g < cap ? g : cap, 256, 0, s>>>(sc);
+    count_launches(1);
+  }
   const bool rs = any_rs(bd);
   switch (bd.s[0].deg) {
     case 0: return rs ? launch_k<0, true>(bd, op, rect, vals, ranges, s) : launch_k<0, false>(bd, op, rect, vals, ranges, s);

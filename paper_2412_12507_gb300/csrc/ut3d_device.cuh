@@ -68,6 +68,7 @@ struct DevScene {
   const float *logits, *sh;
   int n, deg;
   float *gacc;                  // backward accumulators [n][16]
+  float4 *kbrec;                // k-buffer backward: per-particle record [n][4] (M, M mu, mu, sigma), else null
   float *d_means, *d_log_scales, *d_quats, *d_logits, *d_sh;
   int grad_off;                 // flattened offset of this scene in finalize's range
   int sh_vec;                   // sh is 16-byte aligned and (deg+1)^2 * 3 is a multiple of 4

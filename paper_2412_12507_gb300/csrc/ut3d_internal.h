@@ -64,7 +64,7 @@ ut_status launch_composite_fwd(const BatchDesc &bd, const DevOpts &op, const int
                                const uint32_t *ranges, unsigned long long *stats, void *sched, cudaStream_t stream);
 
 // Backward of the batch into the scenes' gradient outputs (accumulators cleared here).
-size_t backward_workspace_bytes(int n);
+size_t backward_workspace_bytes(int n, bool kbuffer);  // accumulators, and the k-buffer record table
 // Scratch of a tile schedule (forward or backward) for `tiles` tiles.
 size_t tile_sched_bytes(int tiles);
 ut_status launch_composite_bwd(const BatchDesc &bd, const DevOpts &op, const int16_t *rect, const uint32_t *vals,
