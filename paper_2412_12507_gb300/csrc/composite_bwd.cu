@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
         A0 = fmaf(c0, w, A0);
         A1 = fmaf(c1, w, A1);
         A2 = fmaf(c2, w, A2);
-        float inv = 1.f / (1.f - al);
+        const float inv = __fdividef(1.f, 1.f - al);  // 1 - al >= 1 - alpha_max > 0
         // dL/dalpha = sum_c g_c (c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha)
         float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
                     g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
         T = T * (1.f - al);
         float da = a > op.alpha_max ? 0.f : dal;
         float sigma = s_geo[b][3].x;
-        dsig = da * a / sigma;
+        dsig = da * __fdividef(a, sigma);
         float dw2 = dresponse<GEN>(op, a, og, dg, dd) * da;
-        float tau = -dot3(og, dg) / dd;
+        float tau = -__fdividef(dot3(og, dg), dd);
         float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
         vv[0] = 2.f * dw2 * pp.x;
         vv[1] = 2.f * dw2 * pp.y;

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
     A0 = fmaf(c0, w, A0);
     A1 = fmaf(c1, w, A1);
     A2 = fmaf(c2, w, A2);
-    const float inv = 1.f / (1.f - al);
+    const float inv = __fdividef(1.f, 1.f - al);  // 1 - al >= 1 - alpha_max > 0
     const float dal = g0 * fmaf(-(Cf0 - A0), inv, c0 * T) + g1 * fmaf(-(Cf1 - A1), inv, c1 * T) +
                       g2 * fmaf(-(Cf2 - A2), inv, c2 * T) + gAT * inv;
     T = Tn;
@@ -165,9 +165,9 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
     const float cc = dot3(cr, cr), dd = dot3(dg, dg);
     const float a = sigma * __expf(-0.5f * __fdividef(cc, dd));
     const float da = a > op.alpha_max ? 0.f : dal;
-    ev_dsig = da * a / sigma;
+    ev_dsig = da * __fdividef(a, sigma);
     const float dw2 = -0.5f * a * da;
-    const float tau = -dot3(og, dg) / dd;
+    const float tau = -__fdividef(dot3(og, dg), dd);
     const float3 pp = make_float3(fmaf(tau, dg.x, og.x), fmaf(tau, dg.y, og.y), fmaf(tau, dg.z, og.z));
     ev_v[0] = 2.f * dw2 * pp.x;
     ev_v[1] = 2.f * dw2 * pp.y;
