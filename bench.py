@@ -151,6 +151,15 @@ def measure_alu_peaks(L, dev, stream, sms):
                    "median of 5 launches"}
 
 
+def queue_ahead(stream, us=300):
+    """Holds `stream` with a device-side spin of a fixed cycle count (about `us` microseconds at
+    2 GHz), so that the calls enqueued after it are queued before the GPU reaches them: a pair of
+    events around one call then times its kernels, not the host's marshalling and launch."""
+    import torch
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(us * 2000))
+
+
 def projection_work(cam, rs_iters=3):
     """FP32 operations and transcendental calls (sqrt, atan2, sin / cos, exp, log, division:
     one each) of the UT projection of one particle, counted from the arithmetic the method
@@ -448,6 +457,7 @@ def run_multiview(dev, steps, warmup, timed):
         calls = {"ut_project": [], "bin_and_sort": [], "composite_forward": [], "composite_backward": []}
         for _ in range(3):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            queue_ahead(stream)
             ev[0].record(stream)
             render.project(scene, cam, best, r.proj)
             ev[1].record(stream)
@@ -498,6 +508,7 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
         ts = []
         for _ in range(n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(stream)
             e0.record(stream)
             fn()
             e1.record(stream)
@@ -638,6 +649,7 @@ def run_forward_workload(name, dev, steps, warmup, timed, alu, hbm):
     for _ in range(max(5, steps)):
         flush.fill_(1)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        queue_ahead(stream)
         ev[0].record(stream)
         render.project(scene, cam, op, r.proj)
         ev[1].record(stream)
@@ -763,6 +775,7 @@ def run_ours(args):
     calls = {"ut_project": [], "bin_and_sort": [], "composite_forward": [], "composite_backward": []}
     for _ in range(max(3, args.steps // 2)):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        queue_ahead(stream)
         ev[0].record(stream)
         render.project(scene, cam, op, r.proj)
         ev[1].record(stream)
