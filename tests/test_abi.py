@@ -51,6 +51,9 @@ def test_workspace_sizes(L):
     w = L.ut_backward_workspace_size(1000, C.byref(cam), C.byref(o))
     tiles = 120 * 68  # 1920x1080 in 16x16 tiles
     assert w >= 1000 * 16 * 4 + 2 * 4 * tiles and w % 256 == 0
+    ok = abi.default_options()
+    ok.kbuffer = 16  # the k-buffer backward adds a 64-byte record per particle
+    assert L.ut_backward_workspace_size(1000, C.byref(cam), C.byref(ok)) >= w + 1000 * 16 * 4
     assert L.ut_backward_workspace_size(-1, C.byref(cam), C.byref(o)) == 0
     assert L.ut_backward_workspace_size(1000, None, C.byref(o)) == 0
     f = L.ut_forward_workspace_size(C.byref(cam), C.byref(o))

@@ -155,11 +155,13 @@ def test_batch_validation():
         render.BatchRenderer(mixed, op).forward([(0, synth.camera("pinhole", 32, 32, fx=30.0))])
 
 
-def test_batch_backward_sums_views_of_a_scene():
+@pytest.mark.parametrize("k", [0, 8])
+def test_batch_backward_sums_views_of_a_scene(k):
     """Three views of one scene plus one of another: each scene's gradient equals the sum of
-    its views' single-view gradients and the FP64 oracle's."""
+    its views' single-view gradients and the FP64 oracle's, in tile order and through the
+    per-ray k-buffer (k = 8: one record table per scene in the batch's gradient workspace)."""
     scenes_np = _scenes()
-    op = synth.options()
+    op = synth.options(kbuffer=k)
     views = [_cams()[k] for k in (0, 2, 4, 1)]  # scene 1 three times, scene 0 once
     br = render.BatchRenderer([render.Scene.from_arrays(s) for s in scenes_np], op, capacity=1 << 12)
     frames = br.forward(views, grad=True)
@@ -168,7 +170,7 @@ def test_batch_backward_sums_views_of_a_scene():
     for (si, cam), f in zip(views, frames):
         H, W = cam["height"], cam["width"]
         pr = oracle.project(scenes_np[si], cam, op, TOL)
-        rf = oracle.render(scenes_np[si], cam, op, proj=pr, tol=TOL)
+        rf = oracle.render(scenes_np[si], cam, dict(op, eps_tau=1e-4) if k else op, proj=pr, tol=TOL)
         keep = (rf["flags"] & oracle.F_BACKWARD_TIES) == 0
         w_rgb = rng.standard_normal((H * W, 3)) * keep[:, None]
         w_a = rng.standard_normal(H * W) * keep
