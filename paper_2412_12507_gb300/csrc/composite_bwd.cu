@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(SMALL ? 256 : 512, SMALL ? 3 : 1)
   const DevCam &cam = view.cam;
   const int lt = tile - view.tile_off;
   const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
-  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
-  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  int lx, ly;
+  tile_pixel(op, (int)threadIdx.x, lx, ly);
+  const int px = tx * op.tile_w + lx;
+  const int py = ty * op.tile_h + ly;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g8 = lane >> 2, t4 = lane & 3;
   float *s_W = reinterpret_cast<float *>(smem + L::wmat()) + (size_t)warp * L::kWarpFloats;

@@ -273,6 +273,21 @@ __device__ __forceinline__ float3 sh_poly_grad(float x, float y, float z, const 
   return make_float3(gx, gy, gz);
 }
 
+// Pixel (lx, ly) of thread t within its tile: each warp takes an 8 x 4 block of the tile when
+// the tile is made of such blocks (a compact footprint meets fewer distinct particles than a
+// 16 x 2 or 32 x 1 strip, so more of the warp's lanes work on each staged particle), else the
+// tile is row-major.  Results do not depend on the mapping: every pixel's walk is its own.
+__device__ __forceinline__ void tile_pixel(const DevOpts &op, int t, int &lx, int &ly) {
+  if (op.tile_w % 8 == 0 && op.tile_h % 4 == 0) {
+    const int lane = t & 31, warp = t >> 5, bx = op.tile_w / 8;
+    lx = (warp % bx) * 8 + (lane & 7);
+    ly = (warp / bx) * 4 + (lane >> 3);
+  } else {
+    lx = t % op.tile_w;
+    ly = t / op.tile_w;
+  }
+}
+
 template <int DEG>
 __device__ __forceinline__ void pixel_setup(const DevCam &cam, const DevOpts &op, int px, int py, bool inside,
                                             float3 &o, float3 &d, float *Y, bool &valid) {

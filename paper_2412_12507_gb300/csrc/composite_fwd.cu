@@ -33,8 +33,10 @@ __global__ void __launch_bounds__(512) k_composite_fwd(const __grid_constant__ B
   const DevCam &cam = view.cam;
   const int lt = tile - view.tile_off;
   const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
-  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
-  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  int lx, ly;
+  tile_pixel(op, (int)threadIdx.x, lx, ly);
+  const int px = tx * op.tile_w + lx;
+  const int py = ty * op.tile_h + ly;
   const bool inside = px < cam.W && py < cam.H;
   float3 o, d;
   float Y[(PDEG + 1) * (PDEG + 1)];
@@ -140,8 +142,10 @@ __global__ void __launch_bounds__(512, 1) k_composite_fwd_kbuffer(const __grid_c
   const DevCam &cam = view.cam;
   const int lt = tile - view.tile_off;
   const int tx = lt % view.tiles_x, ty = lt / view.tiles_x;
-  const int px = tx * op.tile_w + (int)threadIdx.x % op.tile_w;
-  const int py = ty * op.tile_h + (int)threadIdx.x / op.tile_w;
+  int lx, ly;
+  tile_pixel(op, (int)threadIdx.x, lx, ly);
+  const int px = tx * op.tile_w + lx;
+  const int py = ty * op.tile_h + ly;
   const bool inside = px < cam.W && py < cam.H;
   const int K = op.kbuffer, nt = blockDim.x;
   float *kb_tau = s_kb + threadIdx.x, *kb_a = kb_tau + K * nt, *kb_r = kb_a + K * nt, *kb_g = kb_r + K * nt,
