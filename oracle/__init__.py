@@ -82,6 +82,7 @@ def lib():
         L.orc_pixel_ray.restype = C.c_int
         L.orc_pixel_ray.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, C.c_double, P, P, P, P]
         L.orc_sh_basis.argtypes = [C.c_int, P, P]
+        L.orc_sh_basis_grad.argtypes = [C.c_int, P, P, P]
         L.orc_ut_estimate.restype = C.c_int
         L.orc_ut_estimate.argtypes = [C.POINTER(Camera), C.c_double, C.c_int, C.c_double, C.c_double,
                                       C.c_double, P, P, P, P, P, P, P]
@@ -199,6 +200,16 @@ def sh_basis(deg: int, d) -> np.ndarray:
     Y = np.zeros((deg + 1) ** 2)
     lib().orc_sh_basis(deg, _p(d), _p(Y))
     return Y
+
+
+def sh_basis_grad(deg: int, d):
+    """(Y, G): the basis at d and the gradient of its polynomials, G[j][k] = dY_k / d(d_j)."""
+    d = _f64(d)
+    Y = np.zeros(16)
+    G = np.zeros(48)
+    lib().orc_sh_basis_grad(deg, _p(d), _p(Y), _p(G))
+    n = (deg + 1) ** 2
+    return Y[:n], G.reshape(3, 16)[:, :n]
 
 
 def project_point(cam: dict, x, rs_iters: int = 3):

@@ -438,6 +438,53 @@ void orc_sh_basis(int deg, const double dir[3], double *Y) {
   }
 }
 
+/* Gradient of the basis polynomials of orc_sh_basis with respect to (x, y, z), carried through
+ * the same recurrences (forward-mode): d/dx (x + i y)^m = m (x + i y)^(m-1) and
+ * d/dy (x + i y)^m = i m (x + i y)^(m-1) via the product rule on cm, sm; the Legendre part
+ * depends on z alone.  G[16 j + k] = dY_k / d(dir_j) for j = x, y, z (the polynomial's
+ * gradient; the derivative along the unit sphere is its tangential part). */
+void orc_sh_basis_grad(int deg, const double dir[3], double *Y, double *G) {
+  double x = dir[0], y = dir[1], z = dir[2];
+  double cm = 1.0, sm = 0.0, cmx = 0.0, cmy = 0.0, smx = 0.0, smy = 0.0;
+  double pmm = 1.0;
+  for (int k = 0; k < 48; ++k) G[k] = 0.0;
+  for (int m = 0; m <= deg; ++m) {
+    if (m > 0) {
+      double ncm = cm * x - sm * y, nsm = cm * y + sm * x;
+      double ncmx = cmx * x + cm - smx * y, ncmy = cmy * x - smy * y - sm;
+      double nsmx = cmx * y + smx * x + sm, nsmy = cmy * y + cm + smy * x;
+      cm = ncm; sm = nsm; cmx = ncmx; cmy = ncmy; smx = nsmx; smy = nsmy;
+      pmm *= -(2.0 * m - 1.0);
+    }
+    double p_lm2 = 0.0, p_lm1 = 0.0, d_lm2 = 0.0, d_lm1 = 0.0;
+    for (int l = m; l <= deg; ++l) {
+      double p, dp;
+      if (l == m) { p = pmm; dp = 0.0; }
+      else if (l == m + 1) { p = z * (2.0 * m + 1.0) * pmm; dp = (2.0 * m + 1.0) * pmm; }
+      else {
+        p = ((2.0 * l - 1.0) * z * p_lm1 - (l + m - 1.0) * p_lm2) / (double)(l - m);
+        dp = ((2.0 * l - 1.0) * (p_lm1 + z * d_lm1) - (l + m - 1.0) * d_lm2) / (double)(l - m);
+      }
+      p_lm2 = p_lm1; p_lm1 = p; d_lm2 = d_lm1; d_lm1 = dp;
+      double ratio = 1.0;
+      for (int f = l - m + 1; f <= l + m; ++f) ratio /= (double)f;
+      double K = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * ratio);
+      if (m == 0) {
+        int k = l * l + l;
+        Y[k] = K * p;
+        G[32 + k] = K * dp;
+      } else {
+        double s2 = sqrt(2.0) * K;
+        int kc = l * l + l + m, ks = l * l + l - m;
+        Y[kc] = s2 * cm * p;
+        Y[ks] = s2 * sm * p;
+        G[kc] = s2 * cmx * p; G[16 + kc] = s2 * cmy * p; G[32 + kc] = s2 * cm * dp;
+        G[ks] = s2 * smx * p; G[16 + ks] = s2 * smy * p; G[32 + ks] = s2 * sm * dp;
+      }
+    }
+  }
+}
+
 /* ------------------------------------------------------------------ particles */
 
 typedef struct {
@@ -774,7 +821,7 @@ static void orc_particle_dir(const orc_camera *c, double theta_max, int rs_iters
 }
 
 /* colour_mode 1: the SH basis at every particle's direction, and its derivative with respect
- * to the mean by FP64 central differences (the shutter time, like the whole projection, is a
+ * to the mean, analytic (orc_sh_basis_grad; the shutter time, like the whole projection, is a
  * discrete selection and carries no gradient: it is held fixed). */
 static void orc_ctx_colour(orc_ctx *x, const orc_camera *c, double theta_max, const orc_options *op) {
   size_t n = (size_t)(x->n > 0 ? x->n : 1);
@@ -791,16 +838,13 @@ static void orc_ctx_colour(orc_ctx *x, const orc_camera *c, double theta_max, co
     orc_pose_at(c, t, R, T);
     for (int j = 0; j < 3; ++j) C[j] = -(R[j] * T[0] + R[3 + j] * T[1] + R[6 + j] * T[2]);
     double v[3] = {p->mu[0] - C[0], p->mu[1] - C[1], p->mu[2] - C[2]};
-    double h = 1e-5 * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    for (int j = 0; j < 3; ++j) {
-      double vp[3] = {v[0], v[1], v[2]}, vm[3] = {v[0], v[1], v[2]}, Yp[16], Ym[16];
-      vp[j] += h; vm[j] -= h;
-      double np = sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
-      double nm = sqrt(vm[0] * vm[0] + vm[1] * vm[1] + vm[2] * vm[2]);
-      for (int r = 0; r < 3; ++r) { vp[r] /= np; vm[r] /= nm; }
-      orc_sh_basis(x->deg, vp, Yp);
-      orc_sh_basis(x->deg, vm, Ym);
-      for (int k = 0; k < x->nsh; ++k) x->dYdmu[48 * (size_t)i + 16 * j + k] = (Yp[k] - Ym[k]) / (2.0 * h);
+    /* dY/dmu = (I - dir dir^T) grad Y(dir) / |mu - C|, the camera centre C held at the mean's
+     * shutter time; the basis polynomials' gradient analytically */
+    double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), Yd[16], G[48];
+    orc_sh_basis_grad(x->deg, dir, Yd, G);
+    for (int k = 0; k < x->nsh; ++k) {
+      double gd = G[k] * dir[0] + G[16 + k] * dir[1] + G[32 + k] * dir[2];
+      for (int j = 0; j < 3; ++j) x->dYdmu[48 * (size_t)i + 16 * j + k] = (G[16 * j + k] - gd * dir[j]) / len;
     }
   }
 }

@@ -358,6 +358,50 @@ def test_sh_orthonormal(orc):
     assert np.allclose(G, np.eye(16), atol=1e-12)
 
 
+def test_sh_basis_gradient(orc):
+    """The analytic gradient of the basis polynomials (the per-particle colour's dY/dmu) against
+    central differences of the polynomials themselves, and its tangential part against central
+    differences of scipy's spherical harmonics of the normalised direction."""
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(12)
+
+    def real_sh(v):
+        d = v / np.linalg.norm(v)
+        theta, phi = math.acos(max(-1.0, min(1.0, d[2]))), math.atan2(d[1], d[0])
+        out = np.zeros(16)
+        for l in range(4):
+            for m in range(0, l + 1):
+                c = sp.sph_harm_y(l, m, theta, phi) if hasattr(sp, "sph_harm_y") else sp.sph_harm(m, l, phi, theta)
+                if m == 0:
+                    out[l * l + l] = c.real
+                else:
+                    out[l * l + l + m] = math.sqrt(2) * c.real
+                    out[l * l + l - m] = math.sqrt(2) * c.imag
+        return out
+
+    for deg in (1, 2, 3):
+        n = (deg + 1) ** 2
+        for _ in range(10):
+            v = rng.standard_normal(3) * rng.uniform(0.5, 3.0)
+            d = v / np.linalg.norm(v)
+            Y, G = orc.sh_basis_grad(deg, d)
+            assert np.allclose(Y, orc.sh_basis(deg, d), atol=1e-15)
+            h = 1e-6
+            for j in range(3):
+                e = np.zeros(3)
+                e[j] = h
+                fd = (orc.sh_basis(deg, d + e) - orc.sh_basis(deg, d - e)) / (2 * h)
+                assert np.allclose(G[j], fd, atol=1e-8), (deg, j)
+            # derivative of Y(v / |v|) with respect to v: (I - d d^T) grad / |v|
+            T = (G - np.outer(d, d @ G)) / np.linalg.norm(v)
+            hv = 1e-6 * np.linalg.norm(v)
+            for j in range(3):
+                e = np.zeros(3)
+                e[j] = hv
+                fd = (real_sh(v + e) - real_sh(v - e))[:n] / (2 * hv)
+                assert np.allclose(T[j], fd, atol=1e-7), (deg, j)
+
+
 def test_sh_matches_scipy(orc):
     """Real basis with the Condon-Shortley phase: Y_l0 = Re Y_l^0, Y_lm = sqrt2 Re Y_l^m and
     Y_l,-m = sqrt2 Im Y_l^m (m > 0), against scipy's complex spherical harmonics."""
