@@ -395,7 +395,10 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
     float3 ls = make_float3(sc.log_scales[3 * i], sc.log_scales[3 * i + 1], sc.log_scales[3 * i + 2]);
     Particle p;
     bool ok = activate(mu, ls, sc.quats[i], sc.logits[i], p);
-    const float *A = sc.gacc + (size_t)i * 16;
+    // the particle's 16 accumulators as four 16-byte loads (rows are 64-byte aligned)
+    const float4 *A4 = reinterpret_cast<const float4 *>(sc.gacc + (size_t)i * 16);
+    const float4 a0 = A4[0], a1 = A4[1], a2 = A4[2], a3 = A4[3];
+    const float A[16] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3.x, a3.y, a3.z, a3.w};
     float out_m[3] = {0.f, 0.f, 0.f}, out_s[3] = {0.f, 0.f, 0.f}, out_q[4] = {0.f, 0.f, 0.f, 0.f}, out_l = 0.f;
     if (ok) {
       float v0 = A[0], v1 = A[1], v2 = A[2];
@@ -405,17 +408,19 @@ __global__ void k_finalize(const __grid_constant__ BatchDesc bd, int total) {
       float G[9];
       for (int k = 0; k < 3; ++k) {
         float acc = 0.f;
+        const float is = 1.f / p.s[k];
         for (int j = 0; j < 3; ++j) {
           float dm = A[3 + 3 * k + j];
           acc = fmaf(dm, p.M[3 * k + j], acc);
-          G[3 * j + k] = dm / p.s[k];
+          G[3 * j + k] = dm * is;
         }
         out_s[k] = -acc;
       }
       float gq[4];
       rot_grad(p.q, G, gq);
       float dot = gq[0] * p.q[0] + gq[1] * p.q[1] + gq[2] * p.q[2] + gq[3] * p.q[3];
-      for (int j = 0; j < 4; ++j) out_q[j] = (gq[j] - p.q[j] * dot) / p.qn;
+      const float iqn = 1.f / p.qn;
+      for (int j = 0; j < 4; ++j) out_q[j] = (gq[j] - p.q[j] * dot) * iqn;
       out_l = A[12] * p.sigma * (1.f - p.sigma);
     }
     for (int j = 0; j < 3; ++j) {
