@@ -10,6 +10,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
+from gpu_helpers import TOL, compare_frame, sample_pixels  # noqa: E402
 from paper_2412_12507_gb300 import abi, render, synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -78,6 +80,34 @@ def test_requests_in_the_mix_equal_alone_and_plain(use_graphs):
             rgb_p, a_p = _plain(scenes[s], c, op)             # one plain render call
             assert torch.max(torch.abs(rgb_m - rgb_p)).item() <= RGB_TOL
             assert torch.max(torch.abs(a_m - a_p)).item() <= RGB_TOL
+    finally:
+        srv.close()
+
+
+def test_served_images_match_the_oracle_on_sampled_pixels():
+    """Every request of the mix, served batched and overlapped, against the FP64 oracle on
+    seeded pixel samples (the oracle's own projection; near-tie pixels against its bounds)."""
+    from types import SimpleNamespace
+    op = synth.options()
+    scenes_np = _scenes()
+    scenes = [render.Scene.from_arrays(s) for s in scenes_np]
+    reqs = _requests(seed=13, n=10)
+    srv = render.Server(scenes, op, arena_bytes=1 << 30, max_batch_views=4, max_in_flight=3)
+    try:
+        ids = [srv.submit(si, c) for si, c in reqs]
+        for j, (rid, (si, cam)) in enumerate(zip(ids, reqs)):
+            out = srv.wait(rid, 60_000)
+            assert out is not None
+            rgb, alpha, _ = out
+            f = SimpleNamespace(rgb=rgb.clone(), alpha=alpha.clone(), t_final=None)
+            srv.release(rid)
+            W, H = cam["width"], cam["height"]
+            px, py = sample_pixels(W, H, 400, 700 + j)
+            sc = scenes_np[si]
+            ref = oracle.render(sc, cam, op, proj=oracle.project(sc, cam, op, TOL), pixels=(px, py), tol=TOL)
+            r = compare_frame(f, ref)
+            assert r["n_bad"] == 0, (j, cam["model"], r)
+            assert r["n_flagged"] <= 0.1 * r["n"], (j, r)
     finally:
         srv.close()
 
