@@ -4,14 +4,14 @@
 // The blending order of a k-buffer ray is decided per pixel (the closest buffered hit by tau_max,
 // the earlier arrival on equal tau_max, leaves when a new hit meets a full buffer, the rest leave
 // in that order at the end), so a particle is often blended after its batch has left shared
-// memory.  The kernel replays the forward kernel's buffer logic exactly (same staging, same FP32
-// decisions), and at each blend it takes the gradient of that (pixel, particle) pair in the
+// memory.  The kernel replays the forward kernel's buffer logic exactly (the same FP32 decisions
+// and tie-aware search), and at each blend it takes the gradient of that (pixel, particle) pair in the
 // forward order, as the tile-order backward does: the stored final colour gives the colour still
 // to come, S = C_final - A after the pair's own contribution, so
 // dL/dalpha = sum_c g_c (c_c T - S_c / (1 - alpha)) + g_A T_final / (1 - alpha).  The pair's
 // canonical ray (o_g, d_g) is recomputed from the particle's staged record while its batch is in
-// shared memory (about 70% of the blends at k = 16), else from its parameters in global memory,
-// and its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
+// shared memory (about 70% of the blends at k = 16), else from the call's per-particle record
+// table (k_kb_records: M, M mu, mu, sigma), and its contributions (the 13 geometry partials of k_finalize's layout, and dL/dbeta for the
 // unclamped channels) go to the particle's accumulators.  The lanes of a warp blend in step (one
 // blend event per lane per staged particle, and per step of the final drain), and the events of a
 // step are grouped by particle: neighbouring pixels' buffers evolve alike, so a step's 20 or so
