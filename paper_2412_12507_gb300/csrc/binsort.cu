@@ -346,6 +346,12 @@ __device__ __forceinline__ void load_radix_tile(const uint32_t *__restrict__ key
 // broadcast), digit starts from the per-warp counts and a block scan, a scatter into shared
 // memory in digit order, and a write-out grouped by digit (coalesced runs).  The next tile's
 // keys, values and global digit offsets are loaded while the current tile is written out.
+// SELF (lists of at most kSelfRadixTiles tiles): `offsets` holds the upsweep's raw digit-major
+// counts and every block derives its own offsets from them (the digit totals' exclusive scan
+// plus the counts of its digit in the tiles before it), which saves the two scan launches.
+constexpr uint32_t kSelfRadixTiles = 128;
+
+template <bool SELF>
 __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__restrict__ keys_in,
                                                               const uint32_t *__restrict__ vals_in,
                                                               uint32_t *__restrict__ keys_out,
@@ -364,9 +370,27 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
   const int nd = (int)mask + 1;
   uint32_t b = blockIdx.x;
   if (b >= nb) return;
+  __shared__ uint32_t s_dbase[SELF ? 256 : 1];
+  if (SELF) {  // exclusive scan of the digit totals
+    uint32_t t = 0;
+    if (threadIdx.x < nd)
+      for (uint32_t bb = 0; bb < nb; ++bb) t += offsets[(size_t)threadIdx.x * nb + bb];
+    u64 ex;
+    block_excl_scan_u64(t, s_warp, ex);
+    if (threadIdx.x < nd) s_dbase[threadIdx.x] = (uint32_t)ex;
+    __syncthreads();
+  }
+  // global start of this thread's digit in tile bb
+  auto offset_of = [&](uint32_t bb) -> uint32_t {
+    if (threadIdx.x >= nd) return 0u;
+    if (!SELF) return offsets[(size_t)threadIdx.x * nb + bb];
+    uint32_t o = s_dbase[SELF ? threadIdx.x : 0];
+    for (uint32_t b2 = 0; b2 < bb; ++b2) o += offsets[(size_t)threadIdx.x * nb + b2];
+    return o;
+  };
   uint32_t k[kRIPT], v[kRIPT];
   load_radix_tile(keys_in, vals_in, n, b, k, v);
-  uint32_t goff = threadIdx.x < nd ? offsets[(size_t)threadIdx.x * nb + b] : 0u;
+  uint32_t goff = offset_of(b);
   for (; b < nb; b += gridDim.x) {
     for (int d = lane; d < nd; d += 32) s_whist[warp][d] = 0;
     __syncwarp();
@@ -408,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_downsweep(const uint32_t *__
     const uint32_t bn = b + gridDim.x;
     if (bn < nb) {  // prefetch the next tile into the now free registers
       load_radix_tile(keys_in, vals_in, n, bn, k, v);
-      goff = threadIdx.x < nd ? offsets[(size_t)threadIdx.x * nb + bn] : 0u;
+      goff = offset_of(bn);
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kRTile, n - b * kRTile);
@@ -1116,19 +1140,27 @@ void scan(const uint32_t *in, uint32_t *out, L len, u64 max_len, u64 *chunk, u64
 }
 
 // Sorts (keys, vals) in place across the two buffers; returns the buffer index holding the result.
-// Bits [shift0, shift0 + bits) of the keys are sorted.
+// Bits [shift0, shift0 + bits) of the keys are sorted.  With self_offsets, lists of at most
+// kSelfRadixTiles radix tiles skip the spine scan (the downsweep derives its offsets; the spine
+// is then left unscanned, so callers that read it afterwards pass false).
 int radix_sort(uint32_t *keys[2], uint32_t *vals[2], Count cnt, u64 max_count, int shift0, int bits,
-               uint32_t *spine, u64 *chunk, cudaStream_t s) {
+               uint32_t *spine, u64 *chunk, cudaStream_t s, bool self_offsets = false) {
   int cur = 0;
   int g = grid_for(max_count, kRTile);
+  const bool self = self_offsets && ceil_div(max_count, kRTile) <= kSelfRadixTiles;
   for (int shift = shift0; shift < shift0 + bits; shift += kRadixBits) {
     int db = shift0 + bits - shift < kRadixBits ? shift0 + bits - shift : kRadixBits;
     uint32_t mask = (1u << db) - 1u;
     k_radix_upsweep<<<g, kThreads, 0, s>>>(keys[cur], cnt, shift, mask, spine);
-    SpineLen sl{cnt, (int)mask + 1};
-    scan(spine, spine, sl, (u64)(mask + 1) * ceil_div(max_count, kRTile), chunk, nullptr, s);
-    k_radix_downsweep<<<g, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], cnt, shift, mask,
-                                            spine);
+    if (self) {
+      k_radix_downsweep<true><<<g, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], cnt, shift,
+                                                    mask, spine);
+    } else {
+      SpineLen sl{cnt, (int)mask + 1};
+      scan(spine, spine, sl, (u64)(mask + 1) * ceil_div(max_count, kRTile), chunk, nullptr, s);
+      k_radix_downsweep<false><<<g, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], cnt,
+                                                     shift, mask, spine);
+    }
     count_launches(2);
     cur ^= 1;
   }
@@ -1175,7 +1207,7 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     // depth keys, and K = sum of ntiles (reported even when it exceeds the capacity)
     k_depth_init<<<g, kThreads, 0, s>>>(n, depth, ntiles, b.dk[0], b.dv[0], b.total + 1);
     count_launches(1);
-    const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s);
+    const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s, true);
     // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
     // and the caller's vals, arranged so that the row stage lands in vals: the row scatter
     // reads the column values from x[2]; the row radix passes end in vals
