@@ -507,7 +507,7 @@ ut_status bin_and_sort(int32_t n, const float *depth, const int16_t *rect, const
   BatchDesc bd;
   single_view(bd, dc, dop, nullptr, n);
   return launch_bin(bd, depth, rect, ntiles, dop, workspace, key_capacity, keys, vals, tile_ranges, k_out,
-                    reinterpret_cast<cudaStream_t>(stream));
+                    reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 size_t ut_forward_workspace_size(const ut_camera *cam, const ut_options *opt) {
@@ -620,8 +620,8 @@ ut_status render_batch(const ut_scene *scenes, int32_t n_scenes, const ut_view *
   if ((st = launch_project(bd, dop, w, reinterpret_cast<float *>(ws + L.mean2d), reinterpret_cast<float *>(ws + L.cov2d),
                            depth, rect, ntiles, s)) != UT_OK)
     return st;
-  if ((st = launch_bin(bd, depth, rect, ntiles, dop, ws + L.bin, key_capacity, nullptr, vals, ranges, k_out, s)) !=
-      UT_OK)
+  if ((st = launch_bin(bd, depth, rect, ntiles, dop, ws + L.bin, key_capacity, nullptr, vals, ranges, k_out, s,
+                       false)) != UT_OK)
     return st;
   return launch_composite_fwd(bd, dop, rect, vals, ranges, nullptr, ws + L.sched, s);
 }

@@ -1181,7 +1181,7 @@ size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols, int max_rows
 
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
-                     int64_t *k_out, cudaStream_t s) {
+                     int64_t *k_out, cudaStream_t s, bool short_sort) {
   const int n = bd.total_particles;
   const int tiles = bd.total_tiles;
   const short4 *r4 = reinterpret_cast<const short4 *>(rect);
@@ -1207,7 +1207,7 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
     // depth keys, and K = sum of ntiles (reported even when it exceeds the capacity)
     k_depth_init<<<g, kThreads, 0, s>>>(n, depth, ntiles, b.dk[0], b.dv[0], b.total + 1);
     count_launches(1);
-    const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s, true);
+    const int r = radix_sort(b.dk, b.dv, cn, (u64)n, 0, 32, b.spine, b.chunk, s, short_sort);
     // buffer plan: column keys ping-pong in x[0] / x[1]; values (column, then row) over x[2]
     // and the caller's vals, arranged so that the row stage lands in vals: the row scatter
     // reads the column values from x[2]; the row radix passes end in vals

@@ -54,9 +54,12 @@ size_t bin_workspace_bytes(int n, int64_t cap, int tiles, int cols, int max_rows
 ut_status bin_check_args(int32_t n, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                          const ut_camera *cam, const ut_options *opt, int64_t key_capacity, const uint32_t *vals,
                          const uint32_t *tile_ranges, const int64_t *k_out, DevCam &dc, DevOpts &dop, size_t *need);
+// short_sort: a depth sort of at most 128 radix tiles skips its spine scans (fewer launches for
+// small scenes); batches pass false so that one launch sequence serves every scene size and the
+// serving loop's captured graphs stay updatable.
 ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rect, const uint32_t *ntiles,
                      const DevOpts &op, void *ws, int64_t cap, uint64_t *keys, uint32_t *vals, uint32_t *ranges,
-                     int64_t *k_out, cudaStream_t stream);
+                     int64_t *k_out, cudaStream_t stream, bool short_sort);
 
 // Compositing of every global tile of the batch into the views' outputs; sched: scratch of
 // tile_sched_bytes(total tiles) for the tile order.

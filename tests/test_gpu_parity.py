@@ -135,6 +135,24 @@ def test_bin_empty_and_all_culled():
         assert np.all(to_np(f.t_final) == 1.0)
 
 
+@pytest.mark.parametrize("k", [0, 4])
+def test_backward_of_empty_and_all_culled_scenes_is_zero(k):
+    """The backward (tile order and k-buffer) of a scene with no particle, and of one whose
+    every particle is culled, succeeds and writes zero gradients."""
+    cam = synth.camera("pinhole", 64, 64, fx=64.0)
+    op = synth.options(kbuffer=k)
+    for n in (0, 17):
+        rect = np.tile(np.array([[0, 0, -1, -1]], np.int16), (n, 1))
+        g = run_gpu(synth.scene_cube(n, 2, deg=3), cam, op, rect=rect, depth=np.ones(n, np.float32), capacity=64)
+        d_rgb = torch.ones((3, 64, 64), device="cuda")
+        d_a = torch.ones((64, 64), device="cuda")
+        grads = render.composite_backward(g["scene"], cam, op, g["proj"], g["binning"], g["frame"], d_rgb, d_a)
+        torch.cuda.synchronize()
+        for key in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            assert grads[key].shape[0] == n
+            assert not to_np(grads[key]).any(), (k, n, key)
+
+
 def test_bin_capacity_overflow_reports_k_and_writes_nothing():
     W, H = 200, 120
     rect, depth = synth.random_rects(5, 400, W, H, max_w=50, max_h=50)
