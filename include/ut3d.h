@@ -377,7 +377,10 @@ ut_status render_batch_backward(const ut_scene *scenes, int32_t n_scenes, const 
  * and keeps up to max_in_flight batches on the GPU at once on separate streams, so requests
  * that arrive while others render overlap with them on the device.  Completion is detected
  * with CUDA events polled on the host; no kernel waits on anything.  A batch whose key count
- * overflowed its capacity is re-run with a larger capacity before its requests complete.
+ * overflowed its capacity is re-run with a larger capacity before its requests complete; a
+ * request whose batch overflowed six times fails with UT_ERR_CAPACITY (reported by
+ * ut_server_wait).  Outputs are carved from the top of the arena and workspaces from the
+ * bottom, so that outputs waiting for their reader do not fragment the workspaces' space.
  * ------------------------------------------------------------------------------------------ */
 typedef struct ut_server ut_server;
 
