@@ -494,8 +494,9 @@ def run_multiview(dev, steps, warmup, timed):
 def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
     """A/B lines on the bench workload: the UT projection against the first-order EWA one
     (the paper's "Preprocess" comparison with 3DGS; per call, and the whole forward with each),
-    the per-ray k-buffer of "Ours (sorted)" (the paper's "Render" comparison), and the
-    per-particle SH colour mode (forward and forward + backward) against the per-pixel one."""
+    the per-ray k-buffer of "Ours (sorted)" (the paper's "Render" comparison), the
+    per-particle SH colour mode (forward and forward + backward) against the per-pixel one, and
+    the same scene with SH degree 0 (forward and forward + backward)."""
     import torch
     from paper_2412_12507_gb300 import render
     P = cam["width"] * cam["height"]
@@ -557,6 +558,22 @@ def run_variants(scene, cam, op, d_rgb, d_alpha, timed, steps, warmup):
     out["per_particle_colour"] = {"fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "fwd_mpix_s": P / (f_ms / 1e3) / 1e6,
                                   "fwd_bwd_mpix_s": P / (fb_ms / 1e3) / 1e6}
     del r
+    # the same scene with SH degree 0 (the DC colour alone), forward and forward + backward
+    s0 = render.Scene(scene.means, scene.log_scales, scene.quats, scene.opacity_logits,
+                      scene.sh[:, :1, :].contiguous(), 0)
+    r = render.Renderer(cam, op, capacity=1 << 20)
+    r.forward(s0)
+    torch.cuda.synchronize()
+    f_ms = timed(lambda: r.forward(s0, sync_check=False), steps, warmup)
+
+    def fb0():
+        r.forward(s0, sync_check=False)
+        r.backward(s0, d_rgb, d_alpha)
+
+    fb_ms = timed(fb0, steps, warmup)
+    out["sh_degree_0"] = {"fwd_ms": f_ms, "fwd_bwd_ms": fb_ms, "fwd_mpix_s": P / (f_ms / 1e3) / 1e6,
+                          "fwd_bwd_mpix_s": P / (fb_ms / 1e3) / 1e6}
+    del r, s0
     torch.cuda.empty_cache()
     return out
 
