@@ -605,7 +605,7 @@ def call_fractions(call_ms, n, K, M_cols, n_eval, n_blend, P, cam, op, hbm, alu)
         peak = hbm if bound == "hbm" else fp32_peak
         kernels[k] = {"ms": call_ms[k], "bound": bound, "achieved": ach, "peak": peak,
                       "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": ach / peak}
-    # the binning also against the survey's algorithmic model: every key (8 B key + 4 B value)
+    # the binning also against the algorithmic model of a 64-bit key sort: every key (8 B key + 4 B value)
     # emitted, sorted (read + written) and scanned for ranges (44 B / key), 8 B per particle
     kernels["bin_and_sort"]["model_44B_per_key"] = {
         "achieved_gbs": (44.0 * K + 8.0 * n) / 1e9 / (call_ms["bin_and_sort"] / 1e3),
