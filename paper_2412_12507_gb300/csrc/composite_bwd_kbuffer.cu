@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(512, 1) k_composite_bwd_kbuffer(const __grid_c
   float ev_gc[3] = {0.f, 0.f, 0.f}, ev_v[3] = {0.f, 0.f, 0.f}, ev_x[3] = {0.f, 0.f, 0.f}, ev_dsig = 0.f;
 
   // blends the pair (the particle at list position pos, alpha al, clamped colour c) at
-  // transmittance T, with the stop rule of the forward, and adds its gradient contributions
+  // transmittance T, with the stop rule of the forward, and records its gradient contributions
+  // as this lane's event of the step (emit adds them to the particle's accumulators)
   auto blend = [&](float al, float c0, float c1, float c2, uint32_t pos) {
     const float Tn = T * (1.f - al);
     if (Tn < op.t_min) {
