@@ -728,14 +728,16 @@ __global__ void k_col_bounds(const uint32_t *__restrict__ ckeys, Count cc, uint3
 // The chunk plan from the column bounds (one block of 1024 threads).  With dspine, the column
 // order came from one radix pass over all column bits, and the bounds are read off its scanned
 // digit-major counts instead (column c starts at dspine[c * tiles], tiles = radix tiles of the
-// M column entries) and written to colb here.
+// M column entries) and written to colb here; with raw, dspine holds the pass's unscanned
+// counts (the short pass derived its offsets itself) and the bounds come from the exclusive
+// scan of the per-column totals.
 __global__ void __launch_bounds__(1024) k_chunk_plan(const __grid_constant__ BatchDesc bd, uint32_t *__restrict__ colb,
                                                      ChunkPlan pl, const uint32_t *__restrict__ dspine, int ndigits,
-                                                     Count mcnt) {
+                                                     Count mcnt, int raw) {
   __shared__ u64 s_w[33];
   __shared__ u64 s_tot;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, cols = bd.total_cols;
-  if (dspine) {
+  if (dspine && !raw) {
     const uint32_t M = mcnt.get(), nt = (M + kRTile - 1) / kRTile;
     for (int c = t; c < cols; c += 1024) {
       const uint32_t a = M ? dspine[(size_t)c * nt] : 0u;
@@ -744,6 +746,32 @@ __global__ void __launch_bounds__(1024) k_chunk_plan(const __grid_constant__ Bat
       colb[2 * c + 1] = e;
     }
     __syncthreads();
+  } else if (dspine) {
+    const uint32_t M = mcnt.get(), nt = (M + kRTile - 1) / kRTile;
+    u64 carry = 0;
+    for (int c0 = 0; c0 < cols; c0 += 1024) {
+      const int c = c0 + t;
+      uint32_t tot = 0;
+      if (c < cols)
+        for (uint32_t tt = 0; tt < nt; ++tt) tot += dspine[(size_t)c * nt + tt];
+      const u64 inc = warp_incl_scan_u64((u64)tot, lane);
+      if (lane == 31) s_w[warp] = inc;
+      __syncthreads();
+      if (warp == 0) {
+        const u64 w = s_w[lane];
+        const u64 wi = warp_incl_scan_u64(w, lane);
+        s_w[lane] = wi - w;
+        if (lane == 31) s_w[32] = wi;
+      }
+      __syncthreads();
+      if (c < cols) {
+        const uint32_t a = (uint32_t)(carry + s_w[warp] + inc - tot);
+        colb[2 * c] = a;
+        colb[2 * c + 1] = a + tot;
+      }
+      carry += s_w[32];
+      __syncthreads();
+    }
   }
   auto block_sum = [&](u64 x) -> u64 {
     x = warp_incl_scan_u64(x, lane);
@@ -1232,19 +1260,21 @@ ut_status launch_bin(const BatchDesc &bd, const float *depth, const int16_t *rec
       k_emit_cols<false><<<eg, kThreads, 0, s>>>(bd, n, b.dv[r], b.offs, b.cnt, r4, cc, op.tile_w, op.tile_h, ck[0],
                                                  cv[0]);
     count_launches(1);
-    const int rc = radix_sort(ck, cv, cc, (u64)cap, 0, cbits, b.spine, b.chunk, s);
+    // the short pass leaves the spine unscanned: only the single-pass scatter path reads it, raw
+    const bool col_short = short_sort && scatter && cp == 1 && ceil_div((u64)cap, kRTile) <= kSelfRadixTiles;
+    const int rc = radix_sort(ck, cv, cc, (u64)cap, 0, cbits, b.spine, b.chunk, s, col_short);
     const Count ck2{b.total + 1, (u64)cap, 0};
     if (scatter) {
       // 3. row entries scattered straight into (tile, depth) order
       const uint32_t *ckc = ck[rc], *cvc = cv[rc];
       const int blocks = (kChunkWarps + bd.total_cols + kWarps - 1) / kWarps;
       if (cp == 1) {  // bounds from the single column pass's digit counts
-        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, b.spine, 1 << cbits, cc);
+        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, b.spine, 1 << cbits, cc, col_short ? 1 : 0);
       } else {
         if (cudaMemsetAsync(b.colb, 0, sizeof(uint32_t) * 2 * (size_t)bd.total_cols, s) != cudaSuccess)
           return UT_ERR_CUDA;
         k_col_bounds<<<grid_for((u64)cap, kThreads * 4), kThreads, 0, s>>>(ckc, cc, b.colb);
-        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, nullptr, 0, cc);
+        k_chunk_plan<<<1, 1024, 0, s>>>(bd, b.colb, b.plan, nullptr, 0, cc, 0);
         count_launches(1);
       }
       k_row_count<<<blocks, kThreads, sizeof(uint32_t) * kWarps * (max_rows + 1), s>>>(bd, ckc, b.colb, b.plan,
