@@ -1085,7 +1085,13 @@ static int orc_composite_ray(const orc_ctx *x, const orc_scene *sc, const orc_op
  * (front to back, with the same stop rule) and leaves; the new hit takes its place unless it
  * was itself the closest.  At the end of the list the remaining entries are blended in
  * ascending tau.  Returns the number of blended particles.  A selection whose runner-up tau is
- * within eps_tau (relative) of the chosen one may go the other way in FP32: ORC_F_DEPTH_TIE. */
+ * within eps_tau (relative) of the chosen one may go the other way in FP32: ORC_F_DEPTH_TIE.
+ * Bound on what any flagged decision can change (slack, aslack, when given): the decisions
+ * before the first flagged one are the same on both sides, so the colour composited up to it
+ * is the same, and what follows adds at most T_f c_max per channel to either side's colour
+ * (T_f the transmittance at the first flagged decision, c_max the largest clamped colour
+ * channel of any particle that could be a hit at this pixel) and moves T_final within [0, T_f];
+ * a pixel flagged by the ray setup takes T_f = 1. */
 typedef struct {
   double tau, alpha, col[3];
   int seq;
@@ -1104,11 +1110,14 @@ static int orc_kb_pick(const orc_kb_entry *e, int n, double eps, int *tie) {
 static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, const orc_options *op,
                                      const orc_tol *tol, int px, int py, const double o[3], const double d[3],
                                      const double *Y, double rgb[3], double *Tout, int32_t *flags,
-                                     int *stopped_out, orc_contrib *rec, int cap) {
+                                     int *stopped_out, orc_contrib *rec, int cap, double *slack, double *aslack) {
   orc_kb_entry buf[65];
   int k = op->kbuffer < 64 ? op->kbuffer : 64, nbuf = 0, nb = 0, seq = 0, stopped = 0, tie = 0;
   double T = 1.0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
+  /* transmittance at the first flagged decision (-1: none yet), largest possible hit colour */
+  double Tf = flags && (*flags & (ORC_F_PIXEL_EDGE | ORC_F_ILL_COND)) ? 1.0 : -1.0, cmax = 0.0;
+#define ORC_KB_NOTE() do { if (Tf < 0.0) Tf = T; } while (0)
   for (int j = 0; j < x->norder && !stopped; ++j) {
     int i = x->order[j];
     const orc_particle *p = &x->P[i];
@@ -1123,13 +1132,35 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
       double ex = fmin(fabs(px - e[0]), fabs(px - e[1])), ey = fmin(fabs(py - e[2]), fabs(py - e[3]));
       int nx = px >= e[0] - tol->eps_px && px <= e[1] + tol->eps_px;
       int ny = py >= e[2] - tol->eps_px && py <= e[3] + tol->eps_px;
-      if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel))
+      if (nx && ny && (ex < tol->eps_px || ey < tol->eps_px) && a >= op->alpha_min * (1.0 - tol->eps_rel)) {
         *flags |= ORC_F_RECT_EDGE;
+        ORC_KB_NOTE();
+        if (slack) {  /* a hit on the other side: its colour counts for c_max */
+          const float *bt = sc->sh + (size_t)i * x->nsh * 3;
+          const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
+          for (int ch = 0; ch < 3; ++ch) {
+            double s = 0.5;
+            for (int kk = 0; kk < x->nsh; ++kk) s += bt[3 * kk + ch] * Yc[kk];
+            if (s > cmax) cmax = s;
+          }
+        }
+      }
     }
     if (!inside) continue;
-    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) *flags |= ORC_F_ALPHA_MIN;
-    if (a < op->alpha_min) continue;
-    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) *flags |= ORC_F_ALPHA_MAX;
+    if (flags && fabs(a - op->alpha_min) < tol->eps_rel * op->alpha_min) { *flags |= ORC_F_ALPHA_MIN; ORC_KB_NOTE(); }
+    if (a < op->alpha_min) {
+      if (slack && flags && a >= op->alpha_min * (1.0 - tol->eps_rel)) {  /* a near-threshold miss: c_max */
+        const float *bt = sc->sh + (size_t)i * x->nsh * 3;
+        const double *Yc = op->colour_mode == 1 ? x->Yp + 16 * (size_t)i : Y;
+        for (int ch = 0; ch < 3; ++ch) {
+          double s = 0.5;
+          for (int kk = 0; kk < x->nsh; ++kk) s += bt[3 * kk + ch] * Yc[kk];
+          if (s > cmax) cmax = s;
+        }
+      }
+      continue;
+    }
+    if (flags && fabs(a - op->alpha_max) < tol->eps_rel * op->alpha_max) { *flags |= ORC_F_ALPHA_MAX; ORC_KB_NOTE(); }
     orc_kb_entry h;
     h.tau = tau;
     h.alpha = a < op->alpha_max ? a : op->alpha_max;
@@ -1142,15 +1173,17 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
       h.col[ch] = s > 0.0 ? s : 0.0;
       h.c.raw[ch] = s;
       h.c.col[ch] = h.col[ch];
+      if (h.col[ch] > cmax) cmax = h.col[ch];
     }
-    if (flags && orc_clamp_tie(beta, Yc, x->nsh, h.c.raw, tol->eps_rel)) *flags |= ORC_F_CLAMP;
+    if (flags && orc_clamp_tie(beta, Yc, x->nsh, h.c.raw, tol->eps_rel)) { *flags |= ORC_F_CLAMP; ORC_KB_NOTE(); }
     h.c.i = i; h.c.alpha = h.alpha; h.c.a = a; h.c.rho = rho; h.c.tau = tau; h.c.w2 = w2;
     for (int kk = 0; kk < 3; ++kk) { h.c.og[kk] = og[kk]; h.c.dg[kk] = dg[kk]; }
     if (nbuf < k) { buf[nbuf++] = h; continue; }
     buf[nbuf] = h;  /* the closest of the k buffered hits and the new one is blended */
     int b = orc_kb_pick(buf, nbuf + 1, op->eps_tau, &tie);
+    if (tie) ORC_KB_NOTE();
     double Tn = T * (1.0 - buf[b].alpha);
-    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
+    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) { *flags |= ORC_F_TSTOP; ORC_KB_NOTE(); }
     if (Tn < op->t_min) { stopped = 1; break; }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
     if (rec && nb < cap) { rec[nb] = buf[b].c; rec[nb].T = T; }
@@ -1160,8 +1193,9 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
   }
   while (!stopped && nbuf > 0) {  /* end of the list: the rest in ascending tau */
     int b = orc_kb_pick(buf, nbuf, op->eps_tau, &tie);
+    if (tie) ORC_KB_NOTE();
     double Tn = T * (1.0 - buf[b].alpha);
-    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) *flags |= ORC_F_TSTOP;
+    if (flags && fabs(Tn - op->t_min) < tol->eps_t * op->t_min) { *flags |= ORC_F_TSTOP; ORC_KB_NOTE(); }
     if (Tn < op->t_min) { stopped = 1; break; }
     for (int ch = 0; ch < 3; ++ch) rgb[ch] += buf[b].col[ch] * buf[b].alpha * T;
     if (rec && nb < cap) { rec[nb] = buf[b].c; rec[nb].T = T; }
@@ -1169,7 +1203,10 @@ static int orc_composite_ray_kbuffer(const orc_ctx *x, const orc_scene *sc, cons
     ++nb;
     buf[b] = buf[--nbuf];
   }
+#undef ORC_KB_NOTE
   if (flags && tie) *flags |= ORC_F_DEPTH_TIE;
+  if (slack) *slack = Tf > 0.0 ? Tf * cmax : 0.0;
+  if (aslack) *aslack = Tf > 0.0 ? Tf : 0.0;
   *Tout = T;
   if (stopped_out) *stopped_out = stopped;
   return nb;
@@ -1235,7 +1272,8 @@ void orc_render(const orc_scene *sc, const orc_camera *c, const orc_options *op,
     if (rslack) rslack[q] = 0.0;
     if (raslack) raslack[q] = 0.0;
     if (op->kbuffer > 0) {
-      nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, NULL, 0);
+      nblend[q] = orc_composite_ray_kbuffer(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, NULL, 0,
+                                            slack + q, aslack + q);
     } else {
       orc_slack sl;
       nblend[q] = orc_composite_ray(&x, sc, op, tol, px, py, o, d, Y, rgb + 3 * q, &T, &fl, NULL, 0, no_rect, &sl);
@@ -1332,7 +1370,8 @@ void orc_backward(const orc_scene *sc, const orc_camera *c, const orc_options *o
       double rgb[3], Tf;
       /* the blended pairs in blending order: the tile (depth) order, or the k-buffer's order */
       int nb = op->kbuffer > 0
-                   ? orc_composite_ray_kbuffer(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, NULL, rec, x.norder)
+                   ? orc_composite_ray_kbuffer(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, NULL, rec, x.norder,
+                                               NULL, NULL)
                    : orc_composite_ray(&x, sc, op, &tol, px, py, o, d, Y, rgb, &Tf, NULL, rec, x.norder, 0, NULL);
       const double *g = g_rgb + 3 * q;
       double gA = g_alpha[q];

@@ -792,6 +792,43 @@ def test_rect_culling_lossless_for_generalised_kernels(orc, n):
 
 # ------------------------------------------------------------------ "Ours (sorted)": per-ray k-buffer
 
+@pytest.mark.parametrize("k", [1, 4, 16])
+def test_kbuffer_bound_covers_the_other_order_of_exact_ties(orc, k):
+    """Pairs of particles with identical geometry (their tau_max ties exactly at every pixel)
+    and different opacities and colours: swapping each pair's indices swaps their arrival and so
+    the order the tie-break blends them in.  Wherever the two images differ the pixel carries a
+    tie flag, and the difference lies within the oracle's k-buffer bound (slack, aslack) of
+    either render."""
+    n_pairs = 60
+    a = synth.scene_cube(n_pairs, 31, deg=1, log_s=(-2.6, 0.3))
+    b = synth.scene_cube(n_pairs, 32, deg=1, log_s=(-2.6, 0.3))
+    sc = {}
+    for key in ("means", "log_scales", "quats"):
+        sc[key] = np.repeat(a[key], 2, axis=0)
+    for key in ("opacity_logits", "sh"):
+        sc[key] = np.stack([a[key], b[key]], axis=1).reshape((2 * n_pairs,) + a[key].shape[1:])
+    sc["opacity_logits"] = sc["opacity_logits"] + 1.0
+    sc["sh_degree"] = 1
+    sw = {key: (v.reshape((n_pairs, 2) + v.shape[1:])[:, ::-1].reshape(v.shape) if key != "sh_degree" else v)
+          for key, v in sc.items()}
+    cam = synth.camera("pinhole", 48, 40, fx=40.0)
+    op = synth.options(kbuffer=k)
+    tol = dict(eps_px=5e-3, eps_rel=2e-4, eps_t=2e-3, depth_ulps=4, cond_min=0.05)
+    r1 = orc.render(sc, cam, op, proj=orc.project(sc, cam, op, tol), tol=tol)
+    r2 = orc.render(sw, cam, op, proj=orc.project(sw, cam, op, tol), tol=tol)
+    drgb = np.abs(r1["rgb"] - r2["rgb"]).max(axis=1)
+    da = np.abs(r1["alpha"] - r2["alpha"])
+    differ = (drgb > 1e-12) | (da > 1e-12)
+    assert differ.sum() > 20  # the order matters at many pixels
+    tied = (r1["flags"] & orc.F_DEPTH_TIE) != 0
+    assert np.all(tied[differ])
+    for r in (r1, r2):
+        assert np.all(drgb <= r["slack"] * (1 + 1e-12) + 1e-12)
+        assert np.all(da <= r["aslack"] * (1 + 1e-12) + 1e-12)
+    # the bound is not vacuous: it is below the largest colour at most of the tied pixels
+    assert np.median(r1["slack"][tied]) < 1.0
+
+
 def _two_crossing():
     """Two isotropic Gaussians where the mean nearer the camera is reached later along one pixel's
     ray: A sits on the ray at tau = 3.0 (0.05 off it), B at tau = 2.6 but 1.6 off the ray, so
