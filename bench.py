@@ -130,7 +130,7 @@ def measure_alu_peaks(L, dev, stream, sms):
     blocks, threads = sms * 8, 256
     out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
     res = {}
-    for kind, name, iters, flop_per_op in ((0, "fp32", 40000, 2.0), (1, "ex2", 5000, 1.0)):
+    for kind, name, iters, flop_per_op in ((abi.UT_PROBE_FMA, "fp32", 40000, 2.0), (abi.UT_PROBE_EX2, "ex2", 5000, 1.0)):
         def launch():
             abi.check("ut_peak_probe", L.ut_peak_probe(kind, blocks, threads, iters, out.data_ptr(), stream.cuda_stream))
         launch()

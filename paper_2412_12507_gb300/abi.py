@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libut3d.so")
 
 UT_OK, UT_ERR_INVALID_ARG, UT_ERR_CAPACITY, UT_ERR_CUDA, UT_ERR_TIMEOUT, UT_ERR_UNSUPPORTED = range(6)
 CAM_MODELS = {"pinhole": 0, "fisheye": 1, "pinhole_radial": 2}
+UT_PROBE_FMA, UT_PROBE_EX2 = 0, 1  # ut_peak_probe kinds
 
 
 class UtError(RuntimeError):
